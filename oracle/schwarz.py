@@ -1,0 +1,122 @@
+"""Fine-scale overlapping additive Schwarz preconditioner P^f.
+
+Paper: Sec. 4.2 (local preconditioner), Eq. subd, the extended 1D pencil matrix,
+Eq. z and the additive update of P^f.
+Readings:
+  * Extended 1D pencil: the element plus one node on each side; the matrices are
+    the rows/columns -1..n+1 of the three-element 1D assembly (stiffness
+    d_ij = sum_m rho_m phi_i'(t_m) phi_j'(t_m), mass diag(rho)), i.e. homogeneous
+    Dirichlet beyond -1 and n+1. The neighbours are assumed to have the same h.
+  * The eigen-form is the generalised problem K S = M S Lambda with S^T M S = I, so
+    z = 8/(hx hy hz) (S x S x S) diag[1/(4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + c)]
+        (S^T x S^T x S^T) r,
+    which is Eq. z with M^{-1} cancelled (the printed V/V^{-1} indices are inconsistent).
+  * A patch node with exactly one index in {-1, n+1} is the face-neighbour's node one
+    layer inside it, next to the shared face node; nodes with two or more indices
+    outside 0..n, and layers beyond a boundary face, are absent (r = 0, z dropped).
+  * h_x, h_y, h_z: mean length of the element's 4 edges along xi, eta, zeta.
+  * No overlap weights: the corrections are summed.
+Pinned by: the pencil matrices equal the printed extended matrix pattern, the
+fast-diagonalisation solve equals a dense solve of the Kronecker-sum box matrix,
+S^T M S = I and K S = M S Lambda (scipy eigh), symmetry and positivity of P^f.
+"""
+import numpy as np
+import scipy.linalg
+
+from .numbering import HEX_FACES
+
+
+def pencil_matrices(Dh, rho):
+    """Extended 1D stiffness K and mass M (size n+3, rows -1..n+1) by three-element assembly."""
+    n = len(rho) - 1
+    d = Dh.T @ np.diag(rho) @ Dh                 # d_ij = sum_m rho_m phi_i'(t_m) phi_j'(t_m)
+    N = 3 * n + 1                                # nodes -n .. 2n
+    Kf = np.zeros((N, N))
+    Mf = np.zeros(N)
+    for el in range(3):
+        o = el * n
+        Kf[o:o + n + 1, o:o + n + 1] += d
+        Mf[o:o + n + 1] += rho
+    keep = np.arange(n - 1, 2 * n + 2)           # global nodes -1 .. n+1
+    return Kf[np.ix_(keep, keep)], np.diag(Mf[keep])
+
+
+def pencil_eig(K, M):
+    """Generalised eigenpairs K S = M S diag(ev), S^T M S = I (scipy.linalg.eigh)."""
+    ev, S = scipy.linalg.eigh(K, M)
+    return ev, S
+
+
+def patch_table(l2g, nb_elem, nb_face):
+    """ip[e, I, J, K] = global node of extended-box node (I-1, J-1, K-1), or -1 if absent."""
+    E, p = l2g.shape[0], l2g.shape[1]
+    n = p - 1
+    P = n + 3
+    Gn = int(l2g.max()) + 1
+    ip = -np.ones((E, P, P, P), dtype=np.int64)
+    ip[:, 1:n + 2, 1:n + 2, 1:n + 2] = l2g
+    # lookup (element, global node) -> local (i, j, k)
+    keys = (np.arange(E)[:, None] * Gn + l2g.reshape(E, -1)).ravel()
+    order = np.argsort(keys)
+    skeys = keys[order]
+    loc = np.stack(np.unravel_index(np.arange(p ** 3), (p, p, p)), axis=1)
+    for f, (ax, sd) in enumerate(HEX_FACES):
+        has = nb_elem[:, f] >= 0
+        es = np.where(has)[0]
+        if len(es) == 0:
+            continue
+        e2 = nb_elem[es, f]
+        ax2 = np.array([HEX_FACES[g][0] for g in nb_face[es, f]])
+        sd2 = np.array([HEX_FACES[g][1] for g in nb_face[es, f]])
+        sl = [slice(None)] * 3
+        sl[ax] = 0 if sd == 0 else n
+        face_g = l2g[es][(slice(None),) + tuple(sl)]          # [m, p, p] global ids on the face
+        q = (e2[:, None, None] * Gn + face_g)
+        pos = np.searchsorted(skeys, q.ravel())
+        assert np.all(skeys[pos] == q.ravel()), "face node not found in neighbour"
+        lidx = order[pos] % (p ** 3)
+        ijk2 = loc[lidx].reshape(face_g.shape + (3,))          # local coords in the neighbour
+        step = np.where(sd2 == 0, 1, -1)
+        ijk2 = ijk2.copy()
+        rows = np.arange(len(es))
+        ijk2[rows, :, :, ax2] += step[:, None, None]
+        inner = l2g[e2[:, None, None], ijk2[..., 0], ijk2[..., 1], ijk2[..., 2]]
+        dst = [slice(1, n + 2)] * 3
+        dst[ax] = 0 if sd == 0 else P - 1
+        ip[(es,) + tuple(dst)] = inner
+    return ip
+
+
+def fast_diag_solve(rp, S, ev, h, lam):
+    """Eq. z: z = 8/(hx hy hz) S^{x3} diag^{-1} S^{T x3} r for patch arrays rp[e, P, P, P]."""
+    scale = 8.0 / (h[:, 0] * h[:, 1] * h[:, 2])
+    t = np.einsum("ia,eijk->eajk", S, rp)
+    t = np.einsum("jb,eajk->eabk", S, t)
+    t = np.einsum("kc,eabk->eabc", S, t)
+    den = 4.0 * (ev[None, :, None, None] / h[:, 0, None, None, None] ** 2
+                 + ev[None, None, :, None] / h[:, 1, None, None, None] ** 2
+                 + ev[None, None, None, :] / h[:, 2, None, None, None] ** 2) + lam
+    t = t / den * scale[:, None, None, None]
+    t = np.einsum("kc,eabc->eabk", S, t)
+    t = np.einsum("jb,eabk->eajk", S, t)
+    return np.einsum("ia,eajk->eijk", S, t)
+
+
+def box_matrix(K, M, h, lam):
+    """Dense Kronecker-sum operator of one box, C order over (I, J, K)."""
+    hx, hy, hz = h
+    return 4.0 * (np.kron(K, np.kron(M, M)) / hx ** 2 + np.kron(M, np.kron(K, M)) / hy ** 2
+                  + np.kron(M, np.kron(M, K)) / hz ** 2) + lam * np.kron(M, np.kron(M, M))
+
+
+def apply_fine(r, ip, S, ev, h, lam, mask=None):
+    """P^f r: restrict to every patch, solve each box, add the present nodes back."""
+    Gn = r.shape[0]
+    rm = r if mask is None else np.where(mask > 0, 0.0, r)
+    present = ip >= 0
+    rp = np.where(present, rm[np.where(present, ip, 0)], 0.0)
+    zp = fast_diag_solve(rp, S, ev, h, lam)
+    z = np.bincount(ip[present], weights=zp[present], minlength=Gn)
+    if mask is not None:
+        z = np.where(mask > 0, 0.0, z)
+    return z

@@ -1,0 +1,144 @@
+"""Seeded perturbed lattice meshes of [0,1]^3 with random numbering and orientation.
+
+Recipe (the mesh family the solver is exercised on):
+  * an (E+1)^3 lattice of vertices on [0,1]^3, spacing h = 1/E;
+  * every coordinate moved by U(-a*h, a*h); on the boundary only the
+    coordinates tangent to the boundary move, so corners stay fixed, edge
+    vertices slide along their edge and the domain stays exactly [0,1]^3;
+  * vertices and hexes renumbered by random permutations;
+  * every hex's 8-vertex list re-expressed in one of the 24 proper rotations
+    of the reference cube (orientation preserving, so the Jacobian sign is kept).
+Hex vertex order is the VTK/gmsh one: corner c has reference signs
+VTK_CORNER_BITS[c] in (xi, eta, zeta), 0 = -1 and 1 = +1.
+"""
+from dataclasses import dataclass
+import itertools
+import numpy as np
+
+# reference-cube bits (xi, eta, zeta) of each VTK hex corner
+VTK_CORNER_BITS = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                            [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], dtype=np.int64)
+
+
+def _corner_index_of_bits():
+    lut = np.zeros((2, 2, 2), dtype=np.int64)
+    for c, (a, b, d) in enumerate(VTK_CORNER_BITS):
+        lut[a, b, d] = c
+    return lut
+
+
+_CORNER_OF_BITS = _corner_index_of_bits()
+
+
+def _proper_rotations():
+    """The 24 signed permutation matrices with determinant +1."""
+    mats = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=np.int64)
+            for r in range(3):
+                R[r, perm[r]] = signs[r]
+            if round(np.linalg.det(R)) == 1:
+                mats.append(R)
+    return np.array(mats)
+
+
+PROPER_ROTATIONS = _proper_rotations()
+
+
+def _rotation_corner_maps():
+    """For each proper rotation R, the map new-corner -> old-corner.
+
+    A new local corner with sign vector s is the old corner with sign vector R s.
+    """
+    maps = np.zeros((len(PROPER_ROTATIONS), 8), dtype=np.int64)
+    signs = 2 * VTK_CORNER_BITS - 1
+    for r, R in enumerate(PROPER_ROTATIONS):
+        for c in range(8):
+            s_old = R @ signs[c]
+            b = (s_old + 1) // 2
+            maps[r, c] = _CORNER_OF_BITS[b[0], b[1], b[2]]
+    return maps
+
+
+_ROT_MAPS = _rotation_corner_maps()
+
+
+@dataclass
+class HexMesh:
+    """An all-hex mesh: vertex coordinates (n_vert x 3, float64) and hex
+    connectivity (n_hex x 8, int64, VTK corner order)."""
+    xyz: np.ndarray
+    hex2vert: np.ndarray
+    E: int = 0
+    a: float = 0.0
+    seed: int = 0
+
+    @property
+    def n_vert(self):
+        return self.xyz.shape[0]
+
+    @property
+    def n_hex(self):
+        return self.hex2vert.shape[0]
+
+
+def lattice_hex_mesh(E, a=0.0, seed=0, renumber=True, rotate=True, box=(1.0, 1.0, 1.0)):
+    """Perturbed E x E x E hex lattice of the box [0,bx]x[0,by]x[0,bz].
+
+    Parameters: E hexes per direction, a the perturbation amplitude as a fraction of
+    the spacing, seed for numpy.random.default_rng. Returns a HexMesh.
+    """
+    E = int(E)
+    if E < 1:
+        raise ValueError("E must be >= 1")
+    rng = np.random.default_rng(seed)
+    nv1 = E + 1
+    idx = np.arange(nv1)
+    I, J, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    lat = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)   # lattice index of vertex
+    vid_of = lambda i, j, k: i + nv1 * (j + nv1 * k)
+    order = np.argsort(vid_of(lat[:, 0], lat[:, 1], lat[:, 2]))
+    lat = lat[order]                                             # vertex id = i + nv1*(j + nv1*k)
+    h = np.array(box, dtype=np.float64) / E
+    xyz = lat.astype(np.float64) * h
+    d = rng.uniform(-a, a, size=xyz.shape) * h
+    on_bnd = (lat == 0) | (lat == E)
+    d[on_bnd] = 0.0                                              # tangential-only on the boundary
+    xyz = xyz + d
+
+    ci, cj, ck = np.meshgrid(np.arange(E), np.arange(E), np.arange(E), indexing="ij")
+    cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
+    hexes = np.empty((cells.shape[0], 8), dtype=np.int64)
+    for c, (ba, bb, bc) in enumerate(VTK_CORNER_BITS):
+        hexes[:, c] = vid_of(cells[:, 0] + ba, cells[:, 1] + bb, cells[:, 2] + bc)
+
+    if rotate:
+        rot = rng.integers(0, len(PROPER_ROTATIONS), size=hexes.shape[0])
+        hexes = np.take_along_axis(hexes, _ROT_MAPS[rot], axis=1)
+    if renumber:
+        vperm = rng.permutation(xyz.shape[0])          # new id of old vertex
+        new_xyz = np.empty_like(xyz)
+        new_xyz[vperm] = xyz
+        xyz = new_xyz
+        hexes = vperm[hexes]
+        eperm = rng.permutation(hexes.shape[0])
+        hexes = hexes[eperm]
+    return HexMesh(xyz=np.ascontiguousarray(xyz), hex2vert=np.ascontiguousarray(hexes),
+                   E=E, a=float(a), seed=int(seed))
+
+
+def manufactured_u(xyz):
+    """u*(x,y,z) = sin(pi x) sin(pi y) sin(pi z); zero on the boundary of [0,1]^3."""
+    x = np.asarray(xyz, dtype=np.float64)
+    return np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1]) * np.sin(np.pi * x[:, 2])
+
+
+def manufactured_s(xyz, lam):
+    """Source s = lam*u* - laplacian(u*) = (3 pi^2 + lam) u* for the manufactured u*."""
+    return (3.0 * np.pi ** 2 + lam) * manufactured_u(xyz)
+
+
+def gaussian_load(n, seed):
+    """Seeded N(0,1) load vector of length n."""
+    return np.random.default_rng(seed).standard_normal(n)
