@@ -1,0 +1,142 @@
+/*
+ * sem.h - C ABI of a GB300 (sm_103a) spectral-element screened-Poisson solver.
+ *
+ * Problem (Sec. 2, Eq. pde / Eq. pdeweak of Remacle, Gandham & Warburton,
+ * "GPU accelerated spectral finite elements on all-hex meshes"):
+ *     -div(grad u) + lambda u = s  on an unstructured all-hex mesh,
+ *     u = 0 on the Dirichlet part of the boundary,
+ * discretised with order-n GLL spectral elements and solved with matrix-free
+ * preconditioned conjugate gradients (Algorithm 1) and the two-scale additive
+ * Schwarz preconditioner P = P^c + P^f (Sec. 4).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: 0 = SEM_OK, < 0 an error (see the
+ *    SEM_ERR_* codes; sem_last_error() gives a message), > 0 a solver outcome.
+ *  - "_dev" pointers are CUDA device pointers, "_host" pointers host pointers.
+ *    The caller owns every buffer it passes; the library never frees them and
+ *    keeps no reference after the call returns.
+ *  - Global vectors have sem_num_dofs() float64 entries in the library's own
+ *    DOF numbering; sem_dof_coords() gives the position of each DOF.
+ *  - All device work is enqueued on the handle's CUDA stream (given at create,
+ *    changeable with sem_set_stream). Calls that return host-visible results
+ *    (sem_solve, sem_num_dofs) synchronise that stream; the other calls are
+ *    asynchronous with respect to the host.
+ *  - A handle is not thread safe; different handles are independent.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem_s sem_t;
+
+/* status codes */
+#define SEM_OK             0
+#define SEM_ERR_ARG       (-1)  /* bad argument (NULL pointer, order out of 2..8, sizes) */
+#define SEM_ERR_JACOBIAN  (-2)  /* |J| <= 0 at some GLL node (inverted or mirrored hex) */
+#define SEM_ERR_MESH      (-3)  /* non-conforming / non-manifold mesh (a face on > 2 hexes) */
+#define SEM_ERR_CUDA      (-4)  /* a CUDA runtime call failed */
+#define SEM_ERR_OOM       (-5)  /* device or host allocation failed */
+#define SEM_ERR_NAN       (-6)  /* NaN/Inf or a non-positive p^T A p met in the solver */
+#define SEM_ERR_SINGULAR  (-7)  /* coarse matrix not SPD (e.g. pure Neumann with lambda = 0) */
+#define SEM_MAXIT          1    /* sem_solve: maxit reached before the tolerance */
+
+/* sem_create flags */
+#define SEM_GEOM_STORED     0x0  /* store G1..G6 and m per GLL node (Sec. 3.1, 7 factors) */
+#define SEM_GEOM_RECOMPUTE  0x1  /* recompute them from the 8 vertices in the operator (Sec. 3.1) */
+#define SEM_NEUMANN         0x10 /* no Dirichlet nodes (default: Dirichlet on every boundary face) */
+
+/* preconditioner choice for sem_solve (sem_set_precond) */
+#define SEM_PRECOND_TWO_SCALE 0  /* P = P^c + P^f (Sec. 4) */
+#define SEM_PRECOND_FINE      1  /* P = P^f only (Table 1, fine-scale rows) */
+#define SEM_PRECOND_NONE      2  /* P = I */
+
+/*
+ * sem_create - build a problem on a hex mesh (Sec. 2.1-2.4 set-up, Sec. 4 tables).
+ *   vert_xyz_host  3*n_vert doubles, x y z interleaved.
+ *   hex2vert_host  8*n_hex vertex ids in 0..n_vert-1, VTK/gmsh hex corner order
+ *                  (corner c has reference signs (-,-,-),(+,-,-),(+,+,-),(-,+,-),
+ *                  then the same four with zeta = +1).
+ *   order          polynomial order n, 2 <= n <= 8 ((n+1)^3 GLL nodes per hex). At n = 1 the
+ *                  one-node patch extension reaches the neighbour's far vertex, the pencil
+ *                  has no Dirichlet node and the patch problem is singular, so n = 1 is refused.
+ *   lambda         screening coefficient c >= 0 (kappa = 1).
+ *   flags          SEM_GEOM_* | SEM_NEUMANN.
+ *   cuda_stream    cudaStream_t to enqueue work on (NULL = legacy default stream);
+ *                  borrowed, must outlive its use by the handle.
+ *   out            receives the handle; free it with sem_destroy.
+ * The library copies the mesh; it allocates its own device work space here and
+ * frees it in sem_destroy. Errors: SEM_ERR_ARG, SEM_ERR_JACOBIAN, SEM_ERR_MESH,
+ * SEM_ERR_CUDA, SEM_ERR_OOM, SEM_ERR_SINGULAR.
+ */
+int sem_create(const double* vert_xyz_host, int64_t n_vert,
+               const int64_t* hex2vert_host, int64_t n_hex,
+               int order, double lambda, int flags, void* cuda_stream, sem_t** out);
+
+/* sem_destroy - free a handle and all its device memory (NULL is ignored). */
+void sem_destroy(sem_t* h);
+
+/* sem_set_stream - enqueue the handle's later work on another stream. */
+int sem_set_stream(sem_t* h, void* cuda_stream);
+
+/* sem_num_dofs - number of global GLL nodes N (Sec. 2.2). */
+int sem_num_dofs(const sem_t* h, int64_t* n_dof_host);
+
+/* sem_num_elements - number of hexes N_E. */
+int sem_num_elements(const sem_t* h, int64_t* n_hex_host);
+
+/* sem_dof_coords - xyz_dev[3*N]: physical position of every DOF (x y z interleaved). */
+int sem_dof_coords(const sem_t* h, double* xyz_dev);
+
+/* sem_mass - m_dev[N]: assembled lumped GLL mass m_N = sum of m_{ijk;e} (Sec. 2.4, Sec. 4.1). */
+int sem_mass(const sem_t* h, double* m_dev);
+
+/* sem_get_mask / sem_set_mask - mask_dev[N] bytes, 1 = Dirichlet node, 0 = free.
+ * The default mask is every node on a boundary face (or none with SEM_NEUMANN).
+ * sem_set_mask rebuilds the coarse space (free vertices) and its AMG hierarchy. */
+int sem_get_mask(const sem_t* h, uint8_t* mask_dev);
+int sem_set_mask(sem_t* h, const uint8_t* mask_dev);
+
+/* sem_apply_A - y = A_D x (Eq. R / Algorithm 2 then gather, Eq. gather):
+ * rows and columns of Dirichlet nodes are replaced by the identity, so
+ * y_i = x_i on masked nodes. x_dev and y_dev: N doubles, must not alias. */
+int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev);
+
+/* sem_apply_P / sem_apply_Pf / sem_apply_Pc - z = P r with P = P^c + P^f (Sec. 4),
+ * the fine overlapping-patch part P^f alone (Sec. 4.2, Eq. z) or the coarse part
+ * P^c alone (Sec. 4.1, Eq. coarse). r is read as 0 on masked nodes and z is 0
+ * there. r_dev and z_dev: N doubles, must not alias. */
+int sem_apply_P(sem_t* h, const double* r_dev, double* z_dev);
+int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev);
+int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev);
+
+/* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
+int sem_set_precond(sem_t* h, int which);
+
+/*
+ * sem_solve - PCG (Algorithm 1) for A_D x = b from x_0 = 0.
+ *   b_dev          N doubles, read as 0 on masked nodes.
+ *   x_dev          N doubles, output solution (0 on masked nodes).
+ *   rtol, maxit    stop when ||r_k||_2 <= rtol ||b||_2 (recursive residual), or after
+ *                  maxit operator applications.
+ *   iters_host     receives the number of iterations (operator applications).
+ *   res_hist_host  NULL or maxit+1 doubles: ||r_k|| / ||b|| for k = 0..iters.
+ *   true_rel_res_host  NULL or receives ||b - A_D x|| / ||b|| computed afresh.
+ * Returns SEM_OK on convergence, SEM_MAXIT, or an error (SEM_ERR_NAN, ...).
+ * Synchronises the handle's stream.
+ */
+int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit,
+              int* iters_host, double* res_hist_host, double* true_rel_res_host);
+
+/* sem_last_error - message for the last error raised on this thread ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

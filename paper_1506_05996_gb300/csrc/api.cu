@@ -1,0 +1,456 @@
+// C ABI (include/sem.h): handle creation, uploads, operator/preconditioner
+// applications and the PCG driver of Algorithm 1.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+#include "device.h"
+#include "host_setup.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+}  // namespace
+
+struct sem_s {
+  sem::DevProblem d;
+  cudaStream_t stream = nullptr;
+  int flags = 0;
+  int precond = SEM_PRECOND_TWO_SCALE;
+  sem::Numbering nb;
+  sem::Csr A0full;
+  std::vector<uint8_t> mask_host;
+  std::vector<void*> allocs;        // freed at destroy
+  std::vector<void*> coarse_allocs; // freed when the coarse space is rebuilt
+  std::vector<sem::DevAmgLevel> levels;
+  bool coarse_ok = false;
+  std::string coarse_err;
+  double *coords = nullptr, *mN = nullptr, *geo = nullptr;
+  uint8_t* mask = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  sem::PcgState* st_host = nullptr;  // pinned
+
+  template <class T>
+  cudaError_t alloc(T** ptr, size_t count, std::vector<void*>& list) {
+    *ptr = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
+    if (e == cudaSuccess) list.push_back(*ptr);
+    return e;
+  }
+  template <class T>
+  cudaError_t upload(T** ptr, const std::vector<T>& v, std::vector<void*>& list) {
+    cudaError_t e = alloc(ptr, v.size(), list);
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream);
+  }
+  void free_list(std::vector<void*>& list) {
+    for (void* q : list) cudaFree(q);
+    list.clear();
+  }
+};
+
+namespace {
+
+// Coarse space on the free vertices and its AMG hierarchy (Sec. 4.1); rebuilt when
+// the mask changes.
+int build_coarse(sem_t* h) {
+  cudaStreamSynchronize(h->stream);
+  h->free_list(h->coarse_allocs);
+  h->levels.clear();
+  sem::DevProblem& d = h->d;
+  d.nlevels = 0;
+  d.levels = nullptr;
+  d.nfree = 0;
+  h->coarse_ok = false;
+  const sem::Numbering& nb = h->nb;
+  std::vector<int> cvmap(nb.nv, -1), keep;
+  for (int64_t v = 0; v < nb.nv; ++v) {
+    int g = nb.vert_dof[v];
+    if (g >= 0 && h->mask_host[g] == 0) { cvmap[v] = (int)keep.size(); keep.push_back((int)v); }
+  }
+  const int nfree = (int)keep.size();
+  std::vector<int> ecv(8 * nb.ne);
+  for (int64_t q = 0; q < 8 * nb.ne; ++q) ecv[q] = cvmap[nb.hexv[q]];
+  std::vector<int> cv_off(nfree + 1, 0), cv_idx;
+  for (int64_t q = 0; q < 8 * nb.ne; ++q)
+    if (ecv[q] >= 0) cv_off[ecv[q] + 1]++;
+  for (int i = 0; i < nfree; ++i) cv_off[i + 1] += cv_off[i];
+  cv_idx.resize(cv_off[nfree]);
+  {
+    std::vector<int> fill(cv_off.begin(), cv_off.end() - 1);
+    for (int64_t q = 0; q < 8 * nb.ne; ++q)
+      if (ecv[q] >= 0) cv_idx[fill[ecv[q]]++] = (int)q;
+  }
+  int* tmp_i;
+  CK(h->upload(&tmp_i, ecv, h->coarse_allocs)); d.ecv = tmp_i;
+  CK(h->upload(&tmp_i, cv_off, h->coarse_allocs)); d.cv_off = tmp_i;
+  CK(h->upload(&tmp_i, cv_idx, h->coarse_allocs)); d.cv_idx = tmp_i;
+  d.nfree = nfree;
+  if (nfree == 0) { h->coarse_ok = true; return SEM_OK; }
+  sem::Csr A0 = sem::submatrix(h->A0full, keep);
+  sem::Amg amg;
+  std::string err = sem::build_amg(A0, amg);
+  if (!err.empty()) {
+    h->coarse_err = err;
+    d.nfree = 0;
+    return SEM_OK;   // the operator still works; preconditioners needing P^c report it
+  }
+  auto up_csr = [&](const sem::Csr& A, sem::DevCsr& out) -> cudaError_t {
+    out.n = A.n;
+    out.nnz = (int)A.val.size();
+    cudaError_t e = h->upload(&out.ptr, A.ptr, h->coarse_allocs);
+    if (e == cudaSuccess) e = h->upload(&out.col, A.col, h->coarse_allocs);
+    if (e == cudaSuccess) e = h->upload(&out.val, A.val, h->coarse_allocs);
+    return e;
+  };
+  h->levels.resize(amg.levels.size());
+  for (size_t l = 0; l < amg.levels.size(); ++l) {
+    const sem::AmgLevel& L = amg.levels[l];
+    sem::DevAmgLevel& D = h->levels[l];
+    CK(up_csr(L.A, D.A));
+    CK(up_csr(L.P, D.P));
+    CK(up_csr(L.R, D.R));
+    CK(h->upload(&D.dinv, L.dinv, h->coarse_allocs));
+    CK(h->alloc(&D.b, L.A.n, h->coarse_allocs));
+    CK(h->alloc(&D.x, L.A.n, h->coarse_allocs));
+    CK(h->alloc(&D.t, L.A.n, h->coarse_allocs));
+    CK(h->alloc(&D.y, L.A.n, h->coarse_allocs));
+  }
+  double* tmp_d;
+  CK(h->upload(&tmp_d, amg.coarsest_inv, h->coarse_allocs)); d.coarsest_inv = tmp_d;
+  d.coarsest_n = amg.coarsest_n;
+  CK(h->alloc(&d.cb, amg.coarsest_n, h->coarse_allocs));
+  CK(h->alloc(&d.cx, amg.coarsest_n, h->coarse_allocs));
+  CK(h->alloc(&d.cres, nfree, h->coarse_allocs));
+  CK(h->alloc(&d.ctmp, nfree, h->coarse_allocs));
+  CK(h->alloc(&d.Rc, nfree, h->coarse_allocs));
+  CK(h->alloc(&d.Zc, nfree, h->coarse_allocs));
+  d.nlevels = (int)h->levels.size();
+  d.levels = h->levels.data();
+  CK(cudaStreamSynchronize(h->stream));
+  h->coarse_ok = true;
+  return SEM_OK;
+}
+
+int check_handle(const sem_t* h) {
+  if (h == nullptr) return fail(SEM_ERR_ARG, "NULL handle");
+  return SEM_OK;
+}
+
+// z = P r for the chosen parts; `pcg` adds the rz reduction / beta on the device.
+int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
+  sem::DevProblem& d = h->d;
+  const sem::PcgState* st = pcg ? d.st : nullptr;
+  int mode = 0;
+  if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
+    CK(sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
+    mode |= sem::PSUM_FINE;
+  }
+  if (which == SEM_PRECOND_TWO_SCALE || which == -1) {
+    if (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty()))
+      return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
+    CK(sem::launch_coarse_restrict(d, r, st, h->stream));
+    CK(sem::launch_coarse_solve(d, st, h->stream));
+    mode |= sem::PSUM_COARSE;
+  }
+  if (which == SEM_PRECOND_NONE) mode = sem::PSUM_IDENT;
+  CK(sem::launch_psum(d, mode, r, z, pcg, h->stream));
+  return SEM_OK;
+}
+
+}  // namespace
+
+static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2vert_host,
+                       int64_t n_hex, int order, double lambda, int flags);
+
+extern "C" {
+
+const char* sem_last_error(void) { return g_err.c_str(); }
+
+int sem_create(const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2vert_host, int64_t n_hex,
+               int order, double lambda, int flags, void* cuda_stream, sem_t** out) {
+  g_err.clear();
+  if (out == nullptr) return fail(SEM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (vert_xyz_host == nullptr || hex2vert_host == nullptr) return fail(SEM_ERR_ARG, "NULL mesh array");
+  if (n_vert < 8 || n_hex < 1) return fail(SEM_ERR_ARG, "empty mesh");
+  if (order < 2 || order > 8) return fail(SEM_ERR_ARG, "order must be in 2..8");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SEM_ERR_ARG, "lambda must be finite and >= 0");
+  if (flags & ~(SEM_GEOM_RECOMPUTE | SEM_NEUMANN)) return fail(SEM_ERR_ARG, "unknown flag");
+  for (int64_t i = 0; i < 3 * n_vert; ++i)
+    if (!std::isfinite(vert_xyz_host[i])) return fail(SEM_ERR_ARG, "non-finite vertex coordinate");
+
+  sem_t* h = new sem_t();
+  h->stream = (cudaStream_t)cuda_stream;
+  h->flags = flags;
+  int rc = create_impl(h, vert_xyz_host, n_vert, hex2vert_host, n_hex, order, lambda, flags);
+  if (rc != SEM_OK) {
+    sem_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SEM_OK;
+}
+
+}  // extern "C"
+
+static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2vert_host,
+                       int64_t n_hex, int order, double lambda, int flags) {
+  auto bail = [&](int code) { return code; };
+
+  std::string err = sem::number_mesh(vert_xyz_host, n_vert, hex2vert_host, n_hex, order, h->nb);
+  if (!err.empty()) return bail(fail(err.find("range") != std::string::npos || err.find("repeated") != std::string::npos
+                                         ? SEM_ERR_ARG : SEM_ERR_MESH, err));
+  const sem::Numbering& nb = h->nb;
+  const int n = order, p = n + 1, P = n + 3;
+  const int64_t p3 = (int64_t)p * p * p, P3 = (int64_t)P * P * P;
+  std::vector<double> t, rho;
+  sem::gll(n, t, rho);
+  std::vector<double> D = sem::derivative_matrix(n, t);
+  std::vector<int> g2l_off, g2l_idx, owner;
+  sem::gather_csr(nb, g2l_off, g2l_idx, owner);
+  std::vector<int> ip = sem::patch_table(nb);
+  std::vector<int> pg_off(nb.G + 1, 0), pg_idx;
+  for (size_t q = 0; q < ip.size(); ++q)
+    if (ip[q] >= 0) pg_off[ip[q] + 1]++;
+  for (int64_t g = 0; g < nb.G; ++g) pg_off[g + 1] += pg_off[g];
+  pg_idx.resize(pg_off[nb.G]);
+  {
+    std::vector<int> fill(pg_off.begin(), pg_off.end() - 1);
+    for (size_t q = 0; q < ip.size(); ++q)
+      if (ip[q] >= 0) pg_idx[fill[ip[q]]++] = (int)q;
+  }
+  std::vector<double> S, ev;
+  sem::pencil_tables(n, t, rho, D, S, ev);
+  std::vector<double> hbox = sem::box_sizes(nb, vert_xyz_host);
+  std::vector<double> coords = sem::dof_coords(nb, vert_xyz_host, t, owner);
+  std::vector<double> exyz(24 * nb.ne);
+  for (int64_t e = 0; e < nb.ne; ++e)
+    for (int c = 0; c < 8; ++c)
+      for (int a = 0; a < 3; ++a) exyz[24 * e + 3 * c + a] = vert_xyz_host[3 * nb.hexv[8 * e + c] + a];
+  h->mask_host.assign(nb.G, 0);
+  if (!(flags & SEM_NEUMANN)) h->mask_host = nb.boundary;
+
+  sem::DevProblem& d = h->d;
+  d.n = n; d.p = p; d.P = P;
+  d.ne = (int)nb.ne; d.G = (int)nb.G; d.nv = (int)nb.nv;
+  d.lambda = lambda;
+  d.recompute = (flags & SEM_GEOM_RECOMPUTE) != 0;
+  auto& A = h->allocs;
+#define UP(field, vec, T) do { T* q_; CK(h->upload(&q_, vec, A)); d.field = q_; } while (0)
+  UP(l2g, nb.l2g, int);
+  UP(exyz, exyz, double);
+  UP(D, D, double);
+  UP(tg, t, double);
+  UP(rho, rho, double);
+  UP(g2l_off, g2l_off, int);
+  UP(g2l_idx, g2l_idx, int);
+  UP(owner, owner, int);
+  UP(ip, ip, int);
+  UP(pg_off, pg_off, int);
+  UP(pg_idx, pg_idx, int);
+  UP(S, S, double);
+  UP(ev, ev, double);
+  UP(hbox, hbox, double);
+#undef UP
+  CK(h->upload(&h->coords, coords, A));
+  CK(h->upload(&h->mask, h->mask_host, A));
+  d.mask = h->mask;
+  CK(h->alloc(&d.wl, (size_t)(nb.ne * p3), A));
+  CK(h->alloc(&d.wp, (size_t)(nb.ne * P3), A));
+  CK(h->alloc(&d.Re, (size_t)(8 * nb.ne), A));
+  CK(h->alloc(&h->mN, (size_t)nb.G, A));
+  d.nblk = (int)std::min<int64_t>((nb.G + sem::kVecBlock - 1) / sem::kVecBlock, 152 * 8);
+  if (d.nblk < 1) d.nblk = 1;
+  CK(h->alloc(&d.partial, (size_t)d.nblk, A));
+  CK(h->alloc(&d.st, 1, A));
+  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), h->stream));
+  CK(h->alloc(&h->r, (size_t)nb.G, A));
+  CK(h->alloc(&h->z, (size_t)nb.G, A));
+  CK(h->alloc(&h->p, (size_t)nb.G, A));
+  CK(h->alloc(&h->f, (size_t)nb.G, A));
+  {
+    cudaError_t e = cudaMallocHost((void**)&h->st_host, sizeof(sem::PcgState));
+    if (e != cudaSuccess) return bail(fail(SEM_ERR_OOM, "cudaMallocHost failed"));
+  }
+
+  // geometric factors (stored variant) and the assembled lumped mass
+  if (!d.recompute) CK(h->alloc(&h->geo, (size_t)(7 * nb.ne * p3), A));
+  d.geo = h->geo;
+  int* bad;
+  CK(h->alloc(&bad, 1, A));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+  CK(sem::launch_geometry(d, h->geo, d.wl, bad, h->stream));
+  CK(sem::launch_gather_plain(d, d.wl, h->mN, h->stream));
+  int bad_host = 0;
+  CK(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (bad_host) return bail(fail(SEM_ERR_JACOBIAN, "non-positive Jacobian at a GLL node"));
+
+  h->A0full = sem::coarse_matrix(nb, vert_xyz_host, lambda);
+  return build_coarse(h);
+}
+
+extern "C" {
+
+void sem_destroy(sem_t* h) {
+  if (h == nullptr) return;
+  cudaStreamSynchronize(h->stream);
+  h->free_list(h->coarse_allocs);
+  h->free_list(h->allocs);
+  if (h->hist) cudaFree(h->hist);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  delete h;
+}
+
+int sem_set_stream(sem_t* h, void* cuda_stream) {
+  if (int rc = check_handle(h)) return rc;
+  h->stream = (cudaStream_t)cuda_stream;
+  return SEM_OK;
+}
+
+int sem_num_dofs(const sem_t* h, int64_t* n_dof_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_dof_host == nullptr) return fail(SEM_ERR_ARG, "NULL output");
+  *n_dof_host = h->nb.G;
+  return SEM_OK;
+}
+
+int sem_num_elements(const sem_t* h, int64_t* n_hex_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_hex_host == nullptr) return fail(SEM_ERR_ARG, "NULL output");
+  *n_hex_host = h->nb.ne;
+  return SEM_OK;
+}
+
+int sem_dof_coords(const sem_t* h, double* xyz_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (xyz_dev == nullptr) return fail(SEM_ERR_ARG, "NULL output");
+  CK(cudaMemcpyAsync(xyz_dev, h->coords, sizeof(double) * 3 * h->nb.G, cudaMemcpyDeviceToDevice, h->stream));
+  return SEM_OK;
+}
+
+int sem_mass(const sem_t* h, double* m_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (m_dev == nullptr) return fail(SEM_ERR_ARG, "NULL output");
+  CK(cudaMemcpyAsync(m_dev, h->mN, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, h->stream));
+  return SEM_OK;
+}
+
+int sem_get_mask(const sem_t* h, uint8_t* mask_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (mask_dev == nullptr) return fail(SEM_ERR_ARG, "NULL output");
+  CK(cudaMemcpyAsync(mask_dev, h->mask, h->nb.G, cudaMemcpyDeviceToDevice, h->stream));
+  return SEM_OK;
+}
+
+int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (mask_dev == nullptr) return fail(SEM_ERR_ARG, "NULL mask");
+  std::vector<uint8_t> m(h->nb.G);
+  CK(cudaMemcpyAsync(m.data(), mask_dev, h->nb.G, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& v : m) v = v ? 1 : 0;
+  h->mask_host = m;
+  CK(cudaMemcpyAsync(h->mask, h->mask_host.data(), h->nb.G, cudaMemcpyHostToDevice, h->stream));
+  return build_coarse(h);
+}
+
+int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (x_dev == nullptr || y_dev == nullptr || x_dev == y_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  CK(sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
+  CK(sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
+  return SEM_OK;
+}
+
+static int apply_P_common(sem_t* h, int which, const double* r_dev, double* z_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (r_dev == nullptr || z_dev == nullptr || r_dev == z_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  return apply_precond(h, which, r_dev, z_dev, false);
+}
+
+int sem_apply_P(sem_t* h, const double* r_dev, double* z_dev) {
+  return apply_P_common(h, SEM_PRECOND_TWO_SCALE, r_dev, z_dev);
+}
+int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev) {
+  return apply_P_common(h, SEM_PRECOND_FINE, r_dev, z_dev);
+}
+int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev) { return apply_P_common(h, -1, r_dev, z_dev); }
+
+int sem_set_precond(sem_t* h, int which) {
+  if (int rc = check_handle(h)) return rc;
+  if (which < SEM_PRECOND_TWO_SCALE || which > SEM_PRECOND_NONE) return fail(SEM_ERR_ARG, "unknown preconditioner");
+  h->precond = which;
+  return SEM_OK;
+}
+
+int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
+              double* res_hist_host, double* true_rel_res_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (b_dev == nullptr || x_dev == nullptr || b_dev == x_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  sem::DevProblem& d = h->d;
+  if (maxit + 1 > h->hist_cap) {
+    if (h->hist) cudaFree(h->hist);
+    h->hist = nullptr;
+    h->hist_cap = 0;
+    CK(cudaMalloc((void**)&h->hist, sizeof(double) * (maxit + 1)));
+    h->hist_cap = maxit + 1;
+  }
+  cudaStream_t s = h->stream;
+  double* u = x_dev;
+  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
+  CK(sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, h->hist, s));
+  if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
+  CK(sem::launch_pcg_first_direction(d, h->z, h->p, s));
+  const int chunk = 4;
+  for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
+    for (int c = 0; c < chunk; ++c) {
+      CK(sem::launch_ax_local(d, h->p, d.wl, d.st, s));
+      CK(sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
+      CK(sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
+      if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
+      CK(sem::launch_pcg_direction(d, h->z, h->p, s));
+    }
+    CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (h->st_host->done) break;
+  }
+  // true residual ||b - A u|| / ||b|| on the free nodes
+  CK(sem::launch_ax_local(d, u, d.wl, nullptr, s));
+  CK(sem::launch_true_residual(d, b_dev, d.wl, s));
+  CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const sem::PcgState& st = *h->st_host;
+  if (iters_host) *iters_host = st.iter;
+  if (res_hist_host) {
+    CK(cudaMemcpyAsync(res_hist_host, h->hist, sizeof(double) * (st.iter + 1), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (true_rel_res_host) *true_rel_res_host = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
+  if (st.status == -6) return fail(SEM_ERR_NAN, "NaN/Inf or non-positive curvature in PCG");
+  if (!st.done) return fail(SEM_MAXIT, "maxit reached");
+  return st.status == 1 ? SEM_MAXIT : SEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Device-side data of one problem and the kernel launchers (kernels.cu).
+// Layouts (all device memory, element order = the library's order):
+//   l2g   int32 [ne * p^3]       local node l = i + p (j + p k) of element e at e*p^3 + l
+//   geo   f64 [ne][7][p^3]       G1..G6 (= w|J| J^-1 J^-T entries xx xy xz yy yz zz) and m = w|J|
+//   exyz  f64 [ne][8][3]         element vertex coordinates (VTK corner order)
+//   g2l   CSR over DOFs -> local nodes (ascending), owner[g] = first local copy
+//   ip    int32 [ne * P^3]       extended-box patch table, P = n + 3, -1 = absent
+//   pg    CSR over DOFs -> patch entries e*P^3 + q (ascending)
+//   ecv   int32 [ne][8]          coarse (free vertex) index of each corner or -1
+//   cv    CSR over free vertices -> e*8 + corner
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sem {
+
+constexpr int kVecBlock = 256;          // threads per block of the vector kernels
+
+// Scalars of one PCG solve, resident on the device (Algorithm 1).
+struct PcgState {
+  double rz;        // z_k^T r_k
+  double alpha, beta;
+  double bb;        // ||b||^2
+  double rtol;      // stop when ||r_k|| <= rtol ||b||
+  double rr;        // ||r_k||^2
+  double pf;        // p_k^T f
+  double aux;       // spare reduction result (true residual)
+  int iter;         // operator applications done
+  int done;         // 1 once converged / stopped
+  int status;       // 0, SEM_MAXIT (1) or SEM_ERR_NAN (-6)
+  int maxit;
+  unsigned int counter;   // blocks finished in the running reduction
+};
+
+struct DevCsr {
+  int n = 0, nnz = 0;
+  int* ptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+};
+
+struct DevAmgLevel {
+  DevCsr A, P, R;
+  double* dinv = nullptr;
+  double *b = nullptr, *x = nullptr, *t = nullptr, *y = nullptr;   // rhs, iterate, residual, output (size A.n)
+};
+
+struct DevProblem {
+  int n = 0, p = 0, P = 0;
+  int ne = 0, G = 0, nv = 0, nfree = 0;
+  double lambda = 0.0;
+  bool recompute = false;
+  // tables
+  const int* l2g = nullptr;
+  const double* geo = nullptr;
+  const double* exyz = nullptr;
+  const double* D = nullptr;        // p*p, Dhat[i*p + m] = phi_m'(t_i)
+  const double* tg = nullptr;       // p GLL points
+  const double* rho = nullptr;      // p GLL weights
+  const uint8_t* mask = nullptr;
+  const int* g2l_off = nullptr;
+  const int* g2l_idx = nullptr;
+  const int* owner = nullptr;
+  const int* ip = nullptr;
+  const int* pg_off = nullptr;
+  const int* pg_idx = nullptr;
+  const double* S = nullptr;        // P*P, S[row*P + mode]
+  const double* ev = nullptr;       // P
+  const double* hbox = nullptr;     // ne*3
+  const int* ecv = nullptr;
+  const int* cv_off = nullptr;
+  const int* cv_idx = nullptr;
+  // AMG
+  int nlevels = 0;
+  DevAmgLevel* levels = nullptr;    // host array of device levels
+  int coarsest_n = 0;
+  const double* coarsest_inv = nullptr;
+  double* cb = nullptr;             // coarsest rhs / solution work
+  double* cx = nullptr;
+  double* cres = nullptr;           // level-0 residual for repeated cycles
+  double* ctmp = nullptr;
+  // work
+  double* wl = nullptr;             // ne*p^3 local results
+  double* wp = nullptr;             // ne*P^3 patch results
+  double* Re = nullptr;             // ne*8 element coarse residuals
+  double* Rc = nullptr;             // nfree coarse residual
+  double* Zc = nullptr;             // nfree coarse correction
+  double* partial = nullptr;        // reduction partials
+  int nblk = 0;                     // blocks of the vector kernels
+  PcgState* st = nullptr;
+};
+
+// --- geometry set-up ---------------------------------------------------------
+// Computes m_loc (ne*p^3) and, if geo != nullptr, the stored factors; sets *bad = 1
+// if |J| <= 0 anywhere.
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, int* bad, cudaStream_t s);
+
+// --- operator (Eq. R, Algorithm 2) -------------------------------------------
+cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st,
+                            cudaStream_t s);
+// y = gather(wl); masked rows take xin (identity) - sem_apply_A.
+cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y,
+                                   cudaStream_t s);
+// y = gather(wl) on all nodes, no mask (set-up: assembled mass).
+cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y, cudaStream_t s);
+
+// --- preconditioner (Sec. 4) -------------------------------------------------
+cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st,
+                                 cudaStream_t s);
+cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
+cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);
+enum PsumMode { PSUM_FINE = 1, PSUM_COARSE = 2, PSUM_BOTH = 3, PSUM_IDENT = 4 };
+// z = mask ? 0 : fine + coarse parts (or r itself with PSUM_IDENT); if pcg: rz reduction
+// and beta on the device.
+cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg,
+                        cudaStream_t s);
+
+// --- PCG (Algorithm 1) -------------------------------------------------------
+cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol,
+                            int maxit, double* hist, cudaStream_t s);
+cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
+// f = gather(wl) (0 on masked), pf = p.f, alpha = rz / pf.
+cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s);
+cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double* f, double* u, double* r,
+                              double* hist, cudaStream_t s);
+cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
+// aux = ||b - f||^2 over free nodes
+cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s);
+
+}  // namespace sem

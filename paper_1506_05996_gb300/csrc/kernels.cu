@@ -1,0 +1,671 @@
+// sm_103a kernels of the spectral-element solver, FP64 path.
+//
+//  geometry_kernel      G1..G6 and m at every GLL node from the trilinear map (Sec. 2.3-2.4)
+//  ax_local_kernel      local residual r_{ijk;e} of Eq. R / Algorithm 2 (stored or recomputed G)
+//  gather kernels       r_N = sum of local copies (Eq. gather), deterministic CSR order
+//  schwarz_local_kernel fast-diagonalisation patch solve of Eq. z (Sec. 4.2)
+//  coarse kernels       restriction C m^-1 r, AMG V-cycles, prolongation (Sec. 4.1, Eq. coarse)
+//  pcg kernels          fused vector updates and dot products of Algorithm 1; alpha, beta
+//                       and the stopping test are evaluated on the device
+//
+// Reductions are deterministic: fixed grid, fixed per-thread ranges, a fixed
+// shuffle tree per block, and the last block to finish sums the block partials
+// in index order (no spin-waits: a completion counter decides the last block).
+#include <cmath>
+
+#include "device.h"
+
+namespace sem {
+namespace {
+
+__device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
+
+// Sum over a block of BS threads; the result is valid in warp 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v) {
+  static_assert(BS % 32 == 0 && BS <= 1024, "block size");
+  __shared__ double sh[BS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < BS / 32) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Grid reduction: every block writes its partial; the last block to arrive sums the
+// partials in index order. Returns true in all threads of that last block, where
+// `total` is valid in thread 0.
+template <int BS>
+__device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned int* counter, double& total) {
+  __shared__ bool last;
+  const double bs = block_sum<BS>(v);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(&partial[i]);
+  total = block_sum<BS>(s);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// G = w |J| J^-1 J^-T (6 entries) and m = w |J| at reference point (a, b, c) from the
+// 8 vertices xv[corner*3 + dim]. J[r][s] = d x_r / d xi_s of the trilinear map.
+__device__ __forceinline__ void geom_point(const double* xv, double a, double b, double c, double w,
+                                           double G[6], double& m, double& det) {
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double sa = ((q == 1) | (q == 2) | (q == 5) | (q == 6)) ? 1.0 : -1.0;
+    const double sb = ((q == 2) | (q == 3) | (q == 6) | (q == 7)) ? 1.0 : -1.0;
+    const double sc = (q >= 4) ? 1.0 : -1.0;
+    const double fa = 0.5 * (1.0 + sa * a), fb = 0.5 * (1.0 + sb * b), fc = 0.5 * (1.0 + sc * c);
+    const double d0 = 0.5 * sa * fb * fc, d1 = 0.5 * sb * fa * fc, d2 = 0.5 * sc * fa * fb;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double x = xv[3 * q + r];
+      J[r][0] += x * d0;
+      J[r][1] += x * d1;
+      J[r][2] += x * d2;
+    }
+  }
+  double C[3][3];
+  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  const double s = w / det;   // inv(J)[r][c] = C[c][r] / det
+  G[0] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
+  G[1] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
+  G[2] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
+  G[3] = s * (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
+  G[4] = s * (C[0][1] * C[0][2] + C[1][1] * C[1][2] + C[2][1] * C[2][2]);
+  G[5] = s * (C[0][2] * C[0][2] + C[1][2] * C[1][2] + C[2][2] * C[2][2]);
+  m = w * det;
+}
+
+// ----------------------------------------------------------------- geometry
+template <int p>
+__global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d, double* geo, double* mloc,
+                                                             int* bad) {
+  constexpr int p3 = p * p * p;
+  __shared__ double sx[24];
+  const int e = blockIdx.x, t = threadIdx.x;
+  if (t < 24) sx[t] = d.exyz[(size_t)e * 24 + t];
+  __syncthreads();
+  const int i = t % p, j = (t / p) % p, k = t / (p * p);
+  double G[6], m, det;
+  geom_point(sx, d.tg[i], d.tg[j], d.tg[k], d.rho[i] * d.rho[j] * d.rho[k], G, m, det);
+  if (!(det > 0.0)) *bad = 1;
+  mloc[(size_t)e * p3 + t] = m;
+  if (geo != nullptr) {
+    double* gp = geo + (size_t)e * 7 * p3 + t;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gp[c * p3] = G[c];
+    gp[6 * p3] = m;
+  }
+}
+
+// ----------------------------------------------------------------- operator
+// One CTA per element, one thread per GLL node (Algorithm 2): gradient by D,
+// A/B/C by the geometric factors, divergence by D^T, plus lambda m u.
+template <int p, bool RECOMP>
+__global__ void __launch_bounds__(p * p * p) ax_local_kernel(const DevProblem d, const double* __restrict__ x,
+                                                             double* __restrict__ wl, const PcgState* st) {
+  if (stopped(st)) return;
+  constexpr int p3 = p * p * p;
+  __shared__ double sD[p * p], su[p3], sA[p3], sB[p3], sC[p3];
+  __shared__ double sx[24];
+  const int e = blockIdx.x, t = threadIdx.x;
+  const int i = t % p, j = (t / p) % p, k = t / (p * p);
+  if (t < p * p) sD[t] = d.D[t];
+  if (RECOMP && t < 24) sx[t] = d.exyz[(size_t)e * 24 + t];
+  const int g = d.l2g[(size_t)e * p3 + t];
+  const double u = d.mask[g] ? 0.0 : x[g];
+  su[t] = u;
+  __syncthreads();
+  double ur = 0.0, us = 0.0, ut = 0.0;
+#pragma unroll
+  for (int m = 0; m < p; ++m) {
+    ur += sD[i * p + m] * su[m + p * (j + p * k)];
+    us += sD[j * p + m] * su[i + p * (m + p * k)];
+    ut += sD[k * p + m] * su[i + p * (j + p * m)];
+  }
+  double G[6], mm;
+  if (!RECOMP) {
+    const double* gp = d.geo + (size_t)e * 7 * p3 + t;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
+    mm = gp[6 * p3];
+  } else {
+    double det;
+    geom_point(sx, d.tg[i], d.tg[j], d.tg[k], d.rho[i] * d.rho[j] * d.rho[k], G, mm, det);
+  }
+  sA[t] = G[0] * ur + G[1] * us + G[2] * ut;
+  sB[t] = G[1] * ur + G[3] * us + G[4] * ut;
+  sC[t] = G[2] * ur + G[4] * us + G[5] * ut;
+  __syncthreads();
+  double r = 0.0;
+#pragma unroll
+  for (int m = 0; m < p; ++m) {
+    r += sD[m * p + i] * sA[m + p * (j + p * k)];
+    r += sD[m * p + j] * sB[i + p * (m + p * k)];
+    r += sD[m * p + k] * sC[i + p * (j + p * m)];
+  }
+  r += d.lambda * mm * u;
+  wl[(size_t)e * p3 + t] = r;
+}
+
+__global__ void gather_identity_kernel(const DevProblem d, const double* __restrict__ wl,
+                                       const double* __restrict__ xin, double* __restrict__ y) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    if (d.mask[g]) { y[g] = xin[g]; continue; }
+    double s = 0.0;
+    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    y[g] = s;
+  }
+}
+
+__global__ void gather_plain_kernel(const DevProblem d, const double* __restrict__ wl, double* __restrict__ y) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    y[g] = s;
+  }
+}
+
+// ------------------------------------------------------------ fine Schwarz
+// One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of
+// the extended box in each of the six tensor contractions of Eq. z:
+//   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
+//   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
+template <int P>
+__global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d, const double* __restrict__ r,
+                                                              double* __restrict__ wp, const PcgState* st) {
+  if (stopped(st)) return;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  __shared__ double sS[P2], sev[P], s1[P3], s2[P3];
+  const int e = blockIdx.x, tx = threadIdx.x;
+  const int x = tx % P, y = tx / P;
+  sS[tx] = d.S[tx];
+  if (tx < P) sev[tx] = d.ev[tx];
+  const double hx = d.hbox[3 * e], hy = d.hbox[3 * e + 1], hz = d.hbox[3 * e + 2];
+  const double scale = 8.0 / (hx * hy * hz);
+  double col[P];
+  const int* ipe = d.ip + (size_t)e * P3;
+#pragma unroll
+  for (int K = 0; K < P; ++K) {
+    const int g = ipe[x + P * (y + P * K)];
+    col[K] = (g >= 0 && !d.mask[g]) ? r[g] * scale : 0.0;
+  }
+  __syncthreads();
+  // along K: line (I=x, J=y)
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    double v = 0.0;
+#pragma unroll
+    for (int K = 0; K < P; ++K) v += sS[K * P + c] * col[K];
+    s1[x + P * (y + P * c)] = v;
+  }
+  __syncthreads();
+  // along J: line (I=x, c=y)
+#pragma unroll
+  for (int b = 0; b < P; ++b) {
+    double v = 0.0;
+#pragma unroll
+    for (int J = 0; J < P; ++J) v += sS[J * P + b] * s1[x + P * (J + P * y)];
+    s2[x + P * (b + P * y)] = v;
+  }
+  __syncthreads();
+  // along I: line (b=x, c=y), eigenvalue scaling, and back along I
+  {
+    double t3[P];
+    const double lb = sev[x] / (hy * hy), lc = sev[y] / (hz * hz);
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      double v = 0.0;
+#pragma unroll
+      for (int I = 0; I < P; ++I) v += sS[I * P + a] * s2[I + P * (x + P * y)];
+      t3[a] = v / (4.0 * (sev[a] / (hx * hx) + lb + lc) + d.lambda);
+    }
+#pragma unroll
+    for (int I = 0; I < P; ++I) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < P; ++a) v += sS[I * P + a] * t3[a];
+      s2[I + P * (x + P * y)] = v;
+    }
+  }
+  __syncthreads();
+  // back along J: line (I=x, c=y)
+#pragma unroll
+  for (int J = 0; J < P; ++J) {
+    double v = 0.0;
+#pragma unroll
+    for (int b = 0; b < P; ++b) v += sS[J * P + b] * s2[x + P * (b + P * y)];
+    s1[x + P * (J + P * y)] = v;
+  }
+  __syncthreads();
+  // back along K: line (I=x, J=y)
+  double* out = wp + (size_t)e * P3;
+#pragma unroll
+  for (int K = 0; K < P; ++K) {
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < P; ++c) v += sS[K * P + c] * s1[x + P * (y + P * c)];
+    out[x + P * (y + P * K)] = v;
+  }
+}
+
+// ---------------------------------------------------------------- coarse
+// Per element R_{IJK;e} = sum over the element's owned nodes of Phi_I Phi_J Phi_K r_N;
+// summed over elements this is C m^{-1} r (every node counted once, at its owner).
+constexpr int kRestrictBlock = 128;
+__global__ void __launch_bounds__(kRestrictBlock) coarse_restrict_kernel(const DevProblem d, const double* __restrict__ r,
+                                                                         const PcgState* st) {
+  if (stopped(st)) return;
+  const int e = blockIdx.x, p = d.p, p3 = p * p * p;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int l = threadIdx.x; l < p3; l += kRestrictBlock) {
+    const int gl = e * p3 + l;
+    const int g = d.l2g[gl];
+    if (d.owner[g] != gl || d.mask[g]) continue;
+    const double v = r[g];
+    const int i = l % p, j = (l / p) % p, k = l / (p * p);
+    const double ti = d.tg[i], tj = d.tg[j], tk = d.tg[k];
+    const double fx[2] = {0.5 * (1.0 - ti), 0.5 * (1.0 + ti)};
+    const double fy[2] = {0.5 * (1.0 - tj), 0.5 * (1.0 + tj)};
+    const double fz[2] = {0.5 * (1.0 - tk), 0.5 * (1.0 + tk)};
+    acc[0] += v * (fx[0] * fy[0] * fz[0]);
+    acc[1] += v * (fx[1] * fy[0] * fz[0]);
+    acc[2] += v * (fx[1] * fy[1] * fz[0]);
+    acc[3] += v * (fx[0] * fy[1] * fz[0]);
+    acc[4] += v * (fx[0] * fy[0] * fz[1]);
+    acc[5] += v * (fx[1] * fy[0] * fz[1]);
+    acc[6] += v * (fx[1] * fy[1] * fz[1]);
+    acc[7] += v * (fx[0] * fy[1] * fz[1]);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double s = block_sum<kRestrictBlock>(acc[c]);
+    if (threadIdx.x == 0) d.Re[(size_t)e * 8 + c] = s;
+  }
+}
+
+__global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < d.nfree; v += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = d.cv_off[v]; q < d.cv_off[v + 1]; ++q) s += d.Re[d.cv_idx[q]];
+    d.Rc[v] = s;
+  }
+}
+
+// AMG kernels, one thread per row.
+__global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const double* __restrict__ b,
+                                   double* __restrict__ x, double omega, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = omega * dinv[i] * b[i];
+}
+
+__global__ void amg_resid_kernel(DevCsr A, const double* __restrict__ b, const double* __restrict__ x,
+                                 double* __restrict__ t, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
+    t[i] = b[i] - s;
+  }
+}
+
+__global__ void amg_spmv_kernel(DevCsr A, const double* __restrict__ x, double* __restrict__ y, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
+    y[i] = s;
+  }
+}
+
+__global__ void amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc, double* __restrict__ x,
+                                       const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = P.ptr[i]; q < P.ptr[i + 1]; ++q) s += P.val[q] * xc[P.col[q]];
+    x[i] = x[i] + s;
+  }
+}
+
+__global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv, const double* __restrict__ b,
+                                       const double* __restrict__ x, double* __restrict__ xout, double omega,
+                                       const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
+    xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
+  }
+}
+
+__global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + y[i];
+}
+
+// x = Ainv b, one warp per row (dense coarsest level).
+__global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const double* __restrict__ b,
+                                double* __restrict__ x, const PcgState* st) {
+  if (stopped(st)) return;
+  const int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += Ainv[(size_t)row * n + c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = s;
+  }
+}
+
+// ------------------------------------------------------------ P sum and PCG
+template <bool PCG>
+__global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const double* __restrict__ r,
+                                                         double* __restrict__ z) {
+  if (PCG && stopped(d.st)) return;
+  const int p = d.p, p3 = p * p * p;
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (!d.mask[g]) {
+      if (mode & PSUM_IDENT) v += r[g];
+      if (mode & PSUM_FINE)
+        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += d.wp[d.pg_idx[q]];
+      if ((mode & PSUM_COARSE) && d.nfree > 0) {
+        const int l = d.owner[g], e = l / p3, lr = l % p3;
+        const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
+        const double ti = d.tg[i], tj = d.tg[j], tk = d.tg[k];
+        const double fx[2] = {0.5 * (1.0 - ti), 0.5 * (1.0 + ti)};
+        const double fy[2] = {0.5 * (1.0 - tj), 0.5 * (1.0 + tj)};
+        const double fz[2] = {0.5 * (1.0 - tk), 0.5 * (1.0 + tk)};
+        const int* ec = d.ecv + (size_t)e * 8;
+        const double B[8] = {fx[0] * fy[0] * fz[0], fx[1] * fy[0] * fz[0], fx[1] * fy[1] * fz[0], fx[0] * fy[1] * fz[0],
+                             fx[0] * fy[0] * fz[1], fx[1] * fy[0] * fz[1], fx[1] * fy[1] * fz[1], fx[0] * fy[1] * fz[1]};
+        double zc = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cv = ec[c];
+          if (cv >= 0) zc += B[c] * d.Zc[cv];
+        }
+        v += zc;
+      }
+    }
+    z[g] = v;
+    if (PCG) dot += v * r[g];
+  }
+  if (PCG) {
+    double total;
+    if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+      PcgState* st = d.st;
+      if (!isfinite(total)) { st->status = -6; st->done = 1; }
+      if (st->iter > 0) st->beta = total / st->rz;
+      st->rz = total;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
+                                                             double* __restrict__ r, double* __restrict__ u,
+                                                             double rtol, int maxit, double* hist) {
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    const double v = d.mask[g] ? 0.0 : b[g];
+    r[g] = v;
+    u[g] = 0.0;
+    dot += v * v;
+  }
+  double total;
+  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+    PcgState* st = d.st;
+    st->bb = total;
+    st->rtol = rtol;
+    st->rr = total;
+    st->iter = 0;
+    st->maxit = maxit;
+    st->status = 0;
+    st->rz = 0.0;
+    st->beta = 0.0;
+    hist[0] = (total > 0.0) ? 1.0 : 0.0;
+    if (!isfinite(total)) { st->status = -6; st->done = 1; }
+    else if (total == 0.0) st->done = 1;
+    else if (maxit <= 0) { st->status = 1; st->done = 1; }
+  }
+}
+
+__global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
+  if (stopped(d.st)) return;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) p[g] = z[g];
+}
+
+__global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevProblem d, const double* __restrict__ p,
+                                                                     double* __restrict__ f) {
+  if (stopped(d.st)) return;
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (!d.mask[g])
+      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += d.wl[d.g2l_idx[q]];
+    f[g] = s;
+    dot += p[g] * s;
+  }
+  double total;
+  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+    PcgState* st = d.st;
+    st->pf = total;
+    if (!(total > 0.0) || !isfinite(total)) { st->status = -6; st->done = 1; }
+    else st->alpha = st->rz / total;
+  }
+}
+
+__global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem d, const double* __restrict__ p,
+                                                               const double* __restrict__ f, double* __restrict__ u,
+                                                               double* __restrict__ r, double* hist) {
+  if (stopped(d.st)) return;
+  const double alpha = d.st->alpha;
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    u[g] = u[g] + alpha * p[g];
+    const double rn = r[g] - alpha * f[g];
+    r[g] = rn;
+    dot += rn * rn;
+  }
+  double total;
+  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+    PcgState* st = d.st;
+    st->rr = total;
+    const int it = ++st->iter;
+    const double rel = sqrt(total) / sqrt(st->bb);
+    hist[it] = rel;
+    if (!isfinite(total)) { st->status = -6; st->done = 1; }
+    else if (rel <= st->rtol) st->done = 1;
+    else if (it >= st->maxit) { st->status = 1; st->done = 1; }
+  }
+}
+
+__global__ void pcg_direction_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
+  if (stopped(d.st)) return;
+  const double beta = d.st->beta;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) p[g] = z[g] + beta * p[g];
+}
+
+__global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProblem d, const double* __restrict__ b,
+                                                                  const double* __restrict__ wl) {
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    if (d.mask[g]) continue;
+    double s = 0.0;
+    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    const double res = b[g] - s;
+    dot += res * res;
+  }
+  double total;
+  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) d.st->aux = total;
+}
+
+inline int grid_for(int n, int block, int cap) {
+  int g = (n + block - 1) / block;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+constexpr double kOmega = 2.0 / 3.0;
+constexpr int kCycles = 3;
+
+// V(1,1) cycle at `level` for right-hand side b, result in out (out != b).
+cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
+  if (level == d.nlevels) {
+    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    return cudaGetLastError();
+  }
+  const DevAmgLevel& L = d.levels[level];
+  const int n = L.A.n, gb = grid_for(n, 256, 4096);
+  amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
+  amg_resid_kernel<<<gb, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
+  double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
+  const int nc = L.R.n;
+  amg_spmv_kernel<<<grid_for(nc, 256, 4096), 256, 0, s>>>(L.R, L.t, bc, st);
+  cudaError_t err = vcycle(d, level + 1, bc, xc, st, s);
+  if (err != cudaSuccess) return err;
+  amg_prolong_add_kernel<<<gb, 256, 0, s>>>(L.P, xc, L.x, st);
+  amg_jacobi_post_kernel<<<gb, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ================================================================ launchers
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, int* bad, cudaStream_t s) {
+  switch (d.p) {
+#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, mloc, bad); break;
+    GEO_CASE(2) GEO_CASE(3) GEO_CASE(4) GEO_CASE(5) GEO_CASE(6) GEO_CASE(7) GEO_CASE(8) GEO_CASE(9)
+#undef GEO_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
+  switch (d.p) {
+#define AX_CASE(P_)                                                                        \
+  case P_:                                                                                 \
+    if (d.recompute) ax_local_kernel<P_, true><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);  \
+    else ax_local_kernel<P_, false><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);             \
+    break;
+    AX_CASE(2) AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
+#undef AX_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
+  gather_identity_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y, cudaStream_t s) {
+  gather_plain_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
+  switch (d.P) {
+#define SW_CASE(P_) case P_: schwarz_local_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); break;
+    SW_CASE(4) SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
+#undef SW_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s) {
+  if (d.nfree == 0) return cudaSuccess;
+  coarse_restrict_kernel<<<d.ne, kRestrictBlock, 0, s>>>(d, r, st);
+  vertex_gather_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d, st);
+  return cudaGetLastError();
+}
+
+// Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero.
+cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
+  if (d.nfree == 0) return cudaSuccess;
+  cudaError_t err = vcycle(d, 0, d.Rc, d.Zc, st, s);
+  if (err != cudaSuccess || d.nlevels == 0) return err;
+  const DevCsr& A0 = d.levels[0].A;
+  const int gb = grid_for(A0.n, 256, 4096);
+  for (int c = 1; c < kCycles; ++c) {
+    amg_resid_kernel<<<gb, 256, 0, s>>>(A0, d.Rc, d.Zc, d.cres, st);
+    err = vcycle(d, 0, d.cres, d.ctmp, st, s);
+    if (err != cudaSuccess) return err;
+    add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
+  if (pcg) psum_kernel<true><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
+  else psum_kernel<false><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
+                            double* hist, cudaStream_t s) {
+  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
+  pcg_copy_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s) {
+  pcg_gather_alpha_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double* f, double* u, double* r, double* hist,
+                              cudaStream_t s) {
+  pcg_update_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f, u, r, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
+  pcg_direction_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s) {
+  true_residual_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, wl);
+  return cudaGetLastError();
+}
+
+}  // namespace sem

@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libsem.so, one Python function per C entry point.
+
+Only argument marshalling happens here: torch CUDA tensors become device
+pointers, numpy arrays host pointers, and negative status codes become
+SemError exceptions carrying sem_last_error(). Every step of the solver runs
+in the library's CUDA kernels; if libsem.so is missing this module raises on
+import.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsem.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libsem.so is not built (run `python -m paper_1506_05996_gb300.build`)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+SEM_OK = 0
+SEM_ERR_ARG, SEM_ERR_JACOBIAN, SEM_ERR_MESH, SEM_ERR_CUDA = -1, -2, -3, -4
+SEM_ERR_OOM, SEM_ERR_NAN, SEM_ERR_SINGULAR = -5, -6, -7
+SEM_MAXIT = 1
+SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN = 0x0, 0x1, 0x10
+SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
+
+_vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+_P = ctypes.POINTER
+
+_SIGS = {
+    "sem_create": ([_vp, _i64, _vp, _i64, _int, _dbl, _int, _vp, _P(_vp)], _int),
+    "sem_destroy": ([_vp], None),
+    "sem_set_stream": ([_vp, _vp], _int),
+    "sem_num_dofs": ([_vp, _P(_i64)], _int),
+    "sem_num_elements": ([_vp, _P(_i64)], _int),
+    "sem_dof_coords": ([_vp, _vp], _int),
+    "sem_mass": ([_vp, _vp], _int),
+    "sem_get_mask": ([_vp, _vp], _int),
+    "sem_set_mask": ([_vp, _vp], _int),
+    "sem_apply_A": ([_vp, _vp, _vp], _int),
+    "sem_apply_P": ([_vp, _vp, _vp], _int),
+    "sem_apply_Pf": ([_vp, _vp, _vp], _int),
+    "sem_apply_Pc": ([_vp, _vp, _vp], _int),
+    "sem_set_precond": ([_vp, _int], _int),
+    "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
+    "sem_last_error": ([], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+class SemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libsem error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _check(rc):
+    if rc < 0:
+        raise SemError(rc, _lib.sem_last_error().decode())
+    return rc
+
+
+def _dev(t, dtype, n):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor of %s" % dtype)
+    if t.numel() != n:
+        raise ValueError("expected %d elements, got %d" % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def sem_last_error():
+    return _lib.sem_last_error().decode()
+
+
+def sem_create(vert_xyz, hex2vert, order, lam, flags=0, stream=None):
+    xyz = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+    hexes = np.ascontiguousarray(hex2vert, dtype=np.int64)
+    if xyz.ndim != 2 or xyz.shape[1] != 3 or hexes.ndim != 2 or hexes.shape[1] != 8:
+        raise ValueError("vert_xyz must be (n_vert, 3) and hex2vert (n_hex, 8)")
+    h = ctypes.c_void_p()
+    _check(_lib.sem_create(xyz.ctypes.data, xyz.shape[0], hexes.ctypes.data, hexes.shape[0],
+                           int(order), float(lam), int(flags), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sem_destroy(h):
+    _lib.sem_destroy(h)
+
+
+def sem_set_stream(h, stream):
+    return _check(_lib.sem_set_stream(h, _stream_ptr(stream)))
+
+
+def sem_num_dofs(h):
+    n = ctypes.c_int64()
+    _check(_lib.sem_num_dofs(h, ctypes.byref(n)))
+    return n.value
+
+
+def sem_num_elements(h):
+    n = ctypes.c_int64()
+    _check(_lib.sem_num_elements(h, ctypes.byref(n)))
+    return n.value
+
+
+def sem_dof_coords(h, xyz):
+    return _check(_lib.sem_dof_coords(h, _dev(xyz, torch.float64, 3 * sem_num_dofs(h))))
+
+
+def sem_mass(h, m):
+    return _check(_lib.sem_mass(h, _dev(m, torch.float64, sem_num_dofs(h))))
+
+
+def sem_get_mask(h, mask):
+    return _check(_lib.sem_get_mask(h, _dev(mask, torch.uint8, sem_num_dofs(h))))
+
+
+def sem_set_mask(h, mask):
+    return _check(_lib.sem_set_mask(h, _dev(mask, torch.uint8, sem_num_dofs(h))))
+
+
+def sem_apply_A(h, x, y):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_A(h, _dev(x, torch.float64, n), _dev(y, torch.float64, n)))
+
+
+def sem_apply_P(h, r, z):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_P(h, _dev(r, torch.float64, n), _dev(z, torch.float64, n)))
+
+
+def sem_apply_Pf(h, r, z):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_Pf(h, _dev(r, torch.float64, n), _dev(z, torch.float64, n)))
+
+
+def sem_apply_Pc(h, r, z):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_Pc(h, _dev(r, torch.float64, n), _dev(z, torch.float64, n)))
+
+
+def sem_set_precond(h, which):
+    return _check(_lib.sem_set_precond(h, int(which)))
+
+
+def sem_solve(h, b, x, rtol=1e-8, maxit=1000, want_history=True):
+    """Returns (status, iterations, residual history (numpy) or None, true relative residual)."""
+    n = sem_num_dofs(h)
+    it = ctypes.c_int()
+    tr = ctypes.c_double()
+    hist = np.zeros(maxit + 1) if want_history else None
+    rc = _check(_lib.sem_solve(h, _dev(b, torch.float64, n), _dev(x, torch.float64, n), float(rtol),
+                               int(maxit), ctypes.byref(it), hist.ctypes.data if want_history else None,
+                               ctypes.byref(tr)))
+    if want_history:
+        hist = hist[:it.value + 1].copy()
+    return rc, it.value, hist, tr.value
+
+
+class SemProblem:
+    """Owns one handle; convenience wrappers returning torch tensors."""
+
+    def __init__(self, mesh_xyz, hex2vert, order, lam, geom="stored", neumann=False, stream=None,
+                 device="cuda"):
+        flags = SEM_GEOM_RECOMPUTE if geom == "recompute" else SEM_GEOM_STORED
+        if neumann:
+            flags |= SEM_NEUMANN
+        self.device = torch.device(device)
+        self.h = sem_create(mesh_xyz, hex2vert, order, lam, flags, stream)
+        self.n_dof = sem_num_dofs(self.h)
+        self.order = order
+
+    def close(self):
+        if self.h is not None:
+            sem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, dtype=torch.float64, n=None):
+        return torch.empty(self.n_dof if n is None else n, dtype=dtype, device=self.device)
+
+    def dof_coords(self):
+        x = self._vec(n=3 * self.n_dof)
+        sem_dof_coords(self.h, x)
+        return x.view(self.n_dof, 3)
+
+    def mass(self):
+        m = self._vec()
+        sem_mass(self.h, m)
+        return m
+
+    def mask(self):
+        m = self._vec(torch.uint8)
+        sem_get_mask(self.h, m)
+        return m
+
+    def apply_A(self, x):
+        y = self._vec()
+        sem_apply_A(self.h, x, y)
+        return y
+
+    def apply_P(self, r, part="two-scale"):
+        z = self._vec()
+        {"two-scale": sem_apply_P, "fine": sem_apply_Pf, "coarse": sem_apply_Pc}[part](self.h, r, z)
+        return z
+
+    def solve(self, b, rtol=1e-8, maxit=1000, precond="two-scale", x=None):
+        sem_set_precond(self.h, {"two-scale": SEM_PRECOND_TWO_SCALE, "fine": SEM_PRECOND_FINE,
+                                 "none": SEM_PRECOND_NONE}[precond])
+        if x is None:
+            x = self._vec()
+        rc, it, hist, tr = sem_solve(self.h, b, x, rtol, maxit)
+        return x, rc, it, hist, tr

@@ -1,0 +1,34 @@
+"""Shared helpers of the GPU parity tests: a library problem and the oracle on the
+same seeded mesh, with the DOF permutation between them found by position."""
+import numpy as np
+import torch
+
+from oracle.problem import Problem
+from paper_1506_05996_gb300.sem import SemProblem
+
+
+class Pair:
+    def __init__(self, mesh, n, lam, geom="stored", neumann=False, coarse=True, schwarz=True):
+        self.gpu = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom=geom, neumann=neumann)
+        self.ref = Problem(mesh, n, lam, dirichlet=not neumann,
+                           coarse_solver="amg" if coarse else None, with_schwarz=schwarz)
+        X = self.gpu.dof_coords().cpu().numpy()
+        oi = np.lexsort(np.round(self.ref.coords, 9).T)
+        gi = np.lexsort(np.round(X, 9).T)
+        perm = np.empty_like(gi)
+        perm[oi] = gi                       # oracle dof k  <->  gpu dof perm[k]
+        assert np.abs(X[perm] - self.ref.coords).max() < 1e-12
+        self.perm = perm
+        self.perm_t = torch.as_tensor(perm, device="cuda")
+
+    def to_gpu(self, v):
+        out = torch.zeros(self.gpu.n_dof, dtype=torch.float64, device="cuda")
+        out[self.perm_t] = torch.as_tensor(np.ascontiguousarray(v), device="cuda")
+        return out
+
+    def to_ref(self, t):
+        return t.cpu().numpy()[self.perm]
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)

@@ -1,0 +1,159 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerance: 1e-12 relative (max-norm) for the operator and the preconditioner
+in FP64; PCG is compared at equal iteration counts with the histories within
+1e-10 and the solutions within 1e-10 (rounding-order differences grow slowly
+through the recurrences).
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import lattice_hex_mesh, manufactured_s, manufactured_u
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05996_gb300 import build
+    build.build()
+
+
+def _pair(*a, **k):
+    from gpu_util import Pair
+    return Pair(*a, **k)
+
+
+CASES = [  # E, n, lam, a, seed
+    (1, 3, 0.0, 0.1, 0), (2, 4, 1.3, 0.2, 1), (4, 3, 0.0, 0.1, 0), (3, 2, 0.5, 0.2, 2),
+    (2, 5, 2.0, 0.2, 3), (2, 6, 0.0, 0.15, 4), (2, 7, 1.0, 0.2, 5), (2, 8, 0.7, 0.2, 6),
+]
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed", CASES)
+@pytest.mark.parametrize("geom", ["stored", "recompute"])
+def test_operator_parity(E, n, lam, a, seed, geom):
+    from gpu_util import rel_err
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam, geom=geom, coarse=False, schwarz=False)
+    x = np.random.default_rng(seed).standard_normal(P.ref.G)
+    y = P.to_ref(P.gpu.apply_A(P.to_gpu(x)))
+    assert rel_err(y, P.ref.apply_A(x)) <= TOL
+    np.testing.assert_array_equal(P.to_ref(P.gpu.mask()), P.ref.mask)
+    assert rel_err(P.to_ref(P.gpu.mass()), P.ref.m_N) <= TOL
+
+
+def test_operator_neumann_nullspace():
+    from gpu_util import rel_err
+    for lam in (0.0, 1.5):
+        P = _pair(lattice_hex_mesh(3, 0.2, 7), 4, lam, neumann=True, coarse=False, schwarz=False)
+        one = torch.ones(P.gpu.n_dof, dtype=torch.float64, device="cuda")
+        y = P.to_ref(P.gpu.apply_A(one))
+        np.testing.assert_allclose(y, lam * P.ref.m_N, atol=1e-13 * np.abs(P.ref.m_N).max() * max(lam, 1.0) * 50)
+        x = np.random.default_rng(1).standard_normal(P.ref.G)
+        assert rel_err(P.to_ref(P.gpu.apply_A(P.to_gpu(x))), P.ref.apply_A(x)) <= TOL
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed", [(2, 3, 0.0, 0.1, 0), (4, 3, 0.0, 0.1, 0), (3, 5, 1.0, 0.2, 1),
+                                            (2, 8, 0.5, 0.2, 2), (10, 2, 1.0, 0.2, 3)])
+def test_preconditioner_parity(E, n, lam, a, seed):
+    from gpu_util import rel_err
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam)
+    r = np.random.default_rng(seed + 10).standard_normal(P.ref.G)
+    rg = P.to_gpu(r)
+    assert rel_err(P.to_ref(P.gpu.apply_P(rg, "fine")), P.ref.apply_Pf(r)) <= TOL
+    assert rel_err(P.to_ref(P.gpu.apply_P(rg, "coarse")), P.ref.apply_Pc(r)) <= TOL
+    assert rel_err(P.to_ref(P.gpu.apply_P(rg, "two-scale")), P.ref.apply_P(r)) <= TOL
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed,pc", [(4, 3, 0.0, 0.1, 0, "two-scale"), (3, 4, 1.0, 0.2, 1, "fine"),
+                                               (10, 2, 1.0, 0.2, 3, "two-scale"), (3, 3, 0.5, 0.2, 2, "none")])
+def test_pcg_parity(E, n, lam, a, seed, pc):
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam)
+    b = P.ref.load(manufactured_s(P.ref.coords, lam))
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8, maxit=500, precond=pc)
+    u, it_ref, hist_ref = P.ref.solve(b, rtol=1e-8, maxit=500, precond=pc)
+    assert rc == 0
+    assert it == it_ref
+    np.testing.assert_allclose(hist, hist_ref, rtol=1e-9, atol=1e-14)
+    ug = P.to_ref(x)
+    assert np.max(np.abs(ug - u)) <= 1e-10 * np.max(np.abs(u))
+    assert tr <= 2e-8
+    # the discrete solution approximates the manufactured one
+    assert np.max(np.abs(ug - manufactured_u(P.ref.coords))) < 0.05
+
+
+def test_pcg_config1_golden():
+    """4^3 hexes, +-10 %, seed 0, n = 3, lambda = 0: iteration count and history of the
+    committed oracle golden file."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle.json")))
+    P = _pair(lattice_hex_mesh(4, 0.1, 0), 3, 0.0)
+    b = P.ref.load(manufactured_s(P.ref.coords, 0.0))
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+    assert it == gold["iterations"]
+    np.testing.assert_allclose(hist, gold["residual_history"], rtol=1e-9, atol=1e-14)
+
+
+def test_solve_is_deterministic():
+    P = _pair(lattice_hex_mesh(6, 0.2, 4), 4, 1.0)
+    b = P.to_gpu(P.ref.load(manufactured_s(P.ref.coords, 1.0)))
+    x1, _, it1, h1, _ = P.gpu.solve(b)
+    x2, _, it2, h2, _ = P.gpu.solve(b)
+    assert it1 == it2 and np.array_equal(h1, h2)
+    assert torch.equal(x1, x2)
+
+
+def test_edge_cases():
+    from gpu_util import rel_err
+    # single element, all boundary: only interior nodes free, no free vertex (no coarse space)
+    P = _pair(lattice_hex_mesh(1, 0.1, 0), 2, 0.0)
+    b = P.ref.load(np.ones(P.ref.G))
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b))
+    u, it_ref, _ = P.ref.solve(b)
+    assert rc == 0 and it == it_ref and rel_err(P.to_ref(x), u) < 1e-10
+    # zero right-hand side: zero iterations, zero solution
+    x, rc, it, hist, tr = P.gpu.solve(torch.zeros(P.gpu.n_dof, dtype=torch.float64, device="cuda"))
+    assert rc == 0 and it == 0 and float(x.abs().max()) == 0.0
+    # maxit reached
+    P = _pair(lattice_hex_mesh(3, 0.2, 1), 3, 0.0)
+    b = P.to_gpu(P.ref.load(np.ones(P.ref.G)))
+    x, rc, it, hist, tr = P.gpu.solve(b, maxit=3)
+    assert rc == 1 and it == 3 and len(hist) == 4
+    # NaN in the load is reported, not propagated silently
+    bn = b.clone()
+    bn[int(torch.nonzero(P.gpu.mask() == 0)[0])] = float("nan")
+    from paper_1506_05996_gb300.sem import SemError
+    with pytest.raises(SemError):
+        P.gpu.solve(bn)
+    # a mirrored hex (negative Jacobian) is refused
+    from synth import lattice_hex_mesh as lhm
+    m = lhm(2, 0.0, 0)
+    m.hex2vert[0] = m.hex2vert[0][[1, 0, 3, 2, 5, 4, 7, 6]]
+    from paper_1506_05996_gb300.sem import SemProblem
+    with pytest.raises(SemError) as ei:
+        SemProblem(m.xyz, m.hex2vert, 3, 0.0)
+    assert ei.value.code == -2
+
+
+def test_operator_parity_at_full_size():
+    """32^3 hexes, +-20 % (seed 1), n = 7, lambda = 1 (about 11.4 M DOFs): every DOF of
+    A x against the oracle's matrix-free apply, stored and recomputed geometry."""
+    from gpu_util import rel_err, Pair
+    from paper_1506_05996_gb300.sem import SemProblem
+    mesh = lattice_hex_mesh(32, 0.2, 1)
+    P = _pair(mesh, 7, 1.0, geom="stored", coarse=False, schwarz=False)
+    x = np.random.default_rng(2).standard_normal(P.ref.G)
+    y_ref = P.ref.apply_A(x)
+    assert rel_err(P.to_ref(P.gpu.apply_A(P.to_gpu(x))), y_ref) <= TOL
+    xg = P.to_gpu(x)
+    coords = P.gpu.dof_coords().clone()
+    P.gpu.close()
+    rec = SemProblem(mesh.xyz, mesh.hex2vert, 7, 1.0, geom="recompute")
+    assert torch.equal(rec.dof_coords(), coords)      # same numbering in both variants
+    y = rec.apply_A(xg).cpu().numpy()[P.perm]
+    assert rel_err(y, y_ref) <= TOL
