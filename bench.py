@@ -1,0 +1,386 @@
+"""Benchmark: two-scale PCG solve to 1e-8 and the operator apply at n = 7 on GB300.
+
+Workload (the configuration the headline metric is quoted on): 32^3 hexes of the unit
+cube, +-20 % vertex perturbation (seed 1), random renumbering and orientation, order
+n = 7 (11,390,625 DOFs), lambda = 1, manufactured u* = sin(pi x) sin(pi y) sin(pi z),
+homogeneous Dirichlet boundary. A step is one full two-scale PCG solve (Algorithm 1
+with P = P^c + P^f) from u_0 = 0 to ||r|| <= 1e-8 ||b||; value = DOFs solved per
+second (all ranks), ms_per_step = the time-to-1e-8. The operator apply (Ax GDOF/s)
+is measured alongside with stored and recomputed geometric factors.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the CPU oracle on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank solves its own replica (the path does not shard).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Ax GDOF/s & PCG time-to-1e-8 (s) at N=7, % HBM roofline; mixed vs FP64"
+E_FULL, A_FULL, SEED_FULL, ORDER, LAM = 32, 0.2, 1, 7, 1.0
+E_SAMPLE = 8          # CPU-oracle sample: same recipe at 8^3 hexes (185,193 DOFs)
+RTOL = 1e-8
+WORKLOAD = "unit cube 32^3 hexes, +-20% perturbation seed 1, random numbering/orientation, n=7, lambda=1, Dirichlet"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+def _oracle_sample_worker(E, steps, q):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    from synth import lattice_hex_mesh, manufactured_s
+    from oracle.problem import Problem
+    mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
+    pr = Problem(mesh, ORDER, LAM)
+    b = pr.load(manufactured_s(pr.coords, LAM))
+    times, iters = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        u, it, hist = pr.solve(b, rtol=RTOL)
+        times.append(time.perf_counter() - t0)
+        iters.append(int(it))
+    q.put({"G": int(pr.G), "times": times, "iters": iters})
+
+
+def oracle_sample(E, steps):
+    """Runs the oracle in a spawned, single-threaded process (no CUDA state inherited)."""
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_oracle_sample_worker, args=(E, steps, q))
+        p.start()
+        res = q.get()
+        p.join()
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return res
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    res = oracle_sample(E_SAMPLE, W + K)
+    t = res["times"][W:]
+    G = res["G"]
+    per_step = sum(t) / len(t)
+    value = G / per_step / 1e9
+    sample = ("oracle two-scale PCG to 1e-8 on the same recipe at %d^3 hexes (n=7, lambda=1, %d DOFs, "
+              "%d iterations); one full solve per step" % (E_SAMPLE, G, res["iters"][-1]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": K, "warmup": W, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "%d^3 hexes" % E_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def schwarz_flops(n, ne):
+    """Six (n+3)^4 tensor contractions (FMA = 2 flops) plus the paper's 15 (n+3)^3 term."""
+    P = n + 3
+    return ne * (12.0 * P ** 4 + 15.0 * P ** 3)
+
+
+def ax_flops(n, ne):
+    """O_R = N_E [12 (n+1)^4 + 18 (n+1)^3] (Sec. 3.1)."""
+    p = n + 1
+    return ne * (12.0 * p ** 4 + 18.0 * p ** 3)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from synth import lattice_hex_mesh, manufactured_s
+    from paper_1506_05996_gb300 import sem as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fp64_peak_tflops = 1.20   # FP64 FMA loop on this GB300 pool (nominal 1.25 TFLOP/s)
+
+    mesh = lattice_hex_mesh(E_FULL, A_FULL, SEED_FULL)
+    stream = torch.cuda.current_stream()
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored")
+    G, NE = prob.n_dof, mesh.n_hex
+    X = prob.dof_coords()
+    m = prob.mass()
+    # load b = m_N s(x_N) (input preparation, outside the timed region)
+    s_np = manufactured_s(X.cpu().numpy(), LAM)
+    b = (m * torch.as_tensor(s_np, device="cuda")).contiguous()
+    x = torch.empty_like(b)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+
+    def one_solve():
+        rc, it, hist, tr = S.sem_solve(prob.h, b, x, RTOL, 1000, want_history=False)
+        return rc, it, tr
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, L2 flushed between steps (outside the events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    S.sem_profile(prob.h, 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    iters, trs = [], []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        rc, it, tr = one_solve()
+        ev[k][1].record(stream)
+        iters.append(it)
+        trs.append(tr)
+        if rc != 0:
+            raise RuntimeError("solve did not converge: rc=%d" % rc)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    prof = S.sem_profile_read(prob.h)
+    S.sem_profile(prob.h, 0)
+    t_local = sum(a.elapsed_time(bv) for a, bv in ev) / 1e3
+    t_steps = max_over_ranks(t_local)
+    per_step = t_steps / args.steps
+    value = world * G / per_step / 1e9
+    launches = sum(v[0] for v in prof.values())
+
+    # dominant kernel over the timed region and its roofline
+    kern, (nl, tot) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot / nl
+    if kern == "schwarz_local":
+        flops = schwarz_flops(ORDER, NE)
+    elif kern == "ax_local":
+        flops = ax_flops(ORDER, NE)
+    else:
+        flops = None
+    roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
+            "peak_source": "FP64 FMA loop measured on this pool (nominal 1.25 TFLOP/s)",
+            "achieved": (flops / (avg_ms * 1e-3) / 1e12) if flops else None,
+            "avg_launch_ms": avg_ms, "launches": nl, "traffic": None,
+            "share_of_step": tot / (t_local * 1e3)}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] else None
+
+    # ---- operator apply: stored and recomputed geometry (HBM roofline fractions)
+    def time_apply(pr, reps=20):
+        xin = torch.randn(G, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(xin)
+        for _ in range(3):
+            S.sem_apply_A(pr.h, xin, y)
+        S.sem_profile(pr.h, 1)
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.sem_apply_A(pr.h, xin, y)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        pk = S.sem_profile_read(pr.h)
+        S.sem_profile(pr.h, 0)
+        ms = sorted(a.elapsed_time(bv) for a, bv in evs)[reps // 2]
+        kms = pk["ax_local"][1] / pk["ax_local"][0]
+        return ms, kms
+
+    ax = {}
+    p3 = (ORDER + 1) ** 3
+    L = NE * p3
+    for geom, pr in (("stored", prob), ("recompute", None)):
+        if pr is None:
+            pr = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="recompute")
+        ms, kms = time_apply(pr)
+        # algorithmic bytes of one apply: x read, y written (G each), l2g (L int32), stored
+        # factors (7 L f64) or vertex coordinates (24 f64 per element)
+        geo_bytes = 7 * 8 * L if geom == "stored" else 24 * 8 * NE
+        alg_bytes = 16 * G + 4 * L + geo_bytes
+        ax[geom] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
+                    "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
+                    "frac_fp64_peak": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12 / fp64_peak_tflops,
+                    "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                    "frac_hbm_roofline": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        if geom == "recompute":
+            pr.close()
+
+    # ---- end to end through the public API with host buffers
+    b_host = b.cpu().pin_memory()
+    x_host = torch.empty(G, dtype=torch.float64).pin_memory()
+    n_e2e = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        b_dev = b_host.to("cuda", non_blocking=True)
+        rc, it, hist, tr = S.sem_solve(prob.h, b_dev, x, RTOL, 1000, want_history=False)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    t_e2e = max_over_ranks(t_e2e)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        res = oracle_sample(E_SAMPLE, 3)
+        tc = sum(res["times"]) / len(res["times"])
+        cpu = {"value": res["G"] / tc / 1e9, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": ("oracle two-scale PCG to 1e-8, same recipe at %d^3 hexes (%d DOFs, %d iterations), "
+                          "mean of 3 solves, single thread" % (E_SAMPLE, res["G"], res["iters"][-1])),
+               "cpu": cpu_model(), "host_cores_available": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dof": G, "n_hex": NE, "order": ORDER, "lambda": LAM,
+                       "rtol": RTOL, "preconditioner": "two-scale (P^c + P^f)", "geometry": "stored",
+                       "l2": "inputs larger than L2 (0.94 GB stored factors) and a 512 MB flush between steps",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "time_to_1e-8_s": per_step, "iterations": iters[-1], "true_rel_res": trs[-1],
+            "wall_s": t_wall,
+            "ax": ax,
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "roofline": roof,
+            "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,
+                    "d2h_bytes_per_step": 8 * G, "s_per_step": t_e2e},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,22 @@ int sem_set_precond(sem_t* h, int which);
 int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit,
               int* iters_host, double* res_hist_host, double* true_rel_res_host);
 
+/*
+ * sem_profile / sem_profile_read - per-kernel timing of the library's own launches.
+ * While enabled, a CUDA event pair is recorded on the handle's stream around each
+ * kernel launch (or launch group: "coarse_amg" is the whole AMG V-cycle sequence),
+ * and the elapsed times are summed per kernel name when the stream is synchronised.
+ * sem_profile(h, 1) resets the counters and enables; sem_profile(h, 0) disables.
+ * sem_profile_read fills up to max_kernels entries: names_host (64 bytes each, NUL
+ * terminated), launches_host (kernels launched under that name) and total_ms_host
+ * (any may be NULL) and sets
+ * *n_kernels_host to the number of distinct kernels seen. Synchronises the stream.
+ * (Not in the paper: the tracing the paper's GFLOP/s and GB/s tables rest on.)
+ */
+int sem_profile(sem_t* h, int enable);
+int sem_profile_read(sem_t* h, int max_kernels, char* names_host, int64_t* launches_host,
+                     double* total_ms_host, int* n_kernels_host);
+
 /* sem_last_error - message for the last error raised on this thread ("" if none). */
 const char* sem_last_error(void);
 

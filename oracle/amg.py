@@ -14,14 +14,17 @@ library (each written independently from this description):
   * the prolongator is smoothed: P = (I - w_P D^{-1} A) T with
     w_P = (4/3) / max_i (sum_j |a_ij| / a_ii) (a Gershgorin bound, so both sides
     get the same weight in closed form); the coarse matrix is P^T A P;
-  * levels are added while the matrix has more than 512 unknowns and coarsens;
-    the coarsest level is solved with a dense inverse (Cholesky);
+  * levels are added while the matrix has more than 2048 unknowns and a level
+    shrinks the count to at most 3/4; the coarsest level is solved with a dense
+    inverse (Cholesky), up to 4096 unknowns;
   * one cycle is a symmetric V(1,1): x = w D^{-1} b; x += P cycle(P^T (b - A x));
     x += w D^{-1} (b - A x); w = 2/3. P_0 applies three such cycles as a
     stationary iteration from x = 0, so P_0 is a fixed linear SPD operator and
     plain PCG applies (the paper's K-cycle is nonlinear).
 Unsmoothed aggregation with a single V-cycle was tried first: it contracts the
 coarse error by only ~0.8 per cycle and nearly doubles the PCG iteration counts.
+Below ~2000 unknowns the smoothed Galerkin products become nearly dense and the
+pairwise passes stop coarsening, so the hierarchy ends there with a dense solve.
 Parity unpinned: no value in the paper fixes this rule; the tests pin the dense
 coarsest solve, symmetry and positivity of P_0 and its A-norm contraction.
 """
@@ -31,7 +34,9 @@ from scipy.sparse import csr_matrix, diags
 OMEGA = 2.0 / 3.0
 BETA = 0.25
 TIE = 1e-10
-MAX_COARSEST = 512
+MAX_COARSEST = 2048
+MAX_DENSE = 4096
+STALL = 0.75
 PASSES = 3
 N_CYCLES = 3
 
@@ -88,7 +93,7 @@ class AMG:
                 T1 = aggregation_matrix(a, na)
                 Ac = (T1.T @ Ac @ T1).tocsr()
             nc = Ac.shape[0]
-            if nc >= A.shape[0]:
+            if nc > STALL * A.shape[0]:
                 break
             T = aggregation_matrix(agg, nc)
             d = A.diagonal()
@@ -98,7 +103,7 @@ class AMG:
             P.eliminate_zeros()
             self.levels.append((A, 1.0 / d, P))
             A = (P.T @ A @ P).tocsr()
-        if A.shape[0] > 4096:
+        if A.shape[0] > MAX_DENSE:
             raise ValueError("coarsening stalled above the dense limit")
         L = np.linalg.cholesky(A.toarray())           # raises if not SPD
         Linv = np.linalg.inv(L)

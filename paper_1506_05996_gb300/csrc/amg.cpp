@@ -10,12 +10,14 @@
 //  * three pairwise passes per level (each on the Galerkin product of the last)
 //    give tentative aggregates T of up to 8 unknowns;
 //  * P = (I - w_P D^{-1} A) T, w_P = (4/3) / max_i(sum_j |a_ij| / a_ii); A_c = P^T A P;
-//  * levels are added while a level has more than 512 unknowns and coarsens; the
-//    coarsest is inverted densely (Cholesky).
+//  * levels are added while a level has more than 2048 unknowns and the passes
+//    shrink it to at most 3/4; the coarsest (at most 4096 unknowns) is inverted
+//    densely (Cholesky).
 // The cycle applied on the GPU is a symmetric V(1,1) with Jacobi weight 2/3,
 // repeated three times as a stationary iteration.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 #include "host_setup.h"
 
@@ -23,7 +25,8 @@ namespace sem {
 namespace {
 
 const double kBeta = 0.25, kTie = 1e-10;
-const int kMaxCoarsest = 512, kPasses = 3, kDenseLimit = 4096;
+const int kMaxCoarsest = 2048, kPasses = 3, kDenseLimit = 4096;
+const double kStall = 0.75;
 
 std::vector<int> pairwise(const Csr& A, int& na) {
   std::vector<int> agg(A.n, -1);
@@ -107,6 +110,19 @@ Csr aggregation_matrix(const std::vector<int>& agg, int na) {
   return T;
 }
 
+// Runs f(i) for i in [0, n) on the host cores; each i is done by exactly one thread.
+template <class F>
+void parallel_for(int n, F f) {
+  int nt = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 64) nt = 1;
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([=, &f] {
+      for (int i = t; i < n; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
 }  // namespace
 
 std::string build_amg(const Csr& A0, Amg& out) {
@@ -125,7 +141,7 @@ std::string build_amg(const Csr& A0, Amg& out) {
       Ac = spgemm(transpose(T1), spgemm(Ac, T1));
       nc = na;
     }
-    if (nc >= A.n) break;
+    if (nc > kStall * A.n) break;
     Csr T = aggregation_matrix(agg, nc);
     std::vector<double> d(A.n, 0.0);
     double gersh = 0.0;
@@ -187,21 +203,28 @@ std::string build_amg(const Csr& A0, Amg& out) {
       L[(size_t)i * n + j] = t / ljj;
     }
   }
-  for (int j = 0; j < n; ++j) {   // columns of L^{-1} by forward substitution
+  // row j of LiT = column j of L^{-1} (forward substitution, contiguous loops)
+  std::vector<double>& LiT = Li;
+  parallel_for(n, [&](int j) {
+    double* y = &LiT[(size_t)j * n];
     for (int i = j; i < n; ++i) {
+      const double* Lr = &L[(size_t)i * n];
       double s = (i == j) ? 1.0 : 0.0;
-      for (int k = j; k < i; ++k) s -= L[(size_t)i * n + k] * Li[(size_t)k * n + j];
-      Li[(size_t)i * n + j] = s / L[(size_t)i * n + i];
+      for (int k = j; k < i; ++k) s -= Lr[k] * y[k];
+      y[i] = s / Lr[i];
     }
-  }
+  });
   out.coarsest_n = n;
   out.coarsest_inv.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i)
+  parallel_for(n, [&](int i) {   // inv = L^{-T} L^{-1}: (i, j) = sum_k LiT[i][k] LiT[j][k]
+    const double* a = &LiT[(size_t)i * n];
     for (int j = 0; j < n; ++j) {
+      const double* b = &LiT[(size_t)j * n];
       double s = 0.0;
-      for (int k = std::max(i, j); k < n; ++k) s += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      for (int k = std::max(i, j); k < n; ++k) s += a[k] * b[k];
       out.coarsest_inv[(size_t)i * n + j] = s;
     }
+  });
   return "";
 }
 

@@ -28,7 +28,81 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+// Per-kernel timing with CUDA events recorded on the handle's stream around each
+// launch (enabled by sem_profile); accumulated when the stream is synchronised.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> pending;   // (kernel id, first event index)
+  std::vector<uint64_t> pending_kernels;      // kernels launched inside each pending pair
+  uint64_t count_at_begin = 0;
+  int next = 0;
+  std::vector<std::string> names;
+  std::vector<double> total_ms;
+  std::vector<int64_t> launches;
+
+  int id(const char* name) {
+    for (size_t i = 0; i < names.size(); ++i)
+      if (names[i] == name) return (int)i;
+    names.emplace_back(name);
+    total_ms.push_back(0.0);
+    launches.push_back(0);
+    return (int)names.size() - 1;
+  }
+  int begin(cudaStream_t s) {
+    if (!on) return -1;
+    while ((int)pool.size() < next + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool.push_back(e);
+    }
+    int i = next;
+    next += 2;
+    cudaEventRecord(pool[i], s);
+    count_at_begin = sem::kernel_launch_count();
+    return i;
+  }
+  void end(int i, const char* name, cudaStream_t s) {
+    if (i < 0) return;
+    cudaEventRecord(pool[i + 1], s);
+    pending.emplace_back(id(name), i);
+    pending_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
+  }
+  void collect() {   // stream must be synchronised
+    for (size_t q = 0; q < pending.size(); ++q) {
+      const auto& pr = pending[q];
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pool[pr.second], pool[pr.second + 1]) == cudaSuccess) {
+        total_ms[pr.first] += ms;
+        launches[pr.first] += (int64_t)pending_kernels[q];
+      }
+    }
+    pending.clear();
+    pending_kernels.clear();
+    next = 0;
+  }
+  void reset() {
+    pending.clear();
+    pending_kernels.clear();
+    next = 0;
+    names.clear();
+    total_ms.clear();
+    launches.clear();
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+#define PROF(h, name, call)                           \
+  do {                                                \
+    int pi_ = (h)->prof.begin((h)->stream);           \
+    CK(call);                                         \
+    (h)->prof.end(pi_, name, (h)->stream);            \
+  } while (0)
+
 struct sem_s {
+  Profiler prof;
   sem::DevProblem d;
   cudaStream_t stream = nullptr;
   int flags = 0;
@@ -162,18 +236,18 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   const sem::PcgState* st = pcg ? d.st : nullptr;
   int mode = 0;
   if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
-    CK(sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
+    PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
     mode |= sem::PSUM_FINE;
   }
   if (which == SEM_PRECOND_TWO_SCALE || which == -1) {
     if (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty()))
       return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
-    CK(sem::launch_coarse_restrict(d, r, st, h->stream));
-    CK(sem::launch_coarse_solve(d, st, h->stream));
+    PROF(h, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, h->stream));
+    PROF(h, "coarse_amg", sem::launch_coarse_solve(d, st, h->stream));
     mode |= sem::PSUM_COARSE;
   }
   if (which == SEM_PRECOND_NONE) mode = sem::PSUM_IDENT;
-  CK(sem::launch_psum(d, mode, r, z, pcg, h->stream));
+  PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg, h->stream));
   return SEM_OK;
 }
 
@@ -208,6 +282,33 @@ int sem_create(const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2v
     return rc;
   }
   *out = h;
+  return SEM_OK;
+}
+
+int sem_profile(sem_t* h, int enable) {
+  if (int rc = check_handle(h)) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  h->prof.reset();
+  h->prof.on = enable != 0;
+  return SEM_OK;
+}
+
+int sem_profile_read(sem_t* h, int max_kernels, char* names_host, int64_t* launches_host, double* total_ms_host,
+                     int* n_kernels_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_kernels_host == nullptr || max_kernels < 0) return fail(SEM_ERR_ARG, "bad profile arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  h->prof.collect();
+  const int nk = (int)h->prof.names.size();
+  *n_kernels_host = nk;
+  for (int i = 0; i < nk && i < max_kernels; ++i) {
+    if (names_host) {
+      std::strncpy(names_host + 64 * i, h->prof.names[i].c_str(), 63);
+      names_host[64 * i + 63] = 0;
+    }
+    if (launches_host) launches_host[i] = h->prof.launches[i];
+    if (total_ms_host) total_ms_host[i] = h->prof.total_ms[i];
+  }
   return SEM_OK;
 }
 
@@ -247,6 +348,16 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   for (int64_t e = 0; e < nb.ne; ++e)
     for (int c = 0; c < 8; ++c)
       for (int a = 0; a < 3; ++a) exyz[24 * e + 3 * c + a] = vert_xyz_host[3 * nb.hexv[8 * e + c] + a];
+  // Vandermonde B_{IJK,ijk} = Phi_I(t_i) Phi_J(t_j) Phi_K(t_k) (Sec. 4.1), node-major
+  std::vector<double> Btab(8 * p3);
+  for (int k = 0; k < p; ++k)
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i)
+        for (int c = 0; c < 8; ++c) {
+          auto phi = [](int bit, double x) { return bit ? 0.5 * (1.0 + x) : 0.5 * (1.0 - x); };
+          Btab[8 * (i + p * (j + p * k)) + c] = phi(sem::kCornerBits[c][0], t[i]) * phi(sem::kCornerBits[c][1], t[j]) *
+                                                 phi(sem::kCornerBits[c][2], t[k]);
+        }
   h->mask_host.assign(nb.G, 0);
   if (!(flags & SEM_NEUMANN)) h->mask_host = nb.boundary;
 
@@ -271,6 +382,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   UP(S, S, double);
   UP(ev, ev, double);
   UP(hbox, hbox, double);
+  UP(Btab, Btab, double);
 #undef UP
   CK(h->upload(&h->coords, coords, A));
   CK(h->upload(&h->mask, h->mask_host, A));
@@ -378,8 +490,8 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
 int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
   if (int rc = check_handle(h)) return rc;
   if (x_dev == nullptr || y_dev == nullptr || x_dev == y_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
-  CK(sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
-  CK(sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
+  PROF(h, "ax_local", sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
+  PROF(h, "gather", sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
   return SEM_OK;
 }
 
@@ -420,27 +532,28 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   cudaStream_t s = h->stream;
   double* u = x_dev;
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
-  CK(sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, h->hist, s));
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
-  CK(sem::launch_pcg_first_direction(d, h->z, h->p, s));
-  const int chunk = 4;
+  PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
+  const int chunk = 1;   // iterations between host checks of the device-side stop flag
   for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
     for (int c = 0; c < chunk; ++c) {
-      CK(sem::launch_ax_local(d, h->p, d.wl, d.st, s));
-      CK(sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
-      CK(sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
+      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
+      PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
+      PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
       if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
-      CK(sem::launch_pcg_direction(d, h->z, h->p, s));
+      PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, s));
     }
     CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->st_host->done) break;
   }
   // true residual ||b - A u|| / ||b|| on the free nodes
-  CK(sem::launch_ax_local(d, u, d.wl, nullptr, s));
-  CK(sem::launch_true_residual(d, b_dev, d.wl, s));
+  PROF(h, "ax_local", sem::launch_ax_local(d, u, d.wl, nullptr, s));
+  PROF(h, "true_residual", sem::launch_true_residual(d, b_dev, d.wl, s));
   CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  h->prof.collect();
   const sem::PcgState& st = *h->st_host;
   if (iters_host) *iters_host = st.iter;
   if (res_hist_host) {

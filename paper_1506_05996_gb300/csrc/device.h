@@ -68,6 +68,7 @@ struct DevProblem {
   const double* S = nullptr;        // P*P, S[row*P + mode]
   const double* ev = nullptr;       // P
   const double* hbox = nullptr;     // ne*3
+  const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const int* ecv = nullptr;
   const int* cv_off = nullptr;
   const int* cv_idx = nullptr;
@@ -90,6 +91,9 @@ struct DevProblem {
   int nblk = 0;                     // blocks of the vector kernels
   PcgState* st = nullptr;
 };
+
+// Number of kernels this thread has launched through the launchers below.
+uint64_t kernel_launch_count();
 
 // --- geometry set-up ---------------------------------------------------------
 // Computes m_loc (ne*p^3) and, if geo != nullptr, the stored factors; sets *bad = 1

@@ -16,6 +16,10 @@
 #include "device.h"
 
 namespace sem {
+
+static thread_local uint64_t g_kernel_launches = 0;
+uint64_t kernel_launch_count() { return g_kernel_launches; }
+
 namespace {
 
 __device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
@@ -291,19 +295,9 @@ __global__ void __launch_bounds__(kRestrictBlock) coarse_restrict_kernel(const D
     const int g = d.l2g[gl];
     if (d.owner[g] != gl || d.mask[g]) continue;
     const double v = r[g];
-    const int i = l % p, j = (l / p) % p, k = l / (p * p);
-    const double ti = d.tg[i], tj = d.tg[j], tk = d.tg[k];
-    const double fx[2] = {0.5 * (1.0 - ti), 0.5 * (1.0 + ti)};
-    const double fy[2] = {0.5 * (1.0 - tj), 0.5 * (1.0 + tj)};
-    const double fz[2] = {0.5 * (1.0 - tk), 0.5 * (1.0 + tk)};
-    acc[0] += v * (fx[0] * fy[0] * fz[0]);
-    acc[1] += v * (fx[1] * fy[0] * fz[0]);
-    acc[2] += v * (fx[1] * fy[1] * fz[0]);
-    acc[3] += v * (fx[0] * fy[1] * fz[0]);
-    acc[4] += v * (fx[0] * fy[0] * fz[1]);
-    acc[5] += v * (fx[1] * fy[0] * fz[1]);
-    acc[6] += v * (fx[1] * fy[1] * fz[1]);
-    acc[7] += v * (fx[0] * fy[1] * fz[1]);
+    const double* B = d.Btab + 8 * l;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] += v * B[c];
   }
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -321,39 +315,49 @@ __global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
   }
 }
 
-// AMG kernels, one thread per row.
+// AMG kernels. Sparse rows are handled by one warp each (lanes stride over the
+// row, then a fixed shuffle tree), so long coarse-level rows do not serialise.
 __global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const double* __restrict__ b,
                                    double* __restrict__ x, double omega, const PcgState* st) {
   if (stopped(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = omega * dinv[i] * b[i];
 }
 
+__device__ __forceinline__ double warp_row_dot(const DevCsr& A, int row, const double* __restrict__ x, int lane) {
+  double s = 0.0;
+  for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += 32) s += A.val[q] * x[A.col[q]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+#define WARP_ROWS(nrows)                                                              \
+  const int lane = threadIdx.x & 31;                                                  \
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (nrows); i += (gridDim.x * blockDim.x) >> 5)
+
 __global__ void amg_resid_kernel(DevCsr A, const double* __restrict__ b, const double* __restrict__ x,
                                  double* __restrict__ t, const PcgState* st) {
   if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
-    t[i] = b[i] - s;
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) t[i] = b[i] - s;
   }
 }
 
 __global__ void amg_spmv_kernel(DevCsr A, const double* __restrict__ x, double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
-    y[i] = s;
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) y[i] = s;
   }
 }
 
 __global__ void amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc, double* __restrict__ x,
                                        const PcgState* st) {
   if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = P.ptr[i]; q < P.ptr[i + 1]; ++q) s += P.val[q] * xc[P.col[q]];
-    x[i] = x[i] + s;
+  WARP_ROWS(P.n) {
+    const double s = warp_row_dot(P, i, xc, lane);
+    if (lane == 0) x[i] = x[i] + s;
   }
 }
 
@@ -361,12 +365,12 @@ __global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv
                                        const double* __restrict__ x, double* __restrict__ xout, double omega,
                                        const PcgState* st) {
   if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
-    xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
   }
 }
+#undef WARP_ROWS
 
 __global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
@@ -402,14 +406,8 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
         for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += d.wp[d.pg_idx[q]];
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
         const int l = d.owner[g], e = l / p3, lr = l % p3;
-        const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
-        const double ti = d.tg[i], tj = d.tg[j], tk = d.tg[k];
-        const double fx[2] = {0.5 * (1.0 - ti), 0.5 * (1.0 + ti)};
-        const double fy[2] = {0.5 * (1.0 - tj), 0.5 * (1.0 + tj)};
-        const double fz[2] = {0.5 * (1.0 - tk), 0.5 * (1.0 + tk)};
         const int* ec = d.ecv + (size_t)e * 8;
-        const double B[8] = {fx[0] * fy[0] * fz[0], fx[1] * fy[0] * fz[0], fx[1] * fy[1] * fz[0], fx[0] * fy[1] * fz[0],
-                             fx[0] * fy[0] * fz[1], fx[1] * fy[0] * fz[1], fx[1] * fy[1] * fz[1], fx[0] * fy[1] * fz[1]};
+        const double* B = d.Btab + 8 * lr;
         double zc = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -543,20 +541,26 @@ constexpr int kCycles = 3;
 cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
     dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    ++g_kernel_launches;
     return cudaGetLastError();
   }
   const DevAmgLevel& L = d.levels[level];
-  const int n = L.A.n, gb = grid_for(n, 256, 4096);
+  const int n = L.A.n, gb = grid_for(n, 256, 4096), gw = grid_for(32 * n, 256, 8192);
   amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
-  amg_resid_kernel<<<gb, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  ++g_kernel_launches;
+  amg_resid_kernel<<<gw, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  ++g_kernel_launches;
   double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
   double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
   const int nc = L.R.n;
-  amg_spmv_kernel<<<grid_for(nc, 256, 4096), 256, 0, s>>>(L.R, L.t, bc, st);
+  amg_spmv_kernel<<<grid_for(32 * nc, 256, 8192), 256, 0, s>>>(L.R, L.t, bc, st);
+  ++g_kernel_launches;
   cudaError_t err = vcycle(d, level + 1, bc, xc, st, s);
   if (err != cudaSuccess) return err;
-  amg_prolong_add_kernel<<<gb, 256, 0, s>>>(L.P, xc, L.x, st);
-  amg_jacobi_post_kernel<<<gb, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  amg_prolong_add_kernel<<<gw, 256, 0, s>>>(L.P, xc, L.x, st);
+  ++g_kernel_launches;
+  amg_jacobi_post_kernel<<<gw, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -565,7 +569,7 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
 // ================================================================ launchers
 cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, int* bad, cudaStream_t s) {
   switch (d.p) {
-#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, mloc, bad); break;
+#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, mloc, bad); ++g_kernel_launches; break;
     GEO_CASE(2) GEO_CASE(3) GEO_CASE(4) GEO_CASE(5) GEO_CASE(6) GEO_CASE(7) GEO_CASE(8) GEO_CASE(9)
 #undef GEO_CASE
     default: return cudaErrorInvalidValue;
@@ -579,6 +583,7 @@ cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, co
   case P_:                                                                                 \
     if (d.recompute) ax_local_kernel<P_, true><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);  \
     else ax_local_kernel<P_, false><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);             \
+    ++g_kernel_launches;                                                                   \
     break;
     AX_CASE(2) AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
 #undef AX_CASE
@@ -589,17 +594,19 @@ cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, co
 
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
   gather_identity_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y, cudaStream_t s) {
   gather_plain_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, y);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
   switch (d.P) {
-#define SW_CASE(P_) case P_: schwarz_local_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); break;
+#define SW_CASE(P_) case P_: schwarz_local_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
     SW_CASE(4) SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
 #undef SW_CASE
     default: return cudaErrorInvalidValue;
@@ -610,7 +617,9 @@ cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* w
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
   coarse_restrict_kernel<<<d.ne, kRestrictBlock, 0, s>>>(d, r, st);
+  ++g_kernel_launches;
   vertex_gather_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d, st);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
@@ -620,12 +629,14 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   cudaError_t err = vcycle(d, 0, d.Rc, d.Zc, st, s);
   if (err != cudaSuccess || d.nlevels == 0) return err;
   const DevCsr& A0 = d.levels[0].A;
-  const int gb = grid_for(A0.n, 256, 4096);
+  const int gb = grid_for(A0.n, 256, 4096), gw = grid_for(32 * A0.n, 256, 8192);
   for (int c = 1; c < kCycles; ++c) {
-    amg_resid_kernel<<<gb, 256, 0, s>>>(A0, d.Rc, d.Zc, d.cres, st);
+    amg_resid_kernel<<<gw, 256, 0, s>>>(A0, d.Rc, d.Zc, d.cres, st);
+    ++g_kernel_launches;
     err = vcycle(d, 0, d.cres, d.ctmp, st, s);
     if (err != cudaSuccess) return err;
     add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
+    ++g_kernel_launches;
   }
   return cudaGetLastError();
 }
@@ -633,38 +644,45 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
   if (pcg) psum_kernel<true><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
   else psum_kernel<false><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
                             double* hist, cudaStream_t s) {
   pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, hist);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
   pcg_copy_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s) {
   pcg_gather_alpha_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double* f, double* u, double* r, double* hist,
                               cudaStream_t s) {
   pcg_update_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f, u, r, hist);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
   pcg_direction_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s) {
   true_residual_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, wl);
+  ++g_kernel_launches;
   return cudaGetLastError();
 }
 

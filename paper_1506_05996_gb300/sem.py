@@ -44,6 +44,8 @@ _SIGS = {
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
     "sem_set_precond": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
+    "sem_profile": ([_vp, _int], _int),
+    "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
     "sem_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -167,6 +169,25 @@ def sem_solve(h, b, x, rtol=1e-8, maxit=1000, want_history=True):
     if want_history:
         hist = hist[:it.value + 1].copy()
     return rc, it.value, hist, tr.value
+
+
+def sem_profile(h, enable):
+    return _check(_lib.sem_profile(h, int(bool(enable))))
+
+
+def sem_profile_read(h, max_kernels=64):
+    """Returns {kernel name: (launches, total milliseconds)}."""
+    names = ctypes.create_string_buffer(64 * max_kernels)
+    launches = np.zeros(max_kernels, dtype=np.int64)
+    total = np.zeros(max_kernels)
+    nk = ctypes.c_int()
+    _check(_lib.sem_profile_read(h, max_kernels, ctypes.cast(names, ctypes.c_void_p), launches.ctypes.data,
+                                 total.ctypes.data, ctypes.byref(nk)))
+    out = {}
+    for i in range(min(nk.value, max_kernels)):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(total[i]))
+    return out
 
 
 class SemProblem:

@@ -17,7 +17,7 @@ def load():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(s) for s in SRC + [
             os.path.join(ROOT, "paper_1506_05996_gb300", "csrc", "host_setup.h")]):
-        subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", OUT] + SRC, check=True)
+        subprocess.run(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", "-o", OUT] + SRC, check=True)
     lib = ctypes.CDLL(OUT)
     lib.hh_G.restype = ctypes.c_int64
     return lib

@@ -77,7 +77,7 @@ def test_amg_small_is_exact_and_large_is_spd_contraction():
     assert H.sizes() == [small.A0.shape[0]]
     b = np.random.default_rng(3).standard_normal(small.A0.shape[0])
     np.testing.assert_allclose(small.A0 @ H.apply(b), b, atol=1e-12)
-    big = Problem(lattice_hex_mesh(12, 0.2, 1), 1, 1.0, with_schwarz=False)
+    big = Problem(lattice_hex_mesh(16, 0.2, 1), 1, 1.0, with_schwarz=False)
     H = big.amg
     assert len(H.sizes()) >= 2
     A0 = big.A0
