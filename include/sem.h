@@ -148,6 +148,43 @@ int sem_profile(sem_t* h, int enable);
 int sem_profile_read(sem_t* h, int max_kernels, char* names_host, int64_t* launches_host,
                      double* total_ms_host, int* n_kernels_host);
 
+/*
+ * sem_apply_A_noalloc - y = A_D x without any device allocation.
+ * For callers that cannot call cudaMalloc: code running while a stream is being
+ * captured into a CUDA graph (allocation is not allowed there), components whose
+ * device memory is owned and handed out by a host framework, or loops where an
+ * allocator call is not permitted. The caller passes every input and output; the
+ * only scratch (one FP64 value per local GLL node, written by the element kernel and
+ * summed by the gather kernel) is a file-scope static device array of
+ * SEM_NOALLOC_MAX_LOCAL_NODES doubles (16 MiB), held by every GPU that loads the
+ * library until the process exits. It calls no cudaMalloc, cudaFree or allocating
+ * library routine. The paper has no counterpart; it is the operator of Eq. R with
+ * the geometric factors recomputed from the vertices.
+ *   order          2..8.  n_hex, n_dof: sizes; n_hex*(order+1)^3 must not exceed
+ *                  SEM_NOALLOC_MAX_LOCAL_NODES, else SEM_ERR_ARG.
+ *   lambda         screening coefficient >= 0.
+ *   elem_xyz_dev   [n_hex][8][3] vertex coordinates of each hex, VTK corner order.
+ *   l2g_dev        int32 [n_hex*(order+1)^3]: global DOF of local node i + p(j + p k).
+ *   g2l_off_dev    int32 [n_dof+1], g2l_idx_dev int32 [n_hex*(order+1)^3]: for each DOF
+ *                  the local nodes (element*(order+1)^3 + local) that share it.
+ *   mask_dev       uint8 [n_dof], 1 = Dirichlet (y = x there), 0 = free.
+ *   x_dev, y_dev   n_dof doubles each, must not alias.
+ *   cuda_stream    stream to enqueue on (NULL = legacy default stream).
+ * The first call on each device, with that device current, resolves the static
+ * arrays' device addresses and copies the GLL tables there (a synchronous copy);
+ * make that first call before any stream capture. Every call on a device shares
+ * the one scratch array, which keeps the last call's contents (nothing in it needs
+ * to start at zero: every entry is written before it is read), so calls that
+ * overlap on the GPU (other streams, other threads) race and must be serialised by
+ * the caller. Errors: SEM_ERR_ARG, SEM_ERR_CUDA (message in sem_last_error).
+ */
+#define SEM_NOALLOC_MAX_LOCAL_NODES 2097152
+int sem_apply_A_noalloc(int order, int64_t n_hex, int64_t n_dof, double lambda,
+                        const double* elem_xyz_dev, const int32_t* l2g_dev,
+                        const int32_t* g2l_off_dev, const int32_t* g2l_idx_dev,
+                        const uint8_t* mask_dev, const double* x_dev, double* y_dev,
+                        void* cuda_stream);
+
 /* sem_last_error - message for the last error raised on this thread ("" if none). */
 const char* sem_last_error(void);
 

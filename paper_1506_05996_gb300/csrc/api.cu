@@ -256,6 +256,8 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
 static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2vert_host,
                        int64_t n_hex, int order, double lambda, int flags);
 
+int sem::report_error(int code, const std::string& msg) { return fail(code, msg); }
+
 extern "C" {
 
 const char* sem_last_error(void) { return g_err.c_str(); }

@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
 
 namespace sem {
 
@@ -91,6 +92,9 @@ struct DevProblem {
   int nblk = 0;                     // blocks of the vector kernels
   PcgState* st = nullptr;
 };
+
+// Records msg as this thread's sem_last_error() text and returns code (api.cu).
+int report_error(int code, const std::string& msg);
 
 // Number of kernels this thread has launched through the launchers below.
 uint64_t kernel_launch_count();

@@ -44,6 +44,7 @@ _SIGS = {
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
     "sem_set_precond": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
+    "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
     "sem_profile": ([_vp, _int], _int),
     "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
     "sem_last_error": ([], ctypes.c_char_p),
@@ -169,6 +170,16 @@ def sem_solve(h, b, x, rtol=1e-8, maxit=1000, want_history=True):
     if want_history:
         hist = hist[:it.value + 1].copy()
     return rc, it.value, hist, tr.value
+
+
+def sem_apply_A_noalloc(order, n_hex, n_dof, lam, elem_xyz, l2g, g2l_off, g2l_idx, mask, x, y, stream=None):
+    """y = A_D x with caller-owned tables and a static scratch array (no device allocation)."""
+    p3 = (order + 1) ** 3
+    args = [_dev(elem_xyz, torch.float64, 24 * n_hex), _dev(l2g, torch.int32, n_hex * p3),
+            _dev(g2l_off, torch.int32, n_dof + 1), _dev(g2l_idx, torch.int32, n_hex * p3),
+            _dev(mask, torch.uint8, n_dof), _dev(x, torch.float64, n_dof), _dev(y, torch.float64, n_dof)]
+    return _check(_lib.sem_apply_A_noalloc(int(order), int(n_hex), int(n_dof), float(lam), *args,
+                                           _stream_ptr(stream)))
 
 
 def sem_profile(h, enable):

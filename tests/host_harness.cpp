@@ -39,6 +39,10 @@ int hh_setup(const double* xyz, int64_t nv, const int64_t* hex, int64_t ne, int 
 }
 
 int64_t hh_G() { return g_nb.G; }
+void hh_g2l(int* off, int* idx) {
+  std::memcpy(off, g_off.data(), g_off.size() * sizeof(int));
+  std::memcpy(idx, g_idx.data(), g_idx.size() * sizeof(int));
+}
 void hh_l2g(int* out) { std::memcpy(out, g_nb.l2g.data(), g_nb.l2g.size() * sizeof(int)); }
 void hh_elem_perm(int64_t* out) { std::memcpy(out, g_nb.elem_perm.data(), g_nb.elem_perm.size() * sizeof(int64_t)); }
 void hh_coords(double* out) { std::memcpy(out, g_coords.data(), g_coords.size() * sizeof(double)); }

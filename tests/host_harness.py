@@ -38,6 +38,9 @@ class HostTables:
         vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         self.l2g = np.zeros(ne * p ** 3, dtype=np.int32); lib.hh_l2g(vp(self.l2g))
         self.elem_perm = np.zeros(ne, dtype=np.int64); lib.hh_elem_perm(vp(self.elem_perm))
+        self.g2l_off = np.zeros(self.G + 1, dtype=np.int32)
+        self.g2l_idx = np.zeros(ne * p ** 3, dtype=np.int32)
+        lib.hh_g2l(vp(self.g2l_off), vp(self.g2l_idx))
         self.coords = np.zeros(3 * self.G); lib.hh_coords(vp(self.coords))
         self.coords = self.coords.reshape(-1, 3)
         self.boundary = np.zeros(self.G, dtype=np.uint8); lib.hh_boundary(vp(self.boundary))
