@@ -220,7 +220,7 @@ def run_gpu(args):
 
     mesh = lattice_hex_mesh(E_FULL, A_FULL, SEED_FULL)
     stream = torch.cuda.current_stream()
-    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored")
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
     G, NE = prob.n_dof, mesh.n_hex
     X = prob.dof_coords()
     m = prob.mass()
@@ -285,7 +285,8 @@ def run_gpu(args):
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] else None
 
     # ---- operator apply: stored and recomputed geometry (HBM roofline fractions)
-    def time_apply(pr, reps=20):
+    def time_apply(pr, reps=20, prec="fp64"):
+        pr.set_precision(prec)
         xin = torch.randn(G, dtype=torch.float64, device="cuda")
         y = torch.empty_like(xin)
         for _ in range(3):
@@ -304,26 +305,59 @@ def run_gpu(args):
         S.sem_profile(pr.h, 0)
         ms = sorted(a.elapsed_time(bv) for a, bv in evs)[reps // 2]
         kms = pk["ax_local"][1] / pk["ax_local"][0]
+        pr.set_precision("fp64")
         return ms, kms
 
     ax = {}
     p3 = (ORDER + 1) ** 3
     L = NE * p3
-    for geom, pr in (("stored", prob), ("recompute", None)):
-        if pr is None:
-            pr = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="recompute")
-        ms, kms = time_apply(pr)
-        # algorithmic bytes of one apply: x read, y written (G each), l2g (L int32), stored
-        # factors (7 L f64) or vertex coordinates (24 f64 per element)
-        geo_bytes = 7 * 8 * L if geom == "stored" else 24 * 8 * NE
+    rec = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="recompute")
+    for geom, prec, pr in (("stored", "fp64", prob), ("recompute", "fp64", rec),
+                           ("stored", "fp32", prob), ("recompute", "fp32", rec)):
+        ms, kms = time_apply(pr, prec=prec)
+        # algorithmic bytes of one apply: x read and y written (FP64, G each), l2g (int32 per
+        # local node), stored factors (7 per local node, FP64 or FP32) or the 24 vertex
+        # coordinates of each element
+        fb = 8 if prec == "fp64" else 4
+        geo_bytes = 7 * fb * L if geom == "stored" else 24 * 8 * NE
         alg_bytes = 16 * G + 4 * L + geo_bytes
-        ax[geom] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
-                    "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
-                    "frac_fp64_peak": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12 / fp64_peak_tflops,
-                    "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
-                    "frac_hbm_roofline": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak}
-        if geom == "recompute":
-            pr.close()
+        key = geom + ("" if prec == "fp64" else "_fp32")
+        ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
+                   "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
+                   "bytes_per_dof": alg_bytes / G,
+                   "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                   "frac_hbm_roofline": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak}
+        if prec == "fp64":
+            ax[key]["frac_fp64_peak"] = ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12 / fp64_peak_tflops
+    rec.close()
+
+    # ---- mixed path: FP32 operator / preconditioner, FP64 recurrences and replacements
+    prob.set_precision("fp32")
+    for _ in range(args.warmup):
+        one_solve()
+    S.sem_profile(prob.h, 1)
+    mev = []
+    m_iters, m_trs = [], []
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, it, tr = one_solve()
+        e1.record(stream)
+        mev.append((e0, e1))
+        m_iters.append(it)
+        m_trs.append(tr)
+    torch.cuda.synchronize()
+    mprof = S.sem_profile_read(prob.h)
+    S.sem_profile(prob.h, 0)
+    prob.set_precision("fp64")
+    t_mixed = max_over_ranks(sum(a.elapsed_time(bv) for a, bv in mev) / 1e3) / args.steps
+    mixed = {"time_to_1e-8_s": t_mixed, "gdofs_solved": world * G / t_mixed / 1e9, "iterations": m_iters[-1],
+             "true_rel_res": m_trs[-1], "speedup_vs_fp64": per_step / t_mixed,
+             "dtype": "FP32 operator and patch solves; FP64 vectors, dots, recurrences, coarse solve, "
+                      "residual replacement and final check",
+             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(mprof.items(), key=lambda kv: -kv[1][1])}}
 
     # ---- end to end through the public API with host buffers
     b_host = b.cpu().pin_memory()
@@ -360,6 +394,7 @@ def run_gpu(args):
             "time_to_1e-8_s": per_step, "iterations": iters[-1], "true_rel_res": trs[-1],
             "wall_s": t_wall,
             "ax": ax,
+            "mixed": mixed,
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
             "roofline": roof,
             "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,

@@ -49,6 +49,13 @@ typedef struct sem_s sem_t;
 #define SEM_GEOM_STORED     0x0  /* store G1..G6 and m per GLL node (Sec. 3.1, 7 factors) */
 #define SEM_GEOM_RECOMPUTE  0x1  /* recompute them from the 8 vertices in the operator (Sec. 3.1) */
 #define SEM_NEUMANN         0x10 /* no Dirichlet nodes (default: Dirichlet on every boundary face) */
+#define SEM_MIXED           0x100 /* also keep the stored factors in FP32, for SEM_PREC_FP32 */
+
+/* arithmetic of the operator and the preconditioner (sem_set_precision) */
+#define SEM_PREC_FP64  0   /* everything in FP64 (default) */
+#define SEM_PREC_FP32  1   /* Ax and P in FP32; vectors, dots, alpha/beta, residual updates in
+                              FP64; the residual is recomputed with the FP64 operator whenever it
+                              fell by 1e3 and before convergence is accepted */
 
 /* preconditioner choice for sem_solve (sem_set_precond) */
 #define SEM_PRECOND_TWO_SCALE 0  /* P = P^c + P^f (Sec. 4) */
@@ -113,6 +120,13 @@ int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev);
 int sem_apply_P(sem_t* h, const double* r_dev, double* z_dev);
 int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev);
 int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev);
+
+/* sem_set_precision - SEM_PREC_FP64 or SEM_PREC_FP32 for sem_apply_A, sem_apply_P* and
+ * sem_solve. FP32 with stored geometry needs SEM_MIXED at create (SEM_ERR_ARG otherwise).
+ * In FP32, sem_apply_A / sem_apply_P* return FP64 vectors computed with FP32 element
+ * arithmetic and FP64 sums over the local copies; sem_solve still reaches rtol on the true
+ * FP64 residual (the returned history holds the recomputed residual at replacements). */
+int sem_set_precision(sem_t* h, int precision);
 
 /* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
 int sem_set_precond(sem_t* h, int which);

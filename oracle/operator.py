@@ -88,3 +88,27 @@ def apply_dirichlet(A, mask):
     f = (mask == 0).astype(np.float64)
     Pf = diags(f)
     return (Pf @ A @ Pf + diags(1.0 - f)).tocsr()
+
+
+def matfree_abs(x, l2g, Dh, G, m, lam, mask=None):
+    """Magnitude of every term of Eq. R: the matrix-free apply with |D|, |G|, |x| and
+    every sum taken over absolute values, gathered. Rounding bounds of a
+    reduced-precision apply are multiples of this vector (a standard bound for sums of
+    products: |fl(sum a_i b_i) - sum a_i b_i| <= gamma_K sum |a_i||b_i|)."""
+    Gn = int(x.shape[0])
+    xf = np.abs(x) if mask is None else np.where(mask > 0, 0.0, np.abs(x))
+    u = xf[l2g]
+    aD = np.abs(Dh)
+    aG = np.abs(G)
+    ur = np.einsum("im,emjk->eijk", aD, u)
+    us = np.einsum("jm,eimk->eijk", aD, u)
+    ut = np.einsum("km,eijm->eijk", aD, u)
+    A = aG[0] * ur + aG[1] * us + aG[2] * ut
+    B = aG[1] * ur + aG[3] * us + aG[4] * ut
+    C = aG[2] * ur + aG[4] * us + aG[5] * ut
+    r = (np.einsum("mi,emjk->eijk", aD, A) + np.einsum("mj,eimk->eijk", aD, B)
+         + np.einsum("mk,eijm->eijk", aD, C)) + lam * m * u
+    y = np.bincount(l2g.ravel(), weights=r.ravel(), minlength=Gn)
+    if mask is not None:
+        y = np.where(mask > 0, 0.0, y)
+    return y

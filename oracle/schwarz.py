@@ -120,3 +120,17 @@ def apply_fine(r, ip, S, ev, h, lam, mask=None):
     if mask is not None:
         z = np.where(mask > 0, 0.0, z)
     return z
+
+
+def apply_fine_abs(r, ip, S, ev, h, lam, mask=None):
+    """Magnitude of every term of Eq. z (|S|, |r| and positive eigen-sums), summed over
+    the patches: the reference magnitude for rounding bounds of a reduced-precision P^f."""
+    Gn = r.shape[0]
+    rm = np.abs(r) if mask is None else np.where(mask > 0, 0.0, np.abs(r))
+    present = ip >= 0
+    rp = np.where(present, rm[np.where(present, ip, 0)], 0.0)
+    zp = fast_diag_solve(rp, np.abs(S), ev, h, lam)
+    z = np.bincount(ip[present], weights=zp[present], minlength=Gn)
+    if mask is not None:
+        z = np.where(mask > 0, 0.0, z)
+    return z

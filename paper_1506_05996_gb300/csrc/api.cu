@@ -116,6 +116,8 @@ struct sem_s {
   bool coarse_ok = false;
   std::string coarse_err;
   double *coords = nullptr, *mN = nullptr, *geo = nullptr;
+  float* geo32 = nullptr;
+  int precision = SEM_PREC_FP64;
   uint8_t* mask = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr;
   double* hist = nullptr;
@@ -236,7 +238,10 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   const sem::PcgState* st = pcg ? d.st : nullptr;
   int mode = 0;
   if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
-    PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
+    if (d.fp32)
+      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32(d, r, reinterpret_cast<float*>(d.wp), st, h->stream));
+    else
+      PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
     mode |= sem::PSUM_FINE;
   }
   if (which == SEM_PRECOND_TWO_SCALE || which == -1) {
@@ -271,7 +276,7 @@ int sem_create(const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2v
   if (n_vert < 8 || n_hex < 1) return fail(SEM_ERR_ARG, "empty mesh");
   if (order < 2 || order > 8) return fail(SEM_ERR_ARG, "order must be in 2..8");
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SEM_ERR_ARG, "lambda must be finite and >= 0");
-  if (flags & ~(SEM_GEOM_RECOMPUTE | SEM_NEUMANN)) return fail(SEM_ERR_ARG, "unknown flag");
+  if (flags & ~(SEM_GEOM_RECOMPUTE | SEM_NEUMANN | SEM_MIXED)) return fail(SEM_ERR_ARG, "unknown flag");
   for (int64_t i = 0; i < 3 * n_vert; ++i)
     if (!std::isfinite(vert_xyz_host[i])) return fail(SEM_ERR_ARG, "non-finite vertex coordinate");
 
@@ -409,11 +414,13 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
 
   // geometric factors (stored variant) and the assembled lumped mass
   if (!d.recompute) CK(h->alloc(&h->geo, (size_t)(7 * nb.ne * p3), A));
+  if (!d.recompute && (flags & SEM_MIXED)) CK(h->alloc(&h->geo32, (size_t)(7 * nb.ne * p3), A));
   d.geo = h->geo;
+  d.geo32 = h->geo32;
   int* bad;
   CK(h->alloc(&bad, 1, A));
   CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
-  CK(sem::launch_geometry(d, h->geo, d.wl, bad, h->stream));
+  CK(sem::launch_geometry(d, h->geo, h->geo32, d.wl, bad, h->stream));
   CK(sem::launch_gather_plain(d, d.wl, h->mN, h->stream));
   int bad_host = 0;
   CK(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -492,8 +499,14 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
 int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
   if (int rc = check_handle(h)) return rc;
   if (x_dev == nullptr || y_dev == nullptr || x_dev == y_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
-  PROF(h, "ax_local", sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
-  PROF(h, "gather", sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
+  if (h->d.fp32) {
+    float* wl = reinterpret_cast<float*>(h->d.wl);
+    PROF(h, "ax_local", sem::launch_ax_local_f32(h->d, x_dev, wl, nullptr, h->stream));
+    PROF(h, "gather", sem::launch_gather_identity_f32(h->d, wl, x_dev, y_dev, h->stream));
+  } else {
+    PROF(h, "ax_local", sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
+    PROF(h, "gather", sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
+  }
   return SEM_OK;
 }
 
@@ -510,6 +523,16 @@ int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev) {
   return apply_P_common(h, SEM_PRECOND_FINE, r_dev, z_dev);
 }
 int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev) { return apply_P_common(h, -1, r_dev, z_dev); }
+
+int sem_set_precision(sem_t* h, int precision) {
+  if (int rc = check_handle(h)) return rc;
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32) return fail(SEM_ERR_ARG, "unknown precision");
+  if (precision == SEM_PREC_FP32 && !h->d.recompute && h->geo32 == nullptr)
+    return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
+  h->precision = precision;
+  h->d.fp32 = (precision == SEM_PREC_FP32);
+  return SEM_OK;
+}
 
 int sem_set_precond(sem_t* h, int which) {
   if (int rc = check_handle(h)) return rc;
@@ -534,15 +557,29 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   cudaStream_t s = h->stream;
   double* u = x_dev;
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, h->hist, s));
+  const int mixed = d.fp32 ? 1 : 0;
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, mixed, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
   const int chunk = 1;   // iterations between host checks of the device-side stop flag
   for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
     for (int c = 0; c < chunk; ++c) {
-      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
+      if (d.fp32)
+        PROF(h, "ax_local", sem::launch_ax_local_f32(d, h->p, reinterpret_cast<float*>(d.wl), d.st, s));
+      else
+        PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
       PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
       PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
+      if (mixed) {
+        // the update decided whether r must be recomputed with the FP64 operator
+        CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (h->st_host->done) break;
+        if (h->st_host->replace) {
+          PROF(h, "ax_local_fp64", sem::launch_ax_local(d, u, d.wl, d.st, s));
+          PROF(h, "pcg_replace", sem::launch_pcg_replace(d, b_dev, d.wl, h->r, h->hist, s));
+        }
+      }
       if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
       PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, s));
     }

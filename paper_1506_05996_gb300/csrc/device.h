@@ -27,7 +27,11 @@ struct PcgState {
   double rr;        // ||r_k||^2
   double pf;        // p_k^T f
   double aux;       // spare reduction result (true residual)
+  double rel_ref;   // ||r|| / ||b|| at the last residual replacement (mixed path)
   int iter;         // operator applications done
+  int mixed;        // 1: FP32 operator/preconditioner, FP64 recurrences + replacement
+  int replace;      // set by the update: the host runs a residual replacement next
+  int replacements; // replacements done
   int done;         // 1 once converged / stopped
   int status;       // 0, SEM_MAXIT (1) or SEM_ERR_NAN (-6)
   int maxit;
@@ -52,6 +56,8 @@ struct DevProblem {
   int ne = 0, G = 0, nv = 0, nfree = 0;
   double lambda = 0.0;
   bool recompute = false;
+  bool fp32 = false;                // operator and patch solves in FP32 (mixed path)
+  const float* geo32 = nullptr;     // stored factors rounded to FP32 (same layout as geo)
   // tables
   const int* l2g = nullptr;
   const double* geo = nullptr;
@@ -83,8 +89,8 @@ struct DevProblem {
   double* cres = nullptr;           // level-0 residual for repeated cycles
   double* ctmp = nullptr;
   // work
-  double* wl = nullptr;             // ne*p^3 local results
-  double* wp = nullptr;             // ne*P^3 patch results
+  double* wl = nullptr;             // ne*p^3 local results (FP32 view in the mixed path)
+  double* wp = nullptr;             // ne*P^3 patch results (FP32 view in the mixed path)
   double* Re = nullptr;             // ne*8 element coarse residuals
   double* Rc = nullptr;             // nfree coarse residual
   double* Zc = nullptr;             // nfree coarse correction
@@ -102,20 +108,27 @@ uint64_t kernel_launch_count();
 // --- geometry set-up ---------------------------------------------------------
 // Computes m_loc (ne*p^3) and, if geo != nullptr, the stored factors; sets *bad = 1
 // if |J| <= 0 anywhere.
-cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, int* bad, cudaStream_t s);
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, double* mloc, int* bad,
+                            cudaStream_t s);
 
 // --- operator (Eq. R, Algorithm 2) -------------------------------------------
 cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st,
                             cudaStream_t s);
+cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st,
+                                cudaStream_t s);
 // y = gather(wl); masked rows take xin (identity) - sem_apply_A.
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y,
                                    cudaStream_t s);
+cudaError_t launch_gather_identity_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
+                                       cudaStream_t s);
 // y = gather(wl) on all nodes, no mask (set-up: assembled mass).
 cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y, cudaStream_t s);
 
 // --- preconditioner (Sec. 4) -------------------------------------------------
 cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st,
                                  cudaStream_t s);
+cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
+                                     cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);
 enum PsumMode { PSUM_FINE = 1, PSUM_COARSE = 2, PSUM_BOTH = 3, PSUM_IDENT = 4 };
@@ -126,13 +139,16 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 
 // --- PCG (Algorithm 1) -------------------------------------------------------
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol,
-                            int maxit, double* hist, cudaStream_t s);
+                            int maxit, int mixed, double* hist, cudaStream_t s);
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
-// f = gather(wl) (0 on masked), pf = p.f, alpha = rz / pf.
+// f = gather(wl) (0 on masked; FP32 local results when d.fp32), pf = p.f, alpha = rz / pf.
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s);
 cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double* f, double* u, double* r,
                               double* hist, cudaStream_t s);
 cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
+// r = b - gather(wl) with FP64 local results; decides convergence on the true residual.
+cudaError_t launch_pcg_replace(const DevProblem& d, const double* b, const double* wl, double* r, double* hist,
+                               cudaStream_t s);
 // aux = ||b - f||^2 over free nodes
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s);
 

@@ -1,4 +1,6 @@
-// sm_103a kernels of the spectral-element solver, FP64 path.
+// sm_103a kernels of the spectral-element solver. The operator, gather, patch-solve and
+// P-sum kernels are templated on the compute type T (double, or float for the mixed
+// path); global vectors, dot products and the PCG recurrences are always FP64.
 //
 //  geometry_kernel      G1..G6 and m at every GLL node from the trilinear map (Sec. 2.3-2.4)
 //  ax_local_kernel      local residual r_{ijk;e} of Eq. R / Algorithm 2 (stored or recomputed G)
@@ -23,6 +25,10 @@ uint64_t kernel_launch_count() { return g_kernel_launches; }
 namespace {
 
 __device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
+
+// Mixed path: replace the recursive residual by b - A u (FP64 operator) whenever it has
+// dropped by this factor since the last replacement, and before accepting convergence.
+constexpr double kReplaceFactor = 1e-3;
 
 // Sum over a block of BS threads; the result is valid in warp 0.
 template <int BS>
@@ -69,25 +75,26 @@ __device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned 
 
 // G = w |J| J^-1 J^-T (6 entries) and m = w |J| at reference point (a, b, c) from the
 // 8 vertices xv[corner*3 + dim]. J[r][s] = d x_r / d xi_s of the trilinear map.
-__device__ __forceinline__ void geom_point(const double* xv, double a, double b, double c, double w,
-                                           double G[6], double& m, double& det) {
-  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+template <typename T>
+__device__ __forceinline__ void geom_point(const T* xv, T a, T b, T c, T w, T G[6], T& m, T& det) {
+  T J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const T one = 1, half = 0.5;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const double sa = ((q == 1) | (q == 2) | (q == 5) | (q == 6)) ? 1.0 : -1.0;
-    const double sb = ((q == 2) | (q == 3) | (q == 6) | (q == 7)) ? 1.0 : -1.0;
-    const double sc = (q >= 4) ? 1.0 : -1.0;
-    const double fa = 0.5 * (1.0 + sa * a), fb = 0.5 * (1.0 + sb * b), fc = 0.5 * (1.0 + sc * c);
-    const double d0 = 0.5 * sa * fb * fc, d1 = 0.5 * sb * fa * fc, d2 = 0.5 * sc * fa * fb;
+    const T sa = ((q == 1) | (q == 2) | (q == 5) | (q == 6)) ? one : -one;
+    const T sb = ((q == 2) | (q == 3) | (q == 6) | (q == 7)) ? one : -one;
+    const T sc = (q >= 4) ? one : -one;
+    const T fa = half * (one + sa * a), fb = half * (one + sb * b), fc = half * (one + sc * c);
+    const T d0 = half * sa * fb * fc, d1 = half * sb * fa * fc, d2 = half * sc * fa * fb;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const double x = xv[3 * q + r];
+      const T x = xv[3 * q + r];
       J[r][0] += x * d0;
       J[r][1] += x * d1;
       J[r][2] += x * d2;
     }
   }
-  double C[3][3];
+  T C[3][3];
   C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
   C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
   C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
@@ -98,7 +105,7 @@ __device__ __forceinline__ void geom_point(const double* xv, double a, double b,
   C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
   C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
   det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-  const double s = w / det;   // inv(J)[r][c] = C[c][r] / det
+  const T s = w / det;   // inv(J)[r][c] = C[c][r] / det
   G[0] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
   G[1] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
   G[2] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
@@ -110,8 +117,8 @@ __device__ __forceinline__ void geom_point(const double* xv, double a, double b,
 
 // ----------------------------------------------------------------- geometry
 template <int p>
-__global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d, double* geo, double* mloc,
-                                                             int* bad) {
+__global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d, double* geo, float* geo32,
+                                                             double* mloc, int* bad) {
   constexpr int p3 = p * p * p;
   __shared__ double sx[24];
   const int e = blockIdx.x, t = threadIdx.x;
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
   __syncthreads();
   const int i = t % p, j = (t / p) % p, k = t / (p * p);
   double G[6], m, det;
-  geom_point(sx, d.tg[i], d.tg[j], d.tg[k], d.rho[i] * d.rho[j] * d.rho[k], G, m, det);
+  geom_point<double>(sx, d.tg[i], d.tg[j], d.tg[k], d.rho[i] * d.rho[j] * d.rho[k], G, m, det);
   if (!(det > 0.0)) *bad = 1;
   mloc[(size_t)e * p3 + t] = m;
   if (geo != nullptr) {
@@ -128,64 +135,75 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
     for (int c = 0; c < 6; ++c) gp[c * p3] = G[c];
     gp[6 * p3] = m;
   }
+  if (geo32 != nullptr) {   // the same factors rounded to FP32 for the mixed path
+    float* gp = geo32 + (size_t)e * 7 * p3 + t;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gp[c * p3] = (float)G[c];
+    gp[6 * p3] = (float)m;
+  }
 }
+
+template <typename T> __device__ __forceinline__ const T* geo_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* geo_of<double>(const DevProblem& d) { return d.geo; }
+template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
 
 // ----------------------------------------------------------------- operator
 // One CTA per element, one thread per GLL node (Algorithm 2): gradient by D,
 // A/B/C by the geometric factors, divergence by D^T, plus lambda m u.
-template <int p, bool RECOMP>
+template <int p, bool RECOMP, typename T>
 __global__ void __launch_bounds__(p * p * p) ax_local_kernel(const DevProblem d, const double* __restrict__ x,
-                                                             double* __restrict__ wl, const PcgState* st) {
+                                                             T* __restrict__ wl, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int p3 = p * p * p;
-  __shared__ double sD[p * p], su[p3], sA[p3], sB[p3], sC[p3];
-  __shared__ double sx[24];
+  __shared__ T sD[p * p], su[p3], sA[p3], sB[p3], sC[p3];
+  __shared__ T sx[24];
   const int e = blockIdx.x, t = threadIdx.x;
   const int i = t % p, j = (t / p) % p, k = t / (p * p);
-  if (t < p * p) sD[t] = d.D[t];
-  if (RECOMP && t < 24) sx[t] = d.exyz[(size_t)e * 24 + t];
+  if (t < p * p) sD[t] = (T)d.D[t];
+  if (RECOMP && t < 24) sx[t] = (T)d.exyz[(size_t)e * 24 + t];
   const int g = d.l2g[(size_t)e * p3 + t];
-  const double u = d.mask[g] ? 0.0 : x[g];
+  const T u = d.mask[g] ? T(0) : (T)x[g];
   su[t] = u;
   __syncthreads();
-  double ur = 0.0, us = 0.0, ut = 0.0;
+  T ur = 0, us = 0, ut = 0;
 #pragma unroll
   for (int m = 0; m < p; ++m) {
     ur += sD[i * p + m] * su[m + p * (j + p * k)];
     us += sD[j * p + m] * su[i + p * (m + p * k)];
     ut += sD[k * p + m] * su[i + p * (j + p * m)];
   }
-  double G[6], mm;
+  T G[6], mm;
   if (!RECOMP) {
-    const double* gp = d.geo + (size_t)e * 7 * p3 + t;
+    const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + t;
 #pragma unroll
     for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
     mm = gp[6 * p3];
   } else {
-    double det;
-    geom_point(sx, d.tg[i], d.tg[j], d.tg[k], d.rho[i] * d.rho[j] * d.rho[k], G, mm, det);
+    T det;
+    geom_point<T>(sx, (T)d.tg[i], (T)d.tg[j], (T)d.tg[k], (T)(d.rho[i] * d.rho[j] * d.rho[k]), G, mm, det);
   }
   sA[t] = G[0] * ur + G[1] * us + G[2] * ut;
   sB[t] = G[1] * ur + G[3] * us + G[4] * ut;
   sC[t] = G[2] * ur + G[4] * us + G[5] * ut;
   __syncthreads();
-  double r = 0.0;
+  T r = 0;
 #pragma unroll
   for (int m = 0; m < p; ++m) {
     r += sD[m * p + i] * sA[m + p * (j + p * k)];
     r += sD[m * p + j] * sB[i + p * (m + p * k)];
     r += sD[m * p + k] * sC[i + p * (j + p * m)];
   }
-  r += d.lambda * mm * u;
+  r += (T)d.lambda * mm * u;
   wl[(size_t)e * p3 + t] = r;
 }
 
-__global__ void gather_identity_kernel(const DevProblem d, const double* __restrict__ wl,
+template <typename T>
+__global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__ wl,
                                        const double* __restrict__ xin, double* __restrict__ y) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
     double s = 0.0;
-    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += (double)wl[d.g2l_idx[q]];
     y[g] = s;
   }
 }
@@ -203,30 +221,31 @@ __global__ void gather_plain_kernel(const DevProblem d, const double* __restrict
 // the extended box in each of the six tensor contractions of Eq. z:
 //   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
 //   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
-template <int P>
+template <int P, typename T>
 __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d, const double* __restrict__ r,
-                                                              double* __restrict__ wp, const PcgState* st) {
+                                                              T* __restrict__ wp, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
-  __shared__ double sS[P2], sev[P], s1[P3], s2[P3];
+  __shared__ T sS[P2], sev[P], s1[P3], s2[P3];
   const int e = blockIdx.x, tx = threadIdx.x;
   const int x = tx % P, y = tx / P;
-  sS[tx] = d.S[tx];
-  if (tx < P) sev[tx] = d.ev[tx];
-  const double hx = d.hbox[3 * e], hy = d.hbox[3 * e + 1], hz = d.hbox[3 * e + 2];
-  const double scale = 8.0 / (hx * hy * hz);
-  double col[P];
+  sS[tx] = (T)d.S[tx];
+  if (tx < P) sev[tx] = (T)d.ev[tx];
+  const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
+  const T hx = (T)hxd, hy = (T)hyd, hz = (T)hzd;
+  const double scale = 8.0 / (hxd * hyd * hzd);
+  T col[P];
   const int* ipe = d.ip + (size_t)e * P3;
 #pragma unroll
   for (int K = 0; K < P; ++K) {
     const int g = ipe[x + P * (y + P * K)];
-    col[K] = (g >= 0 && !d.mask[g]) ? r[g] * scale : 0.0;
+    col[K] = (g >= 0 && !d.mask[g]) ? (T)(r[g] * scale) : T(0);
   }
   __syncthreads();
   // along K: line (I=x, J=y)
 #pragma unroll
   for (int c = 0; c < P; ++c) {
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
     for (int K = 0; K < P; ++K) v += sS[K * P + c] * col[K];
     s1[x + P * (y + P * c)] = v;
@@ -235,7 +254,7 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   // along J: line (I=x, c=y)
 #pragma unroll
   for (int b = 0; b < P; ++b) {
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
     for (int J = 0; J < P; ++J) v += sS[J * P + b] * s1[x + P * (J + P * y)];
     s2[x + P * (b + P * y)] = v;
@@ -243,18 +262,18 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   __syncthreads();
   // along I: line (b=x, c=y), eigenvalue scaling, and back along I
   {
-    double t3[P];
-    const double lb = sev[x] / (hy * hy), lc = sev[y] / (hz * hz);
+    T t3[P];
+    const T lb = sev[x] / (hy * hy), lc = sev[y] / (hz * hz), four = 4, lam = (T)d.lambda;
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-      double v = 0.0;
+      T v = 0;
 #pragma unroll
       for (int I = 0; I < P; ++I) v += sS[I * P + a] * s2[I + P * (x + P * y)];
-      t3[a] = v / (4.0 * (sev[a] / (hx * hx) + lb + lc) + d.lambda);
+      t3[a] = v / (four * (sev[a] / (hx * hx) + lb + lc) + lam);
     }
 #pragma unroll
     for (int I = 0; I < P; ++I) {
-      double v = 0.0;
+      T v = 0;
 #pragma unroll
       for (int a = 0; a < P; ++a) v += sS[I * P + a] * t3[a];
       s2[I + P * (x + P * y)] = v;
@@ -264,17 +283,17 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   // back along J: line (I=x, c=y)
 #pragma unroll
   for (int J = 0; J < P; ++J) {
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
     for (int b = 0; b < P; ++b) v += sS[J * P + b] * s2[x + P * (b + P * y)];
     s1[x + P * (J + P * y)] = v;
   }
   __syncthreads();
   // back along K: line (I=x, J=y)
-  double* out = wp + (size_t)e * P3;
+  T* out = wp + (size_t)e * P3;
 #pragma unroll
   for (int K = 0; K < P; ++K) {
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
     for (int c = 0; c < P; ++c) v += sS[K * P + c] * s1[x + P * (y + P * c)];
     out[x + P * (y + P * K)] = v;
@@ -282,27 +301,55 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
 }
 
 // ---------------------------------------------------------------- coarse
-// Per element R_{IJK;e} = sum over the element's owned nodes of Phi_I Phi_J Phi_K r_N;
-// summed over elements this is C m^{-1} r (every node counted once, at its owner).
-constexpr int kRestrictBlock = 128;
-__global__ void __launch_bounds__(kRestrictBlock) coarse_restrict_kernel(const DevProblem d, const double* __restrict__ r,
-                                                                         const PcgState* st) {
+// Per element R_{IJK;e} = sum over the element's owned nodes of Phi_I(t_i) Phi_J(t_j)
+// Phi_K(t_k) r_N; summed over elements this is C m^{-1} r (every node counted once, at
+// its owner). Sum-factorised: one thread per (j, k) line contracts i, then (b0, k) pairs
+// contract j, then the 8 corners contract k.
+template <int p>
+__global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem d, const double* __restrict__ r,
+                                                                const PcgState* st) {
   if (stopped(st)) return;
-  const int e = blockIdx.x, p = d.p, p3 = p * p * p;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int l = threadIdx.x; l < p3; l += kRestrictBlock) {
-    const int gl = e * p3 + l;
-    const int g = d.l2g[gl];
-    if (d.owner[g] != gl || d.mask[g]) continue;
-    const double v = r[g];
-    const double* B = d.Btab + 8 * l;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] += v * B[c];
+  constexpr int p3 = p * p * p;
+  __shared__ double sl[2][p * p], sm[2][2][p], phi[2][p];
+  const int e = blockIdx.x, t = threadIdx.x;
+  if (t < p) {
+    phi[0][t] = 0.5 * (1.0 - d.tg[t]);
+    phi[1][t] = 0.5 * (1.0 + d.tg[t]);
   }
+  __syncthreads();
+  {   // thread (j, k): contract over i
+    const int j = t % p, k = t / p;
+    double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const double s = block_sum<kRestrictBlock>(acc[c]);
-    if (threadIdx.x == 0) d.Re[(size_t)e * 8 + c] = s;
+    for (int i = 0; i < p; ++i) {
+      const int l = i + p * (j + p * k), gl = e * p3 + l;
+      const int g = d.l2g[gl];
+      const double v = (d.owner[g] == gl && !d.mask[g]) ? r[g] : 0.0;
+      a0 += phi[0][i] * v;
+      a1 += phi[1][i] * v;
+    }
+    sl[0][t] = a0;
+    sl[1][t] = a1;
+  }
+  __syncthreads();
+  if (t < 2 * p) {   // thread (b0, k): contract over j
+    const int b0 = t / p, k = t % p;
+    double c0 = 0.0, c1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < p; ++j) {
+      c0 += phi[0][j] * sl[b0][j + p * k];
+      c1 += phi[1][j] * sl[b0][j + p * k];
+    }
+    sm[b0][0][k] = c0;
+    sm[b0][1][k] = c1;
+  }
+  __syncthreads();
+  if (t < 8) {   // VTK corner t: contract over k
+    const int b0 = (t == 1 || t == 2 || t == 5 || t == 6), b1 = (t == 2 || t == 3 || t == 6 || t == 7), b2 = (t >= 4);
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < p; ++k) v += phi[b2][k] * sm[b0][b1][k];
+    d.Re[(size_t)e * 8 + t] = v;
   }
 }
 
@@ -392,9 +439,9 @@ __global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const do
 }
 
 // ------------------------------------------------------------ P sum and PCG
-template <bool PCG>
-__global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const double* __restrict__ r,
-                                                         double* __restrict__ z) {
+template <bool PCG, typename T>
+__global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const T* __restrict__ wp,
+                                                         const double* __restrict__ r, double* __restrict__ z) {
   if (PCG && stopped(d.st)) return;
   const int p = d.p, p3 = p * p * p;
   double dot = 0.0;
@@ -403,7 +450,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
     if (!d.mask[g]) {
       if (mode & PSUM_IDENT) v += r[g];
       if (mode & PSUM_FINE)
-        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += d.wp[d.pg_idx[q]];
+        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += (double)wp[d.pg_idx[q]];
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
         const int l = d.owner[g], e = l / p3, lr = l % p3;
         const int* ec = d.ecv + (size_t)e * 8;
@@ -433,7 +480,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
 
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
-                                                             double rtol, int maxit, double* hist) {
+                                                             double rtol, int maxit, int mixed, double* hist) {
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
@@ -452,6 +499,10 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
     st->status = 0;
     st->rz = 0.0;
     st->beta = 0.0;
+    st->rel_ref = 1.0;
+    st->mixed = mixed;
+    st->replace = 0;
+    st->replacements = 0;
     hist[0] = (total > 0.0) ? 1.0 : 0.0;
     if (!isfinite(total)) { st->status = -6; st->done = 1; }
     else if (total == 0.0) st->done = 1;
@@ -464,14 +515,16 @@ __global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) p[g] = z[g];
 }
 
-__global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevProblem d, const double* __restrict__ p,
+template <typename T>
+__global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevProblem d, const T* __restrict__ wl,
+                                                                     const double* __restrict__ p,
                                                                      double* __restrict__ f) {
   if (stopped(d.st)) return;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     double s = 0.0;
     if (!d.mask[g])
-      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += d.wl[d.g2l_idx[q]];
+      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += (double)wl[d.g2l_idx[q]];
     f[g] = s;
     dot += p[g] * s;
   }
@@ -504,8 +557,43 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
     const double rel = sqrt(total) / sqrt(st->bb);
     hist[it] = rel;
     if (!isfinite(total)) { st->status = -6; st->done = 1; }
-    else if (rel <= st->rtol) st->done = 1;
+    else if (st->mixed) {
+      // the recursive residual of the FP32 operator drifts from b - A u: confirm
+      // convergence, or refresh r, with the FP64 operator (residual replacement)
+      if (rel <= st->rtol || rel <= kReplaceFactor * st->rel_ref || it >= st->maxit) st->replace = 1;
+    } else if (rel <= st->rtol) st->done = 1;
     else if (it >= st->maxit) { st->status = 1; st->done = 1; }
+  }
+}
+
+// Residual replacement: r = b - A u with the FP64 operator (local results in wl),
+// and the decision whether the true residual meets the tolerance.
+__global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem d, const double* __restrict__ b,
+                                                                const double* __restrict__ wl, double* __restrict__ r,
+                                                                double* hist) {
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double res = 0.0;
+    if (!d.mask[g]) {
+      double s = 0.0;
+      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+      res = b[g] - s;
+    }
+    r[g] = res;
+    dot += res * res;
+  }
+  double total;
+  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+    PcgState* st = d.st;
+    const double rel = sqrt(total) / sqrt(st->bb);
+    st->rr = total;
+    st->replacements += 1;
+    hist[st->iter] = rel;
+    st->replace = 0;
+    if (!isfinite(total)) { st->status = -6; st->done = 1; }
+    else if (rel <= st->rtol) st->done = 1;
+    else if (st->iter >= st->maxit) { st->status = 1; st->done = 1; }
+    else st->rel_ref = rel;
   }
 }
 
@@ -567,9 +655,10 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
 }  // namespace
 
 // ================================================================ launchers
-cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, int* bad, cudaStream_t s) {
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, double* mloc, int* bad,
+                            cudaStream_t s) {
   switch (d.p) {
-#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, mloc, bad); ++g_kernel_launches; break;
+#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, geo32_out, mloc, bad); ++g_kernel_launches; break;
     GEO_CASE(2) GEO_CASE(3) GEO_CASE(4) GEO_CASE(5) GEO_CASE(6) GEO_CASE(7) GEO_CASE(8) GEO_CASE(9)
 #undef GEO_CASE
     default: return cudaErrorInvalidValue;
@@ -577,23 +666,37 @@ cudaError_t launch_geometry(const DevProblem& d, double* geo_out, double* mloc, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_ax_local_t(const DevProblem& d, const double* x, T* wl, const PcgState* st, cudaStream_t s) {
   switch (d.p) {
-#define AX_CASE(P_)                                                                        \
-  case P_:                                                                                 \
-    if (d.recompute) ax_local_kernel<P_, true><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);  \
-    else ax_local_kernel<P_, false><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);             \
-    ++g_kernel_launches;                                                                   \
+#define AX_CASE(P_)                                                                          \
+  case P_:                                                                                   \
+    if (d.recompute) ax_local_kernel<P_, true, T><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st); \
+    else ax_local_kernel<P_, false, T><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);            \
+    ++g_kernel_launches;                                                                     \
     break;
-    AX_CASE(2) AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
+    AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
 #undef AX_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
+  return launch_ax_local_t<double>(d, x, wl, st, s);
+}
+cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st, cudaStream_t s) {
+  return launch_ax_local_t<float>(d, x, wl, st, s);
+}
+
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
-  gather_identity_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_identity_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
+                                       cudaStream_t s) {
+  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -604,20 +707,32 @@ cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y
   return cudaGetLastError();
 }
 
-cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_schwarz_local_t(const DevProblem& d, const double* r, T* wp, const PcgState* st, cudaStream_t s) {
   switch (d.P) {
-#define SW_CASE(P_) case P_: schwarz_local_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
-    SW_CASE(4) SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
+#define SW_CASE(P_) case P_: schwarz_local_kernel<P_, T><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
+    SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
 #undef SW_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
+cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
+  return launch_schwarz_local_t<double>(d, r, wp, st, s);
+}
+cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
+                                     cudaStream_t s) {
+  return launch_schwarz_local_t<float>(d, r, wp, st, s);
+}
 
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  coarse_restrict_kernel<<<d.ne, kRestrictBlock, 0, s>>>(d, r, st);
-  ++g_kernel_launches;
+  switch (d.p) {
+#define RS_CASE(P_) case P_: coarse_restrict_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, st); ++g_kernel_launches; break;
+    RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6) RS_CASE(7) RS_CASE(8) RS_CASE(9)
+#undef RS_CASE
+    default: return cudaErrorInvalidValue;
+  }
   vertex_gather_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d, st);
   ++g_kernel_launches;
   return cudaGetLastError();
@@ -642,15 +757,21 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
 }
 
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
-  if (pcg) psum_kernel<true><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
-  else psum_kernel<false><<<d.nblk, kVecBlock, 0, s>>>(d, mode, r, z);
+  if (d.fp32) {
+    const float* wp = reinterpret_cast<const float*>(d.wp);
+    if (pcg) psum_kernel<true, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    else psum_kernel<false, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+  } else {
+    if (pcg) psum_kernel<true, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
+    else psum_kernel<false, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
+  }
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
-                            double* hist, cudaStream_t s) {
-  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, hist);
+                            int mixed, double* hist, cudaStream_t s) {
+  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -662,7 +783,8 @@ cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, dou
 }
 
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s) {
-  pcg_gather_alpha_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f);
+  if (d.fp32) pcg_gather_alpha_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, reinterpret_cast<const float*>(d.wl), p, f);
+  else pcg_gather_alpha_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, d.wl, p, f);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -676,6 +798,13 @@ cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double
 
 cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
   pcg_direction_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_replace(const DevProblem& d, const double* b, const double* wl, double* r, double* hist,
+                               cudaStream_t s) {
+  pcg_replace_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, wl, r, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

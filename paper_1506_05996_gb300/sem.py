@@ -22,7 +22,8 @@ SEM_OK = 0
 SEM_ERR_ARG, SEM_ERR_JACOBIAN, SEM_ERR_MESH, SEM_ERR_CUDA = -1, -2, -3, -4
 SEM_ERR_OOM, SEM_ERR_NAN, SEM_ERR_SINGULAR = -5, -6, -7
 SEM_MAXIT = 1
-SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN = 0x0, 0x1, 0x10
+SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED = 0x0, 0x1, 0x10, 0x100
+SEM_PREC_FP64, SEM_PREC_FP32 = 0, 1
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -43,6 +44,7 @@ _SIGS = {
     "sem_apply_Pf": ([_vp, _vp, _vp], _int),
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
     "sem_set_precond": ([_vp, _int], _int),
+    "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
     "sem_profile": ([_vp, _int], _int),
@@ -158,6 +160,10 @@ def sem_set_precond(h, which):
     return _check(_lib.sem_set_precond(h, int(which)))
 
 
+def sem_set_precision(h, precision):
+    return _check(_lib.sem_set_precision(h, int(precision)))
+
+
 def sem_solve(h, b, x, rtol=1e-8, maxit=1000, want_history=True):
     """Returns (status, iterations, residual history (numpy) or None, true relative residual)."""
     n = sem_num_dofs(h)
@@ -205,10 +211,12 @@ class SemProblem:
     """Owns one handle; convenience wrappers returning torch tensors."""
 
     def __init__(self, mesh_xyz, hex2vert, order, lam, geom="stored", neumann=False, stream=None,
-                 device="cuda"):
+                 device="cuda", mixed=False):
         flags = SEM_GEOM_RECOMPUTE if geom == "recompute" else SEM_GEOM_STORED
         if neumann:
             flags |= SEM_NEUMANN
+        if mixed:
+            flags |= SEM_MIXED
         self.device = torch.device(device)
         self.h = sem_create(mesh_xyz, hex2vert, order, lam, flags, stream)
         self.n_dof = sem_num_dofs(self.h)
@@ -227,6 +235,9 @@ class SemProblem:
 
     def _vec(self, dtype=torch.float64, n=None):
         return torch.empty(self.n_dof if n is None else n, dtype=dtype, device=self.device)
+
+    def set_precision(self, prec):
+        sem_set_precision(self.h, {"fp64": SEM_PREC_FP64, "fp32": SEM_PREC_FP32}[prec])
 
     def dof_coords(self):
         x = self._vec(n=3 * self.n_dof)

@@ -12,6 +12,9 @@ class Pair:
         self.gpu = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom=geom, neumann=neumann)
         self.ref = Problem(mesh, n, lam, dirichlet=not neumann,
                            coarse_solver="amg" if coarse else None, with_schwarz=schwarz)
+        self._match()
+
+    def _match(self):
         X = self.gpu.dof_coords().cpu().numpy()
         oi = np.lexsort(np.round(self.ref.coords, 9).T)
         gi = np.lexsort(np.round(X, 9).T)

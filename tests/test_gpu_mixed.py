@@ -1,0 +1,104 @@
+"""Mixed-precision path (SEM_PREC_FP32) against the FP64 oracle.
+
+Per-result bounds. The FP32 operator rounds x and the stored factors to FP32 and
+forms every local result as nested sums of products; on the longest path a value
+passes K = 4p + 8 roundings (p-term gradient, 3-term metric product, 3p-term
+divergence, the c-term, input roundings), so |y32 - y| <= gamma_K u32 |A|(|x|) with
+u32 = 2^-24 and |A|(|x|) the all-absolute apply (oracle.operator.matfree_abs); the FP64
+gather adds nothing at that scale. Recomputed geometry also rounds J, its cofactors and
+|J| in FP32 (about 40 more roundings, amplified by the conditioning of J), so its bound
+uses K = 4p + 8 + 40 kappa where kappa = max over nodes of cond(J)^2 (Frobenius),
+computed by the oracle. The patch solve passes 6P + 4 roundings through |S| products:
+|z32 - z| <= gamma_{6P+4} u32 |S||S^T|(|r|) (oracle.schwarz.apply_fine_abs). The solve
+must reach the FP64 true residual tolerance.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import lattice_hex_mesh, manufactured_s, manufactured_u
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+def gamma(k):
+    return k * U32 / (1 - k * U32)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05996_gb300 import build
+    build.build()
+
+
+def _pair(mesh, n, lam, geom):
+    from gpu_util import Pair
+    P = Pair.__new__(Pair)
+    from paper_1506_05996_gb300.sem import SemProblem
+    from oracle.problem import Problem
+    P.gpu = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom=geom, mixed=(geom == "stored"))
+    P.ref = Problem(mesh, n, lam)
+    Pair._match(P)
+    return P
+
+
+def _cond_J2(pr):
+    from oracle.geometry import jacobians
+    J = jacobians(pr.xyz_e, pr.t)
+    c = np.linalg.norm(J, axis=(-2, -1)) * np.linalg.norm(np.linalg.inv(J), axis=(-2, -1))
+    return float(np.max(c) ** 2)
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed", [(2, 3, 0.0, 0.2, 0), (3, 5, 1.0, 0.2, 1), (2, 7, 0.5, 0.2, 2),
+                                            (2, 8, 2.0, 0.15, 3)])
+@pytest.mark.parametrize("geom", ["stored", "recompute"])
+def test_fp32_operator_within_bound(E, n, lam, a, seed, geom):
+    from oracle.operator import matfree_abs
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam, geom)
+    x = np.random.default_rng(seed).standard_normal(P.ref.G)
+    y64 = P.ref.apply_A(x)
+    P.gpu.set_precision("fp32")
+    y32 = P.to_ref(P.gpu.apply_A(P.to_gpu(x)))
+    yabs = matfree_abs(x, P.ref.l2g, P.ref.Dh, P.ref.Gf, P.ref.m_loc, lam, P.ref.mask)
+    p = n + 1
+    K = 4 * p + 8 + (40 * _cond_J2(P.ref) if geom == "recompute" else 0)
+    free = P.ref.mask == 0
+    ratio = np.max(np.abs(y32 - y64)[free] / (gamma(K) * yabs[free]))
+    assert ratio <= 1.0, ratio
+    # and it is genuinely FP32 arithmetic, not FP64
+    assert np.max(np.abs(y32 - y64)) > 0
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed", [(3, 3, 0.0, 0.2, 0), (2, 7, 1.0, 0.2, 1)])
+def test_fp32_fine_preconditioner_within_bound(E, n, lam, a, seed):
+    from oracle.schwarz import apply_fine_abs
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam, "stored")
+    r = np.random.default_rng(seed + 5).standard_normal(P.ref.G)
+    z64 = P.ref.apply_Pf(r)
+    P.gpu.set_precision("fp32")
+    z32 = P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine"))
+    zabs = apply_fine_abs(r, P.ref.ip, P.ref.S, P.ref.ev, P.ref.h, lam, P.ref.mask)
+    K = 6 * (n + 3) + 4
+    free = P.ref.mask == 0
+    ratio = np.max(np.abs(z32 - z64)[free] / (gamma(K) * zabs[free]))
+    assert ratio <= 1.0, ratio
+
+
+@pytest.mark.parametrize("geom", ["stored", "recompute"])
+def test_mixed_solve_reaches_fp64_tolerance(geom):
+    P = _pair(lattice_hex_mesh(6, 0.2, 4), 5, 1.0, geom)
+    b = P.ref.load(manufactured_s(P.ref.coords, 1.0))
+    u_ref, it_ref, _ = P.ref.solve(b, rtol=1e-8)
+    P.gpu.set_precision("fp32")
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+    assert rc == 0
+    assert tr <= 1e-8                      # the FP64 true residual, computed afresh
+    assert it <= int(1.25 * it_ref) + 2
+    u = P.to_ref(x)
+    # both solutions satisfy ||b - A u|| <= 1e-8 ||b||; their difference is bounded by
+    # 2e-8 ||b|| / lambda_min(A); compare against the manufactured-solution error scale
+    assert np.max(np.abs(u - u_ref)) <= 1e-5 * np.max(np.abs(u_ref))
+    assert np.max(np.abs(u - manufactured_u(P.ref.coords))) < 1e-3
