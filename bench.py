@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
+                    help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
+                         "(a small case for ncu captures), then exit")
     return ap.parse_args()
 
 
@@ -409,9 +412,29 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_kernel_case(E):
+    """A few applies of each hot kernel, FP64 then FP32, on an E^3-hex, n = 7 mesh."""
+    import torch
+    from synth import lattice_hex_mesh
+    from paper_1506_05996_gb300 import sem as S
+    mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
+    x = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "fp32"):
+        prob.set_precision(prec)
+        for _ in range(2):
+            prob.apply_A(x)
+            prob.apply_P(x, "two-scale")
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": E, "n_dof": prob.n_dof}))
+    prob.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args.kernel_case)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
