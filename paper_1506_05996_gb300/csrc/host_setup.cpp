@@ -416,14 +416,53 @@ void pencil_tables(int n, const std::vector<double>& t, const std::vector<double
   M[n + 1] += rho[0];
   M[0] = rho[n - 1];
   M[P - 1] = rho[1];
-  std::vector<double> A(P * P);
-  for (int i = 0; i < P; ++i)
-    for (int j = 0; j < P; ++j) A[i * P + j] = K[i * P + j] / std::sqrt(M[i] * M[j]);
-  std::vector<double> Q;
-  jacobi_eigen(P, A, ev, Q);
+  // K and M are symmetric under the reflection i -> P-1-i, so the eigenvectors split
+  // into even and odd ones. Solve the two half-size problems on the bases
+  // e_i + e_{P-1-i} (and e_mid) and e_i - e_{P-1-i}; modes are stored even first.
+  const int H = P / 2, odd = P & 1, NE = H + odd;
+  auto half_problem = [&](bool even, int m, std::vector<double>& vals, std::vector<double>& vecs) {
+    std::vector<double> Kh(m * m), Mh(m);
+    auto basis = [&](int i, int row) -> double {   // entry `row` of basis vector i
+      if (even && odd && i == H) return row == H ? 1.0 : 0.0;
+      if (row == i) return 1.0;
+      if (row == P - 1 - i) return even ? 1.0 : -1.0;
+      return 0.0;
+    };
+    for (int i = 0; i < m; ++i) {
+      double mi = 0.0;
+      for (int r = 0; r < P; ++r) mi += basis(i, r) * M[r] * basis(i, r);
+      Mh[i] = mi;
+      for (int j = 0; j < m; ++j) {
+        double kij = 0.0;
+        for (int r = 0; r < P; ++r)
+          for (int c = 0; c < P; ++c) kij += basis(i, r) * K[r * P + c] * basis(j, c);
+        Kh[i * m + j] = kij;
+      }
+    }
+    std::vector<double> A(m * m), Q;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) A[i * m + j] = Kh[i * m + j] / std::sqrt(Mh[i] * Mh[j]);
+    jacobi_eigen(m, A, vals, Q);
+    vecs.assign(P * m, 0.0);   // full-length eigenvectors, column a
+    for (int a = 0; a < m; ++a)
+      for (int i = 0; i < m; ++i) {
+        const double y = Q[i * m + a] / std::sqrt(Mh[i]);
+        for (int r = 0; r < P; ++r) vecs[r * m + a] += basis(i, r) * y;
+      }
+  };
+  std::vector<double> ev_e, S_e, ev_o, S_o;
+  half_problem(true, NE, ev_e, S_e);
+  half_problem(false, H, ev_o, S_o);
   S.assign(P * P, 0.0);
-  for (int i = 0; i < P; ++i)
-    for (int a = 0; a < P; ++a) S[i * P + a] = Q[i * P + a] / std::sqrt(M[i]);
+  ev.assign(P, 0.0);
+  for (int a = 0; a < NE; ++a) {
+    ev[a] = ev_e[a];
+    for (int r = 0; r < P; ++r) S[r * P + a] = S_e[r * NE + a];
+  }
+  for (int a = 0; a < H; ++a) {
+    ev[NE + a] = ev_o[a];
+    for (int r = 0; r < P; ++r) S[r * P + NE + a] = S_o[r * H + a];
+  }
 }
 
 std::vector<double> box_sizes(const Numbering& nb, const double* xyz) {

@@ -51,7 +51,8 @@ void gather_csr(const Numbering& nb, std::vector<int>& off, std::vector<int>& id
 std::vector<int> patch_table(const Numbering& nb);
 
 // Extended 1D pencil (rows -1..n+1) stiffness K and diagonal mass M, and the
-// generalised eigenpairs K S = M S diag(ev), S^T M S = I; S[row*P + mode].
+// generalised eigenpairs K S = M S diag(ev), S^T M S = I; S[row*P + mode]. The first
+// ceil(P/2) modes are exactly even under the reflection row -> P-1-row, the rest odd.
 void pencil_tables(int n, const std::vector<double>& t, const std::vector<double>& rho,
                    const std::vector<double>& D, std::vector<double>& S, std::vector<double>& ev);
 

@@ -148,53 +148,152 @@ template <> __device__ __forceinline__ const double* geo_of<double>(const DevPro
 template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
 
 // ----------------------------------------------------------------- operator
-// One CTA per element, one thread per GLL node (Algorithm 2): gradient by D,
-// A/B/C by the geometric factors, divergence by D^T, plus lambda m u.
+// D (the GLL differentiation matrix) is centro-antisymmetric, D[n-i][n-m] = -D[i][m], and so
+// is D^T. With v = v_e + v_o split into its even and odd parts under m -> n-m,
+//   a = D v_e is odd, s = D v_o is even:  (D v)[i] = a_i + s_i,  (D v)[n-i] = -a_i + s_i,
+// and a_i, s_i need only the folded half-tables
+//   Fp[i][m] = (D[i][m] + D[i][n-m]) / 2,   Fm[i][m] = (D[i][m] - D[i][n-m]) / 2   (m < h)
+// applied to e_m = v[m] + v[n-m] and o_m = v[m] - v[n-m] (plus the middle column D[i][h]
+// times v[h] when p is odd): about 3/4 of the multiply-adds of the plain product.
+template <int p, typename T>
+struct FoldedD {
+  static constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
+  T Fp[H * H > 0 ? H * H : 1], Fm[HM * H > 0 ? HM * H : 1], Fmid[H > 0 ? H : 1];
+};
+
+// Fill the folded tables of M (M = D for the gradient, D^T for the divergence) from
+// Dhat[i*p + m] = phi_m'(t_i); called by one thread per entry.
+template <int p, typename T>
+__device__ __forceinline__ void fold_fill(FoldedD<p, T>& F, const double* __restrict__ D, bool transpose, int t) {
+  constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
+  constexpr int n = p - 1;
+  auto M = [&](int i, int m) { return transpose ? D[m * p + i] : D[i * p + m]; };
+  if (t < H * H) {
+    const int i = t / H, m = t % H;
+    F.Fp[t] = (T)(0.5 * (M(i, m) + M(i, n - m)));
+  }
+  if (t < HM * H) {
+    const int i = t / H, m = t % H;
+    F.Fm[t] = (T)(0.5 * (M(i, m) - M(i, n - m)));
+  }
+  if (ODD && t < H) F.Fmid[t] = (T)M(t, H);
+}
+
+template <int p, typename T>
+__device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[p], T (&out)[p]) {
+  constexpr int H = p / 2, ODD = p & 1;
+  constexpr int n = p - 1;
+  T e[H], o[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) { e[m] = v[m] + v[n - m]; o[m] = v[m] - v[n - m]; }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T a = ODD ? F.Fmid[i] * v[H] : T(0), sv = 0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      a += F.Fp[i * H + m] * e[m];
+      sv += F.Fm[i * H + m] * o[m];
+    }
+    out[i] = sv + a;
+    out[n - i] = sv - a;
+  }
+  if (ODD) {
+    T sv = 0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) sv += F.Fm[H * H + m] * o[m];
+    out[H] = sv;
+  }
+}
+
+// One CTA of p*p threads per element (Algorithm 2). Thread (x, y) owns the GLL nodes
+// (x, y, k), k = 0..p-1, for the pointwise work, and one line per direction for the
+// contractions: the gradient by D along i (line j=x, k=y), j (i=x, k=y) and k (i=x, j=y),
+// A/B/C by the geometric factors, the divergence by D^T along the same lines, plus
+// lambda m u.
 template <int p, bool RECOMP, typename T>
-__global__ void __launch_bounds__(p * p * p) ax_local_kernel(const DevProblem d, const double* __restrict__ x,
-                                                             T* __restrict__ wl, const PcgState* st) {
+__global__ void __launch_bounds__(p * p) ax_local_kernel(const DevProblem d, const double* __restrict__ x,
+                                                         T* __restrict__ wl, const PcgState* st) {
   if (stopped(st)) return;
-  constexpr int p3 = p * p * p;
-  __shared__ T sD[p * p], su[p3], sA[p3], sB[p3], sC[p3];
+  constexpr int p2 = p * p, p3 = p * p * p;
+  __shared__ FoldedD<p, T> Fg, Fd;
+  __shared__ T su[p3], sA[p3], sB[p3], sC[p3];
   __shared__ T sx[24];
-  const int e = blockIdx.x, t = threadIdx.x;
-  const int i = t % p, j = (t / p) % p, k = t / (p * p);
-  if (t < p * p) sD[t] = (T)d.D[t];
-  if (RECOMP && t < 24) sx[t] = (T)d.exyz[(size_t)e * 24 + t];
-  const int g = d.l2g[(size_t)e * p3 + t];
-  const T u = d.mask[g] ? T(0) : (T)x[g];
-  su[t] = u;
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int tx = tid % p, ty = tid / p;
+  fold_fill<p, T>(Fg, d.D, false, tid);
+  fold_fill<p, T>(Fd, d.D, true, tid);
+  if (RECOMP)
+    for (int q = tid; q < 24; q += p2) sx[q] = (T)d.exyz[(size_t)e * 24 + q];
+  const int* l2ge = d.l2g + (size_t)e * p3;
+  T uk[p], rk[p], line[p], res[p];
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const int g = l2ge[l];
+    uk[k] = d.mask[g] ? T(0) : (T)x[g];
+    su[l] = uk[k];
+  }
   __syncthreads();
-  T ur = 0, us = 0, ut = 0;
+  // gradient: d/dxi on line (j=tx, k=ty), d/deta on line (i=tx, k=ty), d/dzeta on (i=tx, j=ty)
 #pragma unroll
-  for (int m = 0; m < p; ++m) {
-    ur += sD[i * p + m] * su[m + p * (j + p * k)];
-    us += sD[j * p + m] * su[i + p * (m + p * k)];
-    ut += sD[k * p + m] * su[i + p * (j + p * m)];
-  }
-  T G[6], mm;
-  if (!RECOMP) {
-    const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + t;
+  for (int i = 0; i < p; ++i) line[i] = su[i + p * (tx + p * ty)];
+  fold_apply<p, T>(Fg, line, res);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
-    mm = gp[6 * p3];
-  } else {
-    T det;
-    geom_point<T>(sx, (T)d.tg[i], (T)d.tg[j], (T)d.tg[k], (T)(d.rho[i] * d.rho[j] * d.rho[k]), G, mm, det);
-  }
-  sA[t] = G[0] * ur + G[1] * us + G[2] * ut;
-  sB[t] = G[1] * ur + G[3] * us + G[4] * ut;
-  sC[t] = G[2] * ur + G[4] * us + G[5] * ut;
+  for (int i = 0; i < p; ++i) sA[i + p * (tx + p * ty)] = res[i];
+#pragma unroll
+  for (int j = 0; j < p; ++j) line[j] = su[tx + p * (j + p * ty)];
+  fold_apply<p, T>(Fg, line, res);
+#pragma unroll
+  for (int j = 0; j < p; ++j) sB[tx + p * (j + p * ty)] = res[j];
+  fold_apply<p, T>(Fg, uk, res);
+#pragma unroll
+  for (int k = 0; k < p; ++k) sC[tx + p * (ty + p * k)] = res[k];
   __syncthreads();
-  T r = 0;
+  // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
+  const T lam = (T)d.lambda;
 #pragma unroll
-  for (int m = 0; m < p; ++m) {
-    r += sD[m * p + i] * sA[m + p * (j + p * k)];
-    r += sD[m * p + j] * sB[i + p * (m + p * k)];
-    r += sD[m * p + k] * sC[i + p * (j + p * m)];
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const T ur = sA[l], us = sB[l], ut = sC[l];
+    T G[6], mm;
+    if (!RECOMP) {
+      const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + l;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
+      mm = gp[6 * p3];
+    } else {
+      T det;
+      geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
+    }
+    sA[l] = G[0] * ur + G[1] * us + G[2] * ut;
+    sB[l] = G[1] * ur + G[3] * us + G[4] * ut;
+    sC[l] = G[2] * ur + G[4] * us + G[5] * ut;
+    rk[k] = lam * mm * uk[k];
   }
-  r += (T)d.lambda * mm * u;
-  wl[(size_t)e * p3 + t] = r;
+  __syncthreads();
+  // divergence by D^T: the A lines (j=tx, k=ty) into su, then the B lines (i=tx, k=ty)
+  // added into su, then the C line (i=tx, j=ty) and su added in registers
+#pragma unroll
+  for (int i = 0; i < p; ++i) line[i] = sA[i + p * (tx + p * ty)];
+  fold_apply<p, T>(Fd, line, res);
+#pragma unroll
+  for (int i = 0; i < p; ++i) su[i + p * (tx + p * ty)] = res[i];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < p; ++j) line[j] = sB[tx + p * (j + p * ty)];
+  fold_apply<p, T>(Fd, line, res);
+#pragma unroll
+  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] += res[j];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < p; ++k) line[k] = sC[tx + p * (ty + p * k)];
+  fold_apply<p, T>(Fd, line, res);
+  T* out = wl + (size_t)e * p3;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    out[l] = su[l] + res[k] + rk[k];
+  }
 }
 
 template <typename T>
@@ -217,8 +316,63 @@ __global__ void gather_plain_kernel(const DevProblem d, const double* __restrict
 }
 
 // ------------------------------------------------------------ fine Schwarz
-// One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of
-// the extended box in each of the six tensor contractions of Eq. z:
+// 1/d by Newton-Raphson (x <- x (2 - d x)) from the FP32 reciprocal: two steps take the
+// 2^-24 seed error to below FP64 rounding; used for the per-node eigenvalue sums.
+__device__ __forceinline__ double recip(double d) {
+  double x = (double)(1.0f / (float)d);
+  x = x * (2.0 - d * x);
+  x = x * (2.0 - d * x);
+  return x;
+}
+__device__ __forceinline__ float recip(float d) { return 1.0f / d; }
+
+// Even/odd folded 1D contractions with the pencil eigenvectors S (P x P, modes 0..NE-1
+// even and NE..P-1 odd under row -> P-1-row). fwd: modes t = S^T v; bwd: nodes v = S t.
+template <int P, typename T>
+__device__ __forceinline__ void pencil_fwd(const T* __restrict__ S, const T (&v)[P], T (&t)[P]) {
+  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
+  T e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) { e[k] = v[k] + v[P - 1 - k]; o[k] = v[k] - v[P - 1 - k]; }
+#pragma unroll
+  for (int c = 0; c < NE; ++c) {
+    T a = ODD ? S[H * P + c] * v[H] : T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) a += S[k * P + c] * e[k];
+    t[c] = a;
+  }
+#pragma unroll
+  for (int c = NE; c < P; ++c) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) a += S[k * P + c] * o[k];
+    t[c] = a;
+  }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)[P], T (&v)[P]) {
+  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    T E = 0, O = 0;
+#pragma unroll
+    for (int c = 0; c < NE; ++c) E += S[k * P + c] * t[c];
+#pragma unroll
+    for (int c = NE; c < P; ++c) O += S[k * P + c] * t[c];
+    v[k] = E + O;
+    v[P - 1 - k] = E - O;
+  }
+  if (ODD) {
+    T E = 0;
+#pragma unroll
+    for (int c = 0; c < NE; ++c) E += S[H * P + c] * t[c];
+    v[H] = E;
+  }
+}
+
+// One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
+// extended box in each of the six tensor contractions of Eq. z:
 //   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
 //   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
 template <int P, typename T>
@@ -232,9 +386,9 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   sS[tx] = (T)d.S[tx];
   if (tx < P) sev[tx] = (T)d.ev[tx];
   const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
-  const T hx = (T)hxd, hy = (T)hyd, hz = (T)hzd;
+  const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
   const double scale = 8.0 / (hxd * hyd * hzd);
-  T col[P];
+  T col[P], out[P];
   const int* ipe = d.ip + (size_t)e * P3;
 #pragma unroll
   for (int K = 0; K < P; ++K) {
@@ -243,61 +397,45 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   }
   __syncthreads();
   // along K: line (I=x, J=y)
+  pencil_fwd<P, T>(sS, col, out);
 #pragma unroll
-  for (int c = 0; c < P; ++c) {
-    T v = 0;
-#pragma unroll
-    for (int K = 0; K < P; ++K) v += sS[K * P + c] * col[K];
-    s1[x + P * (y + P * c)] = v;
-  }
+  for (int c = 0; c < P; ++c) s1[x + P * (y + P * c)] = out[c];
   __syncthreads();
   // along J: line (I=x, c=y)
 #pragma unroll
-  for (int b = 0; b < P; ++b) {
-    T v = 0;
+  for (int J = 0; J < P; ++J) col[J] = s1[x + P * (J + P * y)];
+  pencil_fwd<P, T>(sS, col, out);
 #pragma unroll
-    for (int J = 0; J < P; ++J) v += sS[J * P + b] * s1[x + P * (J + P * y)];
-    s2[x + P * (b + P * y)] = v;
-  }
+  for (int b = 0; b < P; ++b) s2[x + P * (b + P * y)] = out[b];
   __syncthreads();
   // along I: line (b=x, c=y), eigenvalue scaling, and back along I
+#pragma unroll
+  for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
+  pencil_fwd<P, T>(sS, col, out);
   {
-    T t3[P];
-    const T lb = sev[x] / (hy * hy), lc = sev[y] / (hz * hz), four = 4, lam = (T)d.lambda;
+    const T four = 4, lam = (T)d.lambda;
+    const T lbc = sev[x] * ihy2 + sev[y] * ihz2;
 #pragma unroll
-    for (int a = 0; a < P; ++a) {
-      T v = 0;
-#pragma unroll
-      for (int I = 0; I < P; ++I) v += sS[I * P + a] * s2[I + P * (x + P * y)];
-      t3[a] = v / (four * (sev[a] / (hx * hx) + lb + lc) + lam);
-    }
-#pragma unroll
-    for (int I = 0; I < P; ++I) {
-      T v = 0;
-#pragma unroll
-      for (int a = 0; a < P; ++a) v += sS[I * P + a] * t3[a];
-      s2[I + P * (x + P * y)] = v;
-    }
+    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (sev[a] * ihx2 + lbc) + lam);
   }
+  pencil_bwd<P, T>(sS, out, col);
+#pragma unroll
+  for (int I = 0; I < P; ++I) s2[I + P * (x + P * y)] = col[I];
   __syncthreads();
   // back along J: line (I=x, c=y)
 #pragma unroll
-  for (int J = 0; J < P; ++J) {
-    T v = 0;
+  for (int b = 0; b < P; ++b) out[b] = s2[x + P * (b + P * y)];
+  pencil_bwd<P, T>(sS, out, col);
 #pragma unroll
-    for (int b = 0; b < P; ++b) v += sS[J * P + b] * s2[x + P * (b + P * y)];
-    s1[x + P * (J + P * y)] = v;
-  }
+  for (int J = 0; J < P; ++J) s1[x + P * (J + P * y)] = col[J];
   __syncthreads();
   // back along K: line (I=x, J=y)
-  T* out = wp + (size_t)e * P3;
 #pragma unroll
-  for (int K = 0; K < P; ++K) {
-    T v = 0;
+  for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
+  pencil_bwd<P, T>(sS, out, col);
+  T* outp = wp + (size_t)e * P3;
 #pragma unroll
-    for (int c = 0; c < P; ++c) v += sS[K * P + c] * s1[x + P * (y + P * c)];
-    out[x + P * (y + P * K)] = v;
-  }
+  for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
 }
 
 // ---------------------------------------------------------------- coarse
@@ -671,8 +809,8 @@ cudaError_t launch_ax_local_t(const DevProblem& d, const double* x, T* wl, const
   switch (d.p) {
 #define AX_CASE(P_)                                                                          \
   case P_:                                                                                   \
-    if (d.recompute) ax_local_kernel<P_, true, T><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st); \
-    else ax_local_kernel<P_, false, T><<<d.ne, P_ * P_ * P_, 0, s>>>(d, x, wl, st);            \
+    if (d.recompute) ax_local_kernel<P_, true, T><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);      \
+    else ax_local_kernel<P_, false, T><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);                 \
     ++g_kernel_launches;                                                                     \
     break;
     AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
