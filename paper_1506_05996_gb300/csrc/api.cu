@@ -94,17 +94,22 @@ struct Profiler {
   }
 };
 
-#define PROF(h, name, call)                           \
+#define PROF_ON(h, strm, name, call)                 \
   do {                                                \
-    int pi_ = (h)->prof.begin((h)->stream);           \
+    int pi_ = (h)->prof.begin(strm);                  \
     CK(call);                                         \
-    (h)->prof.end(pi_, name, (h)->stream);            \
+    (h)->prof.end(pi_, name, strm);                   \
   } while (0)
+#define PROF(h, name, call) PROF_ON(h, (h)->stream, name, call)
 
 struct sem_s {
   Profiler prof;
   sem::DevProblem d;
   cudaStream_t stream = nullptr;
+  // The coarse correction runs on a second, high-priority stream concurrently with the
+  // fine patch solves (P = P^c + P^f are independent until they are summed).
+  cudaStream_t coarse_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int flags = 0;
   int precond = SEM_PRECOND_TWO_SCALE;
   sem::Numbering nb;
@@ -220,6 +225,7 @@ int build_coarse(sem_t* h) {
   CK(h->alloc(&d.ctmp, nfree, h->coarse_allocs));
   CK(h->alloc(&d.Rc, nfree, h->coarse_allocs));
   CK(h->alloc(&d.Zc, nfree, h->coarse_allocs));
+  CK(h->alloc(&d.Zc32, nfree, h->coarse_allocs));
   d.nlevels = (int)h->levels.size();
   d.levels = h->levels.data();
   CK(cudaStreamSynchronize(h->stream));
@@ -237,20 +243,33 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   sem::DevProblem& d = h->d;
   const sem::PcgState* st = pcg ? d.st : nullptr;
   int mode = 0;
+  const bool coarse = (which == SEM_PRECOND_TWO_SCALE || which == -1);
+  if (coarse) {
+    if (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty()))
+      return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
+    // fork: restriction and AMG on the coarse stream
+    cudaStream_t cs = h->coarse_stream;
+    CK(cudaEventRecord(h->ev_fork, h->stream));
+    CK(cudaStreamWaitEvent(cs, h->ev_fork, 0));
+    if (d.fp32 && pcg)
+      PROF_ON(h, cs, "coarse_restrict", sem::launch_coarse_restrict_f32(d, d.r32, st, cs));
+    else
+      PROF_ON(h, cs, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, cs));
+    PROF_ON(h, cs, "coarse_amg", sem::launch_coarse_solve(d, st, cs));
+    CK(cudaEventRecord(h->ev_join, cs));
+    mode |= sem::PSUM_COARSE;
+  }
   if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
-    if (d.fp32)
+    if (d.fp32 && pcg)
+      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32_in32(d, d.r32, reinterpret_cast<float*>(d.wp), st,
+                                                                  h->stream));
+    else if (d.fp32)
       PROF(h, "schwarz_local", sem::launch_schwarz_local_f32(d, r, reinterpret_cast<float*>(d.wp), st, h->stream));
     else
       PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
     mode |= sem::PSUM_FINE;
   }
-  if (which == SEM_PRECOND_TWO_SCALE || which == -1) {
-    if (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty()))
-      return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
-    PROF(h, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, h->stream));
-    PROF(h, "coarse_amg", sem::launch_coarse_solve(d, st, h->stream));
-    mode |= sem::PSUM_COARSE;
-  }
+  if (coarse) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));   // join
   if (which == SEM_PRECOND_NONE) mode = sem::PSUM_IDENT;
   PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg, h->stream));
   return SEM_OK;
@@ -368,6 +387,13 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   h->mask_host.assign(nb.G, 0);
   if (!(flags & SEM_NEUMANN)) h->mask_host = nb.boundary;
 
+  {
+    int lo = 0, hi = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CK(cudaStreamCreateWithPriority(&h->coarse_stream, cudaStreamNonBlocking, hi));
+    CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
   sem::DevProblem& d = h->d;
   d.n = n; d.p = p; d.P = P;
   d.ne = (int)nb.ne; d.G = (int)nb.G; d.nv = (int)nb.nv;
@@ -390,6 +416,10 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   UP(ev, ev, double);
   UP(hbox, hbox, double);
   UP(Btab, Btab, double);
+  {
+    std::vector<float> Bt32(Btab.begin(), Btab.end());
+    UP(Btab32, Bt32, float);
+  }
 #undef UP
   CK(h->upload(&h->coords, coords, A));
   CK(h->upload(&h->mask, h->mask_host, A));
@@ -407,6 +437,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->z, (size_t)nb.G, A));
   CK(h->alloc(&h->p, (size_t)nb.G, A));
   CK(h->alloc(&h->f, (size_t)nb.G, A));
+  CK(h->alloc(&d.p32, (size_t)nb.G, A));
+  CK(h->alloc(&d.r32, (size_t)nb.G, A));
   {
     cudaError_t e = cudaMallocHost((void**)&h->st_host, sizeof(sem::PcgState));
     if (e != cudaSuccess) return bail(fail(SEM_ERR_OOM, "cudaMallocHost failed"));
@@ -436,6 +468,12 @@ extern "C" {
 void sem_destroy(sem_t* h) {
   if (h == nullptr) return;
   cudaStreamSynchronize(h->stream);
+  if (h->coarse_stream) {
+    cudaStreamSynchronize(h->coarse_stream);
+    cudaStreamDestroy(h->coarse_stream);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   h->free_list(h->coarse_allocs);
   h->free_list(h->allocs);
   if (h->hist) cudaFree(h->hist);
@@ -565,7 +603,7 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
     for (int c = 0; c < chunk; ++c) {
       if (d.fp32)
-        PROF(h, "ax_local", sem::launch_ax_local_f32(d, h->p, reinterpret_cast<float*>(d.wl), d.st, s));
+        PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, s));
       else
         PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
       PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));

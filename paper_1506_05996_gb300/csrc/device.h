@@ -76,6 +76,7 @@ struct DevProblem {
   const double* ev = nullptr;       // P
   const double* hbox = nullptr;     // ne*3
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
+  const float* Btab32 = nullptr;    // the same in FP32
   const int* ecv = nullptr;
   const int* cv_off = nullptr;
   const int* cv_idx = nullptr;
@@ -94,6 +95,9 @@ struct DevProblem {
   double* Re = nullptr;             // ne*8 element coarse residuals
   double* Rc = nullptr;             // nfree coarse residual
   double* Zc = nullptr;             // nfree coarse correction
+  float* Zc32 = nullptr;            // its FP32 copy (mixed path)
+  float* p32 = nullptr;             // FP32 copies of the PCG direction and residual (mixed path)
+  float* r32 = nullptr;
   double* partial = nullptr;        // reduction partials
   int nblk = 0;                     // blocks of the vector kernels
   PcgState* st = nullptr;
@@ -116,6 +120,8 @@ cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, co
                             cudaStream_t s);
 cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st,
                                 cudaStream_t s);
+cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
+                                     cudaStream_t s);
 // y = gather(wl); masked rows take xin (identity) - sem_apply_A.
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y,
                                    cudaStream_t s);
@@ -129,7 +135,10 @@ cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* w
                                  cudaStream_t s);
 cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
                                      cudaStream_t s);
+cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
+                                          cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
+cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);
 enum PsumMode { PSUM_FINE = 1, PSUM_COARSE = 2, PSUM_BOTH = 3, PSUM_IDENT = 4 };
 // z = mask ? 0 : fine + coarse parts (or r itself with PSUM_IDENT); if pcg: rz reduction

@@ -210,8 +210,8 @@ __device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[
 // contractions: the gradient by D along i (line j=x, k=y), j (i=x, k=y) and k (i=x, j=y),
 // A/B/C by the geometric factors, the divergence by D^T along the same lines, plus
 // lambda m u.
-template <int p, bool RECOMP, typename T>
-__global__ void __launch_bounds__(p * p) ax_local_kernel(const DevProblem d, const double* __restrict__ x,
+template <int p, bool RECOMP, typename T, typename TX>
+__global__ void __launch_bounds__(p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
                                                          T* __restrict__ wl, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
@@ -301,9 +301,9 @@ __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__
                                        const double* __restrict__ xin, double* __restrict__ y) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
-    double s = 0.0;
-    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += (double)wl[d.g2l_idx[q]];
-    y[g] = s;
+    T s = 0;
+    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    y[g] = (double)s;
   }
 }
 
@@ -375,8 +375,8 @@ __device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)
 // extended box in each of the six tensor contractions of Eq. z:
 //   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
 //   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
-template <int P, typename T>
-__global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d, const double* __restrict__ r,
+template <int P, typename T, typename TR>
+__global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
                                                               T* __restrict__ wp, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
@@ -387,13 +387,13 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
   if (tx < P) sev[tx] = (T)d.ev[tx];
   const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
   const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
-  const double scale = 8.0 / (hxd * hyd * hzd);
+  const T scale = (T)(8.0 / (hxd * hyd * hzd));
   T col[P], out[P];
   const int* ipe = d.ip + (size_t)e * P3;
 #pragma unroll
   for (int K = 0; K < P; ++K) {
     const int g = ipe[x + P * (y + P * K)];
-    col[K] = (g >= 0 && !d.mask[g]) ? (T)(r[g] * scale) : T(0);
+    col[K] = (g >= 0 && !d.mask[g]) ? (T)r[g] * scale : T(0);
   }
   __syncthreads();
   // along K: line (I=x, J=y)
@@ -443,26 +443,26 @@ __global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d
 // Phi_K(t_k) r_N; summed over elements this is C m^{-1} r (every node counted once, at
 // its owner). Sum-factorised: one thread per (j, k) line contracts i, then (b0, k) pairs
 // contract j, then the 8 corners contract k.
-template <int p>
-__global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem d, const double* __restrict__ r,
+template <int p, typename T>
+__global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem d, const T* __restrict__ r,
                                                                 const PcgState* st) {
   if (stopped(st)) return;
   constexpr int p3 = p * p * p;
-  __shared__ double sl[2][p * p], sm[2][2][p], phi[2][p];
+  __shared__ T sl[2][p * p], sm[2][2][p], phi[2][p];
   const int e = blockIdx.x, t = threadIdx.x;
   if (t < p) {
-    phi[0][t] = 0.5 * (1.0 - d.tg[t]);
-    phi[1][t] = 0.5 * (1.0 + d.tg[t]);
+    phi[0][t] = (T)(0.5 * (1.0 - d.tg[t]));
+    phi[1][t] = (T)(0.5 * (1.0 + d.tg[t]));
   }
   __syncthreads();
   {   // thread (j, k): contract over i
     const int j = t % p, k = t / p;
-    double a0 = 0.0, a1 = 0.0;
+    T a0 = 0, a1 = 0;
 #pragma unroll
     for (int i = 0; i < p; ++i) {
       const int l = i + p * (j + p * k), gl = e * p3 + l;
       const int g = d.l2g[gl];
-      const double v = (d.owner[g] == gl && !d.mask[g]) ? r[g] : 0.0;
+      const T v = (d.owner[g] == gl && !d.mask[g]) ? r[g] : T(0);
       a0 += phi[0][i] * v;
       a1 += phi[1][i] * v;
     }
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem
   __syncthreads();
   if (t < 2 * p) {   // thread (b0, k): contract over j
     const int b0 = t / p, k = t % p;
-    double c0 = 0.0, c1 = 0.0;
+    T c0 = 0, c1 = 0;
 #pragma unroll
     for (int j = 0; j < p; ++j) {
       c0 += phi[0][j] * sl[b0][j + p * k];
@@ -484,10 +484,10 @@ __global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem
   __syncthreads();
   if (t < 8) {   // VTK corner t: contract over k
     const int b0 = (t == 1 || t == 2 || t == 5 || t == 6), b1 = (t == 2 || t == 3 || t == 6 || t == 7), b2 = (t >= 4);
-    double v = 0.0;
+    T v = 0;
 #pragma unroll
     for (int k = 0; k < p; ++k) v += phi[b2][k] * sm[b0][b1][k];
-    d.Re[(size_t)e * 8 + t] = v;
+    d.Re[(size_t)e * 8 + t] = (double)v;
   }
 }
 
@@ -577,33 +577,46 @@ __global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const do
 }
 
 // ------------------------------------------------------------ P sum and PCG
+template <typename T> __device__ __forceinline__ const T* btab_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* btab_of<double>(const DevProblem& d) { return d.Btab; }
+template <> __device__ __forceinline__ const float* btab_of<float>(const DevProblem& d) { return d.Btab32; }
+template <typename T> __device__ __forceinline__ const T* zc_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* zc_of<double>(const DevProblem& d) { return d.Zc; }
+template <> __device__ __forceinline__ const float* zc_of<float>(const DevProblem& d) { return d.Zc32; }
+
+// z = P r on the free nodes: the patch results summed over every patch containing the
+// node (fine part) plus the trilinear interpolation of the coarse correction at the node
+// (coarse part, Eq. coarse), accumulated in T; with PCG also z.r and beta (FP64).
 template <bool PCG, typename T>
 __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const T* __restrict__ wp,
                                                          const double* __restrict__ r, double* __restrict__ z) {
   if (PCG && stopped(d.st)) return;
   const int p = d.p, p3 = p * p * p;
+  const T* __restrict__ Bt = btab_of<T>(d);
+  const T* __restrict__ Zc = zc_of<T>(d);
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    double v = 0.0;
+    T v = 0;
     if (!d.mask[g]) {
-      if (mode & PSUM_IDENT) v += r[g];
+      if (mode & PSUM_IDENT) v += (T)r[g];
       if (mode & PSUM_FINE)
-        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += (double)wp[d.pg_idx[q]];
+        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += wp[d.pg_idx[q]];
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
         const int l = d.owner[g], e = l / p3, lr = l % p3;
         const int* ec = d.ecv + (size_t)e * 8;
-        const double* B = d.Btab + 8 * lr;
-        double zc = 0.0;
+        const T* B = Bt + 8 * lr;
+        T zc = 0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int cv = ec[c];
-          if (cv >= 0) zc += B[c] * d.Zc[cv];
+          if (cv >= 0) zc += B[c] * Zc[cv];
         }
         v += zc;
       }
     }
-    z[g] = v;
-    if (PCG) dot += v * r[g];
+    const double vd = (double)v;
+    z[g] = vd;
+    if (PCG) dot += vd * r[g];
   }
   if (PCG) {
     double total;
@@ -616,6 +629,11 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
 }
 
+__global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __restrict__ b, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (float)a[i];
+}
+
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
                                                              double rtol, int maxit, int mixed, double* hist) {
@@ -623,6 +641,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
     r[g] = v;
+    if (mixed) d.r32[g] = (float)v;
     u[g] = 0.0;
     dot += v * v;
   }
@@ -650,7 +669,11 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
 
 __global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
   if (stopped(d.st)) return;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) p[g] = z[g];
+  float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    p[g] = z[g];
+    if (p32) p32[g] = (float)z[g];
+  }
 }
 
 template <typename T>
@@ -660,11 +683,12 @@ __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevPr
   if (stopped(d.st)) return;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     if (!d.mask[g])
-      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += (double)wl[d.g2l_idx[q]];
-    f[g] = s;
-    dot += p[g] * s;
+      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    const double sd = (double)s;
+    f[g] = sd;
+    dot += p[g] * sd;
   }
   double total;
   if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
@@ -680,11 +704,13 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
                                                                double* __restrict__ r, double* hist) {
   if (stopped(d.st)) return;
   const double alpha = d.st->alpha;
+  float* __restrict__ r32 = d.st->mixed ? d.r32 : nullptr;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     u[g] = u[g] + alpha * p[g];
     const double rn = r[g] - alpha * f[g];
     r[g] = rn;
+    if (r32) r32[g] = (float)rn;
     dot += rn * rn;
   }
   double total;
@@ -718,6 +744,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem
       res = b[g] - s;
     }
     r[g] = res;
+    d.r32[g] = (float)res;
     dot += res * res;
   }
   double total;
@@ -738,7 +765,12 @@ __global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem
 __global__ void pcg_direction_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
   if (stopped(d.st)) return;
   const double beta = d.st->beta;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) p[g] = z[g] + beta * p[g];
+  float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    const double pn = z[g] + beta * p[g];
+    p[g] = pn;
+    if (p32) p32[g] = (float)pn;
+  }
 }
 
 __global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProblem d, const double* __restrict__ b,
@@ -804,14 +836,14 @@ cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_o
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_ax_local_t(const DevProblem& d, const double* x, T* wl, const PcgState* st, cudaStream_t s) {
+template <typename T, typename TX>
+cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
   switch (d.p) {
-#define AX_CASE(P_)                                                                          \
-  case P_:                                                                                   \
-    if (d.recompute) ax_local_kernel<P_, true, T><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);      \
-    else ax_local_kernel<P_, false, T><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);                 \
-    ++g_kernel_launches;                                                                     \
+#define AX_CASE(P_)                                                                           \
+  case P_:                                                                                    \
+    if (d.recompute) ax_local_kernel<P_, true, T, TX><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);   \
+    else ax_local_kernel<P_, false, T, TX><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);              \
+    ++g_kernel_launches;                                                                      \
     break;
     AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
 #undef AX_CASE
@@ -821,10 +853,14 @@ cudaError_t launch_ax_local_t(const DevProblem& d, const double* x, T* wl, const
 }
 
 cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<double>(d, x, wl, st, s);
+  return launch_ax_local_t<double, double>(d, x, wl, st, s);
 }
 cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<float>(d, x, wl, st, s);
+  return launch_ax_local_t<float, double>(d, x, wl, st, s);
+}
+cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
+                                     cudaStream_t s) {
+  return launch_ax_local_t<float, float>(d, x, wl, st, s);
 }
 
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
@@ -845,10 +881,10 @@ cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_schwarz_local_t(const DevProblem& d, const double* r, T* wp, const PcgState* st, cudaStream_t s) {
+template <typename T, typename TR>
+cudaError_t launch_schwarz_local_t(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
   switch (d.P) {
-#define SW_CASE(P_) case P_: schwarz_local_kernel<P_, T><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
+#define SW_CASE(P_) case P_: schwarz_local_kernel<P_, T, TR><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
     SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
 #undef SW_CASE
     default: return cudaErrorInvalidValue;
@@ -856,17 +892,22 @@ cudaError_t launch_schwarz_local_t(const DevProblem& d, const double* r, T* wp, 
   return cudaGetLastError();
 }
 cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
-  return launch_schwarz_local_t<double>(d, r, wp, st, s);
+  return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
 }
 cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
                                      cudaStream_t s) {
-  return launch_schwarz_local_t<float>(d, r, wp, st, s);
+  return launch_schwarz_local_t<float, double>(d, r, wp, st, s);
+}
+cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
+                                          cudaStream_t s) {
+  return launch_schwarz_local_t<float, float>(d, r, wp, st, s);
 }
 
-cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_coarse_restrict_t(const DevProblem& d, const T* r, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
   switch (d.p) {
-#define RS_CASE(P_) case P_: coarse_restrict_kernel<P_><<<d.ne, P_ * P_, 0, s>>>(d, r, st); ++g_kernel_launches; break;
+#define RS_CASE(P_) case P_: coarse_restrict_kernel<P_, T><<<d.ne, P_ * P_, 0, s>>>(d, r, st); ++g_kernel_launches; break;
     RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6) RS_CASE(7) RS_CASE(8) RS_CASE(9)
 #undef RS_CASE
     default: return cudaErrorInvalidValue;
@@ -875,12 +916,25 @@ cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const P
   ++g_kernel_launches;
   return cudaGetLastError();
 }
+cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s) {
+  return launch_coarse_restrict_t<double>(d, r, st, s);
+}
+cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s) {
+  return launch_coarse_restrict_t<float>(d, r, st, s);
+}
 
 // Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
   cudaError_t err = vcycle(d, 0, d.Rc, d.Zc, st, s);
-  if (err != cudaSuccess || d.nlevels == 0) return err;
+  if (err != cudaSuccess) return err;
+  if (d.nlevels == 0) {
+    if (d.fp32) {
+      to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
+      ++g_kernel_launches;
+    }
+    return cudaGetLastError();
+  }
   const DevCsr& A0 = d.levels[0].A;
   const int gb = grid_for(A0.n, 256, 4096), gw = grid_for(32 * A0.n, 256, 8192);
   for (int c = 1; c < kCycles; ++c) {
@@ -889,6 +943,10 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
     err = vcycle(d, 0, d.cres, d.ctmp, st, s);
     if (err != cudaSuccess) return err;
     add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
+    ++g_kernel_launches;
+  }
+  if (d.fp32) {
+    to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
     ++g_kernel_launches;
   }
   return cudaGetLastError();
