@@ -176,6 +176,41 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Ranks:
+    """Replica bookkeeping under torchrun: one problem per rank, no data-path collective;
+    only the timing barrier and the max over ranks use the process group."""
+
+    def __init__(self, backend=None, device=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.device = device
+        if self.world > 1 and not dist.is_initialized():
+            kw = {"device_id": device} if (backend == "nccl" and device is not None) else {}
+            dist.init_process_group(backend, **kw)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.world == 1:
+            return float(v)
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device if self.device is not None else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def total_rate(self, units_per_rank, seconds_max):
+        """Whole-job throughput: units processed by all ranks / the slowest rank's time."""
+        return self.world * units_per_rank / seconds_max
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
 def schwarz_flops(n, ne):
     """Six (n+3)^4 tensor contractions (FMA = 2 flops) plus the paper's 15 (n+3)^3 term."""
     P = n + 3
@@ -195,23 +230,11 @@ def run_gpu(args):
     from synth import lattice_hex_mesh, manufactured_s
     from paper_1506_05996_gb300 import sem as S
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", torch.device("cuda", local))
+    world, rank = ranks.world, ranks.rank
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     peaks = {}
     try:
@@ -268,7 +291,7 @@ def run_gpu(args):
     t_local = sum(a.elapsed_time(bv) for a, bv in ev) / 1e3
     t_steps = max_over_ranks(t_local)
     per_step = t_steps / args.steps
-    value = world * G / per_step / 1e9
+    value = ranks.total_rate(G, per_step) / 1e9
     launches = sum(v[0] for v in prof.values())
 
     # dominant kernel over the timed region and its roofline
@@ -408,8 +431,7 @@ def run_gpu(args):
         }
         print(json.dumps(line), flush=True)
     prob.close()
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def run_kernel_case(E):
