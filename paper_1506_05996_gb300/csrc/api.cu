@@ -1,5 +1,6 @@
 // C ABI (include/sem.h): handle creation, uploads, operator/preconditioner
 // applications and the PCG driver of Algorithm 1.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -28,9 +29,34 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+// One PCG iteration (preconditioner, direction, operator, alpha, update) captured as a
+// CUDA graph and replayed once per iteration; with profiling on, its timing events are
+// graph nodes read back after each replay.
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  long key = -1;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> pair_id, pair_idx;
+  std::vector<uint64_t> pair_kernels;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key = -1;
+    for (auto e : events) cudaEventDestroy(e);
+    events.clear();
+    pair_id.clear();
+    pair_idx.clear();
+    pair_kernels.clear();
+  }
+  ~IterGraph() { reset(); }
+};
+
+constexpr int kGraphBase = 1 << 28;
+
 // Per-kernel timing with CUDA events recorded on the handle's stream around each
 // launch (enabled by sem_profile); accumulated when the stream is synchronised.
 struct Profiler {
+  IterGraph* cap = nullptr;   // set while an iteration graph is being captured
   bool on = false;
   std::vector<cudaEvent_t> pool;
   std::vector<std::pair<int, int>> pending;   // (kernel id, first event index)
@@ -51,6 +77,16 @@ struct Profiler {
   }
   int begin(cudaStream_t s) {
     if (!on) return -1;
+    if (cap != nullptr) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return -1;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
+      cap->events.push_back(a);
+      cap->events.push_back(b);
+      cudaEventRecord(a, s);
+      count_at_begin = sem::kernel_launch_count();
+      return kGraphBase + (int)cap->events.size() - 2;
+    }
     while ((int)pool.size() < next + 2) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return -1;
@@ -64,6 +100,14 @@ struct Profiler {
   }
   void end(int i, const char* name, cudaStream_t s) {
     if (i < 0) return;
+    if (i >= kGraphBase) {
+      const int k = i - kGraphBase;
+      cudaEventRecord(cap->events[k + 1], s);
+      cap->pair_id.push_back(id(name));
+      cap->pair_idx.push_back(k);
+      cap->pair_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
+      return;
+    }
     cudaEventRecord(pool[i + 1], s);
     pending.emplace_back(id(name), i);
     pending_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
@@ -80,6 +124,15 @@ struct Profiler {
     pending.clear();
     pending_kernels.clear();
     next = 0;
+  }
+  void collect_graph(const IterGraph& g) {   // after a replay has completed
+    for (size_t q = 0; q < g.pair_id.size(); ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, g.events[g.pair_idx[q]], g.events[g.pair_idx[q] + 1]) == cudaSuccess) {
+        total_ms[g.pair_id[q]] += ms;
+        launches[g.pair_id[q]] += (int64_t)g.pair_kernels[q];
+      }
+    }
   }
   void reset() {
     pending.clear();
@@ -124,7 +177,8 @@ struct sem_s {
   float* geo32 = nullptr;
   int precision = SEM_PREC_FP64;
   uint8_t* mask = nullptr;
-  double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
+  IterGraph graph;
   double* hist = nullptr;
   int hist_cap = 0;
   sem::PcgState* st_host = nullptr;  // pinned
@@ -155,6 +209,7 @@ namespace {
 // the mask changes.
 int build_coarse(sem_t* h) {
   cudaStreamSynchronize(h->stream);
+  h->graph.reset();
   h->free_list(h->coarse_allocs);
   h->levels.clear();
   sem::DevProblem& d = h->d;
@@ -437,6 +492,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->z, (size_t)nb.G, A));
   CK(h->alloc(&h->p, (size_t)nb.G, A));
   CK(h->alloc(&h->f, (size_t)nb.G, A));
+  CK(h->alloc(&h->u, (size_t)nb.G, A));
   CK(h->alloc(&d.p32, (size_t)nb.G, A));
   CK(h->alloc(&d.r32, (size_t)nb.G, A));
   {
@@ -472,6 +528,7 @@ void sem_destroy(sem_t* h) {
     cudaStreamSynchronize(h->coarse_stream);
     cudaStreamDestroy(h->coarse_stream);
   }
+  h->graph.reset();
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   h->free_list(h->coarse_allocs);
@@ -586,48 +643,93 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
   sem::DevProblem& d = h->d;
   if (maxit + 1 > h->hist_cap) {
+    h->graph.reset();
     if (h->hist) cudaFree(h->hist);
     h->hist = nullptr;
     h->hist_cap = 0;
-    CK(cudaMalloc((void**)&h->hist, sizeof(double) * (maxit + 1)));
-    h->hist_cap = maxit + 1;
+    const int cap = std::max(maxit + 1, 1024);
+    CK(cudaMalloc((void**)&h->hist, sizeof(double) * cap));
+    h->hist_cap = cap;
   }
   cudaStream_t s = h->stream;
-  double* u = x_dev;
-  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
+  double* u = h->u;
   const int mixed = d.fp32 ? 1 : 0;
+
+  // operator, alpha and update of one iteration (Algorithm 1), then the stop test on the host
+  auto enqueue_head = [&]() -> int {
+    if (d.fp32)
+      PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, s));
+    else
+      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
+    PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
+    PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
+    return SEM_OK;
+  };
+  // preconditioner and new direction, then the next iteration's head
+  auto enqueue_tail_head = [&]() -> int {
+    if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
+    PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, s));
+    return enqueue_head();
+  };
+  auto read_state = [&]() -> int {
+    CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return SEM_OK;
+  };
+
+  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
   PROF(h, "pcg_init", sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, mixed, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
-  const int chunk = 1;   // iterations between host checks of the device-side stop flag
-  for (int done_iters = 0; done_iters <= maxit; done_iters += chunk) {
-    for (int c = 0; c < chunk; ++c) {
-      if (d.fp32)
-        PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, s));
-      else
-        PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
-      PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
-      PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
-      if (mixed) {
-        // the update decided whether r must be recomputed with the FP64 operator
-        CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (h->st_host->done) break;
-        if (h->st_host->replace) {
-          PROF(h, "ax_local_fp64", sem::launch_ax_local(d, u, d.wl, d.st, s));
-          PROF(h, "pcg_replace", sem::launch_pcg_replace(d, b_dev, d.wl, h->r, h->hist, s));
-        }
-      }
-      if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
-      PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, s));
+  if (int rc = enqueue_head()) return rc;
+
+  // capture the steady-state iteration once per configuration
+  const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3);
+  if (h->graph.key != key) {
+    h->graph.reset();
+    CK(cudaStreamSynchronize(s));
+    if (h->prof.on) h->prof.collect();
+    h->prof.cap = h->prof.on ? &h->graph : nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    int rc = (e == cudaSuccess) ? enqueue_tail_head() : SEM_ERR_CUDA;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    h->prof.cap = nullptr;
+    if (rc != SEM_OK || e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      h->graph.reset();
+      return rc != SEM_OK ? rc : fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
+    e = cudaGraphInstantiate(&h->graph.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph.reset();
+      return fail(SEM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    h->graph.key = key;
+  }
+
+  bool graph_pending = false;   // the last launch was a graph replay whose events are unread
+  for (int guard = 0; guard <= maxit + 1; ++guard) {
     CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (graph_pending && h->prof.on) h->prof.collect_graph(h->graph);
+    graph_pending = false;
     if (h->st_host->done) break;
+    if (mixed && h->st_host->replace) {
+      // the recursive residual is replaced by b - A u with the FP64 operator
+      PROF(h, "ax_local_fp64", sem::launch_ax_local(d, u, d.wl, d.st, s));
+      PROF(h, "pcg_replace", sem::launch_pcg_replace(d, b_dev, d.wl, h->r, h->hist, s));
+      if (int rc = read_state()) return rc;
+      if (h->st_host->done) break;
+    }
+    CK(cudaGraphLaunch(h->graph.exec, s));
+    graph_pending = true;
   }
-  // true residual ||b - A u|| / ||b|| on the free nodes
+  // true residual ||b - A u|| / ||b|| on the free nodes, and the solution out
   PROF(h, "ax_local", sem::launch_ax_local(d, u, d.wl, nullptr, s));
   PROF(h, "true_residual", sem::launch_true_residual(d, b_dev, d.wl, s));
+  CK(cudaMemcpyAsync(x_dev, u, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   h->prof.collect();
