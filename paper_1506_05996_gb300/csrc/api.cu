@@ -162,6 +162,7 @@ struct sem_s {
   // The coarse correction runs on a second, high-priority stream concurrently with the
   // fine patch solves (P = P^c + P^f are independent until they are summed).
   cudaStream_t coarse_stream = nullptr;
+  cudaStream_t capture_stream = nullptr;   // graphs are captured here (not on a legacy stream)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int flags = 0;
   int precond = SEM_PRECOND_TWO_SCALE;
@@ -446,6 +447,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
     int lo = 0, hi = 0;
     CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     CK(cudaStreamCreateWithPriority(&h->coarse_stream, cudaStreamNonBlocking, hi));
+    CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
   }
@@ -529,6 +531,10 @@ void sem_destroy(sem_t* h) {
     cudaStreamDestroy(h->coarse_stream);
   }
   h->graph.reset();
+  if (h->capture_stream) {
+    cudaStreamSynchronize(h->capture_stream);
+    cudaStreamDestroy(h->capture_stream);
+  }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   h->free_list(h->coarse_allocs);
@@ -655,20 +661,22 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   double* u = h->u;
   const int mixed = d.fp32 ? 1 : 0;
 
-  // operator, alpha and update of one iteration (Algorithm 1), then the stop test on the host
+  // operator, alpha and update of one iteration (Algorithm 1), then the stop test on the host;
+  // work goes to h->stream (switched to the capture stream while capturing)
   auto enqueue_head = [&]() -> int {
+    cudaStream_t q = h->stream;
     if (d.fp32)
-      PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, s));
+      PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, q));
     else
-      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, s));
-    PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, s));
-    PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, s));
+      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, q));
+    PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, q));
+    PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, q));
     return SEM_OK;
   };
   // preconditioner and new direction, then the next iteration's head
   auto enqueue_tail_head = [&]() -> int {
     if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
-    PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, s));
+    PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, h->stream));
     return enqueue_head();
   };
   auto read_state = [&]() -> int {
@@ -691,14 +699,17 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
     if (h->prof.on) h->prof.collect();
     h->prof.cap = h->prof.on ? &h->graph : nullptr;
     cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    int rc = (e == cudaSuccess) ? enqueue_tail_head() : SEM_ERR_CUDA;
-    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    h->stream = h->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    int rc = (e == cudaSuccess) ? enqueue_tail_head() : SEM_OK;
+    cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(h->stream, &g) : cudaSuccess;
+    h->stream = s;
     h->prof.cap = nullptr;
     if (rc != SEM_OK || e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       h->graph.reset();
-      return rc != SEM_OK ? rc : fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      if (rc != SEM_OK) return rc;
+      return fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
     e = cudaGraphInstantiate(&h->graph.exec, g, 0);
     cudaGraphDestroy(g);
