@@ -83,7 +83,8 @@ struct Profiler {
       if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
       cap->events.push_back(a);
       cap->events.push_back(b);
-      cudaEventRecord(a, s);
+      // an external record becomes an event-record node, whose times can be read back
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
       count_at_begin = sem::kernel_launch_count();
       return kGraphBase + (int)cap->events.size() - 2;
     }
@@ -102,7 +103,7 @@ struct Profiler {
     if (i < 0) return;
     if (i >= kGraphBase) {
       const int k = i - kGraphBase;
-      cudaEventRecord(cap->events[k + 1], s);
+      cudaEventRecordWithFlags(cap->events[k + 1], s, cudaEventRecordExternal);
       cap->pair_id.push_back(id(name));
       cap->pair_idx.push_back(k);
       cap->pair_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
@@ -131,6 +132,8 @@ struct Profiler {
       if (cudaEventElapsedTime(&ms, g.events[g.pair_idx[q]], g.events[g.pair_idx[q] + 1]) == cudaSuccess) {
         total_ms[g.pair_id[q]] += ms;
         launches[g.pair_id[q]] += (int64_t)g.pair_kernels[q];
+      } else {
+        cudaGetLastError();   // a timing failure must not look like a later launch failure
       }
     }
   }
