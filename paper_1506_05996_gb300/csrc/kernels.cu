@@ -737,13 +737,14 @@ struct AmgArgs {
   const PcgState* st;
 };
 
-// x is written by other CTAs of the cluster between phases: plain (coherent) loads, no
-// __restrict__ that would allow the non-coherent read-only path.
-__device__ __forceinline__ double csr_row_dot(const DevCsr& A, int row, const double* x, int lane) {
+// One thread per row, entries in CSR order (many independent row chains keep the loads
+// of the few SMs in flight). x is written by other CTAs of the cluster between phases:
+// plain (coherent) loads, no __restrict__ that would allow the non-coherent path.
+__device__ __forceinline__ double csr_row(const DevCsr& A, int row, const double* x) {
   double s = 0.0;
-  for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += 32) s += A.val[q] * x[A.col[q]];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const int q1 = A.ptr[row + 1];
+#pragma unroll 4
+  for (int q = A.ptr[row]; q < q1; ++q) s += A.val[q] * x[A.col[q]];
   return s;
 }
 
@@ -764,16 +765,10 @@ __global__ void __cluster_dims__(kAmgCluster, 1, 1) __launch_bounds__(kAmgBlock)
       const DevAmgLevel& L = a.lv[l];
       for (int i = gt; i < L.A.n; i += nthr) L.x[i] = omega * L.dinv[i] * b[i];
       cl.sync();
-      for (int i = gw; i < L.A.n; i += nwarp) {
-        const double sdot = csr_row_dot(L.A, i, L.x, lane);
-        if (lane == 0) L.t[i] = b[i] - sdot;
-      }
+      for (int i = gt; i < L.A.n; i += nthr) L.t[i] = b[i] - csr_row(L.A, i, L.x);
       cl.sync();
       double* bc = (l + 1 == a.nlevels) ? a.cb : a.lv[l + 1].b;
-      for (int i = gw; i < L.R.n; i += nwarp) {
-        const double sdot = csr_row_dot(L.R, i, L.t, lane);
-        if (lane == 0) bc[i] = sdot;
-      }
+      for (int i = gt; i < L.R.n; i += nthr) bc[i] = csr_row(L.R, i, L.t);
       cl.sync();
       b = bc;
     }
@@ -792,16 +787,10 @@ __global__ void __cluster_dims__(kAmgCluster, 1, 1) __launch_bounds__(kAmgBlock)
       const DevAmgLevel& L = a.lv[l];
       const double* xc = (l + 1 == a.nlevels) ? a.cx : a.lv[l + 1].y;
       const double* bl = (l == 0) ? b0 : L.b;
-      for (int i = gw; i < L.P.n; i += nwarp) {
-        const double sdot = csr_row_dot(L.P, i, xc, lane);
-        if (lane == 0) L.x[i] = L.x[i] + sdot;
-      }
+      for (int i = gt; i < L.P.n; i += nthr) L.x[i] = L.x[i] + csr_row(L.P, i, xc);
       cl.sync();
       double* out = (l == 0) ? out0 : L.y;
-      for (int i = gw; i < L.A.n; i += nwarp) {
-        const double sdot = csr_row_dot(L.A, i, L.x, lane);
-        if (lane == 0) out[i] = L.x[i] + omega * L.dinv[i] * (bl[i] - sdot);
-      }
+      for (int i = gt; i < L.A.n; i += nthr) out[i] = L.x[i] + omega * L.dinv[i] * (bl[i] - csr_row(L.A, i, L.x));
       cl.sync();
     }
   };
@@ -810,10 +799,7 @@ __global__ void __cluster_dims__(kAmgCluster, 1, 1) __launch_bounds__(kAmgBlock)
   if (a.nlevels > 0) {
     const DevCsr& A0 = a.lv[0].A;
     for (int c = 1; c < kCycles; ++c) {
-      for (int i = gw; i < A0.n; i += nwarp) {
-        const double sdot = csr_row_dot(A0, i, a.zc, lane);
-        if (lane == 0) a.cres[i] = a.rc[i] - sdot;
-      }
+      for (int i = gt; i < A0.n; i += nthr) a.cres[i] = a.rc[i] - csr_row(A0, i, a.zc);
       cl.sync();
       vcycle(a.cres, a.ctmp);
       for (int i = gt; i < A0.n; i += nthr) a.zc[i] += a.ctmp[i];
