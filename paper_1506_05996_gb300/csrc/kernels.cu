@@ -15,8 +15,6 @@
 // in index order (no spin-waits: a completion counter decides the last block).
 #include <cmath>
 
-#include <cooperative_groups.h>
-
 #include "device.h"
 
 namespace sem {
@@ -502,6 +500,82 @@ __global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
   }
 }
 
+// AMG kernels. Sparse rows are handled by one warp each (lanes stride over the
+// row, then a fixed shuffle tree), so long coarse-level rows do not serialise.
+__global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const double* __restrict__ b,
+                                   double* __restrict__ x, double omega, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = omega * dinv[i] * b[i];
+}
+
+__device__ __forceinline__ double warp_row_dot(const DevCsr& A, int row, const double* __restrict__ x, int lane) {
+  double s = 0.0;
+  for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += 32) s += A.val[q] * x[A.col[q]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+#define WARP_ROWS(nrows)                                                              \
+  const int lane = threadIdx.x & 31;                                                  \
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (nrows); i += (gridDim.x * blockDim.x) >> 5)
+
+__global__ void amg_resid_kernel(DevCsr A, const double* __restrict__ b, const double* __restrict__ x,
+                                 double* __restrict__ t, const PcgState* st) {
+  if (stopped(st)) return;
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) t[i] = b[i] - s;
+  }
+}
+
+__global__ void amg_spmv_kernel(DevCsr A, const double* __restrict__ x, double* __restrict__ y, const PcgState* st) {
+  if (stopped(st)) return;
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) y[i] = s;
+  }
+}
+
+__global__ void amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc, double* __restrict__ x,
+                                       const PcgState* st) {
+  if (stopped(st)) return;
+  WARP_ROWS(P.n) {
+    const double s = warp_row_dot(P, i, xc, lane);
+    if (lane == 0) x[i] = x[i] + s;
+  }
+}
+
+__global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv, const double* __restrict__ b,
+                                       const double* __restrict__ x, double* __restrict__ xout, double omega,
+                                       const PcgState* st) {
+  if (stopped(st)) return;
+  WARP_ROWS(A.n) {
+    const double s = warp_row_dot(A, i, x, lane);
+    if (lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
+  }
+}
+#undef WARP_ROWS
+
+__global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + y[i];
+}
+
+// x = Ainv b, one warp per row (dense coarsest level).
+__global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const double* __restrict__ b,
+                                double* __restrict__ x, const PcgState* st) {
+  if (stopped(st)) return;
+  const int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += Ainv[(size_t)row * n + c] * b[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = s;
+  }
+}
+
 // ------------------------------------------------------------ P sum and PCG
 template <typename T> __device__ __forceinline__ const T* btab_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* btab_of<double>(const DevProblem& d) { return d.Btab; }
@@ -555,6 +629,10 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
 }
 
+__global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __restrict__ b, const PcgState* st) {
+  if (stopped(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (float)a[i];
+}
 
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
@@ -717,99 +795,31 @@ inline int grid_for(int n, int block, int cap) {
 constexpr double kOmega = 2.0 / 3.0;
 constexpr int kCycles = 3;
 
-// The whole coarse solve P_0 (kCycles stationary V(1,1) cycles) in one launch of one
-// thread-block cluster: the CTAs of a cluster are co-scheduled by the hardware, so the
-// phases of the cycle are separated by the cluster barrier (barrier.cluster with
-// release/acquire ordering of the global-memory writes). Sparse rows are handled by one
-// warp each over all warps of the cluster. The cluster occupies kAmgCluster SMs and
-// runs beside the patch solves of the fine preconditioner.
-constexpr int kAmgCluster = 8, kAmgBlock = 1024, kMaxAmgLevels = 12;
-
-struct AmgArgs {
-  int nlevels, nc;
-  DevAmgLevel lv[kMaxAmgLevels];
-  const double* cinv;
-  double *cb, *cx;
-  const double* rc;      // coarse right-hand side
-  double* zc;            // P_0 rc
-  double *cres, *ctmp;
-  float* zc32;           // FP32 copy of zc, or nullptr
-  const PcgState* st;
-};
-
-// One thread per row, entries in CSR order (many independent row chains keep the loads
-// of the few SMs in flight). x is written by other CTAs of the cluster between phases:
-// plain (coherent) loads, no __restrict__ that would allow the non-coherent path.
-__device__ __forceinline__ double csr_row(const DevCsr& A, int row, const double* x) {
-  double s = 0.0;
-  const int q1 = A.ptr[row + 1];
-#pragma unroll 4
-  for (int q = A.ptr[row]; q < q1; ++q) s += A.val[q] * x[A.col[q]];
-  return s;
-}
-
-__global__ void __cluster_dims__(kAmgCluster, 1, 1) __launch_bounds__(kAmgBlock)
-    amg_cluster_kernel(const AmgArgs a) {
-  if (stopped(a.st)) return;
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int nthr = kAmgCluster * kAmgBlock;
-  const int gt = (int)cl.block_rank() * kAmgBlock + threadIdx.x;
-  const int nwarp = nthr / 32, gw = gt / 32, lane = threadIdx.x & 31;
-  const double omega = kOmega;
-
-  // one V(1,1) cycle: right-hand side b0 at level 0, result into out0
-  auto vcycle = [&](const double* b0, double* out0) {
-    const double* b = b0;
-    for (int l = 0; l < a.nlevels; ++l) {          // down: pre-smooth, residual, restrict
-      const DevAmgLevel& L = a.lv[l];
-      for (int i = gt; i < L.A.n; i += nthr) L.x[i] = omega * L.dinv[i] * b[i];
-      cl.sync();
-      for (int i = gt; i < L.A.n; i += nthr) L.t[i] = b[i] - csr_row(L.A, i, L.x);
-      cl.sync();
-      double* bc = (l + 1 == a.nlevels) ? a.cb : a.lv[l + 1].b;
-      for (int i = gt; i < L.R.n; i += nthr) bc[i] = csr_row(L.R, i, L.t);
-      cl.sync();
-      b = bc;
-    }
-    {                                              // coarsest: dense inverse
-      double* out = (a.nlevels == 0) ? out0 : a.cx;
-      for (int row = gw; row < a.nc; row += nwarp) {
-        double sdot = 0.0;
-        for (int c = lane; c < a.nc; c += 32) sdot += a.cinv[(size_t)row * a.nc + c] * b[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
-        if (lane == 0) out[row] = sdot;
-      }
-      cl.sync();
-    }
-    for (int l = a.nlevels - 1; l >= 0; --l) {     // up: prolong, post-smooth
-      const DevAmgLevel& L = a.lv[l];
-      const double* xc = (l + 1 == a.nlevels) ? a.cx : a.lv[l + 1].y;
-      const double* bl = (l == 0) ? b0 : L.b;
-      for (int i = gt; i < L.P.n; i += nthr) L.x[i] = L.x[i] + csr_row(L.P, i, xc);
-      cl.sync();
-      double* out = (l == 0) ? out0 : L.y;
-      for (int i = gt; i < L.A.n; i += nthr) out[i] = L.x[i] + omega * L.dinv[i] * (bl[i] - csr_row(L.A, i, L.x));
-      cl.sync();
-    }
-  };
-
-  vcycle(a.rc, a.zc);
-  if (a.nlevels > 0) {
-    const DevCsr& A0 = a.lv[0].A;
-    for (int c = 1; c < kCycles; ++c) {
-      for (int i = gt; i < A0.n; i += nthr) a.cres[i] = a.rc[i] - csr_row(A0, i, a.zc);
-      cl.sync();
-      vcycle(a.cres, a.ctmp);
-      for (int i = gt; i < A0.n; i += nthr) a.zc[i] += a.ctmp[i];
-      cl.sync();
-    }
+// V(1,1) cycle at `level` for right-hand side b, result in out (out != b).
+cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
+  if (level == d.nlevels) {
+    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    ++g_kernel_launches;
+    return cudaGetLastError();
   }
-  if (a.zc32 != nullptr) {
-    const int n = (a.nlevels > 0) ? a.lv[0].A.n : a.nc;
-    for (int i = gt; i < n; i += nthr) a.zc32[i] = (float)a.zc[i];
-  }
+  const DevAmgLevel& L = d.levels[level];
+  const int n = L.A.n, gb = grid_for(n, 256, 4096), gw = grid_for(32 * n, 256, 8192);
+  amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
+  ++g_kernel_launches;
+  amg_resid_kernel<<<gw, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  ++g_kernel_launches;
+  double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
+  double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
+  const int nc = L.R.n;
+  amg_spmv_kernel<<<grid_for(32 * nc, 256, 8192), 256, 0, s>>>(L.R, L.t, bc, st);
+  ++g_kernel_launches;
+  cudaError_t err = vcycle(d, level + 1, bc, xc, st, s);
+  if (err != cudaSuccess) return err;
+  amg_prolong_add_kernel<<<gw, 256, 0, s>>>(L.P, xc, L.x, st);
+  ++g_kernel_launches;
+  amg_jacobi_post_kernel<<<gw, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  ++g_kernel_launches;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -913,25 +923,32 @@ cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, cons
   return launch_coarse_restrict_t<float>(d, r, st, s);
 }
 
-// Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero, one cluster launch.
+// Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  if (d.nlevels > kMaxAmgLevels) return cudaErrorInvalidValue;
-  AmgArgs a;
-  a.nlevels = d.nlevels;
-  for (int l = 0; l < d.nlevels; ++l) a.lv[l] = d.levels[l];
-  a.nc = d.coarsest_n;
-  a.cinv = d.coarsest_inv;
-  a.cb = d.cb;
-  a.cx = d.cx;
-  a.rc = d.Rc;
-  a.zc = d.Zc;
-  a.cres = d.cres;
-  a.ctmp = d.ctmp;
-  a.zc32 = d.fp32 ? d.Zc32 : nullptr;
-  a.st = st;
-  amg_cluster_kernel<<<kAmgCluster, kAmgBlock, 0, s>>>(a);
-  ++g_kernel_launches;
+  cudaError_t err = vcycle(d, 0, d.Rc, d.Zc, st, s);
+  if (err != cudaSuccess) return err;
+  if (d.nlevels == 0) {
+    if (d.fp32) {
+      to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
+      ++g_kernel_launches;
+    }
+    return cudaGetLastError();
+  }
+  const DevCsr& A0 = d.levels[0].A;
+  const int gb = grid_for(A0.n, 256, 4096), gw = grid_for(32 * A0.n, 256, 8192);
+  for (int c = 1; c < kCycles; ++c) {
+    amg_resid_kernel<<<gw, 256, 0, s>>>(A0, d.Rc, d.Zc, d.cres, st);
+    ++g_kernel_launches;
+    err = vcycle(d, 0, d.cres, d.ctmp, st, s);
+    if (err != cudaSuccess) return err;
+    add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
+    ++g_kernel_launches;
+  }
+  if (d.fp32) {
+    to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
+    ++g_kernel_launches;
+  }
   return cudaGetLastError();
 }
 
