@@ -303,10 +303,15 @@ def run_gpu(args):
         flops = ax_flops(ORDER, NE)
     else:
         flops = None
+    # DRAM bytes per launch from one ncu capture of the same kernel at 24^3 hexes, scaled
+    # by the element count (the traffic is per element); null for other kernels
+    traffic = {"schwarz_local": 169.2e6 * NE / 13824, "ax_local": 518.0e6 * NE / 13824}.get(kern)
     roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
             "peak_source": "FP64 FMA loop measured on this pool (nominal 1.25 TFLOP/s)",
             "achieved": (flops / (avg_ms * 1e-3) / 1e12) if flops else None,
-            "avg_launch_ms": avg_ms, "launches": nl, "traffic": None,
+            "avg_launch_ms": avg_ms, "launches": nl, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read+write of the kernel at 24^3 hexes (profiles/"
+                              "hot_kernels_24cube_n7.md) scaled by the element count",
             "share_of_step": tot / (t_local * 1e3)}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] else None
 
