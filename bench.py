@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--precision-variant", action="store_true",
                     help="48^3 hexes, +-20%% (seed 2), n=7, lambda=0: FP64 vs mixed time-to-1e-8 and the "
                          "per-result error of the mixed solution")
+    ap.add_argument("--batch-variant", action="store_true",
+                    help="24 problems (8^3..24^3 hexes, n in 3..8, +-15%%, seed 3), 4 Gaussian loads each: "
+                         "one at a time vs sem_solve_many, default vs autotuned tile shapes")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
                     help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
                          "(a small case for ncu captures), then exit")
@@ -512,9 +515,84 @@ def run_precision_variant(args):
     prob.close()
 
 
+def run_batch_variant(args):
+    """Batched variant: 24 seeded problems x 4 loads, solved one at a time and together."""
+    import numpy as np
+    import torch
+    from synth import lattice_hex_mesh, gaussian_load
+    from paper_1506_05996_gb300 import sem as S
+    rng = np.random.default_rng(3)
+    specs = [(int(rng.integers(8, 25)), int(rng.integers(3, 9))) for _ in range(24)]
+    t0 = time.perf_counter()
+    handles, bs, xs, dofs, keep = [], [], [], [], []
+    for k, (E, n) in enumerate(specs):
+        mesh = lattice_hex_mesh(E, 0.15, 3000 + k)
+        for r in range(4):
+            st = torch.cuda.Stream()
+            pr = S.SemProblem(mesh.xyz, mesh.hex2vert, n, 0.0, stream=st)
+            free = (pr.mask() == 0).double()
+            b = (torch.as_tensor(gaussian_load(pr.n_dof, 30000 + 4 * k + r), device="cuda") * free).contiguous()
+            handles.append(pr.h)
+            bs.append(b)
+            xs.append(torch.empty_like(b))
+            dofs.append(pr.n_dof)
+            keep.append((pr, st))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+
+    def one_at_a_time():
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        its = []
+        for h, b, x in zip(handles, bs, xs):
+            rc, it, hist, tr = S.sem_solve(h, b, x, RTOL, 1000, want_history=False)
+            its.append(it)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, its
+
+    def batched():
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rc, its, sts = S.sem_solve_many(handles, bs, xs, RTOL, 1000)
+        torch.cuda.synchronize()
+        assert rc == 0, (rc, sts)
+        return time.perf_counter() - t, its
+
+    for _ in range(max(1, args.warmup)):
+        one_at_a_time()
+        batched()
+    reps = max(1, args.steps)
+    t_seq = min(one_at_a_time()[0] for _ in range(reps))
+    t_bat, its = min((batched() for _ in range(reps)), key=lambda v: v[0])
+    tiles = [S.sem_autotune(h) for h in handles]
+    for _ in range(max(1, args.warmup)):
+        batched()
+    t_tuned, its_t = min((batched() for _ in range(reps)), key=lambda v: v[0])
+    total = float(sum(dofs))
+    by_order = {}
+    for (E, n), tl in zip([s for s in specs for _ in range(4)], tiles):
+        by_order.setdefault(n, set()).add(tl)
+    print(json.dumps({"variant": "batch", "config": {
+        "workload": "24 problems: E ~ U{8..24} hexes per direction, n ~ U{3..8}, +-15% perturbation, lambda=0, "
+                    "Dirichlet, 4 Gaussian N(0,1) loads each (seed 3); FP64 two-scale PCG to 1e-8",
+        "problems": [{"E": E, "n": n} for E, n in specs], "solves": len(handles), "total_dofs": int(total),
+        "setup_s": t_setup},
+        "one_at_a_time": {"s": t_seq, "gdofs_solved": total / t_seq / 1e9, "solves_per_s": len(handles) / t_seq},
+        "batched": {"s": t_bat, "gdofs_solved": total / t_bat / 1e9, "solves_per_s": len(handles) / t_bat,
+                    "speedup": t_seq / t_bat},
+        "batched_autotuned": {"s": t_tuned, "gdofs_solved": total / t_tuned / 1e9,
+                              "solves_per_s": len(handles) / t_tuned, "speedup": t_seq / t_tuned,
+                              "tiles_by_order": {str(k): sorted(list(v)) for k, v in sorted(by_order.items())}},
+        "iterations": {"min": int(min(its)), "max": int(max(its)), "mean": float(np.mean(its))}}))
+    for pr, st in keep:
+        pr.close()
+
+
 def main():
     args = parse()
-    if args.precision_variant:
+    if args.batch_variant:
+        run_batch_variant(args)
+    elif args.precision_variant:
         run_precision_variant(args)
     elif args.kernel_case:
         run_kernel_case(args.kernel_case)

@@ -147,6 +147,31 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
               int* iters_host, double* res_hist_host, double* true_rel_res_host);
 
 /*
+ * sem_solve_many - the PCG solves of `count` independent handles advanced together: every
+ * round reads back the state of all active solves, then replays each one's iteration
+ * graph on its own stream, so many small problems share the GPU (the batched form of
+ * Algorithm 1). Give every handle its own CUDA stream (sem_create / sem_set_stream); a
+ * handle may appear once. b_dev[i] / x_dev[i]: load and solution of handles[i], as in
+ * sem_solve (rtol, maxit shared). iters_host[i] and status_host[i] (either may be NULL)
+ * receive each solve's iteration count and sem_solve status. Returns SEM_OK, or the
+ * first error (or SEM_MAXIT) met. Synchronises all the handles' streams.
+ */
+int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev,
+                   double* const* x_dev, double rtol, int maxit, int* iters_host, int* status_host);
+
+/*
+ * sem_set_tiles / sem_autotune - tile shapes of the element kernels: the number of
+ * elements one CTA of the operator (epb_ax) and of the patch solve (epb_sw) processes,
+ * 1, 2, 4 or 8 (at low order an element has only (n+1)^2 and (n+3)^2 threads). A shape not
+ * compiled for the handle's order (shared-memory or thread limits) is refused with
+ * SEM_ERR_ARG. sem_autotune times every compiled shape on the handle's own mesh and
+ * precision and keeps the fastest; it overwrites the handle's work vectors, so call it
+ * between solves. Results are bit-identical for every shape.
+ */
+int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw);
+int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host);
+
+/*
  * sem_profile / sem_profile_read - per-kernel timing of the library's own launches.
  * While enabled, a CUDA event pair is recorded on the handle's stream around each
  * kernel launch (or launch group: "coarse_amg" is the whole AMG V-cycle sequence),

@@ -645,11 +645,23 @@ int sem_set_precond(sem_t* h, int which) {
   return SEM_OK;
 }
 
-int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
-              double* res_hist_host, double* true_rel_res_host) {
-  if (int rc = check_handle(h)) return rc;
-  if (b_dev == nullptr || x_dev == nullptr || b_dev == x_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
-  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+}  // extern "C"
+
+namespace {
+
+// One PCG solve split into steps, so that sem_solve and sem_solve_many share them:
+// begin (initial residual, preconditioner, first operator application, iteration graph),
+// advance (read the device state; residual replacement if asked; replay the iteration
+// graph), finish (true residual, copy out).
+struct SolveCtx {
+  const double* b = nullptr;
+  double* x = nullptr;
+  bool graph_pending = false;   // a replay whose profiling events are unread
+  bool done = false;
+  int rc = SEM_OK;
+};
+
+int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
   sem::DevProblem& d = h->d;
   if (maxit + 1 > h->hist_cap) {
     h->graph.reset();
@@ -682,20 +694,16 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
     PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, h->stream));
     return enqueue_head();
   };
-  auto read_state = [&]() -> int {
-    CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return SEM_OK;
-  };
 
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, b_dev, h->r, u, rtol, maxit, mixed, h->hist, s));
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
   if (int rc = enqueue_head()) return rc;
 
   // capture the steady-state iteration once per configuration
-  const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3);
+  const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
+                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8);
   if (h->graph.key != key) {
     h->graph.reset();
     CK(cudaStreamSynchronize(s));
@@ -722,28 +730,46 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
     }
     h->graph.key = key;
   }
+  c.graph_pending = false;
+  c.done = false;
+  return SEM_OK;
+}
 
-  bool graph_pending = false;   // the last launch was a graph replay whose events are unread
-  for (int guard = 0; guard <= maxit + 1; ++guard) {
+// Enqueue the read-back of the device state (pinned host copy).
+int solve_poll(sem_t* h) {
+  CK(cudaMemcpyAsync(h->st_host, h->d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, h->stream));
+  return SEM_OK;
+}
+
+// After the state read-back completed: stop, or replace the residual if asked, and
+// replay the iteration graph.
+int solve_advance(sem_t* h, SolveCtx& c) {
+  sem::DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  CK(cudaStreamSynchronize(s));
+  if (c.graph_pending && h->prof.on) h->prof.collect_graph(h->graph);
+  c.graph_pending = false;
+  if (h->st_host->done) { c.done = true; return SEM_OK; }
+  if (d.fp32 && h->st_host->replace) {
+    // the recursive residual is replaced by b - A u with the FP64 operator
+    PROF(h, "ax_local_fp64", sem::launch_ax_local(d, h->u, d.wl, d.st, s));
+    PROF(h, "pcg_replace", sem::launch_pcg_replace(d, c.b, d.wl, h->r, h->hist, s));
     CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (graph_pending && h->prof.on) h->prof.collect_graph(h->graph);
-    graph_pending = false;
-    if (h->st_host->done) break;
-    if (mixed && h->st_host->replace) {
-      // the recursive residual is replaced by b - A u with the FP64 operator
-      PROF(h, "ax_local_fp64", sem::launch_ax_local(d, u, d.wl, d.st, s));
-      PROF(h, "pcg_replace", sem::launch_pcg_replace(d, b_dev, d.wl, h->r, h->hist, s));
-      if (int rc = read_state()) return rc;
-      if (h->st_host->done) break;
-    }
-    CK(cudaGraphLaunch(h->graph.exec, s));
-    graph_pending = true;
+    if (h->st_host->done) { c.done = true; return SEM_OK; }
   }
+  CK(cudaGraphLaunch(h->graph.exec, s));
+  c.graph_pending = true;
+  return SEM_OK;
+}
+
+int solve_finish(sem_t* h, SolveCtx& c, int* iters_host, double* res_hist_host, double* true_rel_res_host) {
+  sem::DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
   // true residual ||b - A u|| / ||b|| on the free nodes, and the solution out
-  PROF(h, "ax_local", sem::launch_ax_local(d, u, d.wl, nullptr, s));
-  PROF(h, "true_residual", sem::launch_true_residual(d, b_dev, d.wl, s));
-  CK(cudaMemcpyAsync(x_dev, u, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s));
+  PROF(h, "ax_local", sem::launch_ax_local(d, h->u, d.wl, nullptr, s));
+  PROF(h, "true_residual", sem::launch_true_residual(d, c.b, d.wl, s));
+  CK(cudaMemcpyAsync(c.x, h->u, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   h->prof.collect();
@@ -757,6 +783,137 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   if (st.status == -6) return fail(SEM_ERR_NAN, "NaN/Inf or non-positive curvature in PCG");
   if (!st.done) return fail(SEM_MAXIT, "maxit reached");
   return st.status == 1 ? SEM_MAXIT : SEM_OK;
+}
+
+// Time `reps` launches of fn on the handle's stream with events (milliseconds per launch).
+template <class F>
+int time_launches(sem_t* h, F fn, int reps, float* ms_out) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t err = fn();   // warm-up (and validity of the configuration)
+  if (err == cudaSuccess) {
+    cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < reps && err == cudaSuccess; ++i) err = fn();
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+  }
+  float ms = 0.f;
+  if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  *ms_out = ms / reps;
+  return SEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
+              double* res_hist_host, double* true_rel_res_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (b_dev == nullptr || x_dev == nullptr || b_dev == x_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  SolveCtx c;
+  c.b = b_dev;
+  c.x = x_dev;
+  if (int rc = solve_begin(h, c, rtol, maxit)) return rc;
+  for (int guard = 0; guard <= maxit + 1 && !c.done; ++guard) {
+    if (int rc = solve_poll(h)) return rc;
+    if (int rc = solve_advance(h, c)) return rc;
+  }
+  return solve_finish(h, c, iters_host, res_hist_host, true_rel_res_host);
+}
+
+int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev, double* const* x_dev,
+                   double rtol, int maxit, int* iters_host, int* status_host) {
+  if (count < 0 || (count > 0 && (handles == nullptr || b_dev == nullptr || x_dev == nullptr)))
+    return fail(SEM_ERR_ARG, "bad arrays");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  for (int i = 0; i < count; ++i) {
+    if (handles[i] == nullptr || b_dev[i] == nullptr || x_dev[i] == nullptr || b_dev[i] == x_dev[i])
+      return fail(SEM_ERR_ARG, "bad handle or vector at index " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(SEM_ERR_ARG, "a handle appears twice");
+  }
+  std::vector<SolveCtx> ctx(count);
+  for (int i = 0; i < count; ++i) {
+    ctx[i].b = b_dev[i];
+    ctx[i].x = x_dev[i];
+    if (int rc = solve_begin(handles[i], ctx[i], rtol, maxit)) return rc;
+  }
+  // every round reads back all active states, then advances each solve on its own stream
+  for (int guard = 0; guard <= maxit + 1; ++guard) {
+    bool any = false;
+    for (int i = 0; i < count; ++i)
+      if (!ctx[i].done) {
+        if (int rc = solve_poll(handles[i])) return rc;
+        any = true;
+      }
+    if (!any) break;
+    for (int i = 0; i < count; ++i)
+      if (!ctx[i].done)
+        if (int rc = solve_advance(handles[i], ctx[i])) return rc;
+  }
+  int worst = SEM_OK;
+  for (int i = 0; i < count; ++i) {
+    int it = 0;
+    const int rc = solve_finish(handles[i], ctx[i], &it, nullptr, nullptr);
+    if (iters_host) iters_host[i] = it;
+    if (status_host) status_host[i] = rc;
+    if (rc < 0) worst = rc;
+    else if (rc > 0 && worst == SEM_OK) worst = rc;
+  }
+  return worst;
+}
+
+int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw) {
+  if (int rc = check_handle(h)) return rc;
+  if (!sem::ax_tile_ok(h->d.p, epb_ax) || !sem::sw_tile_ok(h->d.P, epb_sw))
+    return fail(SEM_ERR_ARG, "no kernel with that many elements per CTA for this order");
+  h->d.epb_ax = epb_ax;
+  h->d.epb_sw = epb_sw;
+  h->graph.reset();
+  return SEM_OK;
+}
+
+int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host) {
+  if (int rc = check_handle(h)) return rc;
+  sem::DevProblem& d = h->d;
+  CK(cudaMemsetAsync(h->p, 0, sizeof(double) * h->nb.G, h->stream));
+  CK(cudaMemsetAsync(h->r, 0, sizeof(double) * h->nb.G, h->stream));
+  CK(cudaMemsetAsync(d.p32, 0, sizeof(float) * h->nb.G, h->stream));
+  CK(cudaMemsetAsync(d.r32, 0, sizeof(float) * h->nb.G, h->stream));
+  const int cand[4] = {1, 2, 4, 8};
+  int best_ax = 1, best_sw = 1;
+  float t_ax = 1e30f, t_sw = 1e30f;
+  for (int c : cand) {
+    float ms;
+    d.epb_ax = sem::ax_tile_ok(d.p, c) ? c : 1;
+    auto fa = [&]() -> cudaError_t {
+      return d.fp32 ? sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), nullptr, h->stream)
+                    : sem::launch_ax_local(d, h->p, d.wl, nullptr, h->stream);
+    };
+    if (d.epb_ax == c && time_launches(h, fa, 5, &ms) == SEM_OK && ms < t_ax) { t_ax = ms; best_ax = c; }
+    d.epb_sw = sem::sw_tile_ok(d.P, c) ? c : 1;
+    auto fs = [&]() -> cudaError_t {
+      return d.fp32 ? sem::launch_schwarz_local_f32_in32(d, d.r32, reinterpret_cast<float*>(d.wp), nullptr,
+                                                         h->stream)
+                    : sem::launch_schwarz_local(d, h->r, d.wp, nullptr, h->stream);
+    };
+    if (d.epb_sw == c && time_launches(h, fs, 5, &ms) == SEM_OK && ms < t_sw) { t_sw = ms; best_sw = c; }
+  }
+  d.epb_ax = best_ax;
+  d.epb_sw = best_sw;
+  h->graph.reset();
+  if (epb_ax_host) *epb_ax_host = best_ax;
+  if (epb_sw_host) *epb_sw_host = best_sw;
+  return SEM_OK;
 }
 
 }  // extern "C"

@@ -57,6 +57,8 @@ struct DevProblem {
   double lambda = 0.0;
   bool recompute = false;
   bool fp32 = false;                // operator and patch solves in FP32 (mixed path)
+  int epb_ax = 1, epb_sw = 1;       // elements per CTA of the operator / patch-solve kernels
+                                    // (tile shapes picked by the autotuner; 1, 2, 4 or 8)
   const float* geo32 = nullptr;     // stored factors rounded to FP32 (same layout as geo)
   // tables
   const int* l2g = nullptr;
@@ -114,6 +116,10 @@ uint64_t kernel_launch_count();
 // if |J| <= 0 anywhere.
 cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, double* mloc, int* bad,
                             cudaStream_t s);
+
+// Tile shapes (elements per CTA) compiled for an order: p = n+1 (operator), P = n+3 (patch).
+bool ax_tile_ok(int p, int epb);
+bool sw_tile_ok(int P, int epb);
 
 // --- operator (Eq. R, Algorithm 2) -------------------------------------------
 cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st,

@@ -1,0 +1,253 @@
+// The operator kernel (Eq. R, Algorithm 2): templates shared by k_ax64.cu and k_ax32.cu.
+#pragma once
+
+#include "kcommon.cuh"
+
+namespace sem {
+namespace {
+
+// ----------------------------------------------------------------- operator
+// D (the GLL differentiation matrix) is centro-antisymmetric, D[n-i][n-m] = -D[i][m], and so
+// is D^T. With v = v_e + v_o split into its even and odd parts under m -> n-m,
+//   a = D v_e is odd, s = D v_o is even:  (D v)[i] = a_i + s_i,  (D v)[n-i] = -a_i + s_i,
+// and a_i, s_i need only the folded half-tables
+//   Fp[i][m] = (D[i][m] + D[i][n-m]) / 2,   Fm[i][m] = (D[i][m] - D[i][n-m]) / 2   (m < h)
+// applied to e_m = v[m] + v[n-m] and o_m = v[m] - v[n-m] (plus the middle column D[i][h]
+// times v[h] when p is odd): about 3/4 of the multiply-adds of the plain product.
+template <int p, typename T>
+struct FoldedD {
+  static constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
+  T Fp[H * H > 0 ? H * H : 1], Fm[HM * H > 0 ? HM * H : 1], Fmid[H > 0 ? H : 1];
+};
+
+// Fill the folded tables of M (M = D for the gradient, D^T for the divergence) from
+// Dhat[i*p + m] = phi_m'(t_i); called by one thread per entry.
+template <int p, typename T>
+__device__ __forceinline__ void fold_fill(FoldedD<p, T>& F, const double* __restrict__ D, bool transpose, int t) {
+  constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
+  constexpr int n = p - 1;
+  auto M = [&](int i, int m) { return transpose ? D[m * p + i] : D[i * p + m]; };
+  if (t < H * H) {
+    const int i = t / H, m = t % H;
+    F.Fp[t] = (T)(0.5 * (M(i, m) + M(i, n - m)));
+  }
+  if (t < HM * H) {
+    const int i = t / H, m = t % H;
+    F.Fm[t] = (T)(0.5 * (M(i, m) - M(i, n - m)));
+  }
+  if (ODD && t < H) F.Fmid[t] = (T)M(t, H);
+}
+
+template <int p, typename T>
+__device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[p], T (&out)[p]) {
+  constexpr int H = p / 2, ODD = p & 1;
+  constexpr int n = p - 1;
+  T e[H], o[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) { e[m] = v[m] + v[n - m]; o[m] = v[m] - v[n - m]; }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T a = ODD ? F.Fmid[i] * v[H] : T(0), sv = 0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      a += F.Fp[i * H + m] * e[m];
+      sv += F.Fm[i * H + m] * o[m];
+    }
+    out[i] = sv + a;
+    out[n - i] = sv - a;
+  }
+  if (ODD) {
+    T sv = 0;
+#pragma unroll
+    for (int m = 0; m < H; ++m) sv += F.Fm[H * H + m] * o[m];
+    out[H] = sv;
+  }
+}
+
+// One group of p*p threads per element (Algorithm 2), EPB elements per CTA (a tile shape
+// chosen per order by the autotuner). Thread (x, y) owns the GLL nodes (x, y, k),
+// k = 0..p-1, for the pointwise work, and one line per direction for the contractions:
+// the gradient by D along i (line j=x, k=y), j (i=x, k=y) and k (i=x, j=y), A/B/C by the
+// geometric factors, the divergence by D^T along the same lines, plus lambda m u.
+template <int p, typename T, int EPB>
+constexpr int ax_smem_bytes() {
+  return (int)(2 * sizeof(FoldedD<p, T>) + EPB * (4 * p * p * p + 24) * sizeof(T));
+}
+
+template <int p, bool RECOMP, typename T, typename TX, int EPB>
+__global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
+                                                               T* __restrict__ wl, const PcgState* st) {
+  if (stopped(st)) return;
+  constexpr int p2 = p * p, p3 = p * p * p;
+  __shared__ FoldedD<p, T> Fg, Fd;
+  __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
+  __shared__ T sx_all[EPB * 24];
+  const int grp = threadIdx.x / p2, tid = threadIdx.x % p2;
+  const int e_raw = blockIdx.x * EPB + grp;
+  const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
+  const int e = active ? e_raw : d.ne - 1;
+  T* su = su_all + grp * p3;
+  T* sA = sA_all + grp * p3;
+  T* sB = sB_all + grp * p3;
+  T* sC = sC_all + grp * p3;
+  T* sx = sx_all + grp * 24;
+  const int tx = tid % p, ty = tid / p;
+  fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
+  fold_fill<p, T>(Fd, d.D, true, threadIdx.x);
+  if (RECOMP)
+    for (int q = tid; q < 24; q += p2) sx[q] = (T)d.exyz[(size_t)e * 24 + q];
+  const int* l2ge = d.l2g + (size_t)e * p3;
+  T uk[p], rk[p], line[p], res[p];
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const int g = l2ge[l];
+    uk[k] = d.mask[g] ? T(0) : (T)x[g];
+    su[l] = uk[k];
+  }
+  __syncthreads();
+  // gradient: d/dxi on line (j=tx, k=ty), d/deta on line (i=tx, k=ty), d/dzeta on (i=tx, j=ty)
+#pragma unroll
+  for (int i = 0; i < p; ++i) line[i] = su[i + p * (tx + p * ty)];
+  fold_apply<p, T>(Fg, line, res);
+#pragma unroll
+  for (int i = 0; i < p; ++i) sA[i + p * (tx + p * ty)] = res[i];
+#pragma unroll
+  for (int j = 0; j < p; ++j) line[j] = su[tx + p * (j + p * ty)];
+  fold_apply<p, T>(Fg, line, res);
+#pragma unroll
+  for (int j = 0; j < p; ++j) sB[tx + p * (j + p * ty)] = res[j];
+  fold_apply<p, T>(Fg, uk, res);
+#pragma unroll
+  for (int k = 0; k < p; ++k) sC[tx + p * (ty + p * k)] = res[k];
+  __syncthreads();
+  // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
+  const T lam = (T)d.lambda;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const T ur = sA[l], us = sB[l], ut = sC[l];
+    T G[6], mm;
+    if (!RECOMP) {
+      const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + l;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
+      mm = gp[6 * p3];
+    } else {
+      T det;
+      geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
+    }
+    sA[l] = G[0] * ur + G[1] * us + G[2] * ut;
+    sB[l] = G[1] * ur + G[3] * us + G[4] * ut;
+    sC[l] = G[2] * ur + G[4] * us + G[5] * ut;
+    rk[k] = lam * mm * uk[k];
+  }
+  __syncthreads();
+  // divergence by D^T: the A lines (j=tx, k=ty) into su, then the B lines (i=tx, k=ty)
+  // added into su, then the C line (i=tx, j=ty) and su added in registers
+#pragma unroll
+  for (int i = 0; i < p; ++i) line[i] = sA[i + p * (tx + p * ty)];
+  fold_apply<p, T>(Fd, line, res);
+#pragma unroll
+  for (int i = 0; i < p; ++i) su[i + p * (tx + p * ty)] = res[i];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < p; ++j) line[j] = sB[tx + p * (j + p * ty)];
+  fold_apply<p, T>(Fd, line, res);
+#pragma unroll
+  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] += res[j];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < p; ++k) line[k] = sC[tx + p * (ty + p * k)];
+  fold_apply<p, T>(Fd, line, res);
+  if (!active) return;
+  T* out = wl + (size_t)e * p3;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    out[l] = su[l] + res[k] + rk[k];
+  }
+}
+
+
+template <int p, typename T, int EPB>
+constexpr bool ax_tile_supported() {
+  return ax_smem_bytes<p, T, EPB>() <= 48 * 1024 && (EPB == 1 || EPB * p * p <= 256);
+}
+
+template <int p, typename T>
+bool ax_tile_ok_p(int epb) {
+  switch (epb) {
+    case 1: return ax_tile_supported<p, T, 1>();
+    case 2: return ax_tile_supported<p, T, 2>();
+    case 4: return ax_tile_supported<p, T, 4>();
+    case 8: return ax_tile_supported<p, T, 8>();
+    default: return false;
+  }
+}
+
+template <typename T>
+bool ax_tile_ok_t(int p, int epb) {
+  switch (p) {
+    case 3: return ax_tile_ok_p<3, T>(epb);
+    case 4: return ax_tile_ok_p<4, T>(epb);
+    case 5: return ax_tile_ok_p<5, T>(epb);
+    case 6: return ax_tile_ok_p<6, T>(epb);
+    case 7: return ax_tile_ok_p<7, T>(epb);
+    case 8: return ax_tile_ok_p<8, T>(epb);
+    case 9: return ax_tile_ok_p<9, T>(epb);
+    default: return false;
+  }
+}
+
+template <int p, typename T, typename TX, int EPB>
+cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+  if constexpr (ax_tile_supported<p, T, EPB>()) {
+    const int grid = (d.ne + EPB - 1) / EPB;
+    if (d.recompute) ax_local_kernel<p, true, T, TX, EPB><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st);
+    else ax_local_kernel<p, false, T, TX, EPB><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st);
+    count_launch();
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidConfiguration;
+  }
+}
+
+template <int p, typename T, typename TX>
+cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+  switch (d.epb_ax) {
+    case 2: return launch_ax_epb<p, T, TX, 2>(d, x, wl, st, s);
+    case 4: return launch_ax_epb<p, T, TX, 4>(d, x, wl, st, s);
+    case 8: return launch_ax_epb<p, T, TX, 8>(d, x, wl, st, s);
+    default: return launch_ax_epb<p, T, TX, 1>(d, x, wl, st, s);
+  }
+}
+
+template <typename T, typename TX>
+cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+  switch (d.p) {
+    case 3: return launch_ax_p<3, T, TX>(d, x, wl, st, s);
+    case 4: return launch_ax_p<4, T, TX>(d, x, wl, st, s);
+    case 5: return launch_ax_p<5, T, TX>(d, x, wl, st, s);
+    case 6: return launch_ax_p<6, T, TX>(d, x, wl, st, s);
+    case 7: return launch_ax_p<7, T, TX>(d, x, wl, st, s);
+    case 8: return launch_ax_p<8, T, TX>(d, x, wl, st, s);
+    case 9: return launch_ax_p<9, T, TX>(d, x, wl, st, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
+  return launch_ax_local_t<double, double>(d, x, wl, st, s);
+}
+cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st, cudaStream_t s) {
+  return launch_ax_local_t<float, double>(d, x, wl, st, s);
+}
+cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
+                                     cudaStream_t s) {
+  return launch_ax_local_t<float, float>(d, x, wl, st, s);
+}
+
+
+}  // namespace
+}  // namespace sem

@@ -1,0 +1,223 @@
+// The fine patch-solve kernel (Eq. z): templates shared by k_sw64.cu and k_sw32.cu.
+#pragma once
+
+#include "kcommon.cuh"
+
+namespace sem {
+namespace {
+
+// ------------------------------------------------------------ fine Schwarz
+// 1/d by Newton-Raphson (x <- x (2 - d x)) from the FP32 reciprocal: two steps take the
+// 2^-24 seed error to below FP64 rounding; used for the per-node eigenvalue sums.
+__device__ __forceinline__ double recip(double d) {
+  double x = (double)(1.0f / (float)d);
+  x = x * (2.0 - d * x);
+  x = x * (2.0 - d * x);
+  return x;
+}
+__device__ __forceinline__ float recip(float d) { return 1.0f / d; }
+
+// Even/odd folded 1D contractions with the pencil eigenvectors S (P x P, modes 0..NE-1
+// even and NE..P-1 odd under row -> P-1-row). fwd: modes t = S^T v; bwd: nodes v = S t.
+template <int P, typename T>
+__device__ __forceinline__ void pencil_fwd(const T* __restrict__ S, const T (&v)[P], T (&t)[P]) {
+  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
+  T e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) { e[k] = v[k] + v[P - 1 - k]; o[k] = v[k] - v[P - 1 - k]; }
+#pragma unroll
+  for (int c = 0; c < NE; ++c) {
+    T a = ODD ? S[H * P + c] * v[H] : T(0);
+#pragma unroll
+    for (int k = 0; k < H; ++k) a += S[k * P + c] * e[k];
+    t[c] = a;
+  }
+#pragma unroll
+  for (int c = NE; c < P; ++c) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) a += S[k * P + c] * o[k];
+    t[c] = a;
+  }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)[P], T (&v)[P]) {
+  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    T E = 0, O = 0;
+#pragma unroll
+    for (int c = 0; c < NE; ++c) E += S[k * P + c] * t[c];
+#pragma unroll
+    for (int c = NE; c < P; ++c) O += S[k * P + c] * t[c];
+    v[k] = E + O;
+    v[P - 1 - k] = E - O;
+  }
+  if (ODD) {
+    T E = 0;
+#pragma unroll
+    for (int c = 0; c < NE; ++c) E += S[H * P + c] * t[c];
+    v[H] = E;
+  }
+}
+
+// One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
+// extended box in each of the six tensor contractions of Eq. z:
+//   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
+//   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
+template <int P, typename T, int EPB>
+constexpr int sw_smem_bytes() {
+  return (int)((P * P + P + EPB * 2 * P * P * P) * sizeof(T));
+}
+
+template <int P, typename T, typename TR, int EPB>
+__global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
+                                                                    T* __restrict__ wp, const PcgState* st) {
+  if (stopped(st)) return;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  __shared__ T sS[P2], sev[P], s1_all[EPB * P3], s2_all[EPB * P3];
+  const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
+  const int e_raw = blockIdx.x * EPB + grp;
+  const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
+  const int e = active ? e_raw : d.ne - 1;
+  T* s1 = s1_all + grp * P3;
+  T* s2 = s2_all + grp * P3;
+  const int x = tx % P, y = tx / P;
+  if (threadIdx.x < P2) sS[threadIdx.x] = (T)d.S[threadIdx.x];
+  if (threadIdx.x < P) sev[threadIdx.x] = (T)d.ev[threadIdx.x];
+  const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
+  const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
+  const T scale = (T)(8.0 / (hxd * hyd * hzd));
+  T col[P], out[P];
+  const int* ipe = d.ip + (size_t)e * P3;
+#pragma unroll
+  for (int K = 0; K < P; ++K) {
+    const int g = ipe[x + P * (y + P * K)];
+    col[K] = (g >= 0 && !d.mask[g]) ? (T)r[g] * scale : T(0);
+  }
+  __syncthreads();
+  // along K: line (I=x, J=y)
+  pencil_fwd<P, T>(sS, col, out);
+#pragma unroll
+  for (int c = 0; c < P; ++c) s1[x + P * (y + P * c)] = out[c];
+  __syncthreads();
+  // along J: line (I=x, c=y)
+#pragma unroll
+  for (int J = 0; J < P; ++J) col[J] = s1[x + P * (J + P * y)];
+  pencil_fwd<P, T>(sS, col, out);
+#pragma unroll
+  for (int b = 0; b < P; ++b) s2[x + P * (b + P * y)] = out[b];
+  __syncthreads();
+  // along I: line (b=x, c=y), eigenvalue scaling, and back along I
+#pragma unroll
+  for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
+  pencil_fwd<P, T>(sS, col, out);
+  {
+    const T four = 4, lam = (T)d.lambda;
+    const T lbc = sev[x] * ihy2 + sev[y] * ihz2;
+#pragma unroll
+    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (sev[a] * ihx2 + lbc) + lam);
+  }
+  pencil_bwd<P, T>(sS, out, col);
+#pragma unroll
+  for (int I = 0; I < P; ++I) s2[I + P * (x + P * y)] = col[I];
+  __syncthreads();
+  // back along J: line (I=x, c=y)
+#pragma unroll
+  for (int b = 0; b < P; ++b) out[b] = s2[x + P * (b + P * y)];
+  pencil_bwd<P, T>(sS, out, col);
+#pragma unroll
+  for (int J = 0; J < P; ++J) s1[x + P * (J + P * y)] = col[J];
+  __syncthreads();
+  // back along K: line (I=x, J=y)
+#pragma unroll
+  for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
+  pencil_bwd<P, T>(sS, out, col);
+  if (!active) return;
+  T* outp = wp + (size_t)e * P3;
+#pragma unroll
+  for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
+}
+
+
+template <int P, typename T, int EPB>
+constexpr bool sw_tile_supported() {
+  return sw_smem_bytes<P, T, EPB>() <= 48 * 1024 && (EPB == 1 || EPB * P * P <= 256);
+}
+
+template <int P, typename T>
+bool sw_tile_ok_P(int epb) {
+  switch (epb) {
+    case 1: return sw_tile_supported<P, T, 1>();
+    case 2: return sw_tile_supported<P, T, 2>();
+    case 4: return sw_tile_supported<P, T, 4>();
+    case 8: return sw_tile_supported<P, T, 8>();
+    default: return false;
+  }
+}
+
+template <typename T>
+bool sw_tile_ok_t(int P, int epb) {
+  switch (P) {
+    case 5: return sw_tile_ok_P<5, T>(epb);
+    case 6: return sw_tile_ok_P<6, T>(epb);
+    case 7: return sw_tile_ok_P<7, T>(epb);
+    case 8: return sw_tile_ok_P<8, T>(epb);
+    case 9: return sw_tile_ok_P<9, T>(epb);
+    case 10: return sw_tile_ok_P<10, T>(epb);
+    case 11: return sw_tile_ok_P<11, T>(epb);
+    default: return false;
+  }
+}
+
+template <int P, typename T, typename TR, int EPB>
+cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
+  if constexpr (sw_tile_supported<P, T, EPB>()) {
+    const int grid = (d.ne + EPB - 1) / EPB;
+    schwarz_local_kernel<P, T, TR, EPB><<<grid, EPB * P * P, 0, s>>>(d, r, wp, st);
+    count_launch();
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidConfiguration;
+  }
+}
+
+template <int P, typename T, typename TR>
+cudaError_t launch_sw_P(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
+  switch (d.epb_sw) {
+    case 2: return launch_sw_epb<P, T, TR, 2>(d, r, wp, st, s);
+    case 4: return launch_sw_epb<P, T, TR, 4>(d, r, wp, st, s);
+    case 8: return launch_sw_epb<P, T, TR, 8>(d, r, wp, st, s);
+    default: return launch_sw_epb<P, T, TR, 1>(d, r, wp, st, s);
+  }
+}
+
+template <typename T, typename TR>
+cudaError_t launch_schwarz_local_t(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
+  switch (d.P) {
+    case 5: return launch_sw_P<5, T, TR>(d, r, wp, st, s);
+    case 6: return launch_sw_P<6, T, TR>(d, r, wp, st, s);
+    case 7: return launch_sw_P<7, T, TR>(d, r, wp, st, s);
+    case 8: return launch_sw_P<8, T, TR>(d, r, wp, st, s);
+    case 9: return launch_sw_P<9, T, TR>(d, r, wp, st, s);
+    case 10: return launch_sw_P<10, T, TR>(d, r, wp, st, s);
+    case 11: return launch_sw_P<11, T, TR>(d, r, wp, st, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
+  return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
+}
+cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
+                                     cudaStream_t s) {
+  return launch_schwarz_local_t<float, double>(d, r, wp, st, s);
+}
+cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
+                                          cudaStream_t s) {
+  return launch_schwarz_local_t<float, float>(d, r, wp, st, s);
+}
+
+
+}  // namespace
+}  // namespace sem

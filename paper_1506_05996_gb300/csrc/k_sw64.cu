@@ -1,0 +1,9 @@
+// Patch-solve kernel, FP64 instantiations.
+#include "k_sw.cuh"
+
+namespace sem {
+cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
+  return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
+}
+bool sw_tile_ok(int P, int epb) { return sw_tile_ok_t<double>(P, epb) && sw_tile_ok_t<float>(P, epb); }
+}  // namespace sem

@@ -1,0 +1,111 @@
+// Device helpers shared by the kernel translation units (kernels.cu, k_ax*.cu, k_sw*.cu).
+#pragma once
+
+#include <cmath>
+
+#include "device.h"
+
+namespace sem {
+
+void count_launch();   // adds one to kernel_launch_count() of this thread
+
+namespace {
+
+__device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
+
+// Mixed path: replace the recursive residual by b - A u (FP64 operator) whenever it has
+// dropped by this factor since the last replacement, and before accepting convergence.
+constexpr double kReplaceFactor = 1e-3;
+
+// Sum over a block of BS threads; the result is valid in warp 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v) {
+  static_assert(BS % 32 == 0 && BS <= 1024, "block size");
+  __shared__ double sh[BS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (lane < BS / 32) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
+
+// Grid reduction: every block writes its partial; the last block to arrive sums the
+// partials in index order. Returns true in all threads of that last block, where
+// `total` is valid in thread 0.
+template <int BS>
+__device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned int* counter, double& total) {
+  __shared__ bool last;
+  const double bs = block_sum<BS>(v);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = bs;
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(&partial[i]);
+  total = block_sum<BS>(s);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
+// G = w |J| J^-1 J^-T (6 entries) and m = w |J| at reference point (a, b, c) from the
+// 8 vertices xv[corner*3 + dim]. J[r][s] = d x_r / d xi_s of the trilinear map.
+template <typename T>
+__device__ __forceinline__ void geom_point(const T* xv, T a, T b, T c, T w, T G[6], T& m, T& det) {
+  T J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  const T one = 1, half = 0.5;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const T sa = ((q == 1) | (q == 2) | (q == 5) | (q == 6)) ? one : -one;
+    const T sb = ((q == 2) | (q == 3) | (q == 6) | (q == 7)) ? one : -one;
+    const T sc = (q >= 4) ? one : -one;
+    const T fa = half * (one + sa * a), fb = half * (one + sb * b), fc = half * (one + sc * c);
+    const T d0 = half * sa * fb * fc, d1 = half * sb * fa * fc, d2 = half * sc * fa * fb;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T x = xv[3 * q + r];
+      J[r][0] += x * d0;
+      J[r][1] += x * d1;
+      J[r][2] += x * d2;
+    }
+  }
+  T C[3][3];
+  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+  const T s = w / det;   // inv(J)[r][c] = C[c][r] / det
+  G[0] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
+  G[1] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
+  G[2] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
+  G[3] = s * (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
+  G[4] = s * (C[0][1] * C[0][2] + C[1][1] * C[1][2] + C[2][1] * C[2][2]);
+  G[5] = s * (C[0][2] * C[0][2] + C[1][2] * C[1][2] + C[2][2] * C[2][2]);
+  m = w * det;
+}
+
+template <typename T> __device__ __forceinline__ const T* geo_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* geo_of<double>(const DevProblem& d) { return d.geo; }
+template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
+
+
+}  // namespace
+}  // namespace sem

@@ -1,11 +1,10 @@
-// sm_103a kernels of the spectral-element solver. The operator, gather, patch-solve and
-// P-sum kernels are templated on the compute type T (double, or float for the mixed
-// path); global vectors, dot products and the PCG recurrences are always FP64.
+// sm_103a kernels of the spectral-element solver, except the operator (k_ax*.cu) and
+// the patch solve (k_sw*.cu). Gather and P-sum kernels are templated on the compute
+// type T (double, or float for the mixed path); global vectors, dot products and the
+// PCG recurrences are always FP64.
 //
 //  geometry_kernel      G1..G6 and m at every GLL node from the trilinear map (Sec. 2.3-2.4)
-//  ax_local_kernel      local residual r_{ijk;e} of Eq. R / Algorithm 2 (stored or recomputed G)
 //  gather kernels       r_N = sum of local copies (Eq. gather), deterministic CSR order
-//  schwarz_local_kernel fast-diagonalisation patch solve of Eq. z (Sec. 4.2)
 //  coarse kernels       restriction C m^-1 r, AMG V-cycles, prolongation (Sec. 4.1, Eq. coarse)
 //  pcg kernels          fused vector updates and dot products of Algorithm 1; alpha, beta
 //                       and the stopping test are evaluated on the device
@@ -15,106 +14,16 @@
 // in index order (no spin-waits: a completion counter decides the last block).
 #include <cmath>
 
-#include "device.h"
+#include "kcommon.cuh"
 
 namespace sem {
 
 static thread_local uint64_t g_kernel_launches = 0;
 uint64_t kernel_launch_count() { return g_kernel_launches; }
+void count_launch() { ++g_kernel_launches; }
 
 namespace {
-
-__device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
-
-// Mixed path: replace the recursive residual by b - A u (FP64 operator) whenever it has
-// dropped by this factor since the last replacement, and before accepting convergence.
-constexpr double kReplaceFactor = 1e-3;
-
-// Sum over a block of BS threads; the result is valid in warp 0.
-template <int BS>
-__device__ __forceinline__ double block_sum(double v) {
-  static_assert(BS % 32 == 0 && BS <= 1024, "block size");
-  __shared__ double sh[BS / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = (lane < BS / 32) ? sh[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-  }
-  __syncthreads();
-  return r;
-}
-
-// Grid reduction: every block writes its partial; the last block to arrive sums the
-// partials in index order. Returns true in all threads of that last block, where
-// `total` is valid in thread 0.
-template <int BS>
-__device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned int* counter, double& total) {
-  __shared__ bool last;
-  const double bs = block_sum<BS>(v);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = bs;
-    __threadfence();
-    const unsigned int prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  double s = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) s += __ldcg(&partial[i]);
-  total = block_sum<BS>(s);
-  if (threadIdx.x == 0) *counter = 0u;
-  return true;
-}
-
-// G = w |J| J^-1 J^-T (6 entries) and m = w |J| at reference point (a, b, c) from the
-// 8 vertices xv[corner*3 + dim]. J[r][s] = d x_r / d xi_s of the trilinear map.
-template <typename T>
-__device__ __forceinline__ void geom_point(const T* xv, T a, T b, T c, T w, T G[6], T& m, T& det) {
-  T J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  const T one = 1, half = 0.5;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const T sa = ((q == 1) | (q == 2) | (q == 5) | (q == 6)) ? one : -one;
-    const T sb = ((q == 2) | (q == 3) | (q == 6) | (q == 7)) ? one : -one;
-    const T sc = (q >= 4) ? one : -one;
-    const T fa = half * (one + sa * a), fb = half * (one + sb * b), fc = half * (one + sc * c);
-    const T d0 = half * sa * fb * fc, d1 = half * sb * fa * fc, d2 = half * sc * fa * fb;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      const T x = xv[3 * q + r];
-      J[r][0] += x * d0;
-      J[r][1] += x * d1;
-      J[r][2] += x * d2;
-    }
-  }
-  T C[3][3];
-  C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-  C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-  C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-  C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-  C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-  C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-  const T s = w / det;   // inv(J)[r][c] = C[c][r] / det
-  G[0] = s * (C[0][0] * C[0][0] + C[1][0] * C[1][0] + C[2][0] * C[2][0]);
-  G[1] = s * (C[0][0] * C[0][1] + C[1][0] * C[1][1] + C[2][0] * C[2][1]);
-  G[2] = s * (C[0][0] * C[0][2] + C[1][0] * C[1][2] + C[2][0] * C[2][2]);
-  G[3] = s * (C[0][1] * C[0][1] + C[1][1] * C[1][1] + C[2][1] * C[2][1]);
-  G[4] = s * (C[0][1] * C[0][2] + C[1][1] * C[1][2] + C[2][1] * C[2][2]);
-  G[5] = s * (C[0][2] * C[0][2] + C[1][2] * C[1][2] + C[2][2] * C[2][2]);
-  m = w * det;
-}
-
+using namespace sem;
 // ----------------------------------------------------------------- geometry
 template <int p>
 __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d, double* geo, float* geo32,
@@ -143,159 +52,6 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
   }
 }
 
-template <typename T> __device__ __forceinline__ const T* geo_of(const DevProblem& d);
-template <> __device__ __forceinline__ const double* geo_of<double>(const DevProblem& d) { return d.geo; }
-template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
-
-// ----------------------------------------------------------------- operator
-// D (the GLL differentiation matrix) is centro-antisymmetric, D[n-i][n-m] = -D[i][m], and so
-// is D^T. With v = v_e + v_o split into its even and odd parts under m -> n-m,
-//   a = D v_e is odd, s = D v_o is even:  (D v)[i] = a_i + s_i,  (D v)[n-i] = -a_i + s_i,
-// and a_i, s_i need only the folded half-tables
-//   Fp[i][m] = (D[i][m] + D[i][n-m]) / 2,   Fm[i][m] = (D[i][m] - D[i][n-m]) / 2   (m < h)
-// applied to e_m = v[m] + v[n-m] and o_m = v[m] - v[n-m] (plus the middle column D[i][h]
-// times v[h] when p is odd): about 3/4 of the multiply-adds of the plain product.
-template <int p, typename T>
-struct FoldedD {
-  static constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
-  T Fp[H * H > 0 ? H * H : 1], Fm[HM * H > 0 ? HM * H : 1], Fmid[H > 0 ? H : 1];
-};
-
-// Fill the folded tables of M (M = D for the gradient, D^T for the divergence) from
-// Dhat[i*p + m] = phi_m'(t_i); called by one thread per entry.
-template <int p, typename T>
-__device__ __forceinline__ void fold_fill(FoldedD<p, T>& F, const double* __restrict__ D, bool transpose, int t) {
-  constexpr int H = p / 2, ODD = p & 1, HM = H + ODD;
-  constexpr int n = p - 1;
-  auto M = [&](int i, int m) { return transpose ? D[m * p + i] : D[i * p + m]; };
-  if (t < H * H) {
-    const int i = t / H, m = t % H;
-    F.Fp[t] = (T)(0.5 * (M(i, m) + M(i, n - m)));
-  }
-  if (t < HM * H) {
-    const int i = t / H, m = t % H;
-    F.Fm[t] = (T)(0.5 * (M(i, m) - M(i, n - m)));
-  }
-  if (ODD && t < H) F.Fmid[t] = (T)M(t, H);
-}
-
-template <int p, typename T>
-__device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[p], T (&out)[p]) {
-  constexpr int H = p / 2, ODD = p & 1;
-  constexpr int n = p - 1;
-  T e[H], o[H];
-#pragma unroll
-  for (int m = 0; m < H; ++m) { e[m] = v[m] + v[n - m]; o[m] = v[m] - v[n - m]; }
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    T a = ODD ? F.Fmid[i] * v[H] : T(0), sv = 0;
-#pragma unroll
-    for (int m = 0; m < H; ++m) {
-      a += F.Fp[i * H + m] * e[m];
-      sv += F.Fm[i * H + m] * o[m];
-    }
-    out[i] = sv + a;
-    out[n - i] = sv - a;
-  }
-  if (ODD) {
-    T sv = 0;
-#pragma unroll
-    for (int m = 0; m < H; ++m) sv += F.Fm[H * H + m] * o[m];
-    out[H] = sv;
-  }
-}
-
-// One CTA of p*p threads per element (Algorithm 2). Thread (x, y) owns the GLL nodes
-// (x, y, k), k = 0..p-1, for the pointwise work, and one line per direction for the
-// contractions: the gradient by D along i (line j=x, k=y), j (i=x, k=y) and k (i=x, j=y),
-// A/B/C by the geometric factors, the divergence by D^T along the same lines, plus
-// lambda m u.
-template <int p, bool RECOMP, typename T, typename TX>
-__global__ void __launch_bounds__(p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
-                                                         T* __restrict__ wl, const PcgState* st) {
-  if (stopped(st)) return;
-  constexpr int p2 = p * p, p3 = p * p * p;
-  __shared__ FoldedD<p, T> Fg, Fd;
-  __shared__ T su[p3], sA[p3], sB[p3], sC[p3];
-  __shared__ T sx[24];
-  const int e = blockIdx.x, tid = threadIdx.x;
-  const int tx = tid % p, ty = tid / p;
-  fold_fill<p, T>(Fg, d.D, false, tid);
-  fold_fill<p, T>(Fd, d.D, true, tid);
-  if (RECOMP)
-    for (int q = tid; q < 24; q += p2) sx[q] = (T)d.exyz[(size_t)e * 24 + q];
-  const int* l2ge = d.l2g + (size_t)e * p3;
-  T uk[p], rk[p], line[p], res[p];
-#pragma unroll
-  for (int k = 0; k < p; ++k) {
-    const int l = tx + p * (ty + p * k);
-    const int g = l2ge[l];
-    uk[k] = d.mask[g] ? T(0) : (T)x[g];
-    su[l] = uk[k];
-  }
-  __syncthreads();
-  // gradient: d/dxi on line (j=tx, k=ty), d/deta on line (i=tx, k=ty), d/dzeta on (i=tx, j=ty)
-#pragma unroll
-  for (int i = 0; i < p; ++i) line[i] = su[i + p * (tx + p * ty)];
-  fold_apply<p, T>(Fg, line, res);
-#pragma unroll
-  for (int i = 0; i < p; ++i) sA[i + p * (tx + p * ty)] = res[i];
-#pragma unroll
-  for (int j = 0; j < p; ++j) line[j] = su[tx + p * (j + p * ty)];
-  fold_apply<p, T>(Fg, line, res);
-#pragma unroll
-  for (int j = 0; j < p; ++j) sB[tx + p * (j + p * ty)] = res[j];
-  fold_apply<p, T>(Fg, uk, res);
-#pragma unroll
-  for (int k = 0; k < p; ++k) sC[tx + p * (ty + p * k)] = res[k];
-  __syncthreads();
-  // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
-  const T lam = (T)d.lambda;
-#pragma unroll
-  for (int k = 0; k < p; ++k) {
-    const int l = tx + p * (ty + p * k);
-    const T ur = sA[l], us = sB[l], ut = sC[l];
-    T G[6], mm;
-    if (!RECOMP) {
-      const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + l;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
-      mm = gp[6 * p3];
-    } else {
-      T det;
-      geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
-    }
-    sA[l] = G[0] * ur + G[1] * us + G[2] * ut;
-    sB[l] = G[1] * ur + G[3] * us + G[4] * ut;
-    sC[l] = G[2] * ur + G[4] * us + G[5] * ut;
-    rk[k] = lam * mm * uk[k];
-  }
-  __syncthreads();
-  // divergence by D^T: the A lines (j=tx, k=ty) into su, then the B lines (i=tx, k=ty)
-  // added into su, then the C line (i=tx, j=ty) and su added in registers
-#pragma unroll
-  for (int i = 0; i < p; ++i) line[i] = sA[i + p * (tx + p * ty)];
-  fold_apply<p, T>(Fd, line, res);
-#pragma unroll
-  for (int i = 0; i < p; ++i) su[i + p * (tx + p * ty)] = res[i];
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < p; ++j) line[j] = sB[tx + p * (j + p * ty)];
-  fold_apply<p, T>(Fd, line, res);
-#pragma unroll
-  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] += res[j];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < p; ++k) line[k] = sC[tx + p * (ty + p * k)];
-  fold_apply<p, T>(Fd, line, res);
-  T* out = wl + (size_t)e * p3;
-#pragma unroll
-  for (int k = 0; k < p; ++k) {
-    const int l = tx + p * (ty + p * k);
-    out[l] = su[l] + res[k] + rk[k];
-  }
-}
-
 template <typename T>
 __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__ wl,
                                        const double* __restrict__ xin, double* __restrict__ y) {
@@ -313,129 +69,6 @@ __global__ void gather_plain_kernel(const DevProblem d, const double* __restrict
     for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
     y[g] = s;
   }
-}
-
-// ------------------------------------------------------------ fine Schwarz
-// 1/d by Newton-Raphson (x <- x (2 - d x)) from the FP32 reciprocal: two steps take the
-// 2^-24 seed error to below FP64 rounding; used for the per-node eigenvalue sums.
-__device__ __forceinline__ double recip(double d) {
-  double x = (double)(1.0f / (float)d);
-  x = x * (2.0 - d * x);
-  x = x * (2.0 - d * x);
-  return x;
-}
-__device__ __forceinline__ float recip(float d) { return 1.0f / d; }
-
-// Even/odd folded 1D contractions with the pencil eigenvectors S (P x P, modes 0..NE-1
-// even and NE..P-1 odd under row -> P-1-row). fwd: modes t = S^T v; bwd: nodes v = S t.
-template <int P, typename T>
-__device__ __forceinline__ void pencil_fwd(const T* __restrict__ S, const T (&v)[P], T (&t)[P]) {
-  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
-  T e[H], o[H];
-#pragma unroll
-  for (int k = 0; k < H; ++k) { e[k] = v[k] + v[P - 1 - k]; o[k] = v[k] - v[P - 1 - k]; }
-#pragma unroll
-  for (int c = 0; c < NE; ++c) {
-    T a = ODD ? S[H * P + c] * v[H] : T(0);
-#pragma unroll
-    for (int k = 0; k < H; ++k) a += S[k * P + c] * e[k];
-    t[c] = a;
-  }
-#pragma unroll
-  for (int c = NE; c < P; ++c) {
-    T a = 0;
-#pragma unroll
-    for (int k = 0; k < H; ++k) a += S[k * P + c] * o[k];
-    t[c] = a;
-  }
-}
-
-template <int P, typename T>
-__device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)[P], T (&v)[P]) {
-  constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    T E = 0, O = 0;
-#pragma unroll
-    for (int c = 0; c < NE; ++c) E += S[k * P + c] * t[c];
-#pragma unroll
-    for (int c = NE; c < P; ++c) O += S[k * P + c] * t[c];
-    v[k] = E + O;
-    v[P - 1 - k] = E - O;
-  }
-  if (ODD) {
-    T E = 0;
-#pragma unroll
-    for (int c = 0; c < NE; ++c) E += S[H * P + c] * t[c];
-    v[H] = E;
-  }
-}
-
-// One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
-// extended box in each of the six tensor contractions of Eq. z:
-//   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
-//   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
-template <int P, typename T, typename TR>
-__global__ void __launch_bounds__(P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
-                                                              T* __restrict__ wp, const PcgState* st) {
-  if (stopped(st)) return;
-  constexpr int P2 = P * P, P3 = P * P * P;
-  __shared__ T sS[P2], sev[P], s1[P3], s2[P3];
-  const int e = blockIdx.x, tx = threadIdx.x;
-  const int x = tx % P, y = tx / P;
-  sS[tx] = (T)d.S[tx];
-  if (tx < P) sev[tx] = (T)d.ev[tx];
-  const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
-  const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
-  const T scale = (T)(8.0 / (hxd * hyd * hzd));
-  T col[P], out[P];
-  const int* ipe = d.ip + (size_t)e * P3;
-#pragma unroll
-  for (int K = 0; K < P; ++K) {
-    const int g = ipe[x + P * (y + P * K)];
-    col[K] = (g >= 0 && !d.mask[g]) ? (T)r[g] * scale : T(0);
-  }
-  __syncthreads();
-  // along K: line (I=x, J=y)
-  pencil_fwd<P, T>(sS, col, out);
-#pragma unroll
-  for (int c = 0; c < P; ++c) s1[x + P * (y + P * c)] = out[c];
-  __syncthreads();
-  // along J: line (I=x, c=y)
-#pragma unroll
-  for (int J = 0; J < P; ++J) col[J] = s1[x + P * (J + P * y)];
-  pencil_fwd<P, T>(sS, col, out);
-#pragma unroll
-  for (int b = 0; b < P; ++b) s2[x + P * (b + P * y)] = out[b];
-  __syncthreads();
-  // along I: line (b=x, c=y), eigenvalue scaling, and back along I
-#pragma unroll
-  for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
-  pencil_fwd<P, T>(sS, col, out);
-  {
-    const T four = 4, lam = (T)d.lambda;
-    const T lbc = sev[x] * ihy2 + sev[y] * ihz2;
-#pragma unroll
-    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (sev[a] * ihx2 + lbc) + lam);
-  }
-  pencil_bwd<P, T>(sS, out, col);
-#pragma unroll
-  for (int I = 0; I < P; ++I) s2[I + P * (x + P * y)] = col[I];
-  __syncthreads();
-  // back along J: line (I=x, c=y)
-#pragma unroll
-  for (int b = 0; b < P; ++b) out[b] = s2[x + P * (b + P * y)];
-  pencil_bwd<P, T>(sS, out, col);
-#pragma unroll
-  for (int J = 0; J < P; ++J) s1[x + P * (J + P * y)] = col[J];
-  __syncthreads();
-  // back along K: line (I=x, J=y)
-#pragma unroll
-  for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
-  pencil_bwd<P, T>(sS, out, col);
-  T* outp = wp + (size_t)e * P3;
-#pragma unroll
-  for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
 }
 
 // ---------------------------------------------------------------- coarse
@@ -836,33 +469,6 @@ cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_o
   return cudaGetLastError();
 }
 
-template <typename T, typename TX>
-cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
-  switch (d.p) {
-#define AX_CASE(P_)                                                                           \
-  case P_:                                                                                    \
-    if (d.recompute) ax_local_kernel<P_, true, T, TX><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);   \
-    else ax_local_kernel<P_, false, T, TX><<<d.ne, P_ * P_, 0, s>>>(d, x, wl, st);              \
-    ++g_kernel_launches;                                                                      \
-    break;
-    AX_CASE(3) AX_CASE(4) AX_CASE(5) AX_CASE(6) AX_CASE(7) AX_CASE(8) AX_CASE(9)
-#undef AX_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<double, double>(d, x, wl, st, s);
-}
-cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<float, double>(d, x, wl, st, s);
-}
-cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
-                                     cudaStream_t s) {
-  return launch_ax_local_t<float, float>(d, x, wl, st, s);
-}
-
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
   gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
   ++g_kernel_launches;
@@ -879,28 +485,6 @@ cudaError_t launch_gather_plain(const DevProblem& d, const double* wl, double* y
   gather_plain_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, y);
   ++g_kernel_launches;
   return cudaGetLastError();
-}
-
-template <typename T, typename TR>
-cudaError_t launch_schwarz_local_t(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
-  switch (d.P) {
-#define SW_CASE(P_) case P_: schwarz_local_kernel<P_, T, TR><<<d.ne, P_ * P_, 0, s>>>(d, r, wp, st); ++g_kernel_launches; break;
-    SW_CASE(5) SW_CASE(6) SW_CASE(7) SW_CASE(8) SW_CASE(9) SW_CASE(10) SW_CASE(11)
-#undef SW_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
-  return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
-}
-cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
-                                     cudaStream_t s) {
-  return launch_schwarz_local_t<float, double>(d, r, wp, st, s);
-}
-cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
-                                          cudaStream_t s) {
-  return launch_schwarz_local_t<float, float>(d, r, wp, st, s);
 }
 
 template <typename T>

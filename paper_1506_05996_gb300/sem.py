@@ -47,6 +47,9 @@ _SIGS = {
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
+    "sem_solve_many": ([_int, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
+    "sem_set_tiles": ([_vp, _int, _int], _int),
+    "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
     "sem_profile": ([_vp, _int], _int),
     "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
     "sem_last_error": ([], ctypes.c_char_p),
@@ -186,6 +189,31 @@ def sem_apply_A_noalloc(order, n_hex, n_dof, lam, elem_xyz, l2g, g2l_off, g2l_id
             _dev(mask, torch.uint8, n_dof), _dev(x, torch.float64, n_dof), _dev(y, torch.float64, n_dof)]
     return _check(_lib.sem_apply_A_noalloc(int(order), int(n_hex), int(n_dof), float(lam), *args,
                                            _stream_ptr(stream)))
+
+
+def sem_solve_many(handles, bs, xs, rtol=1e-8, maxit=1000):
+    """Returns (status, iterations list, per-solve statuses)."""
+    k = len(handles)
+    H = (ctypes.c_void_p * k)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    ns = [sem_num_dofs(h) for h in handles]
+    B = (ctypes.c_void_p * k)(*[_dev(b, torch.float64, n).value for b, n in zip(bs, ns)])
+    X = (ctypes.c_void_p * k)(*[_dev(x, torch.float64, n).value for x, n in zip(xs, ns)])
+    its = (ctypes.c_int * k)()
+    sts = (ctypes.c_int * k)()
+    rc = _check(_lib.sem_solve_many(k, ctypes.cast(H, ctypes.c_void_p), ctypes.cast(B, ctypes.c_void_p),
+                                    ctypes.cast(X, ctypes.c_void_p), float(rtol), int(maxit),
+                                    ctypes.cast(its, ctypes.c_void_p), ctypes.cast(sts, ctypes.c_void_p)))
+    return rc, list(its), list(sts)
+
+
+def sem_set_tiles(h, epb_ax, epb_sw):
+    return _check(_lib.sem_set_tiles(h, int(epb_ax), int(epb_sw)))
+
+
+def sem_autotune(h):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.sem_autotune(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def sem_profile(h, enable):
