@@ -224,6 +224,60 @@ int sem_apply_A_noalloc(int order, int64_t n_hex, int64_t n_dof, double lambda,
                         const uint8_t* mask_dev, const double* x_dev, double* y_dev,
                         void* cuda_stream);
 
+/*
+ * Learned correction (not in the paper; an extension of the preconditioner of Sec. 4).
+ * A network N maps the residual left by the two-scale preconditioner to a correction:
+ * z = P r + N(r - A P r), inside flexible PCG: beta_k = z_k.(r_k - r_k-1) / (z_k-1.r_k-1)
+ * (Polak-Ribiere form of Algorithm 1's beta), alpha as in Algorithm 1. For an input
+ * vector v (v = r - A P r in the solver), per element e on its (order+1)^3 GLL grid:
+ *   hbar = mean of the element's three box sizes (the h of the Sec. 4.2 patch solve),
+ *   s_l = (v_N / m_N) hbar^2 at the node's DOF N (m_N = sem_mass), sigma_e = rms of s_l,
+ *   input channels (s / sigma_e, hx/hbar, hy/hbar, hz/hbar, lambda hbar^2 / (1 + lambda hbar^2)),
+ *   three 3x3x3 zero-padded correlations 5 -> 8 -> 8 -> 1 (ReLU after the first two),
+ *   local correction y_l sigma_e; N(r) at a DOF = mean over its local copies; 0 on masked DOFs.
+ * Weights are BF16 copies of FP32 master weights; activations and sums are FP32.
+ * The flat parameter vector (sem_net_num_params() = 3041 floats) is
+ * [W1, b1, W2, b2, W3, b3], W[co][ci][a][c][d] the weight of tap (a, c, d) along (i, j, k)
+ * of the local node index i + p(j + p k). Inside a solve the correction is switched off
+ * (plain P from then on) after two consecutive iterations with ||r_k|| >= 0.9 ||r_k-1||.
+ *
+ * sem_net_create     new network on the current device; He-normal first two layers from
+ *                    the seed, last layer zero (an untrained network adds nothing).
+ * sem_net_destroy    frees it; detach it from every handle (sem_set_learned(h, NULL)) first.
+ * sem_net_get_params / sem_net_set_params  copy the FP32 master parameters (n must equal
+ *                    sem_net_num_params()); set also resets the optimiser state.
+ * sem_net_apply      out_dev = N(v_dev) for the handle's mesh (sem_num_dofs doubles each).
+ * sem_net_pair       one training pair from a PCG iterate x_k of A x = b with solution x_star:
+ *                    r = b - A x_k, z0 = P r (the handle's preconditioner and precision),
+ *                    s_dev = r - A z0 (the network input), delta_dev = x_star - x_k - z0
+ *                    (the wanted correction), both 0 on masked DOFs. Uses the solver's
+ *                    scratch vectors: do not overlap it with sem_solve on the same handle.
+ * sem_net_gradient   training loss of one sample, mean over local nodes of
+ *                    (y_l - t_N / sigma_e)^2 with y = N's local output for input v_dev and
+ *                    t = target_dev (e.g. the pair's delta), and its gradient
+ *                    (grad_host: sem_net_num_params() floats, or NULL).
+ * sem_net_train_step the same, then one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with
+ *                    learning rate lr on the master weights.
+ * sem_set_learned    attaches net (or detaches with NULL) to the handle's sem_solve; the
+ *                    handle allocates its forward work space (22 floats per local node).
+ * These calls synchronise the handle's stream (gradient, train, set_learned) or enqueue on
+ * it (apply). Errors: SEM_ERR_ARG, SEM_ERR_OOM, SEM_ERR_CUDA.
+ */
+typedef struct sem_net_s sem_net_t;
+int sem_net_create(uint64_t seed, sem_net_t** out);
+void sem_net_destroy(sem_net_t* net);
+int sem_net_num_params(void);
+int sem_net_get_params(const sem_net_t* net, float* params_host, int n);
+int sem_net_set_params(sem_net_t* net, const float* params_host, int n);
+int sem_net_apply(sem_net_t* net, sem_t* h, const double* v_dev, double* out_dev);
+int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const double* x_k_dev,
+                 double* s_dev, double* delta_dev);
+int sem_net_gradient(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
+                     float* grad_host, double* loss_host);
+int sem_net_train_step(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
+                       float lr, double* loss_host);
+int sem_set_learned(sem_t* h, sem_net_t* net);
+
 /* sem_last_error - message for the last error raised on this thread ("" if none). */
 const char* sem_last_error(void);
 

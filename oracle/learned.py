@@ -1,8 +1,14 @@
 """Learned correction: a per-element 3D convolutional network (FP64 reference).
 
-Not in the paper. The network adds a correction N(r) to the two-scale preconditioner
-inside flexible PCG (z = P r + N(r)). Definition used by the oracle and, independently
-written, by the GPU kernels:
+Test infrastructure only (like the rest of oracle/): never imported by the library.
+
+Not in the paper. The network corrects what the two-scale preconditioner leaves: inside
+flexible PCG, z = P r + N(r - A P r), with the Polak-Ribiere form of the CG beta,
+beta_k = z_k.(r_k - r_k-1) / (z_k-1.r_k-1), and the correction switched off for the rest
+of a solve after two consecutive iterations with ||r_k|| >= 0.9 ||r_k-1||. Training pairs
+from an iterate x_k of A x = b with solution x*: r = b - A x_k, z0 = P r, input
+s = r - A z0, target delta = x* - x_k - z0 (so A delta = s). Definition used by the
+oracle and, independently written, by the GPU kernels:
 
   features of element e on its (n+1)^3 GLL grid (channel, node):
     hbar = (hx + hy + hz) / 3, s_l = (r_N / m_N) hbar^2 at the node's DOF N,
@@ -16,8 +22,11 @@ written, by the GPU kernels:
   training loss for one sample: mean over all local nodes of (y_l - t_l / sigma_e)^2, t the
     local target correction.
 
-Pinned by: single-channel convolution = scipy.ndimage.correlate (constant 0 mode), and the
-backward pass = central finite differences of the loss in FP64.
+Pinned by: single-channel convolution = scipy.ndimage.correlate (constant 0 mode); the
+backward pass = central finite differences of the loss in FP64; flexible PCG with N = 0
+takes the iterations of plain PCG (for a fixed SPD P, z_k.r_k-1 = 0, so the Polak-Ribiere
+beta equals Algorithm 1's); with N = A^-1 (dense solve) the composed preconditioner is
+A^-1 and the solve ends after one iteration; a training pair satisfies A delta = s.
 """
 import numpy as np
 
@@ -134,3 +143,59 @@ def loss_and_grad(theta, r, target_local, m_N, l2g, h, lam):
     loss = np.sum(d ** 2) / L
     gy = (2.0 / L) * d[:, None]
     return loss, backward(theta, cache, gy)
+
+
+STALL_RATIO = 0.81   # ||r_k||^2 >= 0.81 ||r_k-1||^2, i.e. ||r_k|| >= 0.9 ||r_k-1||
+STALL_COUNT = 2
+
+
+def training_pair(apply_A, apply_P, mask, b, x_star, x_k):
+    """(s, delta): r = b - A x_k, z0 = P r, s = r - A z0, delta = x* - x_k - z0 (0 on masked DOFs)."""
+    free = mask == 0
+    r = np.where(free, b - apply_A(x_k), 0.0)
+    z0 = apply_P(r)
+    s = np.where(free, r - apply_A(z0), 0.0)
+    delta = np.where(free, x_star - x_k - z0, 0.0)
+    return s, delta
+
+
+def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000):
+    """Flexible PCG with z = P r + correction(r - A P r); correction None = plain P.
+
+    Returns (x, iterations, relative residual history, iterations done with the correction on).
+    """
+    free = mask == 0
+    r = np.where(free, b, 0.0)
+    x = np.zeros_like(r)
+    r_prev = np.zeros_like(r)
+    bb = r @ r
+    hist = [1.0 if bb > 0 else 0.0]
+    if bb == 0.0:
+        return x, 0, np.array(hist), 0
+    on = correction is not None
+    stall, on_iters, rr = 0, 0, bb
+    p = None
+    rz_old = None
+    for k in range(1, maxit + 1):
+        z = apply_P(r)
+        if on:
+            z = z + correction(np.where(free, r - apply_A(z), 0.0))
+            on_iters += 1
+        rz = z @ r
+        p = z.copy() if p is None else z + ((rz - z @ r_prev) / rz_old) * p
+        rz_old = rz
+        f = apply_A(p)
+        alpha = rz / (p @ f)
+        x = x + alpha * p
+        r_prev = r
+        r = r - alpha * f
+        rr_new = r @ r
+        if on:
+            stall = stall + 1 if rr_new >= STALL_RATIO * rr else 0
+            if stall >= STALL_COUNT:
+                on = False
+        rr = rr_new
+        hist.append(np.sqrt(rr / bb))
+        if hist[-1] <= rtol:
+            return x, k, np.array(hist), on_iters
+    return x, maxit, np.array(hist), on_iters

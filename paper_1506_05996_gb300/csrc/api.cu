@@ -7,8 +7,7 @@
 #include <vector>
 
 #include "../../include/sem.h"
-#include "device.h"
-#include "host_setup.h"
+#include "handle.h"
 
 namespace {
 
@@ -29,127 +28,6 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
-// One PCG iteration (preconditioner, direction, operator, alpha, update) captured as a
-// CUDA graph and replayed once per iteration; with profiling on, its timing events are
-// graph nodes read back after each replay.
-struct IterGraph {
-  cudaGraphExec_t exec = nullptr;
-  long key = -1;
-  std::vector<cudaEvent_t> events;
-  std::vector<int> pair_id, pair_idx;
-  std::vector<uint64_t> pair_kernels;
-  void reset() {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    key = -1;
-    for (auto e : events) cudaEventDestroy(e);
-    events.clear();
-    pair_id.clear();
-    pair_idx.clear();
-    pair_kernels.clear();
-  }
-  ~IterGraph() { reset(); }
-};
-
-constexpr int kGraphBase = 1 << 28;
-
-// Per-kernel timing with CUDA events recorded on the handle's stream around each
-// launch (enabled by sem_profile); accumulated when the stream is synchronised.
-struct Profiler {
-  IterGraph* cap = nullptr;   // set while an iteration graph is being captured
-  bool on = false;
-  std::vector<cudaEvent_t> pool;
-  std::vector<std::pair<int, int>> pending;   // (kernel id, first event index)
-  std::vector<uint64_t> pending_kernels;      // kernels launched inside each pending pair
-  uint64_t count_at_begin = 0;
-  int next = 0;
-  std::vector<std::string> names;
-  std::vector<double> total_ms;
-  std::vector<int64_t> launches;
-
-  int id(const char* name) {
-    for (size_t i = 0; i < names.size(); ++i)
-      if (names[i] == name) return (int)i;
-    names.emplace_back(name);
-    total_ms.push_back(0.0);
-    launches.push_back(0);
-    return (int)names.size() - 1;
-  }
-  int begin(cudaStream_t s) {
-    if (!on) return -1;
-    if (cap != nullptr) {
-      cudaEvent_t a, b;
-      if (cudaEventCreate(&a) != cudaSuccess) return -1;
-      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return -1; }
-      cap->events.push_back(a);
-      cap->events.push_back(b);
-      // an external record becomes an event-record node, whose times can be read back
-      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
-      count_at_begin = sem::kernel_launch_count();
-      return kGraphBase + (int)cap->events.size() - 2;
-    }
-    while ((int)pool.size() < next + 2) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return -1;
-      pool.push_back(e);
-    }
-    int i = next;
-    next += 2;
-    cudaEventRecord(pool[i], s);
-    count_at_begin = sem::kernel_launch_count();
-    return i;
-  }
-  void end(int i, const char* name, cudaStream_t s) {
-    if (i < 0) return;
-    if (i >= kGraphBase) {
-      const int k = i - kGraphBase;
-      cudaEventRecordWithFlags(cap->events[k + 1], s, cudaEventRecordExternal);
-      cap->pair_id.push_back(id(name));
-      cap->pair_idx.push_back(k);
-      cap->pair_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
-      return;
-    }
-    cudaEventRecord(pool[i + 1], s);
-    pending.emplace_back(id(name), i);
-    pending_kernels.push_back(sem::kernel_launch_count() - count_at_begin);
-  }
-  void collect() {   // stream must be synchronised
-    for (size_t q = 0; q < pending.size(); ++q) {
-      const auto& pr = pending[q];
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, pool[pr.second], pool[pr.second + 1]) == cudaSuccess) {
-        total_ms[pr.first] += ms;
-        launches[pr.first] += (int64_t)pending_kernels[q];
-      }
-    }
-    pending.clear();
-    pending_kernels.clear();
-    next = 0;
-  }
-  void collect_graph(const IterGraph& g) {   // after a replay has completed
-    for (size_t q = 0; q < g.pair_id.size(); ++q) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, g.events[g.pair_idx[q]], g.events[g.pair_idx[q] + 1]) == cudaSuccess) {
-        total_ms[g.pair_id[q]] += ms;
-        launches[g.pair_id[q]] += (int64_t)g.pair_kernels[q];
-      } else {
-        cudaGetLastError();   // a timing failure must not look like a later launch failure
-      }
-    }
-  }
-  void reset() {
-    pending.clear();
-    pending_kernels.clear();
-    next = 0;
-    names.clear();
-    total_ms.clear();
-    launches.clear();
-  }
-  ~Profiler() {
-    for (auto e : pool) cudaEventDestroy(e);
-  }
-};
-
 #define PROF_ON(h, strm, name, call)                 \
   do {                                                \
     int pi_ = (h)->prof.begin(strm);                  \
@@ -157,55 +35,6 @@ struct Profiler {
     (h)->prof.end(pi_, name, strm);                   \
   } while (0)
 #define PROF(h, name, call) PROF_ON(h, (h)->stream, name, call)
-
-struct sem_s {
-  Profiler prof;
-  sem::DevProblem d;
-  cudaStream_t stream = nullptr;
-  // The coarse correction runs on a second, high-priority stream concurrently with the
-  // fine patch solves (P = P^c + P^f are independent until they are summed).
-  cudaStream_t coarse_stream = nullptr;
-  cudaStream_t capture_stream = nullptr;   // graphs are captured here (not on a legacy stream)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  int flags = 0;
-  int precond = SEM_PRECOND_TWO_SCALE;
-  sem::Numbering nb;
-  sem::Csr A0full;
-  std::vector<uint8_t> mask_host;
-  std::vector<void*> allocs;        // freed at destroy
-  std::vector<void*> coarse_allocs; // freed when the coarse space is rebuilt
-  std::vector<sem::DevAmgLevel> levels;
-  bool coarse_ok = false;
-  std::string coarse_err;
-  double *coords = nullptr, *mN = nullptr, *geo = nullptr;
-  float* geo32 = nullptr;
-  int precision = SEM_PREC_FP64;
-  uint8_t* mask = nullptr;
-  double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
-  IterGraph graph;
-  double* hist = nullptr;
-  int hist_cap = 0;
-  sem::PcgState* st_host = nullptr;  // pinned
-
-  template <class T>
-  cudaError_t alloc(T** ptr, size_t count, std::vector<void*>& list) {
-    *ptr = nullptr;
-    if (count == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc((void**)ptr, count * sizeof(T));
-    if (e == cudaSuccess) list.push_back(*ptr);
-    return e;
-  }
-  template <class T>
-  cudaError_t upload(T** ptr, const std::vector<T>& v, std::vector<void*>& list) {
-    cudaError_t e = alloc(ptr, v.size(), list);
-    if (e != cudaSuccess || v.empty()) return e;
-    return cudaMemcpyAsync(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, stream);
-  }
-  void free_list(std::vector<void*>& list) {
-    for (void* q : list) cudaFree(q);
-    list.clear();
-  }
-};
 
 namespace {
 
@@ -330,7 +159,22 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   }
   if (coarse) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));   // join
   if (which == SEM_PRECOND_NONE) mode = sem::PSUM_IDENT;
-  PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg, h->stream));
+  const bool flex = pcg && h->net != nullptr;
+  PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg && !flex, h->stream));
+  if (flex) {
+    // z = P r + N(r - A P r), flexible PCG; the operator application and the network skip
+    // once the correction is switched off (d.st_nn->done), the combine keeps the dots
+    if (d.fp32) {
+      float* wl = reinterpret_cast<float*>(d.wl);
+      PROF(h, "ax_local_flex", sem::launch_ax_local_f32(d, z, wl, d.st_nn, h->stream));
+      PROF(h, "nn_residual", sem::launch_residual_of_f32(d, wl, r, d.nns, st, h->stream));
+    } else {
+      PROF(h, "ax_local_flex", sem::launch_ax_local(d, z, d.wl, d.st_nn, h->stream));
+      PROF(h, "nn_residual", sem::launch_residual_of(d, d.wl, r, d.nns, st, h->stream));
+    }
+    PROF(h, "nn_correction", sem::learned_correction(h, d.nns, st, h->stream));
+    PROF(h, "flex_combine", sem::launch_flex_combine(d, z, r, h->stream));
+  }
   return SEM_OK;
 }
 
@@ -490,7 +334,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->mN, (size_t)nb.G, A));
   d.nblk = (int)std::min<int64_t>((nb.G + sem::kVecBlock - 1) / sem::kVecBlock, 152 * 8);
   if (d.nblk < 1) d.nblk = 1;
-  CK(h->alloc(&d.partial, (size_t)d.nblk, A));
+  CK(h->alloc(&d.partial, (size_t)(2 * d.nblk), A));
   CK(h->alloc(&d.st, 1, A));
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), h->stream));
   CK(h->alloc(&h->r, (size_t)nb.G, A));
@@ -541,6 +385,7 @@ void sem_destroy(sem_t* h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   h->free_list(h->coarse_allocs);
+  h->free_list(h->nn_allocs);
   h->free_list(h->allocs);
   if (h->hist) cudaFree(h->hist);
   if (h->st_host) cudaFreeHost(h->st_host);
@@ -628,6 +473,39 @@ int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev) {
 }
 int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev) { return apply_P_common(h, -1, r_dev, z_dev); }
 
+int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const double* x_k_dev, double* s_dev,
+                 double* delta_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (!b_dev || !x_star_dev || !x_k_dev || !s_dev || !delta_dev || s_dev == delta_dev)
+    return fail(SEM_ERR_ARG, "bad vector arguments");
+  for (const double* in : {b_dev, x_star_dev, x_k_dev})
+    if (in == s_dev || in == delta_dev) return fail(SEM_ERR_ARG, "outputs must not alias inputs");
+  sem::DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  double* r = h->f;    // solver scratch, free between solves
+  double* z0 = h->z;
+  float* wl32 = reinterpret_cast<float*>(d.wl);
+  // r = b - A x_k
+  if (d.fp32) {
+    PROF(h, "ax_local", sem::launch_ax_local_f32(d, x_k_dev, wl32, nullptr, s));
+    PROF(h, "nn_residual", sem::launch_residual_of_f32(d, wl32, b_dev, r, nullptr, s));
+  } else {
+    PROF(h, "ax_local", sem::launch_ax_local(d, x_k_dev, d.wl, nullptr, s));
+    PROF(h, "nn_residual", sem::launch_residual_of(d, d.wl, b_dev, r, nullptr, s));
+  }
+  // z0 = P r, s = r - A z0, delta = x_star - x_k - z0
+  if (int rc = apply_precond(h, h->precond, r, z0, false)) return rc;
+  if (d.fp32) {
+    PROF(h, "ax_local", sem::launch_ax_local_f32(d, z0, wl32, nullptr, s));
+    PROF(h, "nn_residual", sem::launch_residual_of_f32(d, wl32, r, s_dev, nullptr, s));
+  } else {
+    PROF(h, "ax_local", sem::launch_ax_local(d, z0, d.wl, nullptr, s));
+    PROF(h, "nn_residual", sem::launch_residual_of(d, d.wl, r, s_dev, nullptr, s));
+  }
+  PROF(h, "nn_pair", sem::launch_pair_delta(d, x_star_dev, x_k_dev, z0, delta_dev, s));
+  return SEM_OK;
+}
+
 int sem_set_precision(sem_t* h, int precision) {
   if (int rc = check_handle(h)) return rc;
   if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32) return fail(SEM_ERR_ARG, "unknown precision");
@@ -696,14 +574,16 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
   };
 
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, h->hist, s));
+  const int learned = h->net != nullptr ? 1 : 0;
+  if (learned) CK(cudaMemsetAsync(d.st_nn, 0, sizeof(sem::PcgState), s));
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
   if (int rc = enqueue_head()) return rc;
 
   // capture the steady-state iteration once per configuration
   const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
-                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8);
+                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8) | ((long)learned << 12);
   if (h->graph.key != key) {
     h->graph.reset();
     CK(cudaStreamSynchronize(s));

@@ -35,6 +35,9 @@ struct PcgState {
   int done;         // 1 once converged / stopped
   int status;       // 0, SEM_MAXIT (1) or SEM_ERR_NAN (-6)
   int maxit;
+  int learned;      // 1: flexible PCG with the learned correction added to z
+  int stall;        // consecutive iterations with ||r_k|| >= 0.9 ||r_k-1|| (learned)
+  int nn_off;       // 1 once the learned correction was switched off for this solve
   unsigned int counter;   // blocks finished in the running reduction
 };
 
@@ -100,9 +103,13 @@ struct DevProblem {
   float* Zc32 = nullptr;            // its FP32 copy (mixed path)
   float* p32 = nullptr;             // FP32 copies of the PCG direction and residual (mixed path)
   float* r32 = nullptr;
-  double* partial = nullptr;        // reduction partials
+  double* nncorr = nullptr;         // learned correction N(s) (flexible PCG)
+  double* nns = nullptr;            // its input s = r - A P r
+  double* rprev = nullptr;          // r_{k-1} for the Polak-Ribiere beta (flexible PCG)
+  double* partial = nullptr;        // reduction partials (2 * nblk)
   int nblk = 0;                     // blocks of the vector kernels
   PcgState* st = nullptr;
+  PcgState* st_nn = nullptr;        // flexible PCG: done = 1 once the learned correction is off
 };
 
 // Records msg as this thread's sem_last_error() text and returns code (api.cu).
@@ -154,7 +161,7 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 
 // --- PCG (Algorithm 1) -------------------------------------------------------
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol,
-                            int maxit, int mixed, double* hist, cudaStream_t s);
+                            int maxit, int mixed, int learned, double* hist, cudaStream_t s);
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
 // f = gather(wl) (0 on masked; FP32 local results when d.fp32), pf = p.f, alpha = rz / pf.
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s);
@@ -164,6 +171,18 @@ cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p
 // r = b - gather(wl) with FP64 local results; decides convergence on the true residual.
 cudaError_t launch_pcg_replace(const DevProblem& d, const double* b, const double* wl, double* r, double* hist,
                                cudaStream_t s);
+// --- learned correction in flexible PCG (not in the paper) ----------------------
+// out = mask ? 0 : v - gather(wl); with st, skipped once the solve stopped or st->nn_off.
+cudaError_t launch_residual_of(const DevProblem& d, const double* wl, const double* v, double* out,
+                               const PcgState* st, cudaStream_t s);
+cudaError_t launch_residual_of_f32(const DevProblem& d, const float* wl, const double* v, double* out,
+                                   const PcgState* st, cudaStream_t s);
+// z += d.nncorr (unless st->nn_off); rz and the Polak-Ribiere beta from z.r and z.rprev.
+cudaError_t launch_flex_combine(const DevProblem& d, double* z, const double* r, cudaStream_t s);
+// delta = mask ? 0 : xs - xk - z0
+cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const double* xk, const double* z0,
+                              double* delta, cudaStream_t s);
+
 // aux = ||b - f||^2 over free nodes
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s);
 

@@ -60,6 +60,34 @@ __device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned 
   return true;
 }
 
+// Two sums at once (partial holds 2 * gridDim.x entries): the same last-block rule.
+template <int BS>
+__device__ __forceinline__ bool grid_reduce2(double v0, double v1, double* partial, unsigned int* counter,
+                                             double& t0, double& t1) {
+  __shared__ bool last2;
+  const double b0 = block_sum<BS>(v0);
+  const double b1 = block_sum<BS>(v1);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = b0;
+    partial[gridDim.x + blockIdx.x] = b1;
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    last2 = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last2) return false;
+  __threadfence();
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) {
+    s0 += __ldcg(&partial[i]);
+    s1 += __ldcg(&partial[gridDim.x + i]);
+  }
+  t0 = block_sum<BS>(s0);
+  t1 = block_sum<BS>(s1);
+  if (threadIdx.x == 0) *counter = 0u;
+  return true;
+}
+
 // G = w |J| J^-1 J^-T (6 entries) and m = w |J| at reference point (a, b, c) from the
 // 8 vertices xv[corner*3 + dim]. J[r][s] = d x_r / d xi_s of the trilinear map.
 template <typename T>

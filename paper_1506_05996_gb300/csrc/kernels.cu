@@ -269,12 +269,14 @@ __global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __rest
 
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
-                                                             double rtol, int maxit, int mixed, double* hist) {
+                                                             double rtol, int maxit, int mixed, int learned,
+                                                             double* hist) {
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
     r[g] = v;
     if (mixed) d.r32[g] = (float)v;
+    if (learned) d.rprev[g] = 0.0;
     u[g] = 0.0;
     dot += v * v;
   }
@@ -293,6 +295,9 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
     st->mixed = mixed;
     st->replace = 0;
     st->replacements = 0;
+    st->learned = learned;
+    st->stall = 0;
+    st->nn_off = 0;
     hist[0] = (total > 0.0) ? 1.0 : 0.0;
     if (!isfinite(total)) { st->status = -6; st->done = 1; }
     else if (total == 0.0) st->done = 1;
@@ -339,9 +344,12 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
   const double alpha = d.st->alpha;
   float* __restrict__ r32 = d.st->mixed ? d.r32 : nullptr;
   double dot = 0.0;
+  double* __restrict__ rprev = d.st->learned ? d.rprev : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     u[g] = u[g] + alpha * p[g];
-    const double rn = r[g] - alpha * f[g];
+    const double ro = r[g];
+    const double rn = ro - alpha * f[g];
+    if (rprev) rprev[g] = ro;
     r[g] = rn;
     if (r32) r32[g] = (float)rn;
     dot += rn * rn;
@@ -349,6 +357,14 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
   double total;
   if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
     PcgState* st = d.st;
+    if (st->learned) {
+      // a correction that stops reducing the residual is switched off for the rest of the solve
+      st->stall = (total >= 0.81 * st->rr) ? st->stall + 1 : 0;
+      if (st->stall >= 2) {
+        st->nn_off = 1;
+        d.st_nn->done = 1;
+      }
+    }
     st->rr = total;
     const int it = ++st->iter;
     const double rel = sqrt(total) / sqrt(st->bb);
@@ -404,6 +420,56 @@ __global__ void pcg_direction_kernel(const DevProblem d, const double* __restric
     p[g] = pn;
     if (p32) p32[g] = (float)pn;
   }
+}
+
+// out = mask ? 0 : v - gather(wl): the residual of an operator application (flexible PCG:
+// s = r - A P r; training pairs: r = b - A x). Skipped inside PCG once the network is off.
+template <typename T>
+__global__ void __launch_bounds__(kVecBlock) residual_of_kernel(const DevProblem d, const T* __restrict__ wl,
+                                                                const double* __restrict__ v, double* __restrict__ out,
+                                                                const PcgState* st) {
+  if (st != nullptr && (st->done || st->nn_off)) return;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double res = 0.0;
+    if (!d.mask[g]) {
+      T s = 0;
+      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+      res = v[g] - (double)s;
+    }
+    out[g] = res;
+  }
+}
+
+// Flexible PCG: z += N(s) (unless switched off), then z.r and z.r_prev, and
+// beta = z_k.(r_k - r_k-1) / (z_k-1.r_k-1) (Polak-Ribiere form), rz = z_k.r_k.
+__global__ void __launch_bounds__(kVecBlock) flex_combine_kernel(const DevProblem d, double* __restrict__ z,
+                                                                 const double* __restrict__ r) {
+  if (stopped(d.st)) return;
+  const bool use_nn = d.st->nn_off == 0;
+  double zr = 0.0, zrp = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    double v = z[g];
+    if (use_nn) {
+      v += d.nncorr[g];
+      z[g] = v;
+    }
+    zr += v * r[g];
+    zrp += v * d.rprev[g];
+  }
+  double t0, t1;
+  if (grid_reduce2<kVecBlock>(zr, zrp, d.partial, &d.st->counter, t0, t1) && threadIdx.x == 0) {
+    PcgState* st = d.st;
+    if (!isfinite(t0) || !isfinite(t1)) { st->status = -6; st->done = 1; }
+    if (st->iter > 0) st->beta = (t0 - t1) / st->rz;
+    st->rz = t0;
+  }
+}
+
+// Training pair: delta = mask ? 0 : x_star - x_k - z0 (the error left after z0 = P r).
+__global__ void pair_delta_kernel(const DevProblem d, const double* __restrict__ xs, const double* __restrict__ xk,
+                                  const double* __restrict__ z0, double* __restrict__ delta) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x)
+    delta[g] = d.mask[g] ? 0.0 : xs[g] - xk[g] - z0[g];
 }
 
 __global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProblem d, const double* __restrict__ b,
@@ -550,8 +616,8 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 }
 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
-                            int mixed, double* hist, cudaStream_t s) {
-  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, hist);
+                            int mixed, int learned, double* hist, cudaStream_t s) {
+  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -591,6 +657,34 @@ cudaError_t launch_pcg_replace(const DevProblem& d, const double* b, const doubl
 
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s) {
   true_residual_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, wl);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_residual_of(const DevProblem& d, const double* wl, const double* v, double* out,
+                               const PcgState* st, cudaStream_t s) {
+  residual_of_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, v, out, st);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_of_f32(const DevProblem& d, const float* wl, const double* v, double* out,
+                                   const PcgState* st, cudaStream_t s) {
+  residual_of_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, v, out, st);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flex_combine(const DevProblem& d, double* z, const double* r, cudaStream_t s) {
+  flex_combine_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, r);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const double* xk, const double* z0,
+                              double* delta, cudaStream_t s) {
+  pair_delta_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, xs, xk, z0, delta);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

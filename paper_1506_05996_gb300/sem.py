@@ -52,6 +52,16 @@ _SIGS = {
     "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
     "sem_profile": ([_vp, _int], _int),
     "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
+    "sem_net_create": ([ctypes.c_uint64, _P(_vp)], _int),
+    "sem_net_destroy": ([_vp], None),
+    "sem_net_num_params": ([], _int),
+    "sem_net_get_params": ([_vp, _vp, _int], _int),
+    "sem_net_set_params": ([_vp, _vp, _int], _int),
+    "sem_net_apply": ([_vp, _vp, _vp, _vp], _int),
+    "sem_net_pair": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
+    "sem_net_gradient": ([_vp, _vp, _vp, _vp, _vp, _P(_dbl)], _int),
+    "sem_net_train_step": ([_vp, _vp, _vp, _vp, ctypes.c_float, _P(_dbl)], _int),
+    "sem_set_learned": ([_vp, _vp], _int),
     "sem_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -233,6 +243,63 @@ def sem_profile_read(h, max_kernels=64):
         nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(total[i]))
     return out
+
+
+def sem_net_create(seed):
+    net = ctypes.c_void_p()
+    _check(_lib.sem_net_create(int(seed), ctypes.byref(net)))
+    return net
+
+
+def sem_net_destroy(net):
+    _lib.sem_net_destroy(net)
+
+
+def sem_net_num_params():
+    return _lib.sem_net_num_params()
+
+
+def sem_net_get_params(net):
+    out = np.zeros(sem_net_num_params(), dtype=np.float32)
+    _check(_lib.sem_net_get_params(net, out.ctypes.data, out.size))
+    return out
+
+
+def sem_net_set_params(net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(_lib.sem_net_set_params(net, a.ctypes.data, a.size))
+
+
+def sem_net_apply(net, h, r, out):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_net_apply(net, h, _dev(r, torch.float64, n), _dev(out, torch.float64, n)))
+
+
+def sem_net_pair(h, b, x_star, x_k, s, delta):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_net_pair(h, *[_dev(v, torch.float64, n) for v in (b, x_star, x_k, s, delta)]))
+
+
+def sem_net_gradient(net, h, r, target):
+    """Returns (loss, gradient as float32 numpy array)."""
+    n = sem_num_dofs(h)
+    g = np.zeros(sem_net_num_params(), dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.sem_net_gradient(net, h, _dev(r, torch.float64, n), _dev(target, torch.float64, n),
+                                 g.ctypes.data, ctypes.byref(loss)))
+    return loss.value, g
+
+
+def sem_net_train_step(net, h, r, target, lr):
+    n = sem_num_dofs(h)
+    loss = ctypes.c_double()
+    _check(_lib.sem_net_train_step(net, h, _dev(r, torch.float64, n), _dev(target, torch.float64, n),
+                                   float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def sem_set_learned(h, net):
+    return _check(_lib.sem_set_learned(h, net))
 
 
 class SemProblem:

@@ -1,0 +1,189 @@
+"""Learned correction (not in the paper) on the GPU against oracle/learned.py.
+
+The library's network keeps FP32 master weights and computes with their BF16 copies,
+FP32 activations and FP32 sums; the oracle runs the same network in FP64 with the weights
+rounded to BF16 (round to nearest even), so both evaluate the same function and differ by
+FP32 rounding only: forward results within 1e-4 of the largest magnitude, loss within 1e-5
+relative, gradients within 2e-3 of the largest component (FP32 sums over up to 10^4
+terms per weight). Training pairs and the flexible PCG use the FP64 operator and
+preconditioner (1e-10).
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import lattice_hex_mesh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1506_05996_gb300 import build
+    build.build()
+
+
+def _bf16(theta):
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float64."""
+    u = np.ascontiguousarray(theta, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _effective(theta32):
+    """Parameters the kernels use: BF16 weights, FP32 biases."""
+    from oracle import learned
+    out = np.asarray(theta32, dtype=np.float32).astype(np.float64)
+    k = 0
+    for ci, co, _ in learned.LAYERS:
+        nw = co * ci * 27
+        out[k:k + nw] = _bf16(theta32[k:k + nw])
+        k += nw + co
+    return out
+
+
+def _pair(E=3, n=4, lam=1.3, a=0.2, seed=2):
+    from gpu_util import Pair
+    return Pair(lattice_hex_mesh(E, a, seed), n, lam)
+
+
+def _random_net(seed, scale=0.2):
+    from paper_1506_05996_gb300 import sem
+    net = sem.sem_net_create(seed)
+    theta = (np.random.default_rng(seed).standard_normal(sem.sem_net_num_params()) * scale).astype(np.float32)
+    sem.sem_net_set_params(net, theta)
+    return net, theta
+
+
+def test_bf16_rounding_helper():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 1.0 + 2 ** -7], dtype=np.float32)
+    np.testing.assert_array_equal(_bf16(x), [1.0, 1.0, 1.0 + 2 ** -6, -2.5, 1.0 + 2 ** -7])
+
+
+def test_params_roundtrip_and_zero_last_layer():
+    from oracle import learned
+    from paper_1506_05996_gb300 import sem
+    assert sem.sem_net_num_params() == learned.n_params()
+    net = sem.sem_net_create(11)
+    th = sem.sem_net_get_params(net)
+    W3, b3 = learned.unpack(th.astype(np.float64))[2]
+    assert np.all(W3 == 0) and np.all(b3 == 0) and np.abs(th).max() > 0
+    new = np.arange(th.size, dtype=np.float32) * 1e-3
+    sem.sem_net_set_params(net, new)
+    np.testing.assert_array_equal(sem.sem_net_get_params(net), new)
+    with pytest.raises(sem.SemError):
+        sem.sem_net_set_params(net, new[:-1])
+    sem.sem_net_destroy(net)
+
+
+@pytest.mark.parametrize("E,n,lam,seed", [(3, 4, 1.3, 2), (2, 7, 0.0, 3), (2, 2, 5.0, 4)])
+def test_forward_parity(E, n, lam, seed):
+    from oracle import learned
+    from paper_1506_05996_gb300 import sem
+    P = _pair(E, n, lam, seed=seed)
+    net, theta = _random_net(seed)
+    v = np.random.default_rng(seed + 1).standard_normal(P.ref.G) * (P.ref.mask == 0)
+    out = torch.empty(P.gpu.n_dof, dtype=torch.float64, device="cuda")
+    sem.sem_net_apply(net, P.gpu.h, P.to_gpu(v), out)
+    got = P.to_ref(out)
+    ref = learned.correction(_effective(theta), v, P.ref.m_N, P.ref.l2g, P.ref.h, P.ref.lam, P.ref.mask)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    assert np.all(got[P.ref.mask > 0] == 0)
+    sem.sem_net_destroy(net)
+
+
+@pytest.mark.parametrize("E,n,lam,seed", [(3, 4, 1.3, 5), (2, 6, 0.4, 6)])
+def test_gradient_parity(E, n, lam, seed):
+    from oracle import learned
+    from paper_1506_05996_gb300 import sem
+    P = _pair(E, n, lam, seed=seed)
+    net, theta = _random_net(seed, 0.3)
+    rng = np.random.default_rng(seed + 2)
+    v = rng.standard_normal(P.ref.G) * (P.ref.mask == 0)
+    t = rng.standard_normal(P.ref.G) * 0.1
+    loss, g = sem.sem_net_gradient(net, P.gpu.h, P.to_gpu(v), P.to_gpu(t))
+    ref_loss, ref_g = learned.loss_and_grad(_effective(theta), v, t[P.ref.l2g], P.ref.m_N, P.ref.l2g, P.ref.h,
+                                            P.ref.lam)
+    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
+    assert np.max(np.abs(g - ref_g)) <= 2e-3 * np.max(np.abs(ref_g))
+    sem.sem_net_destroy(net)
+
+
+def test_training_pair_parity():
+    from oracle import learned
+    from paper_1506_05996_gb300 import sem
+    from gpu_util import rel_err
+    P = _pair(3, 5, 0.8, seed=7)
+    rng = np.random.default_rng(8)
+    b = P.ref.load(rng.standard_normal(P.ref.G))
+    xs = rng.standard_normal(P.ref.G) * (P.ref.mask == 0)
+    xk = rng.standard_normal(P.ref.G) * (P.ref.mask == 0)
+    s = torch.empty(P.gpu.n_dof, dtype=torch.float64, device="cuda")
+    d = torch.empty_like(s)
+    sem.sem_net_pair(P.gpu.h, P.to_gpu(b), P.to_gpu(xs), P.to_gpu(xk), s, d)
+    rs, rd = learned.training_pair(P.ref.apply_A, P.ref.apply_P, P.ref.mask, b, xs, xk)
+    assert rel_err(P.to_ref(s), rs) <= 1e-10
+    assert rel_err(P.to_ref(d), rd) <= 1e-10
+
+
+def test_untrained_network_gives_plain_pcg():
+    from paper_1506_05996_gb300 import sem
+    from paper_1506_05996_gb300.learn import make_problem
+    prob, b = make_problem(4, 0.2, 9, 5, 1.0)
+    _, rc0, it0, h0, tr0 = prob.solve(b)
+    net = sem.sem_net_create(3)          # last layer zero: N = 0
+    sem.sem_set_learned(prob.h, net)
+    _, rc1, it1, h1, tr1 = prob.solve(b)
+    sem.sem_set_learned(prob.h, None)
+    assert rc0 == rc1 == 0 and abs(it1 - it0) <= 1 and tr1 <= 1e-8
+    k = min(len(h0), len(h1), 8)
+    np.testing.assert_allclose(h1[:k], h0[:k], rtol=1e-6)
+    sem.sem_net_destroy(net)
+
+
+def test_flexible_pcg_parity():
+    """FPCG with a small random network against the oracle's FPCG (same composition, BF16 weights)."""
+    from oracle import learned
+    from paper_1506_05996_gb300 import sem
+    P = _pair(3, 4, 1.0, seed=10)
+    net, theta = _random_net(12, 0.05)
+    eff = _effective(theta)
+    rng = np.random.default_rng(13)
+    b = P.ref.load(rng.standard_normal(P.ref.G))
+    corr = lambda v: learned.correction(eff, v, P.ref.m_N, P.ref.l2g, P.ref.h, P.ref.lam, P.ref.mask)
+    _, it_ref, h_ref, on_ref = learned.fpcg(P.ref.apply_A, P.ref.apply_P, corr, P.ref.mask, b)
+    sem.sem_set_learned(P.gpu.h, net)
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b))
+    sem.sem_set_learned(P.gpu.h, None)
+    assert rc == 0 and tr <= 1e-8
+    assert abs(it - it_ref) <= 2
+    np.testing.assert_allclose(hist[:4], h_ref[:4], rtol=1e-3)
+    sem.sem_net_destroy(net)
+
+
+def test_bad_network_falls_back_and_converges():
+    from paper_1506_05996_gb300 import sem
+    from paper_1506_05996_gb300.learn import make_problem
+    prob, b = make_problem(4, 0.2, 14, 4, 0.5)
+    it0 = prob.solve(b)[2]
+    net, _ = _random_net(15, 3.0)
+    sem.sem_set_learned(prob.h, net)
+    _, rc, it, hist, tr = prob.solve(b, maxit=600)
+    sem.sem_set_learned(prob.h, None)
+    assert rc == 0 and tr <= 1e-8 and hist[-1] <= 1e-8
+    assert it <= 4 * it0 + 20
+    sem.sem_net_destroy(net)
+
+
+def test_training_reduces_loss():
+    from paper_1506_05996_gb300 import sem
+    from paper_1506_05996_gb300.learn import train, training_set
+    samples = training_set(4, 5, 4, seed=1)
+    net = sem.sem_net_create(21)
+    losses = train(net, samples, 150, lr=3e-3, seed=2)
+    first = float(np.mean(losses[:10]))
+    last = float(np.mean(losses[-10:]))
+    assert np.isfinite(losses).all() and last < 0.7 * first, (first, last)
+    sem.sem_net_destroy(net)

@@ -51,3 +51,58 @@ def test_loss_gradient_and_correction_properties():
     # scale equivariance: N(a r) = a N(r) for a > 0 (features are normalised per element)
     c2 = learned.correction(theta, 3.5 * r, pr.m_N, pr.l2g, pr.h, pr.lam, pr.mask)
     np.testing.assert_allclose(c2, 3.5 * c, rtol=1e-12, atol=1e-300)
+
+
+def _small_problem():
+    return Problem(lattice_hex_mesh(3, 0.2, 5), 3, 0.7, coarse_solver="exact")
+
+
+def test_fpcg_without_correction_is_pcg():
+    # fixed SPD P: z_k.r_k-1 = 0, so the Polak-Ribiere beta equals the one of Algorithm 1
+    pr = _small_problem()
+    b = pr.load(np.random.default_rng(3).standard_normal(pr.G))
+    x0, it0, h0 = pr.solve(b, rtol=1e-10)[:3]
+    x1, it1, h1, on = learned.fpcg(pr.apply_A, pr.apply_P, None, pr.mask, b, rtol=1e-10)
+    assert it1 == it0 and on == 0
+    np.testing.assert_allclose(h1, h0, rtol=1e-6, atol=1e-13)
+    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-9 * np.abs(x0).max())
+
+
+def test_fpcg_with_exact_correction_ends_in_one_step():
+    # N = A^-1 on the free DOFs makes P r + N(r - A P r) = A^-1 r
+    pr = _small_problem()
+    A = pr.assembled().toarray()
+    free = pr.mask == 0
+    Aff = A[np.ix_(free, free)]
+    def exact(v):
+        out = np.zeros_like(v)
+        out[free] = np.linalg.solve(Aff, v[free])
+        return out
+    b = pr.load(np.random.default_rng(4).standard_normal(pr.G))
+    x, it, hist, on = learned.fpcg(pr.apply_A, pr.apply_P, exact, pr.mask, b, rtol=1e-10)
+    assert it == 1 and on == 1 and hist[-1] < 1e-11
+
+
+def test_fpcg_stall_switches_correction_off():
+    pr = _small_problem()
+    b = pr.load(np.random.default_rng(5).standard_normal(pr.G))
+    rng = np.random.default_rng(6)
+    noise = lambda v: rng.standard_normal(v.shape) * np.linalg.norm(v) * (pr.mask == 0)
+    x, it, hist, on = learned.fpcg(pr.apply_A, pr.apply_P, noise, pr.mask, b, rtol=1e-8, maxit=400)
+    assert hist[-1] <= 1e-8 and on < it
+    ref_it = pr.solve(b, rtol=1e-8)[1]
+    assert it <= ref_it + on + 10
+
+
+def test_training_pair_satisfies_A_delta_equals_s():
+    pr = _small_problem()
+    A = pr.assembled().toarray()
+    free = pr.mask == 0
+    rng = np.random.default_rng(7)
+    b = pr.load(rng.standard_normal(pr.G))
+    x_star = np.zeros(pr.G)
+    x_star[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
+    x_k = pr.solve(b, rtol=1e-8, maxit=3)[0]
+    s, delta = learned.training_pair(pr.apply_A, pr.apply_P, pr.mask, b, x_star, x_k)
+    np.testing.assert_allclose(pr.apply_A(delta), s, atol=1e-10 * np.abs(s).max())
+    assert np.all(s[~free] == 0) and np.all(delta[~free] == 0)
