@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--batch-variant", action="store_true",
                     help="24 problems (8^3..24^3 hexes, n in 3..8, +-15%%, seed 3), 4 Gaussian loads each: "
                          "one at a time vs sem_solve_many, default vs autotuned tile shapes")
+    ap.add_argument("--learned-variant", action="store_true",
+                    help="learned correction: train on seeded 16^3-hex n=5 meshes (lambda ~ U[0,10]), then "
+                         "plain against flexible PCG with the network on an unseen 32^3-hex n=7 mesh (seed 4)")
+    ap.add_argument("--train-meshes", type=int, default=200)
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
                     help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
                          "(a small case for ncu captures), then exit")
@@ -588,9 +593,72 @@ def run_batch_variant(args):
         pr.close()
 
 
+def run_learned_variant(args):
+    """Learned correction: GPU training on solver-harvested samples, then plain two-scale PCG
+    against flexible PCG with the network (fallback on stall), FP64 and mixed."""
+    import numpy as np
+    import torch
+    from paper_1506_05996_gb300 import sem as S
+    from paper_1506_05996_gb300.learn import harvest, make_problem, timed_solve, train, training_set
+    t0 = time.perf_counter()
+    problems, samples = training_set(args.train_meshes, 16, 5, seed=0)
+    torch.cuda.synchronize()
+    t_harvest = time.perf_counter() - t0
+    net = S.sem_net_create(5)
+    t0 = time.perf_counter()
+    losses = train(net, samples, args.train_steps, lr=3e-3, seed=1, loss="angle")
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    for prob, _ in problems:
+        prob.close()
+    del problems, samples
+    prob, b = make_problem(32, 0.2, 4, ORDER, LAM, mixed=True)
+    # quality on the unseen mesh: A-angle cosine of z0 = P r and z = z0 + N(s) with the error
+    quality = []
+    for s_, d_, r_, z0_ in harvest(prob, b, ks=(0, 2, 8, 24)):
+        c = torch.empty_like(s_)
+        S.sem_net_apply(net, prob.h, s_, c)
+        e = d_ + z0_
+        E = float(e @ r_)
+        cos = lambda z: float(z @ r_) / np.sqrt(float(z @ prob.apply_A(z)) * E)
+        quality.append({"cos_P": cos(z0_), "cos_P_plus_N": cos(z0_ + c)})
+    out = {}
+    for prec in ("fp64", "fp32"):
+        prob.set_precision(prec)
+        row = {}
+        for name, nn in (("plain", None), ("learned", net)):
+            its, ts, trs, used = [], [], [], []
+            for _ in range(max(1, args.steps)):
+                it, dt, tr, rc, u = timed_solve(prob, b, nn, rtol=RTOL, maxit=1000, window=8, ratio=0.5, theta=0.25)
+                its.append(it)
+                ts.append(dt)
+                trs.append(tr)
+                used.append(u)
+            row[name] = {"iterations": its[-1], "time_to_1e-8_s": float(np.median(ts)), "true_rel_res": trs[-1],
+                         "iterations_using_network": used[-1] if nn is not None else 0}
+        row["time_ratio_learned_over_plain"] = row["learned"]["time_to_1e-8_s"] / row["plain"]["time_to_1e-8_s"]
+        row["iteration_gain"] = row["plain"]["iterations"] - row["learned"]["iterations"]
+        out[prec] = row
+    print(json.dumps({"variant": "learned", "config": {
+        "training": "%d seeded 16^3-hex meshes (+-20%%, seeds 1000..), n=5, lambda ~ U[0,10], manufactured and "
+                    "Gaussian loads; samples at PCG iterates k in {0,1,2,4,8,16}; %d Adam steps, angle loss, "
+                    "lr 3e-3 cosine" % (args.train_meshes, args.train_steps),
+        "evaluation": "unseen 32^3-hex mesh, +-20% perturbation seed 4, n=7, lambda=1, manufactured load; "
+                      "flexible PCG z = P r + N(r - A P r), accept if (z0+c).r >= 0.25 z0.r, off when "
+                      "||r_k|| >= 0.5 ||r_k-8||",
+        "n_dof": prob.n_dof, "params": S.sem_net_num_params()},
+        "harvest_s": t_harvest, "train_s": t_train,
+        "loss_first_50": float(np.mean(losses[:50])), "loss_last_300": float(np.mean(losses[-300:])),
+        "unseen_mesh_angle_cosines": quality, **out}))
+    S.sem_net_destroy(net)
+    prob.close()
+
+
 def main():
     args = parse()
-    if args.batch_variant:
+    if args.learned_variant:
+        run_learned_variant(args)
+    elif args.batch_variant:
         run_batch_variant(args)
     elif args.precision_variant:
         run_precision_variant(args)

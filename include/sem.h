@@ -238,8 +238,11 @@ int sem_apply_A_noalloc(int order, int64_t n_hex, int64_t n_dof, double lambda,
  * Weights are BF16 copies of FP32 master weights; activations and sums are FP32.
  * The flat parameter vector (sem_net_num_params() = 3041 floats) is
  * [W1, b1, W2, b2, W3, b3], W[co][ci][a][c][d] the weight of tap (a, c, d) along (i, j, k)
- * of the local node index i + p(j + p k). Inside a solve the correction is switched off
- * (plain P from then on) after two consecutive iterations with ||r_k|| >= 0.9 ||r_k-1||.
+ * of the local node index i + p(j + p k). Inside a solve, with z0 = P r and c = N(r - A z0),
+ * an iteration's direction uses z0 + c only if (z0 + c).r >= accept_theta z0.r (else z0:
+ * every step stays a descent step), and the correction is switched off for the rest of the
+ * solve at the first iteration k >= W with ||r_k|| >= stall_ratio ||r_k-W||, W = stall_window
+ * (both set by sem_set_learned).
  *
  * sem_net_create     new network on the current device; He-normal first two layers from
  *                    the seed, last layer zero (an untrained network adds nothing).
@@ -250,16 +253,34 @@ int sem_apply_A_noalloc(int order, int64_t n_hex, int64_t n_dof, double lambda,
  * sem_net_pair       one training pair from a PCG iterate x_k of A x = b with solution x_star:
  *                    r = b - A x_k, z0 = P r (the handle's preconditioner and precision),
  *                    s_dev = r - A z0 (the network input), delta_dev = x_star - x_k - z0
- *                    (the wanted correction), both 0 on masked DOFs. Uses the solver's
- *                    scratch vectors: do not overlap it with sem_solve on the same handle.
- * sem_net_gradient   training loss of one sample, mean over local nodes of
- *                    (y_l - t_N / sigma_e)^2 with y = N's local output for input v_dev and
- *                    t = target_dev (e.g. the pair's delta), and its gradient
- *                    (grad_host: sem_net_num_params() floats, or NULL).
+ *                    (the wanted correction), all 0 on masked DOFs; r_dev and z0_dev receive
+ *                    r and z0 unless NULL. Uses the solver's scratch vectors: do not overlap
+ *                    it with sem_solve on the same handle.
+ * sem_net_gradient   training loss of one sample (input v_dev, target t = target_dev, e.g.
+ *                    the pair's s and delta) and its gradient (grad_host:
+ *                    sem_net_num_params() floats, or NULL). loss_kind:
+ *                    SEM_NET_LOSS_L2      mean over local nodes of (y_l - t_N / sigma_e)^2,
+ *                                         y = N's local output;
+ *                    SEM_NET_LOSS_ENERGY  1 + (c^T A c - 2 c^T v) / (t^T v) for c = N(v): with
+ *                                         v = A t this is ||t - c||_A^2 / ||t||_A^2, the error
+ *                                         norm CG minimises (one more operator application,
+ *                                         in the handle's precision);
+ *                    SEM_NET_LOSS_ANGLE   1 - z^T r / sqrt((z^T A z)(e^T r)) for z = z0_dev + c
+ *                                         and e = t + z0_dev, with the pair's r_dev and z0_dev
+ *                                         (A e = r): 1 - cos of the A-angle between z and e
+ *                                         (an exact line search along z leaves 1 - cos^2 of
+ *                                         ||e||_A^2), invariant to positive scaling of z.
+ *                    r_dev and z0_dev may be NULL for the first two losses.
  * sem_net_train_step the same, then one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with
  *                    learning rate lr on the master weights.
- * sem_set_learned    attaches net (or detaches with NULL) to the handle's sem_solve; the
- *                    handle allocates its forward work space (22 floats per local node).
+ * sem_set_learned    attaches net (or detaches with NULL) to the handle's sem_solve, with the
+ *                    stall rule's window (0..8; 0 = never switch off) and ratio (> 0) and the
+ *                    acceptance threshold accept_theta (8, 0.5 and 0.25 recommended: the
+ *                    residual norm of two-scale PCG can rise over its first few iterations;
+ *                    -inf accepts every correction); the handle allocates its forward work
+ *                    space (22 floats per local node).
+ * sem_learned_iterations  iterations of the handle's last sem_solve whose direction used the
+ *                    correction.
  * These calls synchronise the handle's stream (gradient, train, set_learned) or enqueue on
  * it (apply). Errors: SEM_ERR_ARG, SEM_ERR_OOM, SEM_ERR_CUDA.
  */
@@ -271,12 +292,19 @@ int sem_net_get_params(const sem_net_t* net, float* params_host, int n);
 int sem_net_set_params(sem_net_t* net, const float* params_host, int n);
 int sem_net_apply(sem_net_t* net, sem_t* h, const double* v_dev, double* out_dev);
 int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const double* x_k_dev,
-                 double* s_dev, double* delta_dev);
+                 double* s_dev, double* delta_dev, double* r_dev, double* z0_dev);
+#define SEM_NET_LOSS_L2      0
+#define SEM_NET_LOSS_ENERGY  1
+#define SEM_NET_LOSS_ANGLE   2
 int sem_net_gradient(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
+                     const double* r_dev, const double* z0_dev, int loss_kind,
                      float* grad_host, double* loss_host);
 int sem_net_train_step(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
-                       float lr, double* loss_host);
-int sem_set_learned(sem_t* h, sem_net_t* net);
+                       const double* r_dev, const double* z0_dev, int loss_kind, float lr,
+                       double* loss_host);
+int sem_set_learned(sem_t* h, sem_net_t* net, int stall_window, double stall_ratio,
+                    double accept_theta);
+int sem_learned_iterations(const sem_t* h, int* used_host);
 
 /* sem_last_error - message for the last error raised on this thread ("" if none). */
 const char* sem_last_error(void);

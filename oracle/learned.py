@@ -5,7 +5,8 @@ Test infrastructure only (like the rest of oracle/): never imported by the libra
 Not in the paper. The network corrects what the two-scale preconditioner leaves: inside
 flexible PCG, z = P r + N(r - A P r), with the Polak-Ribiere form of the CG beta,
 beta_k = z_k.(r_k - r_k-1) / (z_k-1.r_k-1), and the correction switched off for the rest
-of a solve after two consecutive iterations with ||r_k|| >= 0.9 ||r_k-1||. Training pairs
+of a solve at the first iteration k >= W with ||r_k|| >= ratio ||r_k-W|| (W = 0: never;
+W = 8, ratio = 0.5 by default). Training pairs
 from an iterate x_k of A x = b with solution x*: r = b - A x_k, z0 = P r, input
 s = r - A z0, target delta = x* - x_k - z0 (so A delta = s). Definition used by the
 oracle and, independently written, by the GPU kernels:
@@ -19,11 +20,25 @@ oracle and, independently written, by the GPU kernels:
     convolution is a correlation with zero padding on the element grid, bias per channel;
   output: local correction c_l = y_l sigma_e; global correction = average of c_l over the
     local copies of each DOF, zero on Dirichlet DOFs.
-  training loss for one sample: mean over all local nodes of (y_l - t_l / sigma_e)^2, t the
-    local target correction.
+  training losses for one sample (input v, target delta):
+    "l2":     mean over all local nodes of (y_l - t_l / sigma_e)^2, t the local target;
+    "energy": L(c) = 1 + (c^T A c - 2 c^T v) / (delta^T v) for the global correction c,
+              which equals ||delta - c||_A^2 / ||delta||_A^2 when v = A delta (the norm CG
+              minimises); dL/dc = -2 (v - A c) / (delta^T v) on the free DOFs.
+    "angle":  with the pair's residual r and z0 = P r, z = z0 + c and e = delta + z0 (so
+              A e = r): L(c) = 1 - z^T r / sqrt((z^T A z)(e^T r)) = 1 - cos of the A-angle
+              between z and e (1 - (1 - L)^2 is the share of ||e||_A^2 left after an exact
+              line search along z); invariant to positive scaling of z, and it rewards the
+              orientation descent needs. A z = r - q with q = v - A c (since A z0 = r - v);
+              dL/dc = -(r - (a / Q) A z) / sqrt(Q E), a = z^T r, Q = z^T A z, E = e^T r.
+  safeguard inside flexible PCG: the correction is used in an iteration only if
+    (z0 + c)^T r >= theta z0^T r (theta = 0.25 by default), else that iteration takes z0.
 
 Pinned by: single-channel convolution = scipy.ndimage.correlate (constant 0 mode); the
-backward pass = central finite differences of the loss in FP64; flexible PCG with N = 0
+backward pass = central finite differences of the loss in FP64 (both losses); the energy
+loss equals ||delta - c||_A^2 / ||delta||_A^2 from the assembled matrix when v = A delta,
+and is 1 for a zero network; the angle loss gives 1 - cos of the A-angle between z and the
+exact error (assembled matrix, direct solve, exact line search); flexible PCG with N = 0
 takes the iterations of plain PCG (for a fixed SPD P, z_k.r_k-1 = 0, so the Polak-Ribiere
 beta equals Algorithm 1's); with N = A^-1 (dense solve) the composed preconditioner is
 A^-1 and the solve ends after one iteration; a training pair satisfies A delta = s.
@@ -133,6 +148,42 @@ def correction(theta, r, m_N, l2g, h, lam, mask):
     return np.where(mask > 0, 0.0, out)
 
 
+def energy_loss_and_grad(theta, v, delta, apply_A, m_N, l2g, h, lam, mask):
+    """Energy loss of the global correction c = N(v) and its parameter gradient."""
+    x, sigma = features(v, m_N, l2g, h, lam)
+    y, cache = forward(theta, x)
+    G = m_N.shape[0]
+    free = mask == 0
+    cnt = np.bincount(l2g.ravel(), minlength=G)
+    c = np.bincount(l2g.ravel(), weights=(y[:, 0] * sigma[:, None, None, None]).ravel(), minlength=G) / cnt
+    c = np.where(free, c, 0.0)
+    q = np.where(free, v - apply_A(c), 0.0)
+    den = delta @ v
+    loss = 1.0 - c @ (v + q) / den
+    dc = np.where(free, -2.0 * q / den, 0.0)           # dL/dc
+    gy = (dc / cnt)[l2g] * sigma[:, None, None, None]  # dc_N / dy_l = sigma_e / multiplicity
+    return loss, backward(theta, cache, gy[:, None])
+
+
+def angle_loss_and_grad(theta, v, r, z0, delta, apply_A, m_N, l2g, h, lam, mask):
+    """Angle loss of z = z0 + N(v) against the error e = delta + z0, and its parameter gradient."""
+    x, sigma = features(v, m_N, l2g, h, lam)
+    y, cache = forward(theta, x)
+    G = m_N.shape[0]
+    free = mask == 0
+    cnt = np.bincount(l2g.ravel(), minlength=G)
+    c = np.bincount(l2g.ravel(), weights=(y[:, 0] * sigma[:, None, None, None]).ravel(), minlength=G) / cnt
+    c = np.where(free, c, 0.0)
+    q = np.where(free, v - apply_A(c), 0.0)
+    z = z0 + c
+    Az = r - q
+    a, Q, E = z @ r, z @ Az, (delta + z0) @ r
+    loss = 1.0 - a / np.sqrt(Q * E)
+    dc = np.where(free, -(r - (a / Q) * Az) / np.sqrt(Q * E), 0.0)
+    gy = (dc / cnt)[l2g] * sigma[:, None, None, None]
+    return loss, backward(theta, cache, gy[:, None])
+
+
 def loss_and_grad(theta, r, target_local, m_N, l2g, h, lam):
     """Training loss (mean over local nodes of (y - t/sigma)^2) and its parameter gradient."""
     x, sigma = features(r, m_N, l2g, h, lam)
@@ -145,24 +196,22 @@ def loss_and_grad(theta, r, target_local, m_N, l2g, h, lam):
     return loss, backward(theta, cache, gy)
 
 
-STALL_RATIO = 0.81   # ||r_k||^2 >= 0.81 ||r_k-1||^2, i.e. ||r_k|| >= 0.9 ||r_k-1||
-STALL_COUNT = 2
 
 
 def training_pair(apply_A, apply_P, mask, b, x_star, x_k):
-    """(s, delta): r = b - A x_k, z0 = P r, s = r - A z0, delta = x* - x_k - z0 (0 on masked DOFs)."""
+    """(s, delta, r, z0): r = b - A x_k, z0 = P r, s = r - A z0, delta = x* - x_k - z0 (0 on masked DOFs)."""
     free = mask == 0
     r = np.where(free, b - apply_A(x_k), 0.0)
     z0 = apply_P(r)
     s = np.where(free, r - apply_A(z0), 0.0)
     delta = np.where(free, x_star - x_k - z0, 0.0)
-    return s, delta
+    return s, delta, r, z0
 
 
-def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000):
+def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000, window=8, ratio=0.5, theta=0.25):
     """Flexible PCG with z = P r + correction(r - A P r); correction None = plain P.
 
-    Returns (x, iterations, relative residual history, iterations done with the correction on).
+    Returns (x, iterations, relative residual history, iterations that used the correction).
     """
     free = mask == 0
     r = np.where(free, b, 0.0)
@@ -173,14 +222,17 @@ def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000):
     if bb == 0.0:
         return x, 0, np.array(hist), 0
     on = correction is not None
-    stall, on_iters, rr = 0, 0, bb
+    on_iters = 0
+    rrs = [bb]
     p = None
     rz_old = None
     for k in range(1, maxit + 1):
         z = apply_P(r)
         if on:
-            z = z + correction(np.where(free, r - apply_A(z), 0.0))
-            on_iters += 1
+            c = correction(np.where(free, r - apply_A(z), 0.0))
+            if (z + c) @ r >= theta * (z @ r):
+                z = z + c
+                on_iters += 1
         rz = z @ r
         p = z.copy() if p is None else z + ((rz - z @ r_prev) / rz_old) * p
         rz_old = rz
@@ -189,12 +241,10 @@ def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000):
         x = x + alpha * p
         r_prev = r
         r = r - alpha * f
-        rr_new = r @ r
-        if on:
-            stall = stall + 1 if rr_new >= STALL_RATIO * rr else 0
-            if stall >= STALL_COUNT:
-                on = False
-        rr = rr_new
+        rr = r @ r
+        rrs.append(rr)
+        if on and window > 0 and k >= window and rr >= ratio ** 2 * rrs[k - window]:
+            on = False
         hist.append(np.sqrt(rr / bb))
         if hist[-1] <= rtol:
             return x, k, np.array(hist), on_iters

@@ -163,8 +163,9 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg && !flex, h->stream));
   if (flex) {
     // z = P r + N(r - A P r), flexible PCG; the operator application and the network skip
-    // once the correction is switched off (d.st_nn->done), the combine keeps the dots
-    if (d.fp32) {
+    // once the correction is switched off (d.st_nn->done), the combine keeps the dots. The
+    // network's input needs no FP64: the FP32 operator runs whenever its factors exist.
+    if (d.fp32 || d.recompute || d.geo32 != nullptr) {
       float* wl = reinterpret_cast<float*>(d.wl);
       PROF(h, "ax_local_flex", sem::launch_ax_local_f32(d, z, wl, d.st_nn, h->stream));
       PROF(h, "nn_residual", sem::launch_residual_of_f32(d, wl, r, d.nns, st, h->stream));
@@ -334,7 +335,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->mN, (size_t)nb.G, A));
   d.nblk = (int)std::min<int64_t>((nb.G + sem::kVecBlock - 1) / sem::kVecBlock, 152 * 8);
   if (d.nblk < 1) d.nblk = 1;
-  CK(h->alloc(&d.partial, (size_t)(2 * d.nblk), A));
+  CK(h->alloc(&d.partial, (size_t)(4 * d.nblk), A));
   CK(h->alloc(&d.st, 1, A));
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), h->stream));
   CK(h->alloc(&h->r, (size_t)nb.G, A));
@@ -474,12 +475,16 @@ int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev) {
 int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev) { return apply_P_common(h, -1, r_dev, z_dev); }
 
 int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const double* x_k_dev, double* s_dev,
-                 double* delta_dev) {
+                 double* delta_dev, double* r_dev, double* z0_dev) {
   if (int rc = check_handle(h)) return rc;
   if (!b_dev || !x_star_dev || !x_k_dev || !s_dev || !delta_dev || s_dev == delta_dev)
     return fail(SEM_ERR_ARG, "bad vector arguments");
   for (const double* in : {b_dev, x_star_dev, x_k_dev})
-    if (in == s_dev || in == delta_dev) return fail(SEM_ERR_ARG, "outputs must not alias inputs");
+    if (in == s_dev || in == delta_dev || in == r_dev || in == z0_dev)
+      return fail(SEM_ERR_ARG, "outputs must not alias inputs");
+  if ((r_dev && (r_dev == s_dev || r_dev == delta_dev || r_dev == z0_dev)) ||
+      (z0_dev && (z0_dev == s_dev || z0_dev == delta_dev)))
+    return fail(SEM_ERR_ARG, "outputs must not alias each other");
   sem::DevProblem& d = h->d;
   cudaStream_t s = h->stream;
   double* r = h->f;    // solver scratch, free between solves
@@ -503,6 +508,8 @@ int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const 
     PROF(h, "nn_residual", sem::launch_residual_of(d, d.wl, r, s_dev, nullptr, s));
   }
   PROF(h, "nn_pair", sem::launch_pair_delta(d, x_star_dev, x_k_dev, z0, delta_dev, s));
+  if (r_dev) CK(cudaMemcpyAsync(r_dev, r, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s));
+  if (z0_dev) CK(cudaMemcpyAsync(z0_dev, z0, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s));
   return SEM_OK;
 }
 
@@ -576,7 +583,8 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
   const int learned = h->net != nullptr ? 1 : 0;
   if (learned) CK(cudaMemsetAsync(d.st_nn, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, h->hist, s));
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, h->nn_window, h->nn_ratio,
+                                           h->nn_theta, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
   if (int rc = enqueue_head()) return rc;

@@ -19,6 +19,8 @@ namespace sem {
 constexpr int kVecBlock = 256;          // threads per block of the vector kernels
 
 // Scalars of one PCG solve, resident on the device (Algorithm 1).
+constexpr int kMaxStallWindow = 8;
+
 struct PcgState {
   double rz;        // z_k^T r_k
   double alpha, beta;
@@ -36,8 +38,13 @@ struct PcgState {
   int status;       // 0, SEM_MAXIT (1) or SEM_ERR_NAN (-6)
   int maxit;
   int learned;      // 1: flexible PCG with the learned correction added to z
-  int stall;        // consecutive iterations with ||r_k|| >= 0.9 ||r_k-1|| (learned)
   int nn_off;       // 1 once the learned correction was switched off for this solve
+  int stall_window; // switch it off when ||r_k|| >= stall_ratio ||r_k-W|| (W = stall_window, 0 = never)
+  double stall_ratio2;               // stall_ratio^2
+  double nn_theta;  // the correction is used only if (z0 + c).r >= nn_theta z0.r
+  int nn_use;       // 1: this iteration's direction includes the correction
+  int nn_used;      // iterations that used it
+  double rr_win[8];                  // ||r_j||^2 of the last 8 iterations, at j % 8
   unsigned int counter;   // blocks finished in the running reduction
 };
 
@@ -106,7 +113,7 @@ struct DevProblem {
   double* nncorr = nullptr;         // learned correction N(s) (flexible PCG)
   double* nns = nullptr;            // its input s = r - A P r
   double* rprev = nullptr;          // r_{k-1} for the Polak-Ribiere beta (flexible PCG)
-  double* partial = nullptr;        // reduction partials (2 * nblk)
+  double* partial = nullptr;        // reduction partials (4 * nblk)
   int nblk = 0;                     // blocks of the vector kernels
   PcgState* st = nullptr;
   PcgState* st_nn = nullptr;        // flexible PCG: done = 1 once the learned correction is off
@@ -161,7 +168,8 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 
 // --- PCG (Algorithm 1) -------------------------------------------------------
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol,
-                            int maxit, int mixed, int learned, double* hist, cudaStream_t s);
+                            int maxit, int mixed, int learned, int stall_window, double stall_ratio,
+                            double nn_theta, double* hist, cudaStream_t s);
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
 // f = gather(wl) (0 on masked; FP32 local results when d.fp32), pf = p.f, alpha = rz / pf.
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s);
@@ -177,8 +185,8 @@ cudaError_t launch_residual_of(const DevProblem& d, const double* wl, const doub
                                const PcgState* st, cudaStream_t s);
 cudaError_t launch_residual_of_f32(const DevProblem& d, const float* wl, const double* v, double* out,
                                    const PcgState* st, cudaStream_t s);
-// z += d.nncorr (unless st->nn_off); rz and the Polak-Ribiere beta from z.r and z.rprev.
-cudaError_t launch_flex_combine(const DevProblem& d, double* z, const double* r, cudaStream_t s);
+// decides whether this iteration uses d.nncorr (st->nn_use); rz and the Polak-Ribiere beta
+cudaError_t launch_flex_combine(const DevProblem& d, const double* z, const double* r, cudaStream_t s);
 // delta = mask ? 0 : xs - xk - z0
 cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const double* xk, const double* z0,
                               double* delta, cudaStream_t s);

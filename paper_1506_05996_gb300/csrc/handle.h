@@ -163,6 +163,9 @@ struct sem_s {
   sem::PcgState* st_host = nullptr;  // pinned
   // learned correction (not in the paper): attached network and its forward work space
   sem_net_t* net = nullptr;
+  int nn_window = 8;        // stall rule of the flexible PCG (sem_set_learned)
+  double nn_ratio = 0.5;
+  double nn_theta = 0.25;   // per-iteration acceptance of the correction
   sem::NnWork nnws;
   std::vector<void*> nn_allocs;
 

@@ -221,6 +221,109 @@ __global__ void __launch_bounds__(kNnBlock) nn_loss_kernel(const DevProblem d, c
   if (threadIdx.x == 0) eloss[e] = tot;
 }
 
+// per block: sums of delta.v and c.(v + q) over the DOFs (partials [2][gridDim.x])
+__global__ void __launch_bounds__(kVecBlock) nn_energy_dots_kernel(int G, const double* __restrict__ v,
+                                                                   const double* __restrict__ delta,
+                                                                   const double* __restrict__ c,
+                                                                   const double* __restrict__ q,
+                                                                   double* __restrict__ partial) {
+  double a = 0.0, b = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    a += delta[g] * v[g];
+    b += c[g] * (v[g] + q[g]);
+  }
+  const double sa = block_sum<kVecBlock>(a);
+  const double sb = block_sum<kVecBlock>(b);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sa;
+    partial[gridDim.x + blockIdx.x] = sb;
+  }
+}
+
+// loss = 1 - c.(v + q) / delta.v; coef[0] = delta.v (partials summed in block order)
+__global__ void nn_energy_finish_kernel(int nb, const double* __restrict__ partial, double* __restrict__ coef,
+                                        double* __restrict__ loss) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      a += partial[i];
+      b += partial[nb + i];
+    }
+    coef[0] = a;
+    *loss = 1.0 - b / a;
+  }
+}
+
+// energy: dL/dc = -2 q / delta.v, written over q
+__global__ void nn_energy_dc_kernel(int G, const double* __restrict__ coef, double* __restrict__ q) {
+  const double k = -2.0 / coef[0];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) q[g] *= k;
+}
+
+// per block: a = z.r, Q = z.(r - q) (= z^T A z), E = (delta + z0).r with z = z0 + c
+__global__ void __launch_bounds__(kVecBlock) nn_angle_dots_kernel(int G, const double* __restrict__ r,
+                                                                  const double* __restrict__ z0,
+                                                                  const double* __restrict__ delta,
+                                                                  const double* __restrict__ c,
+                                                                  const double* __restrict__ q,
+                                                                  double* __restrict__ partial) {
+  double a = 0.0, Q = 0.0, E = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const double z = z0[g] + c[g], rg = r[g];
+    a += z * rg;
+    Q += z * (rg - q[g]);
+    E += (delta[g] + z0[g]) * rg;
+  }
+  const double sa = block_sum<kVecBlock>(a);
+  const double sQ = block_sum<kVecBlock>(Q);
+  const double sE = block_sum<kVecBlock>(E);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sa;
+    partial[gridDim.x + blockIdx.x] = sQ;
+    partial[2 * gridDim.x + blockIdx.x] = sE;
+  }
+}
+
+// loss = 1 - a / sqrt(Q E); coef = (-1 / sqrt(Q E), a / Q)
+__global__ void nn_angle_finish_kernel(int nb, const double* __restrict__ partial, double* __restrict__ coef,
+                                       double* __restrict__ loss) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double a = 0.0, Q = 0.0, E = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      a += partial[i];
+      Q += partial[nb + i];
+      E += partial[2 * nb + i];
+    }
+    const double rs = 1.0 / sqrt(Q * E);
+    *loss = 1.0 - a * rs;
+    coef[0] = -rs;
+    coef[1] = a / Q;
+  }
+}
+
+// angle: dL/dc = k1 (r - k2 A z) with A z = r - q, written over q (0 on masked DOFs: r, q are)
+__global__ void nn_angle_dc_kernel(int G, const double* __restrict__ coef, const double* __restrict__ r,
+                                   double* __restrict__ q) {
+  const double k1 = coef[0], k2 = coef[1];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    q[g] = k1 * (r[g] - k2 * (r[g] - q[g]));
+}
+
+// dL/dy_l = dL/dc_N sigma_e / multiplicity_N, 0 on masked DOFs
+template <int p>
+__global__ void __launch_bounds__(kNnBlock) nn_dc_to_gout_kernel(const DevProblem d, const double* __restrict__ dc,
+                                                                 const double* __restrict__ sigma,
+                                                                 float* __restrict__ gout) {
+  constexpr int p3 = p * p * p;
+  const int e = blockIdx.x;
+  const double sg = sigma[e];
+  for (int l = threadIdx.x; l < p3; l += kNnBlock) {
+    const int g = d.l2g[(size_t)e * p3 + l];
+    const double mult = (double)(d.g2l_off[g + 1] - d.g2l_off[g]);
+    gout[(size_t)e * p3 + l] = d.mask[g] ? 0.0f : (float)(dc[g] * sg / mult);
+  }
+}
+
 __global__ void sum_in_order_kernel(int n, const double* __restrict__ v, double scale, double* __restrict__ out) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double s = 0.0;
@@ -283,9 +386,23 @@ cudaError_t forward_p(const DevProblem& d, const NnWeights& w, const NnWork& ws,
 }
 
 template <int p>
-cudaError_t backward_p(const DevProblem& d, const NnWeights& w, const NnWork& ws, const double* target,
-                       double invL, cudaStream_t s) {
+cudaError_t loss_l2_p(const DevProblem& d, const NnWork& ws, const double* target, double invL, cudaStream_t s) {
   nn_loss_kernel<p><<<d.ne, kNnBlock, 0, s>>>(d, ws.y, ws.sigma, target, ws.g3, ws.eloss, invL);
+  sum_in_order_kernel<<<1, 32, 0, s>>>(d.ne, ws.eloss, invL, ws.loss);
+  count_launch();
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int p>
+cudaError_t dc_to_gout_p(const DevProblem& d, const NnWork& ws, cudaStream_t s) {
+  nn_dc_to_gout_kernel<p><<<d.ne, kNnBlock, 0, s>>>(d, ws.q, ws.sigma, ws.g3);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int p>
+cudaError_t backward_p(const DevProblem& d, const NnWeights& w, const NnWork& ws, cudaStream_t s) {
   // layer 3 (8 -> 1): weights, then data into layer-2 activations (masked by ReLU)
   conv_bwd_weight_kernel<p, kNnHid, 1><<<d.ne, kNnBlock, 0, s>>>(ws.g3, ws.a2, ws.partial, kNnParams, kOffW3);
   conv_bwd_data_kernel<p, kNnHid, 1, true><<<d.ne, kNnBlock, 0, s>>>(ws.g3, w.w16 + kOffW3, ws.a2, ws.g2);
@@ -295,8 +412,7 @@ cudaError_t backward_p(const DevProblem& d, const NnWeights& w, const NnWork& ws
   // layer 1 (5 -> 8): weights only
   conv_bwd_weight_kernel<p, kNnIn, kNnHid><<<d.ne, kNnBlock, 0, s>>>(ws.g1, ws.x0, ws.partial, kNnParams, kOffW1);
   reduce_partials_kernel<<<(kNnParams + 255) / 256, 256, 0, s>>>(d.ne, kNnParams, kNnParams, ws.partial, ws.grad);
-  sum_in_order_kernel<<<1, 32, 0, s>>>(d.ne, ws.eloss, invL, ws.loss);
-  for (int q = 0; q < 8; ++q) count_launch();
+  for (int q = 0; q < 6; ++q) count_launch();
   return cudaGetLastError();
 }
 
@@ -316,18 +432,49 @@ cudaError_t nn_forward(const DevProblem& d, const NnWeights& w, const NnWork& ws
   }
 }
 
-cudaError_t nn_backward(const DevProblem& d, const NnWeights& w, const NnWork& ws, const double* target, cudaStream_t s) {
-  const double invL = 1.0 / ((double)d.ne * d.p * d.p * d.p);
-  switch (d.p) {
-    case 3: return backward_p<3>(d, w, ws, target, invL, s);
-    case 4: return backward_p<4>(d, w, ws, target, invL, s);
-    case 5: return backward_p<5>(d, w, ws, target, invL, s);
-    case 6: return backward_p<6>(d, w, ws, target, invL, s);
-    case 7: return backward_p<7>(d, w, ws, target, invL, s);
-    case 8: return backward_p<8>(d, w, ws, target, invL, s);
-    case 9: return backward_p<9>(d, w, ws, target, invL, s);
-    default: return cudaErrorInvalidValue;
+#define NN_DISPATCH_P(call)           \
+  switch (d.p) {                      \
+    case 3: { constexpr int P_ = 3; return call; } \
+    case 4: { constexpr int P_ = 4; return call; } \
+    case 5: { constexpr int P_ = 5; return call; } \
+    case 6: { constexpr int P_ = 6; return call; } \
+    case 7: { constexpr int P_ = 7; return call; } \
+    case 8: { constexpr int P_ = 8; return call; } \
+    case 9: { constexpr int P_ = 9; return call; } \
+    default: return cudaErrorInvalidValue;          \
   }
+
+cudaError_t nn_loss_l2(const DevProblem& d, const NnWork& ws, const double* target, cudaStream_t s) {
+  const double invL = 1.0 / ((double)d.ne * d.p * d.p * d.p);
+  NN_DISPATCH_P(loss_l2_p<P_>(d, ws, target, invL, s))
+}
+
+cudaError_t nn_loss_energy(const DevProblem& d, const NnWork& ws, const double* v, const double* delta,
+                           cudaStream_t s) {
+  if (d.nblk > kNnMaxVecBlocks) return cudaErrorInvalidValue;
+  nn_energy_dots_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, v, delta, ws.c, ws.q, ws.dots);
+  nn_energy_finish_kernel<<<1, 32, 0, s>>>(d.nblk, ws.dots, ws.coef, ws.loss);
+  nn_energy_dc_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, ws.coef, ws.q);
+  for (int q = 0; q < 3; ++q) count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  NN_DISPATCH_P(dc_to_gout_p<P_>(d, ws, s))
+}
+
+cudaError_t nn_loss_angle(const DevProblem& d, const NnWork& ws, const double* r, const double* z0,
+                          const double* delta, cudaStream_t s) {
+  if (d.nblk > kNnMaxVecBlocks) return cudaErrorInvalidValue;
+  nn_angle_dots_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, r, z0, delta, ws.c, ws.q, ws.dots);
+  nn_angle_finish_kernel<<<1, 32, 0, s>>>(d.nblk, ws.dots, ws.coef, ws.loss);
+  nn_angle_dc_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, ws.coef, r, ws.q);
+  for (int q = 0; q < 3; ++q) count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  NN_DISPATCH_P(dc_to_gout_p<P_>(d, ws, s))
+}
+
+cudaError_t nn_backward(const DevProblem& d, const NnWeights& w, const NnWork& ws, cudaStream_t s) {
+  NN_DISPATCH_P(backward_p<P_>(d, w, ws, s))
 }
 
 cudaError_t nn_gather(const DevProblem& d, const NnWork& ws, double* out, const PcgState* st, cudaStream_t s) {

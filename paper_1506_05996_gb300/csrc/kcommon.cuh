@@ -60,30 +60,34 @@ __device__ __forceinline__ bool grid_reduce(double v, double* partial, unsigned 
   return true;
 }
 
-// Two sums at once (partial holds 2 * gridDim.x entries): the same last-block rule.
-template <int BS>
-__device__ __forceinline__ bool grid_reduce2(double v0, double v1, double* partial, unsigned int* counter,
-                                             double& t0, double& t1) {
-  __shared__ bool last2;
-  const double b0 = block_sum<BS>(v0);
-  const double b1 = block_sum<BS>(v1);
+// NV sums at once (partial holds NV * gridDim.x entries): the same last-block rule;
+// tot[] is valid in thread 0 of the last block.
+template <int BS, int NV>
+__device__ __forceinline__ bool grid_reduce_n(const double (&v)[NV], double* partial, unsigned int* counter,
+                                              double (&tot)[NV]) {
+  __shared__ bool last_n;
+  double bsum[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) bsum[k] = block_sum<BS>(v[k]);
   if (threadIdx.x == 0) {
-    partial[blockIdx.x] = b0;
-    partial[gridDim.x + blockIdx.x] = b1;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partial[k * gridDim.x + blockIdx.x] = bsum[k];
     __threadfence();
     const unsigned int prev = atomicAdd(counter, 1u);
-    last2 = (prev == gridDim.x - 1);
+    last_n = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last2) return false;
+  if (!last_n) return false;
   __threadfence();
-  double s0 = 0.0, s1 = 0.0;
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) {
-    s0 += __ldcg(&partial[i]);
-    s1 += __ldcg(&partial[gridDim.x + i]);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s[k] += __ldcg(&partial[k * gridDim.x + i]);
   }
-  t0 = block_sum<BS>(s0);
-  t1 = block_sum<BS>(s1);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = block_sum<BS>(s[k]);
   if (threadIdx.x == 0) *counter = 0u;
   return true;
 }

@@ -270,6 +270,7 @@ __global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __rest
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
                                                              double rtol, int maxit, int mixed, int learned,
+                                                             int stall_window, double stall_ratio, double nn_theta,
                                                              double* hist) {
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
@@ -296,8 +297,13 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
     st->replace = 0;
     st->replacements = 0;
     st->learned = learned;
-    st->stall = 0;
     st->nn_off = 0;
+    st->stall_window = stall_window;
+    st->nn_theta = nn_theta;
+    st->nn_use = 0;
+    st->nn_used = 0;
+    st->stall_ratio2 = stall_ratio * stall_ratio;
+    st->rr_win[0] = total;
     hist[0] = (total > 0.0) ? 1.0 : 0.0;
     if (!isfinite(total)) { st->status = -6; st->done = 1; }
     else if (total == 0.0) st->done = 1;
@@ -308,9 +314,11 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
 __global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
   if (stopped(d.st)) return;
   float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
+  const double* __restrict__ c = (d.st->learned && d.st->nn_use) ? d.nncorr : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    p[g] = z[g];
-    if (p32) p32[g] = (float)z[g];
+    const double pn = c ? z[g] + c[g] : z[g];
+    p[g] = pn;
+    if (p32) p32[g] = (float)pn;
   }
 }
 
@@ -357,16 +365,18 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
   double total;
   if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
     PcgState* st = d.st;
+    st->rr = total;
+    const int it = ++st->iter;
     if (st->learned) {
-      // a correction that stops reducing the residual is switched off for the rest of the solve
-      st->stall = (total >= 0.81 * st->rr) ? st->stall + 1 : 0;
-      if (st->stall >= 2) {
+      // a correction under which the residual stops dropping over the window is switched
+      // off for the rest of the solve
+      const int W = st->stall_window;
+      if (W > 0 && it >= W && total >= st->stall_ratio2 * st->rr_win[(it - W) % kMaxStallWindow]) {
         st->nn_off = 1;
         d.st_nn->done = 1;
       }
+      st->rr_win[it % kMaxStallWindow] = total;
     }
-    st->rr = total;
-    const int it = ++st->iter;
     const double rel = sqrt(total) / sqrt(st->bb);
     hist[it] = rel;
     if (!isfinite(total)) { st->status = -6; st->done = 1; }
@@ -415,8 +425,9 @@ __global__ void pcg_direction_kernel(const DevProblem d, const double* __restric
   if (stopped(d.st)) return;
   const double beta = d.st->beta;
   float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
+  const double* __restrict__ c = (d.st->learned && d.st->nn_use) ? d.nncorr : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    const double pn = z[g] + beta * p[g];
+    const double pn = (c ? z[g] + c[g] : z[g]) + beta * p[g];
     p[g] = pn;
     if (p32) p32[g] = (float)pn;
   }
@@ -440,28 +451,35 @@ __global__ void __launch_bounds__(kVecBlock) residual_of_kernel(const DevProblem
   }
 }
 
-// Flexible PCG: z += N(s) (unless switched off), then z.r and z.r_prev, and
-// beta = z_k.(r_k - r_k-1) / (z_k-1.r_k-1) (Polak-Ribiere form), rz = z_k.r_k.
-__global__ void __launch_bounds__(kVecBlock) flex_combine_kernel(const DevProblem d, double* __restrict__ z,
+// Flexible PCG with z0 = P r in z and the correction c in d.nncorr: the correction is used
+// in this iteration (st->nn_use) only if it is on and keeps descent, (z0 + c).r >= theta z0.r;
+// then rz = z.r and beta = z_k.(r_k - r_k-1) / (z_k-1.r_k-1) (Polak-Ribiere form) for the
+// chosen z. z itself keeps z0; the direction kernels add c when st->nn_use.
+__global__ void __launch_bounds__(kVecBlock) flex_combine_kernel(const DevProblem d, const double* __restrict__ z,
                                                                  const double* __restrict__ r) {
   if (stopped(d.st)) return;
-  const bool use_nn = d.st->nn_off == 0;
-  double zr = 0.0, zrp = 0.0;
+  const bool on = d.st->nn_off == 0;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};   // z0.r, c.r, z0.rprev, c.rprev
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    double v = z[g];
-    if (use_nn) {
-      v += d.nncorr[g];
-      z[g] = v;
+    const double zg = z[g], rg = r[g], rp = d.rprev[g];
+    v[0] += zg * rg;
+    v[2] += zg * rp;
+    if (on) {
+      const double cg = d.nncorr[g];
+      v[1] += cg * rg;
+      v[3] += cg * rp;
     }
-    zr += v * r[g];
-    zrp += v * d.rprev[g];
   }
-  double t0, t1;
-  if (grid_reduce2<kVecBlock>(zr, zrp, d.partial, &d.st->counter, t0, t1) && threadIdx.x == 0) {
+  double t[4];
+  if (grid_reduce_n<kVecBlock, 4>(v, d.partial, &d.st->counter, t) && threadIdx.x == 0) {
     PcgState* st = d.st;
-    if (!isfinite(t0) || !isfinite(t1)) { st->status = -6; st->done = 1; }
-    if (st->iter > 0) st->beta = (t0 - t1) / st->rz;
-    st->rz = t0;
+    const int use = (on && isfinite(t[1]) && isfinite(t[3]) && t[0] + t[1] >= st->nn_theta * t[0]) ? 1 : 0;
+    const double zr = t[0] + (use ? t[1] : 0.0), zrp = t[2] + (use ? t[3] : 0.0);
+    st->nn_use = use;
+    st->nn_used += use;
+    if (!isfinite(zr) || !isfinite(zrp)) { st->status = -6; st->done = 1; }
+    if (st->iter > 0) st->beta = (zr - zrp) / st->rz;
+    st->rz = zr;
   }
 }
 
@@ -616,8 +634,10 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 }
 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
-                            int mixed, int learned, double* hist, cudaStream_t s) {
-  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, hist);
+                            int mixed, int learned, int stall_window, double stall_ratio, double nn_theta,
+                            double* hist, cudaStream_t s) {
+  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, stall_window, stall_ratio,
+                                                nn_theta, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -676,7 +696,7 @@ cudaError_t launch_residual_of_f32(const DevProblem& d, const float* wl, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_flex_combine(const DevProblem& d, double* z, const double* r, cudaStream_t s) {
+cudaError_t launch_flex_combine(const DevProblem& d, const double* z, const double* r, cudaStream_t s) {
   flex_combine_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, r);
   ++g_kernel_launches;
   return cudaGetLastError();

@@ -29,15 +29,29 @@ struct NnWork {
   double* sigma = nullptr;            // per-element scale sigma_e
   float *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *partial = nullptr, *grad = nullptr;
   double *eloss = nullptr, *loss = nullptr;
+  // energy / angle losses: global correction c, q = v - A c (then dL/dc in place), block
+  // partials and the loss coefficients
+  double *c = nullptr, *q = nullptr, *dots = nullptr, *coef = nullptr;
 };
+
+constexpr int kNnMaxVecBlocks = 2048;   // >= DevProblem::nblk (partials of the energy dots)
+
+enum NnLoss { NN_LOSS_L2 = 0, NN_LOSS_ENERGY = 1, NN_LOSS_ANGLE = 2 };
 
 // features + the three convolutions: ws.y (local outputs) and ws.sigma; with st (inside
 // flexible PCG) the kernels do nothing once the solve stopped or st->nn_off is set
 cudaError_t nn_forward(const DevProblem& d, const NnWeights& w, const NnWork& ws, const double* r, const double* mN,
                        const PcgState* st, cudaStream_t s);
-// loss against the global target (sampled at the local nodes), backward, ws.grad and *ws.loss
-cudaError_t nn_backward(const DevProblem& d, const NnWeights& w, const NnWork& ws, const double* target,
-                        cudaStream_t s);
+// L2 loss against the global target (sampled at the local nodes): *ws.loss and ws.g3 = dL/dy
+cudaError_t nn_loss_l2(const DevProblem& d, const NnWork& ws, const double* target, cudaStream_t s);
+// energy loss, given ws.c = N(v) and ws.q = mask ? 0 : v - A c: *ws.loss and ws.g3 = dL/dy
+cudaError_t nn_loss_energy(const DevProblem& d, const NnWork& ws, const double* v, const double* delta,
+                           cudaStream_t s);
+// angle loss of z = z0 + c against e = delta + z0 (A e = r), given ws.c and ws.q as above
+cudaError_t nn_loss_angle(const DevProblem& d, const NnWork& ws, const double* r, const double* z0,
+                          const double* delta, cudaStream_t s);
+// backward through the three convolutions from ws.g3: ws.grad
+cudaError_t nn_backward(const DevProblem& d, const NnWeights& w, const NnWork& ws, cudaStream_t s);
 // global correction from ws.y, ws.sigma (average over local copies, 0 on masked DOFs)
 cudaError_t nn_gather(const DevProblem& d, const NnWork& ws, double* out, const PcgState* st, cudaStream_t s);
 cudaError_t nn_adam(NnWeights& w, const NnWork& ws, float lr, int step, cudaStream_t s);

@@ -1,5 +1,6 @@
 // C ABI of the learned correction (include/sem.h, sem_net_*): network objects, training
 // steps on the GPU, and the correction N(r) added to the preconditioner in flexible PCG.
+#include <cmath>
 #include <cstring>
 #include <random>
 #include <string>
@@ -64,6 +65,10 @@ int ensure_work(sem::NnWork& ws, std::vector<void*>& list, int ne, int p3, bool 
     CKN(dalloc(&ws.grad, (size_t)sem::kNnParams, list));
     CKN(dalloc(&ws.eloss, (size_t)ne, list));
     CKN(dalloc(&ws.loss, 1, list));
+    CKN(dalloc(&ws.c, L, list));   // G <= ne p^3
+    CKN(dalloc(&ws.q, L, list));
+    CKN(dalloc(&ws.dots, (size_t)(2 * sem::kNnMaxVecBlocks), list));
+    CKN(dalloc(&ws.coef, 2, list));
   }
   return SEM_OK;
 }
@@ -155,26 +160,50 @@ int sem_net_set_params(sem_net_t* net, const float* params_host, int n) {
   return SEM_OK;
 }
 
-int sem_net_gradient(sem_net_t* net, sem_t* h, const double* r_dev, const double* target_dev, float* grad_host,
-                     double* loss_host) {
+int sem_net_gradient(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
+                     const double* r_dev, const double* z0_dev, int loss_kind, float* grad_host, double* loss_host) {
   if (net == nullptr) return fail(SEM_ERR_ARG, "NULL network");
-  if (int rc = check_vecs(h, r_dev, target_dev)) return rc;
+  if (int rc = check_vecs(h, v_dev, target_dev)) return rc;
+  if (loss_kind != SEM_NET_LOSS_L2 && loss_kind != SEM_NET_LOSS_ENERGY && loss_kind != SEM_NET_LOSS_ANGLE)
+    return fail(SEM_ERR_ARG, "unknown loss");
+  if (loss_kind == SEM_NET_LOSS_ANGLE && (r_dev == nullptr || z0_dev == nullptr))
+    return fail(SEM_ERR_ARG, "the angle loss needs r and z0");
   const int p3 = h->d.p * h->d.p * h->d.p;
   if (int rc = ensure_work(net->ws, net->ws_allocs, h->d.ne, p3, true)) return rc;
+  const sem::DevProblem& d = h->d;
+  const sem::NnWork& ws = net->ws;
   cudaStream_t s = h->stream;
-  CKN(sem::nn_forward(h->d, net->w, net->ws, r_dev, h->mN, nullptr, s));
-  CKN(sem::nn_backward(h->d, net->w, net->ws, target_dev, s));
-  if (grad_host) CKN(cudaMemcpyAsync(grad_host, net->ws.grad, sizeof(float) * sem::kNnParams, cudaMemcpyDeviceToHost, s));
+  CKN(sem::nn_forward(d, net->w, ws, v_dev, h->mN, nullptr, s));
+  if (loss_kind == SEM_NET_LOSS_L2) {
+    CKN(sem::nn_loss_l2(d, ws, target_dev, s));
+  } else {
+    // c = N(v), q = v - A c (the handle's operator precision), then the loss and dL/dy
+    CKN(sem::nn_gather(d, ws, ws.c, nullptr, s));
+    if (d.fp32) {
+      float* wl = reinterpret_cast<float*>(d.wl);
+      CKN(sem::launch_ax_local_f32(d, ws.c, wl, nullptr, s));
+      CKN(sem::launch_residual_of_f32(d, wl, v_dev, ws.q, nullptr, s));
+    } else {
+      CKN(sem::launch_ax_local(d, ws.c, d.wl, nullptr, s));
+      CKN(sem::launch_residual_of(d, d.wl, v_dev, ws.q, nullptr, s));
+    }
+    if (loss_kind == SEM_NET_LOSS_ENERGY)
+      CKN(sem::nn_loss_energy(d, ws, v_dev, target_dev, s));
+    else
+      CKN(sem::nn_loss_angle(d, ws, r_dev, z0_dev, target_dev, s));
+  }
+  CKN(sem::nn_backward(d, net->w, ws, s));
+  if (grad_host) CKN(cudaMemcpyAsync(grad_host, ws.grad, sizeof(float) * sem::kNnParams, cudaMemcpyDeviceToHost, s));
   double loss = 0.0;
-  CKN(cudaMemcpyAsync(&loss, net->ws.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CKN(cudaMemcpyAsync(&loss, ws.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   CKN(cudaStreamSynchronize(s));
   if (loss_host) *loss_host = loss;
   return SEM_OK;
 }
 
-int sem_net_train_step(sem_net_t* net, sem_t* h, const double* r_dev, const double* target_dev, float lr,
-                       double* loss_host) {
-  if (int rc = sem_net_gradient(net, h, r_dev, target_dev, nullptr, loss_host)) return rc;
+int sem_net_train_step(sem_net_t* net, sem_t* h, const double* v_dev, const double* target_dev,
+                       const double* r_dev, const double* z0_dev, int loss_kind, float lr, double* loss_host) {
+  if (int rc = sem_net_gradient(net, h, v_dev, target_dev, r_dev, z0_dev, loss_kind, nullptr, loss_host)) return rc;
   net->step += 1;
   CKN(sem::nn_adam(net->w, net->ws, lr, net->step, h->stream));
   CKN(cudaStreamSynchronize(h->stream));
@@ -191,10 +220,22 @@ int sem_net_apply(sem_net_t* net, sem_t* h, const double* r_dev, double* out_dev
   return SEM_OK;
 }
 
-int sem_set_learned(sem_t* h, sem_net_t* net) {
+int sem_set_learned(sem_t* h, sem_net_t* net, int stall_window, double stall_ratio, double accept_theta) {
   if (h == nullptr) return fail(SEM_ERR_ARG, "NULL handle");
+  if (stall_window < 0 || stall_window > sem::kMaxStallWindow || !(stall_ratio > 0.0) || !std::isfinite(stall_ratio) ||
+      std::isnan(accept_theta))
+    return fail(SEM_ERR_ARG, "stall_window must be in 0..8, stall_ratio > 0 and accept_theta a number");
   CKN(cudaStreamSynchronize(h->stream));
+  h->nn_window = stall_window;
+  h->nn_ratio = stall_ratio;
+  h->nn_theta = accept_theta;
   return sem::learned_attach(h, net);
+}
+
+int sem_learned_iterations(const sem_t* h, int* used_host) {
+  if (h == nullptr || used_host == nullptr) return fail(SEM_ERR_ARG, "NULL argument");
+  *used_host = (h->net != nullptr && h->st_host != nullptr) ? h->st_host->nn_used : 0;
+  return SEM_OK;
 }
 
 }  // extern "C"

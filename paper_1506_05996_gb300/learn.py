@@ -16,8 +16,8 @@ import numpy as np
 import torch
 
 from synth import gaussian_load, lattice_hex_mesh, manufactured_s
-from .sem import (SEM_GEOM_RECOMPUTE, SemProblem, sem_net_create, sem_net_destroy, sem_net_pair,
-                  sem_net_train_step, sem_set_learned)
+from .sem import (SEM_GEOM_RECOMPUTE, SemProblem, sem_learned_iterations, sem_net_create, sem_net_destroy,
+                  sem_net_pair, sem_net_train_step, sem_set_learned)
 
 
 def make_problem(E, a, seed, n, lam, load="manufactured", geom="stored", mixed=False, load_seed=0):
@@ -34,49 +34,54 @@ def make_problem(E, a, seed, n, lam, load="manufactured", geom="stored", mixed=F
     return prob, b.contiguous()
 
 
-def harvest(prob, b, ks=(1, 2, 4, 8, 16)):
-    """Training pairs (s, delta) at the iterates x_k of plain PCG (k in ks, below convergence)."""
+def harvest(prob, b, ks=(0, 1, 2, 4, 8, 16), net=None):
+    """Training samples (s, delta, r, z0) at the iterates x_k (k in ks, below convergence) of
+    PCG, or of the flexible PCG with `net` attached (samples from the solver's own path)."""
     sem_set_learned(prob.h, None)
     xs, _, it, _, _ = prob.solve(b, rtol=1e-11, maxit=2000)
-    pairs = []
+    sem_set_learned(prob.h, net)
+    out = []
     for k in ks:
         if k >= it:
             break
-        xk = prob.solve(b, rtol=0.0, maxit=k)[0]
-        s = torch.empty_like(b)
-        d = torch.empty_like(b)
-        sem_net_pair(prob.h, b, xs, xk, s, d)
-        pairs.append((s, d))
-    return pairs
+        xk = prob.solve(b, rtol=0.0, maxit=k)[0] if k > 0 else torch.zeros_like(b)
+        vecs = [torch.empty_like(b) for _ in range(4)]
+        sem_net_pair(prob.h, b, xs, xk, *vecs)
+        out.append(tuple(vecs))
+    sem_set_learned(prob.h, None)
+    return out
 
 
-def training_set(n_meshes, E, n, a=0.2, lam_max=10.0, seed=0, ks=(1, 2, 4, 8, 16)):
+def training_set(n_meshes, E, n, a=0.2, lam_max=10.0, seed=0, ks=(0, 1, 2, 4, 8, 16)):
     """Seeded training problems: E^3 hexes, order n, lambda ~ U[0, lam_max], alternating a
-    manufactured and a Gaussian load; returns [(problem, s, delta)]."""
+    manufactured and a Gaussian load; returns (problems with their loads, samples
+    [(problem, s, delta, r, z0)])."""
     rng = np.random.default_rng(seed)
-    samples = []
+    problems, samples = [], []
     for m in range(n_meshes):
         lam = float(rng.uniform(0.0, lam_max))
         prob, b = make_problem(E, a, 1000 + seed * 100000 + m, n, lam, geom="recompute",
                                load="manufactured" if m % 2 == 0 else "gaussian", load_seed=77 + m)
-        samples += [(prob, s, d) for s, d in harvest(prob, b, ks)]
-    return samples
+        problems.append((prob, b))
+        samples += [(prob,) + v for v in harvest(prob, b, ks)]
+    return problems, samples
 
 
-def train(net, samples, steps, lr=2e-3, seed=0):
+def train(net, samples, steps, lr=1e-3, seed=0, loss="angle"):
     """Adam steps on randomly drawn samples with a cosine learning-rate decay; the losses."""
     rng = np.random.default_rng(seed)
     losses = []
     for t in range(steps):
-        prob, s, d = samples[int(rng.integers(len(samples)))]
+        prob, s, d, r, z0 = samples[int(rng.integers(len(samples)))]
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * t / steps))
-        losses.append(sem_net_train_step(net, prob.h, s, d, lr_t))
+        losses.append(sem_net_train_step(net, prob.h, s, d, lr_t, loss, r, z0))
     return losses
 
 
-def timed_solve(prob, b, net, rtol=1e-8, maxit=2000, reps=1):
-    """(iterations, seconds per solve, true relative residual) with the network attached or not."""
-    sem_set_learned(prob.h, net)
+def timed_solve(prob, b, net, rtol=1e-8, maxit=2000, reps=1, window=8, ratio=0.5, theta=0.25):
+    """(iterations, seconds per solve, true relative residual, status, iterations that used the
+    correction) with the network attached or not."""
+    sem_set_learned(prob.h, net, window, ratio, theta)
     x = torch.empty_like(b)
     prob.solve(b, rtol=rtol, maxit=maxit, x=x)      # warm-up (graph capture)
     torch.cuda.synchronize()
@@ -85,8 +90,9 @@ def timed_solve(prob, b, net, rtol=1e-8, maxit=2000, reps=1):
         _, rc, it, _, tr = prob.solve(b, rtol=rtol, maxit=maxit, x=x)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / reps
+    used = sem_learned_iterations(prob.h)
     sem_set_learned(prob.h, None)
-    return it, dt, tr, rc
+    return it, dt, tr, rc, used
 
 
 __all__ = ["make_problem", "harvest", "training_set", "train", "timed_solve", "sem_net_create",

@@ -25,6 +25,7 @@ SEM_MAXIT = 1
 SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED = 0x0, 0x1, 0x10, 0x100
 SEM_PREC_FP64, SEM_PREC_FP32 = 0, 1
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
+SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 _P = ctypes.POINTER
@@ -58,10 +59,11 @@ _SIGS = {
     "sem_net_get_params": ([_vp, _vp, _int], _int),
     "sem_net_set_params": ([_vp, _vp, _int], _int),
     "sem_net_apply": ([_vp, _vp, _vp, _vp], _int),
-    "sem_net_pair": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
-    "sem_net_gradient": ([_vp, _vp, _vp, _vp, _vp, _P(_dbl)], _int),
-    "sem_net_train_step": ([_vp, _vp, _vp, _vp, ctypes.c_float, _P(_dbl)], _int),
-    "sem_set_learned": ([_vp, _vp], _int),
+    "sem_net_pair": ([_vp] * 8, _int),
+    "sem_net_gradient": ([_vp] * 6 + [_int, _vp, _P(_dbl)], _int),
+    "sem_net_train_step": ([_vp] * 6 + [_int, ctypes.c_float, _P(_dbl)], _int),
+    "sem_set_learned": ([_vp, _vp, _int, _dbl, _dbl], _int),
+    "sem_learned_iterations": ([_vp, _P(_int)], _int),
     "sem_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -275,31 +277,43 @@ def sem_net_apply(net, h, r, out):
     return _check(_lib.sem_net_apply(net, h, _dev(r, torch.float64, n), _dev(out, torch.float64, n)))
 
 
-def sem_net_pair(h, b, x_star, x_k, s, delta):
+def sem_net_pair(h, b, x_star, x_k, s, delta, r=None, z0=None):
     n = sem_num_dofs(h)
-    return _check(_lib.sem_net_pair(h, *[_dev(v, torch.float64, n) for v in (b, x_star, x_k, s, delta)]))
+    opt = [None if v is None else _dev(v, torch.float64, n) for v in (r, z0)]
+    return _check(_lib.sem_net_pair(h, *[_dev(v, torch.float64, n) for v in (b, x_star, x_k, s, delta)], *opt))
 
 
-def sem_net_gradient(net, h, r, target):
+def sem_net_gradient(net, h, v, target, loss="energy", r=None, z0=None):
     """Returns (loss, gradient as float32 numpy array)."""
     n = sem_num_dofs(h)
     g = np.zeros(sem_net_num_params(), dtype=np.float32)
-    loss = ctypes.c_double()
-    _check(_lib.sem_net_gradient(net, h, _dev(r, torch.float64, n), _dev(target, torch.float64, n),
-                                 g.ctypes.data, ctypes.byref(loss)))
-    return loss.value, g
+    out = ctypes.c_double()
+    opt = [None if t is None else _dev(t, torch.float64, n) for t in (r, z0)]
+    _check(_lib.sem_net_gradient(net, h, _dev(v, torch.float64, n), _dev(target, torch.float64, n), *opt,
+                                 _LOSS[loss], g.ctypes.data, ctypes.byref(out)))
+    return out.value, g
 
 
-def sem_net_train_step(net, h, r, target, lr):
+def sem_net_train_step(net, h, v, target, lr, loss="energy", r=None, z0=None):
     n = sem_num_dofs(h)
-    loss = ctypes.c_double()
-    _check(_lib.sem_net_train_step(net, h, _dev(r, torch.float64, n), _dev(target, torch.float64, n),
-                                   float(lr), ctypes.byref(loss)))
-    return loss.value
+    out = ctypes.c_double()
+    opt = [None if t is None else _dev(t, torch.float64, n) for t in (r, z0)]
+    _check(_lib.sem_net_train_step(net, h, _dev(v, torch.float64, n), _dev(target, torch.float64, n), *opt,
+                                   _LOSS[loss], float(lr), ctypes.byref(out)))
+    return out.value
 
 
-def sem_set_learned(h, net):
-    return _check(_lib.sem_set_learned(h, net))
+_LOSS = {"l2": SEM_NET_LOSS_L2, "energy": SEM_NET_LOSS_ENERGY, "angle": SEM_NET_LOSS_ANGLE}
+
+
+def sem_set_learned(h, net, stall_window=8, stall_ratio=0.5, accept_theta=0.25):
+    return _check(_lib.sem_set_learned(h, net, int(stall_window), float(stall_ratio), float(accept_theta)))
+
+
+def sem_learned_iterations(h):
+    n = ctypes.c_int()
+    _check(_lib.sem_learned_iterations(h, ctypes.byref(n)))
+    return n.value
 
 
 class SemProblem:

@@ -88,7 +88,7 @@ def test_fpcg_stall_switches_correction_off():
     b = pr.load(np.random.default_rng(5).standard_normal(pr.G))
     rng = np.random.default_rng(6)
     noise = lambda v: rng.standard_normal(v.shape) * np.linalg.norm(v) * (pr.mask == 0)
-    x, it, hist, on = learned.fpcg(pr.apply_A, pr.apply_P, noise, pr.mask, b, rtol=1e-8, maxit=400)
+    x, it, hist, on = learned.fpcg(pr.apply_A, pr.apply_P, noise, pr.mask, b, rtol=1e-8, maxit=400, theta=-1e300)
     assert hist[-1] <= 1e-8 and on < it
     ref_it = pr.solve(b, rtol=1e-8)[1]
     assert it <= ref_it + on + 10
@@ -103,6 +103,76 @@ def test_training_pair_satisfies_A_delta_equals_s():
     x_star = np.zeros(pr.G)
     x_star[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
     x_k = pr.solve(b, rtol=1e-8, maxit=3)[0]
-    s, delta = learned.training_pair(pr.apply_A, pr.apply_P, pr.mask, b, x_star, x_k)
+    s, delta, r, z0 = learned.training_pair(pr.apply_A, pr.apply_P, pr.mask, b, x_star, x_k)
     np.testing.assert_allclose(pr.apply_A(delta), s, atol=1e-10 * np.abs(s).max())
+    np.testing.assert_allclose(pr.apply_A(delta + z0), r, atol=1e-10 * np.abs(r).max())
     assert np.all(s[~free] == 0) and np.all(delta[~free] == 0)
+
+
+def test_energy_loss_is_energy_norm_ratio_and_gradient_is_exact():
+    pr = _small_problem()
+    A = pr.assembled().toarray()
+    free = pr.mask == 0
+    rng = np.random.default_rng(9)
+    delta = rng.standard_normal(pr.G) * free
+    v = np.where(free, A @ delta, 0.0)
+    theta = rng.standard_normal(learned.n_params()) * 0.2
+    args = (pr.apply_A, pr.m_N, pr.l2g, pr.h, pr.lam, pr.mask)
+    loss, g = learned.energy_loss_and_grad(theta, v, delta, *args)
+    c = learned.correction(theta, v, pr.m_N, pr.l2g, pr.h, pr.lam, pr.mask)
+    d = delta - c
+    assert abs(loss - (d @ A @ d) / (delta @ A @ delta)) <= 1e-10 * loss
+    zero = theta.copy()
+    W3, b3 = learned.unpack(zero)[2]
+    W3[...] = 0.0
+    b3[...] = 0.0
+    assert abs(learned.energy_loss_and_grad(zero, v, delta, *args)[0] - 1.0) < 1e-12
+    for i in rng.choice(theta.size, 12, replace=False):
+        e = np.zeros_like(theta)
+        e[i] = 1e-6
+        fd = (learned.energy_loss_and_grad(theta + e, v, delta, *args)[0]
+              - learned.energy_loss_and_grad(theta - e, v, delta, *args)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_angle_loss_is_line_search_energy_and_gradient_is_exact():
+    pr = _small_problem()
+    A = pr.assembled().toarray()
+    free = pr.mask == 0
+    rng = np.random.default_rng(10)
+    b = pr.load(rng.standard_normal(pr.G))
+    x_star = np.zeros(pr.G)
+    x_star[free] = np.linalg.solve(A[np.ix_(free, free)], b[free])
+    x_k = pr.solve(b, rtol=1e-8, maxit=2)[0]
+    s, delta, r, z0 = learned.training_pair(pr.apply_A, pr.apply_P, pr.mask, b, x_star, x_k)
+    theta = rng.standard_normal(learned.n_params()) * 0.2
+    args = (pr.apply_A, pr.m_N, pr.l2g, pr.h, pr.lam, pr.mask)
+    loss, g = learned.angle_loss_and_grad(theta, s, r, z0, delta, *args)
+    z = z0 + learned.correction(theta, s, pr.m_N, pr.l2g, pr.h, pr.lam, pr.mask)
+    e = x_star - x_k
+    alpha = (z @ A @ e) / (z @ A @ z)                      # exact line search along z
+    left = (e - alpha * z) @ A @ (e - alpha * z) / (e @ A @ e)
+    assert abs(1.0 - (1.0 - loss) ** 2 - left) <= 1e-9
+    assert (loss < 1.0) == (z @ A @ e > 0)
+    for i in rng.choice(theta.size, 12, replace=False):
+        d = np.zeros_like(theta)
+        d[i] = 1e-6
+        fd = (learned.angle_loss_and_grad(theta + d, s, r, z0, delta, *args)[0]
+              - learned.angle_loss_and_grad(theta - d, s, r, z0, delta, *args)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_fpcg_safeguard_rejects_a_correction_that_cancels_descent():
+    pr = _small_problem()
+    b = pr.load(np.random.default_rng(11).standard_normal(pr.G))
+    # a correction c = -2 z0 turns every step into an ascent direction: always rejected
+    last = {}
+
+    def P(r):
+        last["z"] = pr.apply_P(r)
+        return last["z"]
+
+    flip = lambda v: -2.0 * last["z"]
+    x, it, hist, on = learned.fpcg(pr.apply_A, P, flip, pr.mask, b, rtol=1e-10, window=0)
+    ref = pr.solve(b, rtol=1e-10)
+    assert on == 0 and it == ref[1]
