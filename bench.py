@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--learned-variant", action="store_true",
                     help="learned correction: train on seeded 16^3-hex n=5 meshes (lambda ~ U[0,10]), then "
                          "plain against flexible PCG with the network on an unseen 32^3-hex n=7 mesh (seed 4)")
+    ap.add_argument("--heat-variant", action="store_true",
+                    help="heat equation: 70 backward-Euler steps on a 16x16x244-hex rod (moving source, "
+                         "kappa 1e-2, dt 0.04), orders 2..7, recomputed geometry, FP64 and mixed")
+    ap.add_argument("--heat-orders", default="2,3,4,5,6,7")
     ap.add_argument("--train-meshes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
@@ -654,9 +658,60 @@ def run_learned_variant(args):
     prob.close()
 
 
+def run_heat_variant(args):
+    """The paper's heat-equation experiment (Sec. 5) on a synthetic rod: wall time for 70 steps."""
+    import numpy as np
+    import torch
+    from synth import lattice_hex_mesh, moving_source
+    from paper_1506_05996_gb300 import sem as S
+    kappa, dt, q0, rho, cp, steps = 1e-2, 0.04, 1000.0, 7000.0, 0.8, 70
+    lam = 1.0 / (kappa * dt)
+    mesh = lattice_hex_mesh((16, 16, 244), 0.2, 5, box=(1.0, 1.0, 15.25))
+    rows = []
+    for n in [int(v) for v in args.heat_orders.split(",")]:
+        t0 = time.perf_counter()
+        prob = S.SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom="recompute", neumann=True)
+        t_setup = time.perf_counter() - t0
+        X = prob.dof_coords().cpu().numpy()
+        # the moving source at every step, prepared before the timed loop (input synthesis)
+        gs = [torch.as_tensor(moving_source(X, dt * (k + 1), q0=q0) / (rho * cp * kappa), device="cuda")
+              for k in range(steps)]
+        row = {"n": n, "n_dof": prob.n_dof, "setup_s": t_setup}
+        for prec in ("fp64", "fp32"):
+            prob.set_precision(prec)
+            u = torch.zeros(prob.n_dof, dtype=torch.float64, device="cuda")
+            S.sem_heat_step(prob.h, u, gs[0], torch.empty_like(u), RTOL, 1000)   # warm-up (graph capture)
+            torch.cuda.synchronize()
+            its = []
+            t0 = time.perf_counter()
+            for k in range(steps):
+                rc, it, tr = S.sem_heat_step(prob.h, u, gs[k], u, RTOL, 1000)
+                its.append(it)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            row[prec] = {"wall_s_70_steps": wall, "iterations_total": int(sum(its)),
+                         "iterations_per_step": [int(min(its)), int(max(its))],
+                         "gdof_steps_per_s": prob.n_dof * steps / wall / 1e9,
+                         "final_max_u": float(u.abs().max())}
+        rows.append(row)
+        prob.close()
+        del gs
+    print(json.dumps({"variant": "heat", "config": {
+        "workload": "rod [0,1]x[0,1]x[0,15.25], 16x16x244 = 62,464 hexes, +-20% perturbation seed 5, insulated "
+                    "(Neumann) boundary; backward Euler, kappa 1e-2, dt 0.04, c = 1/dt (lambda = 1/(kappa dt) "
+                    "= 2500); moving Gaussian source Q = 1000 exp(-|x-c(t)|^2/(2*0.25^2)), c(t) = (0.5, 0.5, "
+                    "1 + 2t), rho 7000, c_p 0.8; 70 steps, each to 1e-8 of its right-hand side from the "
+                    "previous field; recomputed geometric factors",
+        "paper": "Table 4: 70 steps on a 62,540-hex rod, CUDA on a GTX 980 in FP32: 13.4 / 14.8 / 32.1 / 53.6 / "
+                 "90.3 / 134.9 s for n = 2..7 (context: other hardware, other mesh, tolerance not stated)"},
+        "orders": rows}))
+
+
 def main():
     args = parse()
-    if args.learned_variant:
+    if args.heat_variant:
+        run_heat_variant(args)
+    elif args.learned_variant:
         run_learned_variant(args)
     elif args.batch_variant:
         run_batch_variant(args)

@@ -225,6 +225,23 @@ int sem_apply_A_noalloc(int order, int64_t n_hex, int64_t n_dof, double lambda,
                         void* cuda_stream);
 
 /*
+ * sem_heat_step - one backward-Euler step of the heat equation (Sec. 5, heat experiment).
+ * The model problem c u - div(kappa grad u) = s with c = 1/dt and s = u_prev/dt + Q/(rho c_p),
+ * divided by kappa, is this handle's operator with lambda = 1/(kappa dt) (give that lambda
+ * to sem_create):  A u = M (lambda u_prev + g),  g = Q / (rho c_p kappa).
+ *   u_prev_dev  previous field (sem_num_dofs doubles; 0 on masked DOFs).
+ *   g_dev       scaled source g at the DOFs (its masked entries are ignored).
+ *   u_dev       new field (may alias u_prev_dev, not g_dev).
+ * The step solves A d = M (lambda u_prev + g) - A u_prev (residual with the FP64 operator)
+ * by sem_solve's method (handle precision, preconditioner, network) from d = 0, i.e. with
+ * u_prev as the initial guess, stopping when the residual is <= rtol ||M (lambda u_prev + g)||,
+ * then u = u_prev + d. iters_host and true_rel_res_host (relative to the full right-hand
+ * side) may be NULL. Returns like sem_solve. Synchronises the handle's stream.
+ */
+int sem_heat_step(sem_t* h, const double* u_prev_dev, const double* g_dev, double* u_dev,
+                  double rtol, int maxit, int* iters_host, double* true_rel_res_host);
+
+/*
  * Learned correction (not in the paper; an extension of the preconditioner of Sec. 4).
  * A network N maps the residual left by the two-scale preconditioner to a correction:
  * z = P r + N(r - A P r), inside flexible PCG: beta_k = z_k.(r_k - r_k-1) / (z_k-1.r_k-1)

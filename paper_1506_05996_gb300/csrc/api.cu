@@ -718,6 +718,51 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   return solve_finish(h, c, iters_host, res_hist_host, true_rel_res_host);
 }
 
+int sem_heat_step(sem_t* h, const double* u_prev_dev, const double* g_dev, double* u_dev, double rtol, int maxit,
+                  int* iters_host, double* true_rel_res_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (!u_prev_dev || !g_dev || !u_dev || u_dev == g_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  sem::DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  const size_t G = (size_t)h->nb.G;
+  if (h->heat_b == nullptr) {
+    CK(h->alloc(&h->heat_b, G, h->allocs));
+    CK(h->alloc(&h->heat_d, G, h->allocs));
+    CK(h->alloc(&h->heat_norms, 2, h->allocs));
+  }
+  // b' = M (lambda u_prev + g) - A u_prev with the FP64 operator: the step solves for the
+  // increment, so u_prev is the initial guess; the tolerance stays relative to the full
+  // right-hand side M (lambda u_prev + g)
+  PROF(h, "ax_local_fp64", sem::launch_ax_local(d, u_prev_dev, d.wl, nullptr, s));
+  PROF(h, "heat_rhs", sem::launch_heat_rhs(d, d.wl, h->mN, u_prev_dev, g_dev, h->heat_b, h->heat_norms, s));
+  double norms[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(norms, h->heat_norms, sizeof(norms), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!std::isfinite(norms[0]) || !std::isfinite(norms[1])) return fail(SEM_ERR_NAN, "NaN/Inf in the heat step");
+  if (norms[1] == 0.0 || norms[1] <= rtol * rtol * norms[0]) {
+    if (u_dev != u_prev_dev) CK(cudaMemcpyAsync(u_dev, u_prev_dev, sizeof(double) * G, cudaMemcpyDeviceToDevice, s));
+    if (iters_host) *iters_host = 0;
+    if (true_rel_res_host) *true_rel_res_host = norms[0] > 0.0 ? std::sqrt(norms[1] / norms[0]) : 0.0;
+    return SEM_OK;
+  }
+  const double scale = std::sqrt(norms[1] / norms[0]);   // ||b'|| / ||b||
+  SolveCtx c;
+  c.b = h->heat_b;
+  c.x = h->heat_d;
+  if (int rc = solve_begin(h, c, rtol / scale, maxit)) return rc;
+  for (int guard = 0; guard <= maxit + 1 && !c.done; ++guard) {
+    if (int rc = solve_poll(h)) return rc;
+    if (int rc = solve_advance(h, c)) return rc;
+  }
+  double tr = 0.0;
+  const int rc = solve_finish(h, c, iters_host, nullptr, &tr);
+  if (rc < 0) return rc;
+  PROF(h, "heat_update", sem::launch_add_vectors(d, u_prev_dev, h->heat_d, u_dev, s));
+  if (true_rel_res_host) *true_rel_res_host = tr * scale;
+  return rc;
+}
+
 int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev, double* const* x_dev,
                    double rtol, int maxit, int* iters_host, int* status_host) {
   if (count < 0 || (count > 0 && (handles == nullptr || b_dev == nullptr || x_dev == nullptr)))

@@ -191,6 +191,14 @@ cudaError_t launch_flex_combine(const DevProblem& d, const double* z, const doub
 cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const double* xk, const double* z0,
                               double* delta, cudaStream_t s);
 
+// --- backward-Euler heat step (Sec. 5) -------------------------------------------
+// out = mask ? 0 : m (lambda u_prev + g) - gather(wl); norms = (||m (lambda u_prev + g)||^2,
+// ||out||^2) over the free DOFs
+cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
+                            const double* g, double* out, double* norms, cudaStream_t s);
+// y = a + b
+cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const double* b, double* y, cudaStream_t s);
+
 // aux = ||b - f||^2 over free nodes
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s);
 

@@ -161,6 +161,7 @@ struct sem_s {
   double* hist = nullptr;
   int hist_cap = 0;
   sem::PcgState* st_host = nullptr;  // pinned
+  double *heat_b = nullptr, *heat_d = nullptr, *heat_norms = nullptr;   // sem_heat_step scratch
   // learned correction (not in the paper): attached network and its forward work space
   sem_net_t* net = nullptr;
   int nn_window = 8;        // stall rule of the flexible PCG (sem_set_learned)

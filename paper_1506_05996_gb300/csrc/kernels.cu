@@ -483,6 +483,40 @@ __global__ void __launch_bounds__(kVecBlock) flex_combine_kernel(const DevProble
   }
 }
 
+// Backward-Euler step (Sec. 5): out = mask ? 0 : m (lambda u_prev + g) - gather(wl), wl the FP64
+// local results of A u_prev; norms[0] = ||m (lambda u_prev + g)||^2, norms[1] = ||out||^2
+// over the free DOFs.
+__global__ void __launch_bounds__(kVecBlock) heat_rhs_kernel(const DevProblem d, const double* __restrict__ wl,
+                                                             const double* __restrict__ mN,
+                                                             const double* __restrict__ u_prev,
+                                                             const double* __restrict__ g, double* __restrict__ out,
+                                                             double* __restrict__ norms) {
+  double v[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.G; i += gridDim.x * blockDim.x) {
+    double res = 0.0;
+    if (!d.mask[i]) {
+      const double bf = mN[i] * (d.lambda * u_prev[i] + g[i]);
+      double s = 0.0;
+      for (int q = d.g2l_off[i]; q < d.g2l_off[i + 1]; ++q) s += wl[d.g2l_idx[q]];
+      res = bf - s;
+      v[0] += bf * bf;
+      v[1] += res * res;
+    }
+    out[i] = res;
+  }
+  double t[2];
+  if (grid_reduce_n<kVecBlock, 2>(v, d.partial, &d.st->counter, t) && threadIdx.x == 0) {
+    norms[0] = t[0];
+    norms[1] = t[1];
+  }
+}
+
+// y = a + b
+__global__ void add_vectors_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                   double* __restrict__ y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = a[i] + b[i];
+}
+
 // Training pair: delta = mask ? 0 : x_star - x_k - z0 (the error left after z0 = P r).
 __global__ void pair_delta_kernel(const DevProblem d, const double* __restrict__ xs, const double* __restrict__ xk,
                                   const double* __restrict__ z0, double* __restrict__ delta) {
@@ -705,6 +739,20 @@ cudaError_t launch_flex_combine(const DevProblem& d, const double* z, const doub
 cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const double* xk, const double* z0,
                               double* delta, cudaStream_t s) {
   pair_delta_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, xs, xk, z0, delta);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
+                            const double* g, double* out, double* norms, cudaStream_t s) {
+  heat_rhs_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, mN, u_prev, g, out, norms);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const double* b, double* y, cudaStream_t s) {
+  add_vectors_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, a, b, y);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -49,6 +49,7 @@ _SIGS = {
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
     "sem_solve_many": ([_int, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
+    "sem_heat_step": ([_vp, _vp, _vp, _vp, _dbl, _int, _P(_int), _P(_dbl)], _int),
     "sem_set_tiles": ([_vp, _int, _int], _int),
     "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
     "sem_profile": ([_vp, _int], _int),
@@ -201,6 +202,17 @@ def sem_apply_A_noalloc(order, n_hex, n_dof, lam, elem_xyz, l2g, g2l_off, g2l_id
             _dev(mask, torch.uint8, n_dof), _dev(x, torch.float64, n_dof), _dev(y, torch.float64, n_dof)]
     return _check(_lib.sem_apply_A_noalloc(int(order), int(n_hex), int(n_dof), float(lam), *args,
                                            _stream_ptr(stream)))
+
+
+def sem_heat_step(h, u_prev, g, u, rtol=1e-8, maxit=1000):
+    """One backward-Euler step; returns (status, iterations, true relative residual)."""
+    n = sem_num_dofs(h)
+    it = ctypes.c_int()
+    tr = ctypes.c_double()
+    rc = _check(_lib.sem_heat_step(h, _dev(u_prev, torch.float64, n), _dev(g, torch.float64, n),
+                                   _dev(u, torch.float64, n), float(rtol), int(maxit), ctypes.byref(it),
+                                   ctypes.byref(tr)))
+    return rc, it.value, tr.value
 
 
 def sem_solve_many(handles, bs, xs, rtol=1e-8, maxit=1000):

@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs: perturbed all-hex meshes of the unit cube and loads.
+"""Seeded synthetic inputs: perturbed all-hex meshes of boxes and loads.
 
 This module is shared by the test oracle, the tests and the benchmark. It
 holds no arithmetic of the spectral-element method itself: it only draws
@@ -6,7 +6,7 @@ vertex coordinates, hex connectivity, permutations, orientations and
 right-hand sides from a seeded generator.
 """
 from .mesh import (HexMesh, lattice_hex_mesh, manufactured_u, manufactured_s,
-                   gaussian_load, PROPER_ROTATIONS, VTK_CORNER_BITS)
+                   gaussian_load, moving_source, PROPER_ROTATIONS, VTK_CORNER_BITS)
 
 __all__ = ["HexMesh", "lattice_hex_mesh", "manufactured_u", "manufactured_s",
-           "gaussian_load", "PROPER_ROTATIONS", "VTK_CORNER_BITS"]
+           "gaussian_load", "moving_source", "PROPER_ROTATIONS", "VTK_CORNER_BITS"]

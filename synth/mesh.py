@@ -84,30 +84,30 @@ class HexMesh:
 
 
 def lattice_hex_mesh(E, a=0.0, seed=0, renumber=True, rotate=True, box=(1.0, 1.0, 1.0)):
-    """Perturbed E x E x E hex lattice of the box [0,bx]x[0,by]x[0,bz].
+    """Perturbed Ex x Ey x Ez hex lattice of the box [0,bx]x[0,by]x[0,bz].
 
-    Parameters: E hexes per direction, a the perturbation amplitude as a fraction of
-    the spacing, seed for numpy.random.default_rng. Returns a HexMesh.
+    Parameters: E hexes per direction (an int, or (Ex, Ey, Ez) for a rod or slab), a the
+    perturbation amplitude as a fraction of the spacing, seed for numpy.random.default_rng.
+    Returns a HexMesh.
     """
-    E = int(E)
-    if E < 1:
-        raise ValueError("E must be >= 1")
+    Es = np.array([int(E)] * 3 if np.ndim(E) == 0 else [int(v) for v in E], dtype=np.int64)
+    if Es.shape != (3,) or Es.min() < 1:
+        raise ValueError("E must be >= 1 (or three counts >= 1)")
     rng = np.random.default_rng(seed)
-    nv1 = E + 1
-    idx = np.arange(nv1)
-    I, J, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    nx, ny, nz = (Es + 1).tolist()
+    I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     lat = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1)   # lattice index of vertex
-    vid_of = lambda i, j, k: i + nv1 * (j + nv1 * k)
+    vid_of = lambda i, j, k: i + nx * (j + ny * k)
     order = np.argsort(vid_of(lat[:, 0], lat[:, 1], lat[:, 2]))
-    lat = lat[order]                                             # vertex id = i + nv1*(j + nv1*k)
-    h = np.array(box, dtype=np.float64) / E
+    lat = lat[order]                                             # vertex id = i + nx*(j + ny*k)
+    h = np.array(box, dtype=np.float64) / Es
     xyz = lat.astype(np.float64) * h
     d = rng.uniform(-a, a, size=xyz.shape) * h
-    on_bnd = (lat == 0) | (lat == E)
+    on_bnd = (lat == 0) | (lat == Es)
     d[on_bnd] = 0.0                                              # tangential-only on the boundary
     xyz = xyz + d
 
-    ci, cj, ck = np.meshgrid(np.arange(E), np.arange(E), np.arange(E), indexing="ij")
+    ci, cj, ck = np.meshgrid(np.arange(Es[0]), np.arange(Es[1]), np.arange(Es[2]), indexing="ij")
     cells = np.stack([ci.ravel(), cj.ravel(), ck.ravel()], axis=1)
     hexes = np.empty((cells.shape[0], 8), dtype=np.int64)
     for c, (ba, bb, bc) in enumerate(VTK_CORNER_BITS):
@@ -125,7 +125,7 @@ def lattice_hex_mesh(E, a=0.0, seed=0, renumber=True, rotate=True, box=(1.0, 1.0
         eperm = rng.permutation(hexes.shape[0])
         hexes = hexes[eperm]
     return HexMesh(xyz=np.ascontiguousarray(xyz), hex2vert=np.ascontiguousarray(hexes),
-                   E=E, a=float(a), seed=int(seed))
+                   E=int(Es[0]) if np.ndim(E) == 0 else tuple(Es.tolist()), a=float(a), seed=int(seed))
 
 
 def manufactured_u(xyz):
@@ -137,6 +137,13 @@ def manufactured_u(xyz):
 def manufactured_s(xyz, lam):
     """Source s = lam*u* - laplacian(u*) = (3 pi^2 + lam) u* for the manufactured u*."""
     return (3.0 * np.pi ** 2 + lam) * manufactured_u(xyz)
+
+
+def moving_source(xyz, t, q0=1000.0, width=0.25, start=(0.5, 0.5, 1.0), velocity=(0.0, 0.0, 2.0)):
+    """Volume heat source Q(x, t) = q0 exp(-|x - c(t)|^2 / (2 width^2)), c(t) = start + velocity t."""
+    x = np.asarray(xyz, dtype=np.float64)
+    c = np.asarray(start, dtype=np.float64) + np.asarray(velocity, dtype=np.float64) * t
+    return q0 * np.exp(-np.sum((x - c) ** 2, axis=1) / (2.0 * width ** 2))
 
 
 def gaussian_load(n, seed):
