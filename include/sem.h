@@ -57,6 +57,12 @@ typedef struct sem_s sem_t;
                               FP64; the residual is recomputed with the FP64 operator whenever it
                               fell by 1e3 and before convergence is accepted */
 
+/* coarse solver P_0 of the two-scale preconditioner (sem_set_coarse_solver) */
+#define SEM_COARSE_VCYCLE  0  /* smoothed aggregation, three V(1,1) damped-Jacobi cycles: a fixed SPD
+                                 operator, plain PCG (default) */
+#define SEM_COARSE_KCYCLE  1  /* the paper's (Sec. 4.1): unsmoothed aggregation, one recursive K-cycle
+                                 with damped Jacobi; nonlinear, so sem_solve switches to flexible PCG */
+
 /* preconditioner choice for sem_solve (sem_set_precond) */
 #define SEM_PRECOND_TWO_SCALE 0  /* P = P^c + P^f (Sec. 4) */
 #define SEM_PRECOND_FINE      1  /* P = P^f only (Table 1, fine-scale rows) */
@@ -130,6 +136,13 @@ int sem_set_precision(sem_t* h, int precision);
 
 /* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
 int sem_set_precond(sem_t* h, int which);
+
+/* sem_set_coarse_solver - choose P_0 (SEM_COARSE_*); rebuilds the AMG hierarchy on the host
+ * (Sec. 4.1). With SEM_COARSE_KCYCLE each coarse level above the dense one takes two
+ * flexible-CG steps preconditioned by the K-cycle below it, combined as the A-orthogonal
+ * projection onto their span; sem_solve then uses beta_k = z_k.(r_k - r_k-1) / (z_k-1.r_k-1).
+ * Errors: SEM_ERR_ARG, SEM_ERR_CUDA, SEM_ERR_OOM. */
+int sem_set_coarse_solver(sem_t* h, int kind);
 
 /*
  * sem_solve - PCG (Algorithm 1) for A_D x = b from x_0 = 0.

@@ -21,6 +21,15 @@ library (each written independently from this description):
     x += w D^{-1} (b - A x); w = 2/3. P_0 applies three such cycles as a
     stationary iteration from x = 0, so P_0 is a fixed linear SPD operator and
     plain PCG applies (the paper's K-cycle is nonlinear).
+The paper's own cycle (kind "kcycle"): unsmoothed aggregation (tentative prolongator T
+from two pairwise passes, aggregates of up to 4; A_c = T^T A T) with the recursive K-cycle
+of its reference [notay2010aggregation] and damped Jacobi (w = 2/3): at a level, pre-smooth
+from zero, restrict the residual r_c; on the next level, unless it is the dense one, take
+two flexible-CG steps preconditioned by the K-cycle there, c1 = K(r_c),
+c2 = K(r_c - a A c1) with a = c1.r_c / c1.A c1, and the coarse correction e_c is the
+Galerkin projection of A_c^-1 r_c onto span{c1, c2} (one-dimensional when c2 is
+A-parallel to c1); prolong, post-smooth. One K-cycle is P_0. It is nonlinear in r_c, so
+the outer solve is flexible PCG.
 Unsmoothed aggregation with a single V-cycle was tried first: it contracts the
 coarse error by only ~0.8 per cycle and nearly doubles the PCG iteration counts.
 Below ~2000 unknowns the smoothed Galerkin products become nearly dense and the
@@ -78,16 +87,23 @@ def aggregation_matrix(agg, na):
     return csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, na))
 
 
-class AMG:
-    """Smoothed-aggregation hierarchy and the P_0 = three V(1,1) cycles."""
+KC_PASSES = 2
+KC_PARALLEL = 1e-14   # c2 counts as A-parallel to c1 when det(Gram) <= KC_PARALLEL (c1.Ac1)(c2.Ac2)
 
-    def __init__(self, A0):
+
+class AMG:
+    """Aggregation hierarchy: smoothed with P_0 = three V(1,1) cycles (kind "vcycle"), or
+    unsmoothed with P_0 = one K-cycle (kind "kcycle")."""
+
+    def __init__(self, A0, kind="vcycle"):
+        self.kind = kind
         self.levels = []              # (A, Dinv, P)
         A = csr_matrix(A0)
+        passes = PASSES if kind == "vcycle" else KC_PASSES
         while A.shape[0] > MAX_COARSEST:
             agg = np.arange(A.shape[0])
             Ac = A
-            for _ in range(PASSES):
+            for _ in range(passes):
                 a, na = pairwise_pass(Ac)
                 agg = a[agg]
                 T1 = aggregation_matrix(a, na)
@@ -97,10 +113,13 @@ class AMG:
                 break
             T = aggregation_matrix(agg, nc)
             d = A.diagonal()
-            gersh = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / d)
-            wP = (4.0 / 3.0) / gersh
-            P = (T - wP * (diags(1.0 / d) @ (A @ T))).tocsr()
-            P.eliminate_zeros()
+            if kind == "vcycle":
+                gersh = np.max(np.asarray(abs(A).sum(axis=1)).ravel() / d)
+                wP = (4.0 / 3.0) / gersh
+                P = (T - wP * (diags(1.0 / d) @ (A @ T))).tocsr()
+                P.eliminate_zeros()
+            else:
+                P = T.tocsr()
             self.levels.append((A, 1.0 / d, P))
             A = (P.T @ A @ P).tocsr()
         if A.shape[0] > MAX_DENSE:
@@ -123,8 +142,43 @@ class AMG:
         x = x + OMEGA * Dinv * (b - A @ x)
         return x
 
+    def level_matrix(self, level):
+        return self.levels[level][0] if level < len(self.levels) else None
+
+    def kcycle(self, b, level=0):
+        """One K-cycle at `level` for right-hand side b."""
+        if level == len(self.levels):
+            return self.coarsest_inv @ b
+        A, Dinv, P = self.levels[level]
+        x = OMEGA * Dinv * b
+        rc = P.T @ (b - A @ x)
+        ec = self.coarse_correction(rc, level + 1)[0]
+        x = x + P @ ec
+        return x + OMEGA * Dinv * (b - A @ x)
+
+    def coarse_correction(self, rc, level):
+        """(e_c, c1, c2) on `level` for the restricted residual rc (c1, c2 None when exact)."""
+        if level == len(self.levels):
+            return self.coarsest_inv @ rc, None, None
+        Ac = self.levels[level][0]
+        c1 = self.kcycle(rc, level)
+        Ac1 = Ac @ c1
+        step = (c1 @ rc) / (c1 @ Ac1) if c1 @ Ac1 > 0 else 0.0
+        c2 = self.kcycle(rc - step * Ac1, level)
+        Ac2 = Ac @ c2
+        gram = np.array([[c1 @ Ac1, c1 @ Ac2], [c2 @ Ac1, c2 @ Ac2]])
+        rhs = np.array([c1 @ rc, c2 @ rc])
+        if not gram[0, 0] > 0:                       # r_c = 0
+            return np.zeros_like(rc), c1, c2
+        if np.linalg.det(gram) <= KC_PARALLEL * gram[0, 0] * gram[1, 1]:
+            return (rhs[0] / gram[0, 0]) * c1, c1, c2
+        a, b = np.linalg.solve(gram, rhs)
+        return a * c1 + b * c2, c1, c2
+
     def apply(self, b):
-        """P_0 b: N_CYCLES stationary V-cycles from zero."""
+        """P_0 b: one K-cycle (kind "kcycle"), or N_CYCLES stationary V-cycles from zero."""
+        if self.kind == "kcycle":
+            return self.kcycle(b)
         A = self.levels[0][0] if self.levels else None
         x = self.vcycle(b)
         for _ in range(N_CYCLES - 1):

@@ -65,8 +65,8 @@ class Problem:
         self.free_vert = np.where(self.mask[vdof] == 0)[0]        # ascending vertex id
         fv = self.free_vert
         self.A0 = csr_matrix(A0full[fv][:, fv])
-        if self.coarse_solver == "amg":
-            self.amg = amg.AMG(self.A0)
+        if self.coarse_solver in ("amg", "kcycle"):
+            self.amg = amg.AMG(self.A0, kind="vcycle" if self.coarse_solver == "amg" else "kcycle")
             self.P0 = self.amg.apply
         elif self.coarse_solver == "exact":
             A0d = self.A0.toarray()
@@ -101,7 +101,8 @@ class Problem:
     def solve(self, b, rtol=1e-8, maxit=1000, precond="two-scale"):
         bm = np.where(self.mask > 0, 0.0, b)
         P = {"two-scale": self.apply_P, "fine": self.apply_Pf, "none": lambda r: r.copy()}[precond]
-        return pcg.pcg(self.apply_A, P, bm, rtol, maxit)
+        flexible = self.coarse_solver == "kcycle" and precond == "two-scale"   # the K-cycle is nonlinear
+        return (pcg.fpcg if flexible else pcg.pcg)(self.apply_A, P, bm, rtol, maxit)
 
     def assembled(self):
         """Sparse A_D by explicit element-matrix assembly (small meshes only)."""

@@ -15,6 +15,8 @@
 //    densely (Cholesky).
 // The cycle applied on the GPU is a symmetric V(1,1) with Jacobi weight 2/3,
 // repeated three times as a stationary iteration.
+// The paper's own variant (kAmgKcycle): unsmoothed aggregation, i.e. two pairwise passes
+// (aggregates of up to 4) and P = T, A_c = T^T A T, applied as one recursive K-cycle.
 #include <algorithm>
 #include <cmath>
 #include <thread>
@@ -125,15 +127,17 @@ void parallel_for(int n, F f) {
 
 }  // namespace
 
-std::string build_amg(const Csr& A0, Amg& out) {
+std::string build_amg(const Csr& A0, Amg& out, int kind) {
   out.levels.clear();
+  const bool smoothed = (kind == kAmgVcycle);
+  const int passes = smoothed ? kPasses : 2;
   Csr A = A0;
   while (A.n > kMaxCoarsest) {
     std::vector<int> agg(A.n);
     for (int i = 0; i < A.n; ++i) agg[i] = i;
     Csr Ac = A;
     int nc = A.n;
-    for (int pass = 0; pass < kPasses; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
       int na;
       std::vector<int> a = pairwise(Ac, na);
       for (int i = 0; i < A.n; ++i) agg[i] = a[agg[i]];
@@ -153,6 +157,18 @@ std::string build_amg(const Csr& A0, Amg& out) {
       }
       if (!(d[i] > 0)) return "coarse matrix has a non-positive diagonal";
       gersh = std::max(gersh, rs / d[i]);
+    }
+    AmgLevel lv;
+    if (!smoothed) {
+      lv.A = A;
+      lv.P = T;
+      lv.R = transpose(T);
+      lv.dinv.resize(A.n);
+      for (int i = 0; i < A.n; ++i) lv.dinv[i] = 1.0 / d[i];
+      Csr Anext = spgemm(lv.R, spgemm(A, T));
+      out.levels.push_back(std::move(lv));
+      A = std::move(Anext);
+      continue;
     }
     const double wP = (4.0 / 3.0) / gersh;
     Csr AT = spgemm(A, T);
@@ -175,7 +191,6 @@ std::string build_amg(const Csr& A0, Amg& out) {
       }
       P.ptr[i + 1] = (int)P.col.size();
     }
-    AmgLevel lv;
     lv.A = A;
     lv.P = P;
     lv.R = transpose(P);

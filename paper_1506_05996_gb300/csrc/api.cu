@@ -77,7 +77,8 @@ int build_coarse(sem_t* h) {
   if (nfree == 0) { h->coarse_ok = true; return SEM_OK; }
   sem::Csr A0 = sem::submatrix(h->A0full, keep);
   sem::Amg amg;
-  std::string err = sem::build_amg(A0, amg);
+  d.amg_kind = h->amg_kind;
+  std::string err = sem::build_amg(A0, amg, h->amg_kind == SEM_COARSE_KCYCLE ? sem::kAmgKcycle : sem::kAmgVcycle);
   if (!err.empty()) {
     h->coarse_err = err;
     d.nfree = 0;
@@ -103,7 +104,15 @@ int build_coarse(sem_t* h) {
     CK(h->alloc(&D.x, L.A.n, h->coarse_allocs));
     CK(h->alloc(&D.t, L.A.n, h->coarse_allocs));
     CK(h->alloc(&D.y, L.A.n, h->coarse_allocs));
+    if (h->amg_kind == SEM_COARSE_KCYCLE) {
+      CK(h->alloc(&D.c1, L.A.n, h->coarse_allocs));
+      CK(h->alloc(&D.c2, L.A.n, h->coarse_allocs));
+      CK(h->alloc(&D.v1, L.A.n, h->coarse_allocs));
+      CK(h->alloc(&D.v2, L.A.n, h->coarse_allocs));
+      CK(h->alloc(&D.scal, 8, h->coarse_allocs));
+    }
   }
+  if (h->amg_kind == SEM_COARSE_KCYCLE && d.rprev == nullptr) CK(h->alloc(&d.rprev, (size_t)h->nb.G, h->allocs));
   double* tmp_d;
   CK(h->upload(&tmp_d, amg.coarsest_inv, h->coarse_allocs)); d.coarsest_inv = tmp_d;
   d.coarsest_n = amg.coarsest_n;
@@ -159,9 +168,12 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   }
   if (coarse) CK(cudaStreamWaitEvent(h->stream, h->ev_join, 0));   // join
   if (which == SEM_PRECOND_NONE) mode = sem::PSUM_IDENT;
-  const bool flex = pcg && h->net != nullptr;
+  // flexible PCG when P varies between applications: the K-cycle is nonlinear, and the
+  // learned correction depends on r
+  const bool learned = pcg && h->net != nullptr;
+  const bool flex = pcg && (learned || (coarse && d.amg_kind == SEM_COARSE_KCYCLE));
   PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg && !flex, h->stream));
-  if (flex) {
+  if (learned) {
     // z = P r + N(r - A P r), flexible PCG; the operator application and the network skip
     // once the correction is switched off (d.st_nn->done), the combine keeps the dots. The
     // network's input needs no FP64: the FP32 operator runs whenever its factors exist.
@@ -174,8 +186,8 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
       PROF(h, "nn_residual", sem::launch_residual_of(d, d.wl, r, d.nns, st, h->stream));
     }
     PROF(h, "nn_correction", sem::learned_correction(h, d.nns, st, h->stream));
-    PROF(h, "flex_combine", sem::launch_flex_combine(d, z, r, h->stream));
   }
+  if (flex) PROF(h, "flex_combine", sem::launch_flex_combine(d, z, r, h->stream));
   return SEM_OK;
 }
 
@@ -523,6 +535,14 @@ int sem_set_precision(sem_t* h, int precision) {
   return SEM_OK;
 }
 
+int sem_set_coarse_solver(sem_t* h, int kind) {
+  if (int rc = check_handle(h)) return rc;
+  if (kind != SEM_COARSE_VCYCLE && kind != SEM_COARSE_KCYCLE) return fail(SEM_ERR_ARG, "unknown coarse solver");
+  if (kind == h->amg_kind) return SEM_OK;
+  h->amg_kind = kind;
+  return build_coarse(h);
+}
+
 int sem_set_precond(sem_t* h, int which) {
   if (int rc = check_handle(h)) return rc;
   if (which < SEM_PRECOND_TWO_SCALE || which > SEM_PRECOND_NONE) return fail(SEM_ERR_ARG, "unknown preconditioner");
@@ -582,16 +602,18 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
 
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
   const int learned = h->net != nullptr ? 1 : 0;
+  const int flexible = (learned || (d.amg_kind == SEM_COARSE_KCYCLE && h->precond == SEM_PRECOND_TWO_SCALE)) ? 1 : 0;
   if (learned) CK(cudaMemsetAsync(d.st_nn, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, h->nn_window, h->nn_ratio,
-                                           h->nn_theta, h->hist, s));
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, flexible, h->nn_window,
+                                           h->nn_ratio, h->nn_theta, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
   if (int rc = enqueue_head()) return rc;
 
   // capture the steady-state iteration once per configuration
   const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
-                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8) | ((long)learned << 12);
+                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8) | ((long)learned << 12) |
+                   ((long)d.amg_kind << 13);
   if (h->graph.key != key) {
     h->graph.reset();
     CK(cudaStreamSynchronize(s));

@@ -37,7 +37,8 @@ struct PcgState {
   int done;         // 1 once converged / stopped
   int status;       // 0, SEM_MAXIT (1) or SEM_ERR_NAN (-6)
   int maxit;
-  int learned;      // 1: flexible PCG with the learned correction added to z
+  int learned;      // 1: the learned correction is added to z (flexible PCG)
+  int flexible;     // 1: Polak-Ribiere beta (the K-cycle or the network make P vary)
   int nn_off;       // 1 once the learned correction was switched off for this solve
   int stall_window; // switch it off when ||r_k|| >= stall_ratio ||r_k-W|| (W = stall_window, 0 = never)
   double stall_ratio2;               // stall_ratio^2
@@ -59,6 +60,8 @@ struct DevAmgLevel {
   DevCsr A, P, R;
   double* dinv = nullptr;
   double *b = nullptr, *x = nullptr, *t = nullptr, *y = nullptr;   // rhs, iterate, residual, output (size A.n)
+  // K-cycle: the two inner directions c1, c2, their images A c1, A c2, and 8 scalars
+  double *c1 = nullptr, *c2 = nullptr, *v1 = nullptr, *v2 = nullptr, *scal = nullptr;
 };
 
 struct DevProblem {
@@ -94,6 +97,7 @@ struct DevProblem {
   const int* cv_idx = nullptr;
   // AMG
   int nlevels = 0;
+  int amg_kind = 0;                 // 0: three V(1,1) cycles (linear); 1: one K-cycle (nonlinear)
   DevAmgLevel* levels = nullptr;    // host array of device levels
   int coarsest_n = 0;
   const double* coarsest_inv = nullptr;
@@ -168,7 +172,7 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 
 // --- PCG (Algorithm 1) -------------------------------------------------------
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol,
-                            int maxit, int mixed, int learned, int stall_window, double stall_ratio,
+                            int maxit, int mixed, int learned, int flexible, int stall_window, double stall_ratio,
                             double nn_theta, double* hist, cudaStream_t s);
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s);
 // f = gather(wl) (0 on masked; FP32 local results when d.fp32), pf = p.f, alpha = rz / pf.

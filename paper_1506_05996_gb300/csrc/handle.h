@@ -155,6 +155,7 @@ struct sem_s {
   double *coords = nullptr, *mN = nullptr, *geo = nullptr;
   float* geo32 = nullptr;
   int precision = SEM_PREC_FP64;
+  int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
   uint8_t* mask = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
   IterGraph graph;

@@ -79,8 +79,11 @@ struct Amg {
   int coarsest_n = 0;
   std::vector<double> coarsest_inv;   // dense, row major
 };
+// kAmgVcycle: smoothed aggregation (three pairwise passes), applied as three V(1,1) cycles;
+// kAmgKcycle: unsmoothed aggregation (two passes, P = T), applied as one K-cycle (Sec. 4.1).
+enum AmgKind { kAmgVcycle = 0, kAmgKcycle = 1 };
 // Returns "" or an error message (not SPD, stalled).
-std::string build_amg(const Csr& A0, Amg& out);
+std::string build_amg(const Csr& A0, Amg& out, int kind = kAmgVcycle);
 Csr submatrix(const Csr& A, const std::vector<int>& keep);   // rows/cols in keep, renumbered
 
 }  // namespace sem

@@ -209,6 +209,84 @@ __global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const do
   }
 }
 
+// K-cycle (Sec. 4.1, the recursive cycle of the paper's AMG reference): two flexible-CG
+// steps on a coarse level, c1 = K(r_c), c2 = K(r_c - (c1.r_c / c1.A c1) A c1), and the
+// correction e_c = a c1 + b c2 that is A-orthogonal projection of A^-1 r_c onto
+// span{c1, c2}: b = alpha2 / rho2, a = alpha1 / rho1 - gamma b / rho1 with
+// rho1 = c1.A c1, alpha1 = c1.r_c, gamma = c2.A c1, beta = c2.A c2, alpha2 = c2.r2,
+// rho2 = beta - gamma^2 / rho1 (one direction when rho2 <= 1e-14 beta). The level's
+// vectors are small: one block sums them in a fixed order.
+constexpr int kKcBlock = 512;
+constexpr double kKcParallel = 1e-14;
+
+// scal[0] = c1.v1 (rho1), scal[1] = c1.rc (alpha1)
+__global__ void __launch_bounds__(kKcBlock) kc_dots1_kernel(int n, const double* __restrict__ c1,
+                                                            const double* __restrict__ v1,
+                                                            const double* __restrict__ rc, double* __restrict__ scal,
+                                                            const PcgState* st) {
+  if (stopped(st)) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += kKcBlock) {
+    a += c1[i] * v1[i];
+    b += c1[i] * rc[i];
+  }
+  a = block_sum<kKcBlock>(a);
+  b = block_sum<kKcBlock>(b);
+  if (threadIdx.x == 0) {
+    scal[0] = a;
+    scal[1] = b;
+  }
+}
+
+// rc -= (alpha1 / rho1) v1 (rc becomes r2)
+__global__ void kc_r2_kernel(int n, const double* __restrict__ v1, const double* __restrict__ scal,
+                             double* __restrict__ rc, const PcgState* st) {
+  if (stopped(st)) return;
+  const double step = scal[0] > 0.0 ? scal[1] / scal[0] : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) rc[i] -= step * v1[i];
+}
+
+// scal[2] = c2.v1 (gamma), scal[3] = c2.v2 (beta), scal[4] = c2.r2 (alpha2)
+__global__ void __launch_bounds__(kKcBlock) kc_dots2_kernel(int n, const double* __restrict__ c2,
+                                                            const double* __restrict__ v1,
+                                                            const double* __restrict__ v2,
+                                                            const double* __restrict__ r2, double* __restrict__ scal,
+                                                            const PcgState* st) {
+  if (stopped(st)) return;
+  double g = 0.0, b = 0.0, a = 0.0;
+  for (int i = threadIdx.x; i < n; i += kKcBlock) {
+    g += c2[i] * v1[i];
+    b += c2[i] * v2[i];
+    a += c2[i] * r2[i];
+  }
+  g = block_sum<kKcBlock>(g);
+  b = block_sum<kKcBlock>(b);
+  a = block_sum<kKcBlock>(a);
+  if (threadIdx.x == 0) {
+    scal[2] = g;
+    scal[3] = b;
+    scal[4] = a;
+  }
+}
+
+// ec = a c1 + b c2 (the projection above)
+__global__ void kc_combine_kernel(int n, const double* __restrict__ c1, const double* __restrict__ c2,
+                                  const double* __restrict__ scal, double* __restrict__ ec, const PcgState* st) {
+  if (stopped(st)) return;
+  const double rho1 = scal[0], alpha1 = scal[1], gamma = scal[2], beta = scal[3], alpha2 = scal[4];
+  double a = 0.0, b = 0.0;
+  if (rho1 > 0.0) {
+    const double rho2 = beta - gamma * gamma / rho1;
+    if (rho2 <= kKcParallel * beta) {
+      a = alpha1 / rho1;
+    } else {
+      b = alpha2 / rho2;
+      a = alpha1 / rho1 - gamma * b / rho1;
+    }
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ec[i] = a * c1[i] + b * c2[i];
+}
+
 // ------------------------------------------------------------ P sum and PCG
 template <typename T> __device__ __forceinline__ const T* btab_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* btab_of<double>(const DevProblem& d) { return d.Btab; }
@@ -270,14 +348,14 @@ __global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __rest
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
                                                              double rtol, int maxit, int mixed, int learned,
-                                                             int stall_window, double stall_ratio, double nn_theta,
-                                                             double* hist) {
+                                                             int flexible, int stall_window, double stall_ratio,
+                                                             double nn_theta, double* hist) {
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
     r[g] = v;
     if (mixed) d.r32[g] = (float)v;
-    if (learned) d.rprev[g] = 0.0;
+    if (flexible) d.rprev[g] = 0.0;
     u[g] = 0.0;
     dot += v * v;
   }
@@ -297,7 +375,8 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
     st->replace = 0;
     st->replacements = 0;
     st->learned = learned;
-    st->nn_off = 0;
+    st->flexible = flexible;
+    st->nn_off = learned ? 0 : 1;
     st->stall_window = stall_window;
     st->nn_theta = nn_theta;
     st->nn_use = 0;
@@ -352,7 +431,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
   const double alpha = d.st->alpha;
   float* __restrict__ r32 = d.st->mixed ? d.r32 : nullptr;
   double dot = 0.0;
-  double* __restrict__ rprev = d.st->learned ? d.rprev : nullptr;
+  double* __restrict__ rprev = d.st->flexible ? d.rprev : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     u[g] = u[g] + alpha * p[g];
     const double ro = r[g];
@@ -573,6 +652,50 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
   return cudaGetLastError();
 }
 
+
+// One K-cycle at `level` for right-hand side b, result in out (out != b).
+cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
+  if (level == d.nlevels) {
+    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
+  const DevAmgLevel& L = d.levels[level];
+  const int n = L.A.n, gb = grid_for(n, 256, 4096), gw = grid_for(32 * n, 256, 8192);
+  amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
+  amg_resid_kernel<<<gw, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  g_kernel_launches += 2;
+  const int nc = L.R.n;
+  cudaError_t err;
+  double* ec;
+  if (level + 1 == d.nlevels) {
+    amg_spmv_kernel<<<grid_for(32 * nc, 256, 8192), 256, 0, s>>>(L.R, L.t, d.cb, st);
+    ++g_kernel_launches;
+    err = kcycle(d, level + 1, d.cb, d.cx, st, s);   // the dense level: exact
+    if (err != cudaSuccess) return err;
+    ec = d.cx;
+  } else {
+    const DevAmgLevel& N = d.levels[level + 1];
+    const int gbc = grid_for(nc, 256, 4096), gwc = grid_for(32 * nc, 256, 8192);
+    amg_spmv_kernel<<<gwc, 256, 0, s>>>(L.R, L.t, N.b, st);
+    ++g_kernel_launches;
+    if ((err = kcycle(d, level + 1, N.b, N.c1, st, s)) != cudaSuccess) return err;
+    amg_spmv_kernel<<<gwc, 256, 0, s>>>(N.A, N.c1, N.v1, st);
+    kc_dots1_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c1, N.v1, N.b, N.scal, st);
+    kc_r2_kernel<<<gbc, 256, 0, s>>>(nc, N.v1, N.scal, N.b, st);
+    g_kernel_launches += 3;
+    if ((err = kcycle(d, level + 1, N.b, N.c2, st, s)) != cudaSuccess) return err;
+    amg_spmv_kernel<<<gwc, 256, 0, s>>>(N.A, N.c2, N.v2, st);
+    kc_dots2_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c2, N.v1, N.v2, N.b, N.scal, st);
+    kc_combine_kernel<<<gbc, 256, 0, s>>>(nc, N.c1, N.c2, N.scal, N.y, st);
+    g_kernel_launches += 3;
+    ec = N.y;
+  }
+  amg_prolong_add_kernel<<<gw, 256, 0, s>>>(L.P, ec, L.x, st);
+  amg_jacobi_post_kernel<<<gw, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  g_kernel_launches += 2;
+  return cudaGetLastError();
+}
 }  // namespace
 
 // ================================================================ launchers
@@ -625,12 +748,12 @@ cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, cons
   return launch_coarse_restrict_t<float>(d, r, st, s);
 }
 
-// Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero.
+// Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero, or one K-cycle.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  cudaError_t err = vcycle(d, 0, d.Rc, d.Zc, st, s);
+  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s) : vcycle(d, 0, d.Rc, d.Zc, st, s);
   if (err != cudaSuccess) return err;
-  if (d.nlevels == 0) {
+  if (d.nlevels == 0 || d.amg_kind == 1) {
     if (d.fp32) {
       to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
       ++g_kernel_launches;
@@ -668,10 +791,10 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 }
 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
-                            int mixed, int learned, int stall_window, double stall_ratio, double nn_theta,
-                            double* hist, cudaStream_t s) {
-  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, stall_window, stall_ratio,
-                                                nn_theta, hist);
+                            int mixed, int learned, int flexible, int stall_window, double stall_ratio,
+                            double nn_theta, double* hist, cudaStream_t s) {
+  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, flexible, stall_window,
+                                                stall_ratio, nn_theta, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

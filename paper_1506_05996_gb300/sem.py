@@ -26,6 +26,7 @@ SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED = 0x0, 0x1, 0x10, 0x
 SEM_PREC_FP64, SEM_PREC_FP32 = 0, 1
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
+SEM_COARSE_VCYCLE, SEM_COARSE_KCYCLE = 0, 1
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 _P = ctypes.POINTER
@@ -45,6 +46,7 @@ _SIGS = {
     "sem_apply_Pf": ([_vp, _vp, _vp], _int),
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
     "sem_set_precond": ([_vp, _int], _int),
+    "sem_set_coarse_solver": ([_vp, _int], _int),
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
@@ -174,6 +176,10 @@ def sem_apply_Pc(h, r, z):
 
 def sem_set_precond(h, which):
     return _check(_lib.sem_set_precond(h, int(which)))
+
+
+def sem_set_coarse_solver(h, kind):
+    return _check(_lib.sem_set_coarse_solver(h, {"vcycle": SEM_COARSE_VCYCLE, "kcycle": SEM_COARSE_KCYCLE}.get(kind, kind)))
 
 
 def sem_set_precision(h, precision):
@@ -356,6 +362,9 @@ class SemProblem:
 
     def _vec(self, dtype=torch.float64, n=None):
         return torch.empty(self.n_dof if n is None else n, dtype=dtype, device=self.device)
+
+    def set_coarse_solver(self, kind):
+        sem_set_coarse_solver(self.h, kind)
 
     def set_precision(self, prec):
         sem_set_precision(self.h, {"fp64": SEM_PREC_FP64, "fp32": SEM_PREC_FP32}[prec])

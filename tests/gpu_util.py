@@ -8,10 +8,12 @@ from paper_1506_05996_gb300.sem import SemProblem
 
 
 class Pair:
-    def __init__(self, mesh, n, lam, geom="stored", neumann=False, coarse=True, schwarz=True):
+    def __init__(self, mesh, n, lam, geom="stored", neumann=False, coarse=True, schwarz=True, kcycle=False):
         self.gpu = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom=geom, neumann=neumann)
+        if kcycle:
+            self.gpu.set_coarse_solver("kcycle")
         self.ref = Problem(mesh, n, lam, dirichlet=not neumann,
-                           coarse_solver="amg" if coarse else None, with_schwarz=schwarz)
+                           coarse_solver=("kcycle" if kcycle else "amg") if coarse else None, with_schwarz=schwarz)
         self._match()
 
     def _match(self):

@@ -17,7 +17,8 @@ sem::Csr g_A0;
 
 extern "C" {
 
-int hh_setup(const double* xyz, int64_t nv, const int64_t* hex, int64_t ne, int n, double lam, int neumann) {
+int hh_setup(const double* xyz, int64_t nv, const int64_t* hex, int64_t ne, int n, double lam, int neumann,
+             int amg_kind) {
   std::string err = sem::number_mesh(xyz, nv, hex, ne, n, g_nb);
   if (!err.empty()) return -1;
   sem::gll(n, g_t, g_rho);
@@ -34,7 +35,7 @@ int hh_setup(const double* xyz, int64_t nv, const int64_t* hex, int64_t ne, int 
     if (g >= 0 && (neumann || g_nb.boundary[g] == 0)) g_keep.push_back((int)v);
   }
   g_A0 = sem::submatrix(A0full, g_keep);
-  err = sem::build_amg(g_A0, g_amg);
+  err = sem::build_amg(g_A0, g_amg, amg_kind);
   return err.empty() ? 0 : -2;
 }
 

@@ -135,8 +135,8 @@ def test_angle_gradient_parity(E, n, lam, seed):
     P = _pair(E, n, lam, seed=seed)
     net, theta = _random_net(seed + 40, 0.3)
     rng = np.random.default_rng(seed + 4)
-    b = P.ref.load(rng.standard_normal(P.ref.G))
     xs = rng.standard_normal(P.ref.G) * (P.ref.mask == 0)
+    b = P.ref.apply_A(xs) * (P.ref.mask == 0)      # x* solves A x = b, so r = A e as the loss assumes
     xk = 0.5 * xs
     s, delta, r, z0 = learned.training_pair(P.ref.apply_A, P.ref.apply_P, P.ref.mask, b, xs, xk)
     loss, g = sem.sem_net_gradient(net, P.gpu.h, P.to_gpu(s), P.to_gpu(delta), loss="angle", r=P.to_gpu(r),

@@ -63,12 +63,12 @@ def test_numbering_patch_and_tables(lib, E, n, a, seed):
     np.testing.assert_allclose(np.sort(H.ev), np.sort(ref.ev), rtol=1e-12, atol=1e-13)
 
 
-@pytest.mark.parametrize("E,n,lam", [(16, 1, 1.0), (20, 2, 0.0)])
-def test_amg_hierarchy_matches_oracle(lib, E, n, lam):
+@pytest.mark.parametrize("E,n,lam,kind", [(16, 1, 1.0, 0), (20, 2, 0.0, 0), (24, 1, 0.5, 1), (20, 2, 0.0, 1)])
+def test_amg_hierarchy_matches_oracle(lib, E, n, lam, kind):
     mesh = lattice_hex_mesh(E, 0.2, 1)
-    H = HostTables(lib, mesh, n, lam)
+    H = HostTables(lib, mesh, n, lam, amg_kind=kind)
     assert H.rc == 0
-    ref = Problem(mesh, n, lam, with_schwarz=False)
+    ref = Problem(mesh, n, lam, with_schwarz=False, coarse_solver=("amg", "kcycle")[kind])
     np.testing.assert_array_equal(H.keep, ref.free_vert)
     assert H.amg_sizes == ref.amg.sizes()
     for l, (A, Dinv, Pm) in enumerate(ref.amg.levels):

@@ -135,3 +135,66 @@ def test_table1_trend_two_scale_flat_fine_only_grows():
     assert two[2] <= 1.5 * two[1]
     assert fine[2] >= 1.6 * fine[1]
     assert fine[2] > 1.5 * two[2]
+
+
+def _q1_free(E, seed=1, lam=1.0):
+    return Problem(lattice_hex_mesh(E, 0.2, seed), 1, lam, with_schwarz=False, coarse_solver="kcycle")
+
+
+def test_unsmoothed_aggregation_is_piecewise_constant_galerkin():
+    pr = _q1_free(28)
+    H = pr.amg
+    assert len(H.levels) >= 2
+    A = pr.A0
+    for Al, Dinv, P in H.levels:
+        P = sp.csr_matrix(P)
+        assert np.all(np.diff(P.indptr) == 1) and np.all(P.data == 1.0)   # one aggregate per unknown
+        assert max(np.bincount(P.indices)) <= 4                           # two pairwise passes
+        Ac = P.T @ Al @ P
+        one, onec = np.ones(Al.shape[0]), np.ones(P.shape[1])
+        assert abs(onec @ (Ac @ onec) - one @ (Al @ one)) <= 1e-12 * abs(one @ (Al @ one))
+
+
+def test_kcycle_on_two_levels_is_the_two_grid_cycle():
+    pr = _q1_free(14)
+    H = pr.amg
+    assert len(H.levels) == 1
+    A, Dinv, P = H.levels[0]
+    Ad = A.toarray()
+    Pd = P.toarray()
+    Ac = Pd.T @ Ad @ Pd
+    b = np.random.default_rng(7).standard_normal(A.shape[0])
+    x = (2.0 / 3.0) * Dinv * b
+    x = x + Pd @ np.linalg.solve(Ac, Pd.T @ (b - Ad @ x))
+    x = x + (2.0 / 3.0) * Dinv * (b - Ad @ x)
+    np.testing.assert_allclose(H.kcycle(b), x, rtol=0, atol=1e-10 * np.abs(x).max())
+
+
+def test_kcycle_inner_correction_is_galerkin_on_two_directions():
+    pr = _q1_free(24)
+    H = pr.amg
+    assert len(H.levels) >= 2
+    A1 = H.levels[1][0]
+    rc = np.random.default_rng(8).standard_normal(A1.shape[0])
+    ec, c1, c2 = H.coarse_correction(rc, 1)
+    res = rc - A1 @ ec
+    for c in (c1, c2):
+        assert abs(c @ res) <= 1e-10 * np.linalg.norm(c) * np.linalg.norm(rc)
+
+
+def test_flexible_cg_with_kcycle_is_h_independent():
+    its = []
+    for E in (18, 24, 32):          # one, two and three aggregation levels above the dense one
+        pr = _q1_free(E)
+        b = np.random.default_rng(9).standard_normal(pr.A0.shape[0])
+        its.append(pcg.fpcg(lambda v: pr.A0 @ v, pr.amg.apply, b, rtol=1e-8)[1])
+    assert max(its) - min(its) <= 3 and max(its) <= 20, its
+
+
+def test_fpcg_with_fixed_spd_preconditioner_is_pcg():
+    pr = Problem(lattice_hex_mesh(3, 0.2, 4), 3, 1.0, coarse_solver="exact")
+    b = pr.load(np.random.default_rng(10).standard_normal(pr.G))
+    h0 = pcg.pcg(pr.apply_A, pr.apply_P, b, 1e-10)[2]
+    h1 = pcg.fpcg(pr.apply_A, pr.apply_P, b, 1e-10)[2]
+    assert len(h0) == len(h1)
+    np.testing.assert_allclose(h1, h0, rtol=1e-6, atol=1e-13)
