@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--kcycle-variant", action="store_true",
                     help="coarse solver: the paper's K-cycle (unsmoothed aggregation, flexible PCG) against "
                          "the default three V-cycles on the 32^3 n=7 workload, FP64 and mixed")
+    ap.add_argument("--patch-variant", action="store_true",
+                    help="P^f patches: face layers only against the full (n+3)^3 box, 32^3 n=7, FP64 and mixed")
     ap.add_argument("--train-meshes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
@@ -710,6 +712,39 @@ def run_heat_variant(args):
         "orders": rows}))
 
 
+def run_patch_variant(args):
+    """P^f patches with face layers only (default) against the full (n+3)^3 box, headline workload."""
+    import numpy as np
+    import torch
+    from synth import lattice_hex_mesh, manufactured_s
+    from paper_1506_05996_gb300 import sem as S
+    mesh = lattice_hex_mesh(32, A_FULL, SEED_FULL)
+    out = {}
+    for patch in ("face", "full"):
+        prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True, patch=patch)
+        X = prob.dof_coords()
+        b = (prob.mass() * torch.as_tensor(manufactured_s(X.cpu().numpy(), LAM), device="cuda")).contiguous()
+        row = {}
+        for prec in ("fp64", "fp32"):
+            prob.set_precision(prec)
+            x = torch.empty_like(b)
+            for _ in range(max(1, args.warmup)):
+                S.sem_solve(prob.h, b, x, RTOL, 1000, want_history=False)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc, it, _, tr = S.sem_solve(prob.h, b, x, RTOL, 1000, want_history=False)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            row[prec] = {"iterations": it, "time_to_1e-8_s": float(np.median(ts)), "true_rel_res": tr}
+        out[patch] = row
+        prob.close()
+    print(json.dumps({"variant": "patch", "config": {"workload": WORKLOAD,
+                      "face": "box nodes with one index in {-1, n+1} (face layers), others absent",
+                      "full": "all (n+3)^3 box nodes (edge and corner layers filled)"}, **out}))
+
+
 def run_kcycle_variant(args):
     """P_0 as the paper's K-cycle against the default V-cycles, same workload as the headline."""
     import numpy as np
@@ -760,7 +795,9 @@ def run_kcycle_variant(args):
 
 def main():
     args = parse()
-    if args.kcycle_variant:
+    if args.patch_variant:
+        run_patch_variant(args)
+    elif args.kcycle_variant:
         run_kcycle_variant(args)
     elif args.heat_variant:
         run_heat_variant(args)

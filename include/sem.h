@@ -50,6 +50,8 @@ typedef struct sem_s sem_t;
 #define SEM_GEOM_RECOMPUTE  0x1  /* recompute them from the 8 vertices in the operator (Sec. 3.1) */
 #define SEM_NEUMANN         0x10 /* no Dirichlet nodes (default: Dirichlet on every boundary face) */
 #define SEM_MIXED           0x100 /* also keep the stored factors in FP32, for SEM_PREC_FP32 */
+#define SEM_PATCH_FULL      0x1000 /* P^f patches with the edge and corner layers too: all (n+3)^3
+                                      box nodes of Sec. 4.2 (default: face layers only) */
 
 /* arithmetic of the operator and the preconditioner (sem_set_precision) */
 #define SEM_PREC_FP64  0   /* everything in FP64 (default) */

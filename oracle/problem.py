@@ -12,7 +12,7 @@ from . import gll, numbering, geometry, operator, schwarz, coarse, amg, pcg
 
 
 class Problem:
-    def __init__(self, mesh, n, lam, dirichlet=True, coarse_solver="amg", with_schwarz=True):
+    def __init__(self, mesh, n, lam, dirichlet=True, coarse_solver="amg", with_schwarz=True, patch="face"):
         self.mesh = mesh
         self.n = n
         self.lam = float(lam)
@@ -31,6 +31,7 @@ class Problem:
         else:
             self.mask = np.zeros(self.G, dtype=np.uint8)
         self.coarse_solver = coarse_solver
+        self.patch = patch
         if with_schwarz:
             self._setup_schwarz()
         if coarse_solver is not None:
@@ -43,6 +44,8 @@ class Problem:
         self.ev, self.S = schwarz.pencil_eig(K, M)
         self.h = geometry.element_box_sizes(self.xyz_e)
         self.ip = schwarz.patch_table(self.l2g, self.nb_elem, self.nb_face)
+        if self.patch == "full":
+            self.ip = schwarz.fill_edges_corners(self.ip, self.l2g)
 
     # --- coarse scale -------------------------------------------------------
     def _setup_coarse(self):

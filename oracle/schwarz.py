@@ -14,11 +14,15 @@ Readings:
   * A patch node with exactly one index in {-1, n+1} is the face-neighbour's node one
     layer inside it, next to the shared face node; nodes with two or more indices
     outside 0..n, and layers beyond a boundary face, are absent (r = 0, z dropped).
+    With patch = "full" (fill_edges_corners) the edge and corner layers are filled too,
+    giving the (n+3)^3 nodes per subdomain that Sec. 4.2 counts.
   * h_x, h_y, h_z: mean length of the element's 4 edges along xi, eta, zeta.
   * No overlap weights: the corrections are summed.
 Pinned by: the pencil matrices equal the printed extended matrix pattern, the
 fast-diagonalisation solve equals a dense solve of the Kronecker-sum box matrix,
-S^T M S = I and K S = M S Lambda (scipy eigh), symmetry and positivity of P^f.
+S^T M S = I and K S = M S Lambda (scipy eigh), symmetry and positivity of P^f; on an
+unperturbed lattice the filled box nodes sit where the element's (affine) map, extended
+one GLL step beyond each face, puts them.
 """
 import numpy as np
 import scipy.linalg
@@ -85,6 +89,50 @@ def patch_table(l2g, nb_elem, nb_face):
         dst[ax] = 0 if sd == 0 else P - 1
         ip[(es,) + tuple(dst)] = inner
     return ip
+
+
+def fill_edges_corners(ip, l2g):
+    """Full-box patches: the box nodes with two or three indices in {-1, n+1} (edge and corner
+    layers), which `patch_table` leaves absent, taken from the GLL grid graph.
+
+    The graph joins the global nodes that are adjacent along a local axis of some element.
+    A box node with out-of-range axes S has, for each axis in S, a box neighbour one step
+    back inside along that axis; the node is the one common graph neighbour of those that is
+    not already in the element's box (edges first, then corners). Absent when a needed
+    neighbour is absent or the common neighbour is not unique.
+    """
+    E, p = l2g.shape[0], l2g.shape[1]
+    n = p - 1
+    P = n + 3
+    adj = {}
+    for ax in range(3):
+        a = np.moveaxis(l2g, ax + 1, 1)
+        for x, y in zip(a[:, :-1].ravel().tolist(), a[:, 1:].ravel().tolist()):
+            adj.setdefault(x, set()).add(y)
+            adj.setdefault(y, set()).add(x)
+    out = ip.copy()
+    rng = range(-1, n + 2)
+    out_of = lambda c: [d for d in range(3) if c[d] < 0 or c[d] > n]
+    for level in (2, 3):
+        for e in range(E):
+            box = set(out[e][out[e] >= 0].tolist())
+            for c in [(I, J, K) for K in rng for J in rng for I in rng]:
+                S = out_of(c)
+                if len(S) != level:
+                    continue
+                nbrs = []
+                for d in S:
+                    c2 = list(c)
+                    c2[d] = 0 if c[d] < 0 else n
+                    nbrs.append(int(out[e, c2[0] + 1, c2[1] + 1, c2[2] + 1]))
+                if min(nbrs) < 0:
+                    continue
+                cand = set.intersection(*[adj.get(g, set()) for g in nbrs]) - box
+                if len(cand) == 1:
+                    g = cand.pop()
+                    out[e, c[0] + 1, c[1] + 1, c[2] + 1] = g
+                    box.add(g)
+    return out
 
 
 def fast_diag_solve(rp, S, ev, h, lam):

@@ -211,7 +211,7 @@ int sem_create(const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2v
   if (n_vert < 8 || n_hex < 1) return fail(SEM_ERR_ARG, "empty mesh");
   if (order < 2 || order > 8) return fail(SEM_ERR_ARG, "order must be in 2..8");
   if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(SEM_ERR_ARG, "lambda must be finite and >= 0");
-  if (flags & ~(SEM_GEOM_RECOMPUTE | SEM_NEUMANN | SEM_MIXED)) return fail(SEM_ERR_ARG, "unknown flag");
+  if (flags & ~(SEM_GEOM_RECOMPUTE | SEM_NEUMANN | SEM_MIXED | SEM_PATCH_FULL)) return fail(SEM_ERR_ARG, "unknown flag");
   for (int64_t i = 0; i < 3 * n_vert; ++i)
     if (!std::isfinite(vert_xyz_host[i])) return fail(SEM_ERR_ARG, "non-finite vertex coordinate");
 
@@ -271,7 +271,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   std::vector<double> D = sem::derivative_matrix(n, t);
   std::vector<int> g2l_off, g2l_idx, owner;
   sem::gather_csr(nb, g2l_off, g2l_idx, owner);
-  std::vector<int> ip = sem::patch_table(nb);
+  std::vector<int> ip = sem::patch_table(nb, (flags & SEM_PATCH_FULL) != 0);
   std::vector<int> pg_off(nb.G + 1, 0), pg_idx;
   for (size_t q = 0; q < ip.size(); ++q)
     if (ip[q] >= 0) pg_off[ip[q] + 1]++;

@@ -315,7 +315,42 @@ void gather_csr(const Numbering& nb, std::vector<int>& off, std::vector<int>& id
   for (int64_t g = 0; g < nb.G; ++g) owner[g] = idx[off[g]];
 }
 
-std::vector<int> patch_table(const Numbering& nb) {
+namespace {
+
+// Global DOF at the virtual local coordinate c (entries in -1..n+1) of element e: the
+// element's own node when all entries are in 0..n; otherwise, for the first axis outside,
+// the point carried across that face into the neighbour, one layer inside it, and resolved
+// there (each step brings one axis inside, so at most three steps); -1 across a face
+// without a neighbour.
+int virtual_node(const Numbering& nb, int64_t e, const int c[3]) {
+  const int n = nb.n, p = nb.p;
+  for (int d1 = 0; d1 < 3; ++d1) {
+    if (c[d1] >= 0 && c[d1] <= n) continue;
+    const int s1 = c[d1] > n ? 1 : 0, f = 2 * d1 + s1;
+    const int e2 = nb.face_elem[6 * e + f];
+    if (e2 < 0) return -1;
+    const int f2 = nb.face_idx[6 * e + f];
+    int u1, v1, d2 = f2 / 2, s2 = f2 % 2, u2, v2;
+    face_axes(d1, u1, v1);
+    face_axes(d2, u2, v2);
+    int vid1[2][2], vid2[2][2];
+    face_vids(&nb.hexv[8 * e], d1, s1, vid1);
+    face_vids(&nb.hexv[8 * (int64_t)e2], d2, s2, vid2);
+    int cs, ct, a2, b2;
+    to_canonical(face_frame(vid1), n, c[u1], c[v1], cs, ct);   // affine, so valid outside 0..n too
+    from_canonical(face_frame(vid2), n, cs, ct, a2, b2);
+    int c2[3];
+    c2[d2] = s2 ? n - 1 : 1;
+    c2[u2] = a2;
+    c2[v2] = b2;
+    return virtual_node(nb, e2, c2);
+  }
+  return nb.l2g[e * p * p * p + c[0] + p * (c[1] + p * c[2])];
+}
+
+}  // namespace
+
+std::vector<int> patch_table(const Numbering& nb, bool full) {
   const int n = nb.n, p = nb.p, P = n + 3, P3 = P * P * P, p3 = p * p * p;
   const int64_t ne = nb.ne;
   std::vector<int> ip((size_t)ne * P3, -1);
@@ -349,6 +384,15 @@ std::vector<int> patch_table(const Numbering& nb) {
           ip[e * P3 + ext(c1[0], c1[1], c1[2])] = g;
         }
     }
+    if (!full) continue;
+    for (int K = -1; K <= n + 1; ++K)
+      for (int J = -1; J <= n + 1; ++J)
+        for (int I = -1; I <= n + 1; ++I) {
+          const int outside = (I < 0 || I > n) + (J < 0 || J > n) + (K < 0 || K > n);
+          if (outside < 2) continue;
+          const int c[3] = {I, J, K};
+          ip[e * P3 + ext(I, J, K)] = virtual_node(nb, e, c);
+        }
   }
   return ip;
 }

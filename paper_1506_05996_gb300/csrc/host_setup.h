@@ -47,8 +47,9 @@ void gather_csr(const Numbering& nb, std::vector<int>& off, std::vector<int>& id
                 std::vector<int>& owner);
 
 // Extended-box patch table (Sec. 4.2): ip[e][(I+1) + P((J+1) + P(K+1))] = global DOF of
-// box node (I, J, K), -1 <= I,J,K <= n+1, or -1 if absent.
-std::vector<int> patch_table(const Numbering& nb);
+// box node (I, J, K), -1 <= I,J,K <= n+1, or -1 if absent. Face layers only, or (full)
+// also the edge and corner layers: the (n+3)^3 nodes per subdomain that Sec. 4.2 counts.
+std::vector<int> patch_table(const Numbering& nb, bool full = false);
 
 // Extended 1D pencil (rows -1..n+1) stiffness K and diagonal mass M, and the
 // generalised eigenpairs K S = M S diag(ev), S^T M S = I; S[row*P + mode]. The first

@@ -22,7 +22,7 @@ SEM_OK = 0
 SEM_ERR_ARG, SEM_ERR_JACOBIAN, SEM_ERR_MESH, SEM_ERR_CUDA = -1, -2, -3, -4
 SEM_ERR_OOM, SEM_ERR_NAN, SEM_ERR_SINGULAR = -5, -6, -7
 SEM_MAXIT = 1
-SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED = 0x0, 0x1, 0x10, 0x100
+SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED, SEM_PATCH_FULL = 0x0, 0x1, 0x10, 0x100, 0x1000
 SEM_PREC_FP64, SEM_PREC_FP32 = 0, 1
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
@@ -338,8 +338,10 @@ class SemProblem:
     """Owns one handle; convenience wrappers returning torch tensors."""
 
     def __init__(self, mesh_xyz, hex2vert, order, lam, geom="stored", neumann=False, stream=None,
-                 device="cuda", mixed=False):
+                 device="cuda", mixed=False, patch="face"):
         flags = SEM_GEOM_RECOMPUTE if geom == "recompute" else SEM_GEOM_STORED
+        if patch == "full":
+            flags |= SEM_PATCH_FULL
         if neumann:
             flags |= SEM_NEUMANN
         if mixed:

@@ -18,13 +18,13 @@ sem::Csr g_A0;
 extern "C" {
 
 int hh_setup(const double* xyz, int64_t nv, const int64_t* hex, int64_t ne, int n, double lam, int neumann,
-             int amg_kind) {
+             int amg_kind, int patch_full) {
   std::string err = sem::number_mesh(xyz, nv, hex, ne, n, g_nb);
   if (!err.empty()) return -1;
   sem::gll(n, g_t, g_rho);
   g_D = sem::derivative_matrix(n, g_t);
   sem::gather_csr(g_nb, g_off, g_idx, g_owner);
-  g_ip = sem::patch_table(g_nb);
+  g_ip = sem::patch_table(g_nb, patch_full != 0);
   sem::pencil_tables(n, g_t, g_rho, g_D, g_S, g_ev);
   g_hbox = sem::box_sizes(g_nb, xyz);
   g_coords = sem::dof_coords(g_nb, xyz, g_t, g_owner);

@@ -24,13 +24,13 @@ def load():
 
 
 class HostTables:
-    def __init__(self, lib, mesh, n, lam, neumann=False, amg_kind=0):
+    def __init__(self, lib, mesh, n, lam, neumann=False, amg_kind=0, patch="face"):
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         hexes = np.ascontiguousarray(mesh.hex2vert, dtype=np.int64)
         rc = lib.hh_setup(xyz.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(xyz.shape[0]),
                           hexes.ctypes.data_as(ctypes.c_void_p), ctypes.c_int64(hexes.shape[0]),
                           ctypes.c_int(n), ctypes.c_double(lam), ctypes.c_int(int(neumann)),
-                          ctypes.c_int(int(amg_kind)))
+                          ctypes.c_int(int(amg_kind)), ctypes.c_int(int(patch == "full")))
         self.rc = rc
         if rc != 0:
             return

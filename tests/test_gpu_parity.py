@@ -157,3 +157,27 @@ def test_operator_parity_at_full_size():
     assert torch.equal(rec.dof_coords(), coords)      # same numbering in both variants
     y = rec.apply_A(xg).cpu().numpy()[P.perm]
     assert rel_err(y, y_ref) <= TOL
+
+
+@pytest.mark.parametrize("E,n,lam,seed", [(3, 3, 0.5, 21), (2, 6, 1.0, 22)])
+def test_full_patch_parity(E, n, lam, seed):
+    """P^f with the edge and corner layers filled (SEM_PATCH_FULL) against the oracle."""
+    from gpu_util import rel_err
+    from oracle.problem import Problem
+    from paper_1506_05996_gb300.sem import SemProblem
+    mesh = lattice_hex_mesh(E, 0.2, seed)
+    gpu = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, patch="full")
+    ref = Problem(mesh, n, lam, patch="full")
+    X = gpu.dof_coords().cpu().numpy()
+    oi, gi = np.lexsort(np.round(ref.coords, 9).T), np.lexsort(np.round(X, 9).T)
+    perm = np.empty_like(gi)
+    perm[oi] = gi
+    r = np.random.default_rng(seed).standard_normal(ref.G) * (ref.mask == 0)
+    rg = torch.zeros(gpu.n_dof, dtype=torch.float64, device="cuda")
+    rg[torch.as_tensor(perm, device="cuda")] = torch.as_tensor(r, device="cuda")
+    assert rel_err(gpu.apply_P(rg, "fine").cpu().numpy()[perm], ref.apply_Pf(r)) <= TOL
+    b = ref.load(manufactured_s(ref.coords, lam))
+    bg = torch.zeros_like(rg)
+    bg[torch.as_tensor(perm, device="cuda")] = torch.as_tensor(b, device="cuda")
+    assert gpu.solve(bg)[2] == ref.solve(b)[1]
+    gpu.close()

@@ -28,13 +28,14 @@ def match(ref_xyz, lib_xyz):
     return perm
 
 
-@pytest.mark.parametrize("E,n,a,seed", [(1, 3, 0.1, 0), (3, 3, 0.2, 1), (2, 5, 0.15, 2), (4, 2, 0.2, 3),
-                                        (2, 2, 0.1, 4), (3, 8, 0.2, 5)])
-def test_numbering_patch_and_tables(lib, E, n, a, seed):
+@pytest.mark.parametrize("E,n,a,seed,patch", [(1, 3, 0.1, 0, "face"), (3, 3, 0.2, 1, "face"), (2, 5, 0.15, 2, "face"),
+                                              (4, 2, 0.2, 3, "face"), (2, 2, 0.1, 4, "face"), (3, 8, 0.2, 5, "face"),
+                                              (3, 3, 0.2, 1, "full"), (4, 2, 0.2, 3, "full"), (3, 5, 0.1, 6, "full")])
+def test_numbering_patch_and_tables(lib, E, n, a, seed, patch):
     mesh = lattice_hex_mesh(E, a, seed)
-    H = HostTables(lib, mesh, n, 0.3)
+    H = HostTables(lib, mesh, n, 0.3, patch=patch)
     assert H.rc == 0
-    ref = Problem(mesh, n, 0.3, coarse_solver=None)
+    ref = Problem(mesh, n, 0.3, coarse_solver=None, patch=patch)
     assert H.G == ref.G
     perm = match(ref.coords, H.coords)          # oracle dof -> lib dof
     inv = np.empty_like(perm)

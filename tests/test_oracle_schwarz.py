@@ -102,3 +102,23 @@ def test_fine_preconditioner_symmetric_positive():
     Px, Py = pr.apply_Pf(x), pr.apply_Pf(y)
     assert abs(y @ Px - x @ Py) < 1e-12 * abs(y @ Px)
     assert x @ Px > 0
+
+
+def test_full_box_nodes_extend_the_element_map_on_a_lattice():
+    """On an unperturbed (affine) lattice, rotated and renumbered, every filled box node of the
+    full patch lies at the element's map evaluated one GLL step beyond the faces."""
+    from oracle.problem import Problem
+    from oracle.numbering import trilinear_points
+    from synth import lattice_hex_mesh
+    E, n = 4, 3
+    pr = Problem(lattice_hex_mesh(E, 0.0, 7), n, 1.0, coarse_solver=None, patch="full")
+    t = pr.t
+    ext = np.concatenate([[t[0] - (t[1] - t[0])], t, [t[-1] + (t[-1] - t[-2])]])
+    X = trilinear_points(pr.xyz_e, ext)                 # [E, P, P, P, 3]
+    present = pr.ip >= 0
+    np.testing.assert_allclose(pr.coords[pr.ip[present]], X[present], atol=1e-12)
+    # interior elements have every box node; boundary elements miss only the outside layers
+    inside = np.all((X > -1e-12) & (X < 1 + 1e-12), axis=-1)
+    np.testing.assert_array_equal(present, inside)
+    face = Problem(lattice_hex_mesh(E, 0.0, 7), n, 1.0, coarse_solver=None)
+    assert (face.ip >= 0).sum() < present.sum()
