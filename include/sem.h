@@ -65,6 +65,11 @@ typedef struct sem_s sem_t;
 #define SEM_COARSE_KCYCLE  1  /* the paper's (Sec. 4.1): unsmoothed aggregation, one recursive K-cycle
                                  with damped Jacobi; nonlinear, so sem_solve switches to flexible PCG */
 
+/* how sem_solve and sem_solve_many drive the iterations (sem_set_loop) */
+#define SEM_LOOP_HOST    0  /* one graph replay per iteration, the host reads the state in between */
+#define SEM_LOOP_DEVICE  1  /* the whole solve is one graph (a device-evaluated while loop); with
+                               sem_solve_many all solves are one graph launch (default) */
+
 /* preconditioner choice for sem_solve (sem_set_precond) */
 #define SEM_PRECOND_TWO_SCALE 0  /* P = P^c + P^f (Sec. 4) */
 #define SEM_PRECOND_FINE      1  /* P = P^f only (Table 1, fine-scale rows) */
@@ -138,6 +143,14 @@ int sem_set_precision(sem_t* h, int precision);
 
 /* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
 int sem_set_precond(sem_t* h, int which);
+
+/* sem_set_loop - SEM_LOOP_DEVICE (default) or SEM_LOOP_HOST. Both run the same kernels in the
+ * same order, so results are bit-identical. With the device loop a solve is captured once
+ * per configuration (precision, preconditioner, coarse solver, tiles, network, rtol, maxit)
+ * as a graph whose while node runs one iteration per round until the device state says
+ * done (never more than maxit + 2 rounds); with profiling on (sem_profile) the host loop
+ * is used. Errors: SEM_ERR_ARG. */
+int sem_set_loop(sem_t* h, int mode);
 
 /* sem_set_coarse_solver - choose P_0 (SEM_COARSE_*); rebuilds the AMG hierarchy on the host
  * (Sec. 4.1). With SEM_COARSE_KCYCLE each coarse level above the dense one takes two

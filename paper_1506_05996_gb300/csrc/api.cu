@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,30 @@ int fail(int code, const std::string& msg) {
 
 }  // namespace
 
+namespace {
+
+// The last batch graph of sem_solve_many (all its solves in one launch), kept while the
+// same handles, in the same configuration, are solved again.
+struct BatchGraph {
+  std::vector<sem_t*> handles;
+  std::vector<uint64_t> epochs;
+  std::vector<long> keys;
+  double rtol = -1.0;
+  int maxit = -1;
+  cudaGraphExec_t exec = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    handles.clear();
+    epochs.clear();
+    keys.clear();
+  }
+};
+std::mutex g_batch_mutex;
+BatchGraph g_batch;
+
+}  // namespace
+
 #define PROF_ON(h, strm, name, call)                 \
   do {                                                \
     int pi_ = (h)->prof.begin(strm);                  \
@@ -42,7 +67,7 @@ namespace {
 // the mask changes.
 int build_coarse(sem_t* h) {
   cudaStreamSynchronize(h->stream);
-  h->graph.reset();
+  h->invalidate();
   h->free_list(h->coarse_allocs);
   h->levels.clear();
   sem::DevProblem& d = h->d;
@@ -385,12 +410,16 @@ extern "C" {
 
 void sem_destroy(sem_t* h) {
   if (h == nullptr) return;
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    if (std::find(g_batch.handles.begin(), g_batch.handles.end(), h) != g_batch.handles.end()) g_batch.reset();
+  }
   cudaStreamSynchronize(h->stream);
   if (h->coarse_stream) {
     cudaStreamSynchronize(h->coarse_stream);
     cudaStreamDestroy(h->coarse_stream);
   }
-  h->graph.reset();
+  h->invalidate();
   if (h->capture_stream) {
     cudaStreamSynchronize(h->capture_stream);
     cudaStreamDestroy(h->capture_stream);
@@ -535,6 +564,13 @@ int sem_set_precision(sem_t* h, int precision) {
   return SEM_OK;
 }
 
+int sem_set_loop(sem_t* h, int mode) {
+  if (int rc = check_handle(h)) return rc;
+  if (mode != SEM_LOOP_HOST && mode != SEM_LOOP_DEVICE) return fail(SEM_ERR_ARG, "unknown loop mode");
+  h->loop_mode = mode;
+  return SEM_OK;
+}
+
 int sem_set_coarse_solver(sem_t* h, int kind) {
   if (int rc = check_handle(h)) return rc;
   if (kind != SEM_COARSE_VCYCLE && kind != SEM_COARSE_KCYCLE) return fail(SEM_ERR_ARG, "unknown coarse solver");
@@ -566,10 +602,9 @@ struct SolveCtx {
   int rc = SEM_OK;
 };
 
-int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
-  sem::DevProblem& d = h->d;
+int ensure_hist(sem_t* h, int maxit) {
   if (maxit + 1 > h->hist_cap) {
-    h->graph.reset();
+    h->invalidate();
     if (h->hist) cudaFree(h->hist);
     h->hist = nullptr;
     h->hist_cap = 0;
@@ -577,43 +612,69 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
     CK(cudaMalloc((void**)&h->hist, sizeof(double) * cap));
     h->hist_cap = cap;
   }
+  return SEM_OK;
+}
+
+// The steps of Algorithm 1 as enqueue functions; work goes to h->stream (switched to the
+// capture stream while capturing).
+// Operator, alpha and update of one iteration, with the stop test on the device.
+int enqueue_head(sem_t* h) {
+  sem::DevProblem& d = h->d;
+  cudaStream_t q = h->stream;
+  if (d.fp32)
+    PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, q));
+  else
+    PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, q));
+  PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, q));
+  PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, h->u, h->r, h->hist, q));
+  return SEM_OK;
+}
+
+// Preconditioner and new direction, then the next iteration's head.
+int enqueue_tail_head(sem_t* h) {
+  if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
+  PROF(h, "pcg_direction", sem::launch_pcg_direction(h->d, h->z, h->p, h->stream));
+  return enqueue_head(h);
+}
+
+// Initial residual, preconditioner, first direction and the first head.
+int enqueue_start(sem_t* h, const double* b, double rtol, int maxit) {
+  sem::DevProblem& d = h->d;
   cudaStream_t s = h->stream;
-  double* u = h->u;
-  const int mixed = d.fp32 ? 1 : 0;
-
-  // operator, alpha and update of one iteration (Algorithm 1), then the stop test on the host;
-  // work goes to h->stream (switched to the capture stream while capturing)
-  auto enqueue_head = [&]() -> int {
-    cudaStream_t q = h->stream;
-    if (d.fp32)
-      PROF(h, "ax_local", sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), d.st, q));
-    else
-      PROF(h, "ax_local", sem::launch_ax_local(d, h->p, d.wl, d.st, q));
-    PROF(h, "pcg_gather_alpha", sem::launch_pcg_gather_alpha(d, h->p, h->f, q));
-    PROF(h, "pcg_update", sem::launch_pcg_update(d, h->p, h->f, u, h->r, h->hist, q));
-    return SEM_OK;
-  };
-  // preconditioner and new direction, then the next iteration's head
-  auto enqueue_tail_head = [&]() -> int {
-    if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
-    PROF(h, "pcg_direction", sem::launch_pcg_direction(d, h->z, h->p, h->stream));
-    return enqueue_head();
-  };
-
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
+  const int mixed = d.fp32 ? 1 : 0;
   const int learned = h->net != nullptr ? 1 : 0;
   const int flexible = (learned || (d.amg_kind == SEM_COARSE_KCYCLE && h->precond == SEM_PRECOND_TWO_SCALE)) ? 1 : 0;
   if (learned) CK(cudaMemsetAsync(d.st_nn, 0, sizeof(sem::PcgState), s));
-  PROF(h, "pcg_init", sem::launch_pcg_init(d, c.b, h->r, u, rtol, maxit, mixed, learned, flexible, h->nn_window,
+  PROF(h, "pcg_init", sem::launch_pcg_init(d, b, h->r, h->u, rtol, maxit, mixed, learned, flexible, h->nn_window,
                                            h->nn_ratio, h->nn_theta, h->hist, s));
   if (int rc = apply_precond(h, h->precond, h->r, h->z, true)) return rc;
   PROF(h, "pcg_direction", sem::launch_pcg_first_direction(d, h->z, h->p, s));
-  if (int rc = enqueue_head()) return rc;
+  return enqueue_head(h);
+}
+
+// Mixed path: the recursive residual replaced by b - A u with the FP64 operator.
+int enqueue_replacement(sem_t* h, const double* b) {
+  sem::DevProblem& d = h->d;
+  PROF(h, "ax_local_fp64", sem::launch_ax_local(d, h->u, d.wl, d.st, h->stream));
+  PROF(h, "pcg_replace", sem::launch_pcg_replace(d, b, d.wl, h->r, h->hist, h->stream));
+  return SEM_OK;
+}
+
+// Configuration bits the captured graphs depend on.
+long graph_key(const sem_t* h) {
+  const sem::DevProblem& d = h->d;
+  return (long)(d.fp32 ? 1 : 0) | ((long)h->precond << 1) | ((long)h->prof.on << 3) | ((long)d.epb_ax << 4) |
+         ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13);
+}
+
+int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
+  if (int rc = ensure_hist(h, maxit)) return rc;
+  cudaStream_t s = h->stream;
+  if (int rc = enqueue_start(h, c.b, rtol, maxit)) return rc;
 
   // capture the steady-state iteration once per configuration
-  const long key = (long)mixed | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
-                   ((long)d.epb_ax << 4) | ((long)d.epb_sw << 8) | ((long)learned << 12) |
-                   ((long)d.amg_kind << 13);
+  const long key = graph_key(h);
   if (h->graph.key != key) {
     h->graph.reset();
     CK(cudaStreamSynchronize(s));
@@ -622,7 +683,7 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
     cudaGraph_t g = nullptr;
     h->stream = h->capture_stream;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
-    int rc = (e == cudaSuccess) ? enqueue_tail_head() : SEM_OK;
+    int rc = (e == cudaSuccess) ? enqueue_tail_head(h) : SEM_OK;
     cudaError_t e2 = (e == cudaSuccess) ? cudaStreamEndCapture(h->stream, &g) : cudaSuccess;
     h->stream = s;
     h->prof.cap = nullptr;
@@ -661,9 +722,7 @@ int solve_advance(sem_t* h, SolveCtx& c) {
   c.graph_pending = false;
   if (h->st_host->done) { c.done = true; return SEM_OK; }
   if (d.fp32 && h->st_host->replace) {
-    // the recursive residual is replaced by b - A u with the FP64 operator
-    PROF(h, "ax_local_fp64", sem::launch_ax_local(d, h->u, d.wl, d.st, s));
-    PROF(h, "pcg_replace", sem::launch_pcg_replace(d, c.b, d.wl, h->r, h->hist, s));
+    if (int rc = enqueue_replacement(h, c.b)) return rc;
     CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->st_host->done) { c.done = true; return SEM_OK; }
@@ -693,6 +752,148 @@ int solve_finish(sem_t* h, SolveCtx& c, int* iters_host, double* res_hist_host, 
   if (st.status == -6) return fail(SEM_ERR_NAN, "NaN/Inf or non-positive curvature in PCG");
   if (!st.done) return fail(SEM_MAXIT, "maxit reached");
   return st.status == 1 ? SEM_MAXIT : SEM_OK;
+}
+
+// ---- device-driven solve loop --------------------------------------------------------
+// Captures fn's work (h->stream switched to the capture stream; the coarse stream joins
+// through its events) into graph g after the nodes deps; sinks receives the capture's last
+// nodes, for the next node to depend on.
+template <class F>
+int capture_into(sem_t* h, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, F fn,
+                 std::vector<cudaGraphNode_t>& sinks) {
+  cudaStream_t saved = h->stream;
+  h->stream = h->capture_stream;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->stream, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                                deps.size(), cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    h->stream = saved;
+    return fail(SEM_ERR_CUDA, std::string("cudaStreamBeginCaptureToGraph: ") + cudaGetErrorString(e));
+  }
+  const int rc = fn();
+  cudaStreamCaptureStatus status;
+  const cudaGraphNode_t* dl = nullptr;
+  size_t nd = 0;
+  const cudaError_t e1 = cudaStreamGetCaptureInfo(h->stream, &status, nullptr, nullptr, &dl, nullptr, &nd);
+  if (e1 == cudaSuccess && dl != nullptr) sinks.assign(dl, dl + nd);
+  else sinks.clear();
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(h->stream, &out);
+  h->stream = saved;
+  if (rc != SEM_OK) return rc;
+  if (e1 != cudaSuccess || e2 != cudaSuccess)
+    return fail(SEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+  return SEM_OK;
+}
+
+int add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle hc,
+                    cudaGraphConditionalNodeType type, cudaGraphNode_t& node, cudaGraph_t& body) {
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hc;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  CK(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &prm));
+  body = prm.conditional.phGraph_out[0];
+  return SEM_OK;
+}
+
+// Appends one whole solve of handle h into graph g, independent of the graph's other
+// nodes: the initial steps and the first head, then WHILE (not done, at most maxit + 2
+// rounds) { preconditioner, direction, head }. The mixed path adds, after each head, an
+// IF node with the FP64 residual replacement. The right-hand side is read from h->bbuf.
+int build_loop(sem_t* h, cudaGraph_t g, double rtol, int maxit) {
+  sem::DevProblem& d = h->d;
+  const bool mixed = d.fp32;
+  const int limit = maxit + 2;
+  std::vector<cudaGraphNode_t> deps, tmp;
+  cudaGraphConditionalHandle hw;
+  CK(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
+  auto set_loop = [&]() -> int {
+    CK(sem::launch_loop_cond(d.st, h->loop_guard, limit, hw, h->stream));
+    return SEM_OK;
+  };
+  // IF (replacement requested) { FP64 residual replacement } inside graph gg after deps
+  auto add_replacement = [&](cudaGraph_t gg, std::vector<cudaGraphNode_t>& dd) -> int {
+    cudaGraphConditionalHandle hi;
+    CK(cudaGraphConditionalHandleCreate(&hi, gg, 0, 0));
+    if (int rc = capture_into(h, gg, dd, [&]() -> int {
+          CK(sem::launch_replace_cond(d.st, hi, h->stream));
+          return SEM_OK;
+        }, dd)) return rc;
+    cudaGraphNode_t node;
+    cudaGraph_t body;
+    if (int rc = add_conditional(gg, dd, hi, cudaGraphCondTypeIf, node, body)) return rc;
+    if (int rc = capture_into(h, body, {}, [&]() { return enqueue_replacement(h, h->bbuf); }, tmp)) return rc;
+    dd.assign(1, node);
+    return SEM_OK;
+  };
+  if (int rc = capture_into(h, g, {}, [&]() -> int {
+        CK(cudaMemsetAsync(h->loop_guard, 0, sizeof(int), h->stream));
+        return enqueue_start(h, h->bbuf, rtol, maxit);
+      }, deps)) return rc;
+  if (mixed)
+    if (int rc = add_replacement(g, deps)) return rc;
+  if (int rc = capture_into(h, g, deps, set_loop, deps)) return rc;
+  cudaGraphNode_t wnode;
+  cudaGraph_t wbody;
+  if (int rc = add_conditional(g, deps, hw, cudaGraphCondTypeWhile, wnode, wbody)) return rc;
+  std::vector<cudaGraphNode_t> bd;
+  if (int rc = capture_into(h, wbody, {}, [&]() { return enqueue_tail_head(h); }, bd)) return rc;
+  if (mixed)
+    if (int rc = add_replacement(wbody, bd)) return rc;
+  return capture_into(h, wbody, bd, set_loop, bd);
+}
+
+int ensure_loop_buffers(sem_t* h) {
+  if (h->bbuf == nullptr) CK(h->alloc(&h->bbuf, (size_t)h->nb.G, h->allocs));
+  if (h->loop_guard == nullptr) CK(h->alloc(&h->loop_guard, 1, h->allocs));
+  return SEM_OK;
+}
+
+int instantiate(cudaGraph_t g, cudaGraphExec_t& exec) {
+  cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) {
+    exec = nullptr;
+    return fail(SEM_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  return SEM_OK;
+}
+
+// One solve as one graph launch (no host round trip per iteration).
+int solve_device_loop(sem_t* h, const double* b, double* x, double rtol, int maxit, int* iters_host,
+                      double* res_hist_host, double* true_rel_res_host) {
+  if (int rc = ensure_hist(h, maxit)) return rc;
+  if (int rc = ensure_loop_buffers(h)) return rc;
+  const long key = graph_key(h);
+  if (h->loop.key != key || h->loop.rtol != rtol || h->loop.maxit != maxit) {
+    h->loop.reset();
+    CK(cudaStreamSynchronize(h->stream));
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    int rc = build_loop(h, g, rtol, maxit);
+    if (rc == SEM_OK) rc = instantiate(g, h->loop.exec);
+    cudaGraphDestroy(g);
+    if (rc != SEM_OK) return rc;
+    h->loop.key = key;
+    h->loop.rtol = rtol;
+    h->loop.maxit = maxit;
+  }
+  CK(cudaMemcpyAsync(h->bbuf, b, sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaGraphLaunch(h->loop.exec, h->stream));
+  SolveCtx c;
+  c.b = b;
+  c.x = x;
+  return solve_finish(h, c, iters_host, res_hist_host, true_rel_res_host);
+}
+
+bool batch_matches(int count, sem_t* const* hs, double rtol, int maxit) {
+  if (g_batch.exec == nullptr || (int)g_batch.handles.size() != count || g_batch.rtol != rtol ||
+      g_batch.maxit != maxit)
+    return false;
+  for (int i = 0; i < count; ++i)
+    if (g_batch.handles[i] != hs[i] || g_batch.epochs[i] != hs[i]->epoch || g_batch.keys[i] != graph_key(hs[i]))
+      return false;
+  return true;
 }
 
 // Time `reps` launches of fn on the handle's stream with events (milliseconds per launch).
@@ -729,6 +930,8 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   if (int rc = check_handle(h)) return rc;
   if (b_dev == nullptr || x_dev == nullptr || b_dev == x_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
   if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  if (h->loop_mode == SEM_LOOP_DEVICE && !h->prof.on)
+    return solve_device_loop(h, b_dev, x_dev, rtol, maxit, iters_host, res_hist_host, true_rel_res_host);
   SolveCtx c;
   c.b = b_dev;
   c.x = x_dev;
@@ -797,6 +1000,56 @@ int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev,
       if (handles[j] == handles[i]) return fail(SEM_ERR_ARG, "a handle appears twice");
   }
   std::vector<SolveCtx> ctx(count);
+  bool device = count > 0;
+  for (int i = 0; i < count; ++i) device = device && handles[i]->loop_mode == SEM_LOOP_DEVICE && !handles[i]->prof.on;
+  if (device) {
+    // every solve appended to one graph and launched once
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (int i = 0; i < count; ++i) {
+      if (int rc = ensure_hist(handles[i], maxit)) return rc;
+      if (int rc = ensure_loop_buffers(handles[i])) return rc;
+    }
+    if (!batch_matches(count, handles, rtol, maxit)) {
+      g_batch.reset();
+      cudaGraph_t g;
+      CK(cudaGraphCreate(&g, 0));
+      int rc = SEM_OK;
+      for (int i = 0; i < count && rc == SEM_OK; ++i) {
+        cudaStreamSynchronize(handles[i]->stream);
+        rc = build_loop(handles[i], g, rtol, maxit);
+      }
+      if (rc == SEM_OK) rc = instantiate(g, g_batch.exec);
+      cudaGraphDestroy(g);
+      if (rc != SEM_OK) return rc;
+      for (int i = 0; i < count; ++i) {
+        g_batch.handles.push_back(handles[i]);
+        g_batch.epochs.push_back(handles[i]->epoch);
+        g_batch.keys.push_back(graph_key(handles[i]));
+      }
+      g_batch.rtol = rtol;
+      g_batch.maxit = maxit;
+    }
+    cudaStream_t s0 = handles[0]->stream;
+    for (int i = 0; i < count; ++i) {
+      sem_t* h = handles[i];
+      if (h->stream != s0) CK(cudaStreamSynchronize(h->stream));   // the caller's work on b
+      CK(cudaMemcpyAsync(h->bbuf, b_dev[i], sizeof(double) * h->nb.G, cudaMemcpyDeviceToDevice, s0));
+    }
+    CK(cudaGraphLaunch(g_batch.exec, s0));
+    CK(cudaStreamSynchronize(s0));
+    int worst = SEM_OK;
+    for (int i = 0; i < count; ++i) {
+      ctx[i].b = b_dev[i];
+      ctx[i].x = x_dev[i];
+      int it = 0;
+      const int rc = solve_finish(handles[i], ctx[i], &it, nullptr, nullptr);
+      if (iters_host) iters_host[i] = it;
+      if (status_host) status_host[i] = rc;
+      if (rc < 0) worst = rc;
+      else if (rc > 0 && worst == SEM_OK) worst = rc;
+    }
+    return worst;
+  }
   for (int i = 0; i < count; ++i) {
     ctx[i].b = b_dev[i];
     ctx[i].x = x_dev[i];
@@ -833,7 +1086,7 @@ int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw) {
     return fail(SEM_ERR_ARG, "no kernel with that many elements per CTA for this order");
   h->d.epb_ax = epb_ax;
   h->d.epb_sw = epb_sw;
-  h->graph.reset();
+  h->invalidate();
   return SEM_OK;
 }
 
@@ -865,7 +1118,7 @@ int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host) {
   }
   d.epb_ax = best_ax;
   d.epb_sw = best_sw;
-  h->graph.reset();
+  h->invalidate();
   if (epb_ax_host) *epb_ax_host = best_ax;
   if (epb_sw_host) *epb_sw_host = best_sw;
   return SEM_OK;

@@ -203,6 +203,11 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
 // y = a + b
 cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const double* b, double* y, cudaStream_t s);
 
+// --- device-driven solve loop (graph conditional nodes) ----------------------------
+// WHILE condition: !st->done and ++*guard <= limit; IF condition: st->replace && !st->done
+cudaError_t launch_loop_cond(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_replace_cond(const PcgState* st, cudaGraphConditionalHandle h, cudaStream_t s);
+
 // aux = ||b - f||^2 over free nodes
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s);
 

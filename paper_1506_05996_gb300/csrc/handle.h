@@ -34,6 +34,24 @@ struct IterGraph {
   ~IterGraph() { reset(); }
 };
 
+// A whole solve as one graph (device-driven loop): the initial steps, then a WHILE node
+// around one iteration (with an IF node for the mixed path's residual replacement), so a
+// solve is one graph launch with no host round trip per iteration.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  long key = -1;
+  double rtol = -1.0;
+  int maxit = -1;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key = -1;
+    rtol = -1.0;
+    maxit = -1;
+  }
+  ~LoopGraph() { reset(); }
+};
+
 constexpr int kGraphBase = 1 << 28;
 
 // Per-kernel timing with CUDA events recorded on the handle's stream around each
@@ -159,6 +177,16 @@ struct sem_s {
   uint8_t* mask = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
   IterGraph graph;
+  LoopGraph loop;
+  int loop_mode = SEM_LOOP_DEVICE;
+  uint64_t epoch = 0;               // bumped whenever captured graphs become stale
+  double* bbuf = nullptr;           // right-hand side copied in before a device-driven solve
+  int* loop_guard = nullptr;        // iteration guard of the device-driven loop
+  void invalidate() {
+    graph.reset();
+    loop.reset();
+    ++epoch;
+  }
   double* hist = nullptr;
   int hist_cap = 0;
   sem::PcgState* st_host = nullptr;  // pinned

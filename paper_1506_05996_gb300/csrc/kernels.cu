@@ -596,6 +596,21 @@ __global__ void add_vectors_kernel(int n, const double* __restrict__ a, const do
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = a[i] + b[i];
 }
 
+// Device-driven solve loop (a CUDA graph WHILE node around one iteration): the loop runs
+// while the solve is not done, and never more than `limit` times (an independent guard,
+// so the graph ends whatever the solver state). One thread sets the condition.
+__global__ void loop_cond_kernel(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int g = ++*guard;
+    cudaGraphSetConditional(h, (st->done == 0 && g <= limit) ? 1u : 0u);
+  }
+}
+
+// The IF node of the mixed path: run the FP64 residual replacement when the update asked.
+__global__ void replace_cond_kernel(const PcgState* st, cudaGraphConditionalHandle h) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, (st->replace != 0 && st->done == 0) ? 1u : 0u);
+}
+
 // Training pair: delta = mask ? 0 : x_star - x_k - z0 (the error left after z0 = P r).
 __global__ void pair_delta_kernel(const DevProblem d, const double* __restrict__ xs, const double* __restrict__ xk,
                                   const double* __restrict__ z0, double* __restrict__ delta) {
@@ -876,6 +891,19 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
 
 cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const double* b, double* y, cudaStream_t s) {
   add_vectors_kernel<<<d.nblk, kVecBlock, 0, s>>>(d.G, a, b, y);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_loop_cond(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h, cudaStream_t s) {
+  loop_cond_kernel<<<1, 32, 0, s>>>(st, guard, limit, h);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replace_cond(const PcgState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  replace_cond_kernel<<<1, 32, 0, s>>>(st, h);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -84,7 +84,7 @@ namespace sem {
 
 int learned_attach(sem_t* h, sem_net_t* net) {
   h->net = net;
-  h->graph.reset();
+  h->invalidate();
   if (net == nullptr) return SEM_OK;
   const int p3 = h->d.p * h->d.p * h->d.p;
   if (int rc = ensure_work(h->nnws, h->nn_allocs, h->d.ne, p3, false)) return rc;

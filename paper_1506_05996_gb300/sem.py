@@ -27,6 +27,7 @@ SEM_PREC_FP64, SEM_PREC_FP32 = 0, 1
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
 SEM_COARSE_VCYCLE, SEM_COARSE_KCYCLE = 0, 1
+SEM_LOOP_HOST, SEM_LOOP_DEVICE = 0, 1
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 _P = ctypes.POINTER
@@ -47,6 +48,7 @@ _SIGS = {
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
     "sem_set_precond": ([_vp, _int], _int),
     "sem_set_coarse_solver": ([_vp, _int], _int),
+    "sem_set_loop": ([_vp, _int], _int),
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
@@ -180,6 +182,10 @@ def sem_set_precond(h, which):
 
 def sem_set_coarse_solver(h, kind):
     return _check(_lib.sem_set_coarse_solver(h, {"vcycle": SEM_COARSE_VCYCLE, "kcycle": SEM_COARSE_KCYCLE}.get(kind, kind)))
+
+
+def sem_set_loop(h, mode):
+    return _check(_lib.sem_set_loop(h, {"host": SEM_LOOP_HOST, "device": SEM_LOOP_DEVICE}.get(mode, mode)))
 
 
 def sem_set_precision(h, precision):
