@@ -152,6 +152,13 @@ int sem_set_precond(sem_t* h, int which);
  * is used. Errors: SEM_ERR_ARG. */
 int sem_set_loop(sem_t* h, int mode);
 
+/* sem_set_overlap - in the FP32 path the coarse branch (a chain of small AMG kernels) runs
+ * beside the patch solves of P^f; those CTAs are then capped to fill all but reserve_sms SMs
+ * (their kernel loops over the elements), so the coarse kernels find free slots instead of
+ * queueing behind them. 0 = no cap. Default 32 of the GPU's SMs. Results do not depend on
+ * it. Errors: SEM_ERR_ARG. */
+int sem_set_overlap(sem_t* h, int reserve_sms);
+
 /* sem_set_coarse_solver - choose P_0 (SEM_COARSE_*); rebuilds the AMG hierarchy on the host
  * (Sec. 4.1). With SEM_COARSE_KCYCLE each coarse level above the dense one takes two
  * flexible-CG steps preconditioned by the K-cycle below it, combined as the A-orthogonal

@@ -169,24 +169,34 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   if (coarse) {
     if (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty()))
       return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
-    // fork: restriction and AMG on the coarse stream
+    // fork: AMG on the coarse stream, beside the patch solves. In FP64 the patch solves are
+    // long enough to hide the restriction too, so it goes on the coarse stream; in FP32 the
+    // restriction, slowed by sharing the SMs with them, would lengthen the critical path,
+    // so it runs first, alone on the GPU, and only the latency-bound AMG kernels overlap.
     cudaStream_t cs = h->coarse_stream;
+    const bool restrict_first = d.fp32;
+    if (restrict_first) {
+      if (pcg)
+        PROF(h, "coarse_restrict", sem::launch_coarse_restrict_f32(d, d.r32, st, h->stream));
+      else
+        PROF(h, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, h->stream));
+    }
     CK(cudaEventRecord(h->ev_fork, h->stream));
     CK(cudaStreamWaitEvent(cs, h->ev_fork, 0));
-    if (d.fp32 && pcg)
-      PROF_ON(h, cs, "coarse_restrict", sem::launch_coarse_restrict_f32(d, d.r32, st, cs));
-    else
-      PROF_ON(h, cs, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, cs));
+    if (!restrict_first) PROF_ON(h, cs, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, cs));
     PROF_ON(h, cs, "coarse_amg", sem::launch_coarse_solve(d, st, cs));
     CK(cudaEventRecord(h->ev_join, cs));
     mode |= sem::PSUM_COARSE;
   }
   if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
+    // FP32 patch solves leave h->overlap_sms SMs' worth of slots to the coarse branch
+    sem::DevProblem dd = d;
+    dd.sw_reserve_sms = (coarse && d.fp32) ? h->overlap_sms : 0;
     if (d.fp32 && pcg)
-      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32_in32(d, d.r32, reinterpret_cast<float*>(d.wp), st,
+      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32_in32(dd, d.r32, reinterpret_cast<float*>(d.wp), st,
                                                                   h->stream));
     else if (d.fp32)
-      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32(d, r, reinterpret_cast<float*>(d.wp), st, h->stream));
+      PROF(h, "schwarz_local", sem::launch_schwarz_local_f32(dd, r, reinterpret_cast<float*>(d.wp), st, h->stream));
     else
       PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
     mode |= sem::PSUM_FINE;
@@ -561,6 +571,14 @@ int sem_set_precision(sem_t* h, int precision) {
     return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
   h->precision = precision;
   h->d.fp32 = (precision == SEM_PREC_FP32);
+  return SEM_OK;
+}
+
+int sem_set_overlap(sem_t* h, int reserve_sms) {
+  if (int rc = check_handle(h)) return rc;
+  if (reserve_sms < 0 || reserve_sms > 1024) return fail(SEM_ERR_ARG, "reserve_sms out of range");
+  h->overlap_sms = reserve_sms;
+  h->invalidate();
   return SEM_OK;
 }
 

@@ -174,6 +174,7 @@ struct sem_s {
   float* geo32 = nullptr;
   int precision = SEM_PREC_FP64;
   int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
+  int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch
   uint8_t* mask = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
   IterGraph graph;

@@ -78,14 +78,18 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   constexpr int P2 = P * P, P3 = P * P * P;
   __shared__ T sS[P2], sev[P], s1_all[EPB * P3], s2_all[EPB * P3];
   const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
-  const int e_raw = blockIdx.x * EPB + grp;
-  const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
-  const int e = active ? e_raw : d.ne - 1;
   T* s1 = s1_all + grp * P3;
   T* s2 = s2_all + grp * P3;
   const int x = tx % P, y = tx / P;
   if (threadIdx.x < P2) sS[threadIdx.x] = (T)d.S[threadIdx.x];
   if (threadIdx.x < P) sev[threadIdx.x] = (T)d.ev[threadIdx.x];
+  // element groups strided over the grid (the grid may be capped below the group count to
+  // leave SMs to the concurrent coarse branch); every thread of a CTA runs the same rounds
+  const int ngroups = (d.ne + EPB - 1) / EPB;
+  for (int blk = blockIdx.x; blk < ngroups; blk += gridDim.x) {
+  const int e_raw = blk * EPB + grp;
+  const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
+  const int e = active ? e_raw : d.ne - 1;
   const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
   const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
   const T scale = (T)(8.0 / (hxd * hyd * hzd));
@@ -134,10 +138,12 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
 #pragma unroll
   for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
   pencil_bwd<P, T>(sS, out, col);
-  if (!active) return;
-  T* outp = wp + (size_t)e * P3;
+  if (active) {
+    T* outp = wp + (size_t)e * P3;
 #pragma unroll
-  for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
+    for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
+  }
+  }
 }
 
 
@@ -174,7 +180,16 @@ bool sw_tile_ok_t(int P, int epb) {
 template <int P, typename T, typename TR, int EPB>
 cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
   if constexpr (sw_tile_supported<P, T, EPB>()) {
-    const int grid = (d.ne + EPB - 1) / EPB;
+    int grid = (d.ne + EPB - 1) / EPB;
+    if (d.sw_reserve_sms > 0) {
+      // as many CTAs as fit on all but sw_reserve_sms SMs, so that slots stay free
+      int dev = 0, nsm = 0, per_sm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_local_kernel<P, T, TR, EPB>, EPB * P * P, 0);
+      const int cap = (nsm - d.sw_reserve_sms) * per_sm;
+      if (cap > 0 && cap < grid) grid = cap;
+    }
     schwarz_local_kernel<P, T, TR, EPB><<<grid, EPB * P * P, 0, s>>>(d, r, wp, st);
     count_launch();
     return cudaGetLastError();

@@ -49,6 +49,7 @@ _SIGS = {
     "sem_set_precond": ([_vp, _int], _int),
     "sem_set_coarse_solver": ([_vp, _int], _int),
     "sem_set_loop": ([_vp, _int], _int),
+    "sem_set_overlap": ([_vp, _int], _int),
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
@@ -182,6 +183,10 @@ def sem_set_precond(h, which):
 
 def sem_set_coarse_solver(h, kind):
     return _check(_lib.sem_set_coarse_solver(h, {"vcycle": SEM_COARSE_VCYCLE, "kcycle": SEM_COARSE_KCYCLE}.get(kind, kind)))
+
+
+def sem_set_overlap(h, reserve_sms):
+    return _check(_lib.sem_set_overlap(h, int(reserve_sms)))
 
 
 def sem_set_loop(h, mode):
