@@ -12,7 +12,8 @@ from . import gll, numbering, geometry, operator, schwarz, coarse, amg, pcg
 
 
 class Problem:
-    def __init__(self, mesh, n, lam, dirichlet=True, coarse_solver="amg", with_schwarz=True, patch="face"):
+    def __init__(self, mesh, n, lam, dirichlet=True, coarse_solver="amg", with_schwarz=True, patch="face",
+                 pencils="boundary"):
         self.mesh = mesh
         self.n = n
         self.lam = float(lam)
@@ -32,6 +33,7 @@ class Problem:
             self.mask = np.zeros(self.G, dtype=np.uint8)
         self.coarse_solver = coarse_solver
         self.patch = patch
+        self.pencils = pencils
         if with_schwarz:
             self._setup_schwarz()
         if coarse_solver is not None:
@@ -46,6 +48,16 @@ class Problem:
         self.ip = schwarz.patch_table(self.l2g, self.nb_elem, self.nb_face)
         if self.patch == "full":
             self.ip = schwarz.fill_edges_corners(self.ip, self.l2g)
+        self.variants = None
+        if self.pencils == "boundary":
+            free = schwarz.free_sides(self.nb_elem, self.l2g, self.mask)
+            var = free[:, :, 0].astype(np.int64) + 2 * free[:, :, 1].astype(np.int64)
+            table = []
+            for v in range(4):
+                Kv, Mv = schwarz.pencil_variant(self.Dh, self.rho, bool(v & 1), bool(v & 2))
+                ev, S = schwarz.pencil_eig(Kv, Mv)
+                table.append((S, ev))
+            self.variants = (var, table)
 
     # --- coarse scale -------------------------------------------------------
     def _setup_coarse(self):
@@ -82,7 +94,7 @@ class Problem:
         return operator.matfree_apply(x, self.l2g, self.Dh, self.Gf, self.m_loc, self.lam, self.mask)
 
     def apply_Pf(self, r):
-        return schwarz.apply_fine(r, self.ip, self.S, self.ev, self.h, self.lam, self.mask)
+        return schwarz.apply_fine(r, self.ip, self.S, self.ev, self.h, self.lam, self.mask, self.variants)
 
     def apply_Pc(self, r):
         rm = np.where(self.mask > 0, 0.0, r)

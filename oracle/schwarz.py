@@ -7,6 +7,11 @@ Readings:
     the rows/columns -1..n+1 of the three-element 1D assembly (stiffness
     d_ij = sum_m rho_m phi_i'(t_m) phi_j'(t_m), mass diag(rho)), i.e. homogeneous
     Dirichlet beyond -1 and n+1. The neighbours are assumed to have the same h.
+  * "Suitable boundary conditions" (Sec. 4.2) at a side with no neighbour that is not
+    Dirichlet (a natural-boundary face): that side's neighbour is left out of the
+    assembly, so the end node keeps its own element's share alone, and the row beyond it
+    is decoupled (pencil_variant; Problem(pencils="boundary"), the default). Dirichlet
+    faces keep the extended pencil (their nodes are masked).
   * The eigen-form is the generalised problem K S = M S Lambda with S^T M S = I, so
     z = 8/(hx hy hz) (S x S x S) diag[1/(4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + c)]
         (S^T x S^T x S^T) r,
@@ -22,7 +27,8 @@ Pinned by: the pencil matrices equal the printed extended matrix pattern, the
 fast-diagonalisation solve equals a dense solve of the Kronecker-sum box matrix,
 S^T M S = I and K S = M S Lambda (scipy eigh), symmetry and positivity of P^f; on an
 unperturbed lattice the filled box nodes sit where the element's (affine) map, extended
-one GLL step beyond each face, puts them.
+one GLL step beyond each face, puts them; the variant pencil without free sides is the
+extended one, and on one undistorted, insulated hex P^f = A^-1.
 """
 import numpy as np
 import scipy.linalg
@@ -43,6 +49,46 @@ def pencil_matrices(Dh, rho):
         Mf[o:o + n + 1] += rho
     keep = np.arange(n - 1, 2 * n + 2)           # global nodes -1 .. n+1
     return Kf[np.ix_(keep, keep)], np.diag(Mf[keep])
+
+
+def pencil_variant(Dh, rho, low_free, high_free):
+    """Extended 1D pencil of an element with no neighbour on its low and/or high side (a
+    free, natural-boundary side): only the present elements are assembled, so the end node
+    on a free side keeps its own element's share alone; the row beyond a free side has no
+    node and is decoupled (K = M = 1 there, and its data is always zero)."""
+    n = len(rho) - 1
+    d = Dh.T @ np.diag(rho) @ Dh
+    N = 3 * n + 1
+    Kf = np.zeros((N, N))
+    Mf = np.zeros(N)
+    for el, present in ((0, not low_free), (1, True), (2, not high_free)):
+        if present:
+            o = el * n
+            Kf[o:o + n + 1, o:o + n + 1] += d
+            Mf[o:o + n + 1] += rho
+    keep = np.arange(n - 1, 2 * n + 2)
+    K, m = Kf[np.ix_(keep, keep)], Mf[keep].copy()
+    for row, free in ((0, low_free), (n + 2, high_free)):
+        if free:
+            K[row, :] = 0.0
+            K[:, row] = 0.0
+            K[row, row] = 1.0
+            m[row] = 1.0
+    return K, np.diag(m)
+
+
+def free_sides(nb_elem, l2g, mask):
+    """free[e, axis, side]: the element has no neighbour there and the face is not wholly
+    masked (a natural-boundary face)."""
+    E, p = l2g.shape[0], l2g.shape[1]
+    n = p - 1
+    free = np.zeros((E, 3, 2), dtype=bool)
+    for f, (ax, sd) in enumerate(HEX_FACES):
+        sl = [slice(None)] * 3
+        sl[ax] = 0 if sd == 0 else n
+        face = l2g[(slice(None),) + tuple(sl)].reshape(E, -1)
+        free[:, ax, sd] = (nb_elem[:, f] < 0) & ~np.all(mask[face] > 0, axis=1)
+    return free
 
 
 def pencil_eig(K, M):
@@ -157,13 +203,39 @@ def box_matrix(K, M, h, lam):
                   + np.kron(M, np.kron(M, K)) / hz ** 2) + lam * np.kron(M, np.kron(M, M))
 
 
-def apply_fine(r, ip, S, ev, h, lam, mask=None):
-    """P^f r: restrict to every patch, solve each box, add the present nodes back."""
+def fast_diag_solve_axes(rp, S3, ev3, h, lam):
+    """Eq. z with its own pencil per axis: S3 = (Sx, Sy, Sz), ev3 = (evx, evy, evz)."""
+    (Sx, Sy, Sz), (ex, ey, ez) = S3, ev3
+    scale = 8.0 / (h[:, 0] * h[:, 1] * h[:, 2])
+    t = np.einsum("ia,eijk->eajk", Sx, rp)
+    t = np.einsum("jb,eajk->eabk", Sy, t)
+    t = np.einsum("kc,eabk->eabc", Sz, t)
+    den = 4.0 * (ex[None, :, None, None] / h[:, 0, None, None, None] ** 2
+                 + ey[None, None, :, None] / h[:, 1, None, None, None] ** 2
+                 + ez[None, None, None, :] / h[:, 2, None, None, None] ** 2) + lam
+    t = t / den * scale[:, None, None, None]
+    t = np.einsum("kc,eabc->eabk", Sz, t)
+    t = np.einsum("jb,eabk->eajk", Sy, t)
+    return np.einsum("ia,eajk->eijk", Sx, t)
+
+
+def apply_fine(r, ip, S, ev, h, lam, mask=None, variants=None):
+    """P^f r: restrict to every patch, solve each box, add the present nodes back. With
+    variants = (var[E, 3] in 0..3 = low_free + 2 high_free, [(S, ev)] per variant), each
+    element uses the pencil of its sides along each axis."""
     Gn = r.shape[0]
     rm = r if mask is None else np.where(mask > 0, 0.0, r)
     present = ip >= 0
     rp = np.where(present, rm[np.where(present, ip, 0)], 0.0)
-    zp = fast_diag_solve(rp, S, ev, h, lam)
+    if variants is None:
+        zp = fast_diag_solve(rp, S, ev, h, lam)
+    else:
+        var, table = variants
+        zp = np.zeros_like(rp)
+        for combo in {tuple(v) for v in var.tolist()}:
+            sel = np.all(var == np.array(combo), axis=1)
+            zp[sel] = fast_diag_solve_axes(rp[sel], [table[c][0] for c in combo], [table[c][1] for c in combo],
+                                           h[sel], lam)
     z = np.bincount(ip[present], weights=zp[present], minlength=Gn)
     if mask is not None:
         z = np.where(mask > 0, 0.0, z)

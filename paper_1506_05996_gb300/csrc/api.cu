@@ -155,6 +155,19 @@ int build_coarse(sem_t* h) {
   return SEM_OK;
 }
 
+// Pencil variant of every element side (natural boundary where a side has no neighbour
+// and its face is not wholly masked); none anywhere -> d.pvar = null (the plain kernel path).
+int update_free_sides(sem_t* h) {
+  std::vector<uint8_t> fs = sem::free_sides(h->nb, h->mask_host);
+  bool any = false;
+  for (uint8_t v : fs) any = any || v != 0;
+  CK(cudaMemcpyAsync(h->pvar, fs.data(), fs.size(), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->d.pvar = any ? h->pvar : nullptr;
+  h->invalidate();
+  return SEM_OK;
+}
+
 int check_handle(const sem_t* h) {
   if (h == nullptr) return fail(SEM_ERR_ARG, "NULL handle");
   return SEM_OK;
@@ -366,6 +379,18 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   UP(pg_idx, pg_idx, int);
   UP(S, S, double);
   UP(ev, ev, double);
+  {
+    // pencils of element sides on a natural boundary: free low, free high, free both
+    std::vector<double> Sv, evv;
+    for (int v = 1; v <= 3; ++v) {
+      std::vector<double> Sk, ek;
+      sem::pencil_variant_tables(n, rho, D, (v & 1) != 0, (v & 2) != 0, Sk, ek);
+      Sv.insert(Sv.end(), Sk.begin(), Sk.end());
+      evv.insert(evv.end(), ek.begin(), ek.end());
+    }
+    UP(Sv, Sv, double);
+    UP(evv, evv, double);
+  }
   UP(hbox, hbox, double);
   UP(Btab, Btab, double);
   {
@@ -376,6 +401,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->upload(&h->coords, coords, A));
   CK(h->upload(&h->mask, h->mask_host, A));
   d.mask = h->mask;
+  CK(h->alloc(&h->pvar, (size_t)nb.ne, A));
+  if (int rc = update_free_sides(h)) return rc;
   CK(h->alloc(&d.wl, (size_t)(nb.ne * p3), A));
   CK(h->alloc(&d.wp, (size_t)(nb.ne * P3), A));
   CK(h->alloc(&d.Re, (size_t)(8 * nb.ne), A));
@@ -494,6 +521,7 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
   for (auto& v : m) v = v ? 1 : 0;
   h->mask_host = m;
   CK(cudaMemcpyAsync(h->mask, h->mask_host.data(), h->nb.G, cudaMemcpyHostToDevice, h->stream));
+  if (int rc = update_free_sides(h)) return rc;
   return build_coarse(h);
 }
 

@@ -91,6 +91,9 @@ struct DevProblem {
   const int* pg_idx = nullptr;
   const double* S = nullptr;        // P*P, S[row*P + mode]
   const double* ev = nullptr;       // P
+  const uint8_t* pvar = nullptr;    // [ne] free sides (bit 2a low, 2a+1 high) or null if none
+  const double* Sv = nullptr;       // [3][P*P] pencils with a free low / high / both side(s)
+  const double* evv = nullptr;      // [3][P]
   const double* hbox = nullptr;     // ne*3
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* Btab32 = nullptr;    // the same in FP32

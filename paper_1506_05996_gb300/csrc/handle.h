@@ -176,6 +176,7 @@ struct sem_s {
   int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
   int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch
   uint8_t* mask = nullptr;
+  uint8_t* pvar = nullptr;          // free sides of every element (see update_free_sides)
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;
   IterGraph graph;
   LoopGraph loop;

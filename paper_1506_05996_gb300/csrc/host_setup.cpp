@@ -398,6 +398,72 @@ std::vector<int> patch_table(const Numbering& nb, bool full) {
 }
 
 // ------------------------------------------------------------ pencil tables
+void pencil_variant_tables(int n, const std::vector<double>& rho, const std::vector<double>& D, bool low_free,
+                           bool high_free, std::vector<double>& S, std::vector<double>& ev) {
+  const int p = n + 1, P = n + 3;
+  std::vector<double> d(p * p, 0.0);
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int m = 0; m < p; ++m) d[i * p + j] += rho[m] * D[m * p + i] * D[m * p + j];
+  // box rows 0..P-1 are pencil rows -1..n+1
+  std::vector<double> K(P * P, 0.0), M(P, 0.0);
+  for (int i = 0; i < p; ++i) {
+    M[i + 1] += rho[i];
+    for (int j = 0; j < p; ++j) K[(i + 1) * P + (j + 1)] += d[i * p + j];
+  }
+  if (low_free) {
+    K[0] = 1.0;
+    M[0] = 1.0;
+  } else {   // left neighbour: its nodes n-1, n on rows -1, 0
+    K[0] += d[(n - 1) * p + (n - 1)];
+    K[0 * P + 1] += d[(n - 1) * p + n];
+    K[1 * P + 0] += d[n * p + (n - 1)];
+    K[1 * P + 1] += d[n * p + n];
+    M[0] += rho[n - 1];
+    M[1] += rho[n];
+  }
+  if (high_free) {
+    K[(P - 1) * P + (P - 1)] = 1.0;
+    M[P - 1] = 1.0;
+  } else {   // right neighbour: its nodes 0, 1 on rows n, n+1
+    K[(P - 2) * P + (P - 2)] += d[0];
+    K[(P - 2) * P + (P - 1)] += d[1];
+    K[(P - 1) * P + (P - 2)] += d[p];
+    K[(P - 1) * P + (P - 1)] += d[p + 1];
+    M[P - 2] += rho[0];
+    M[P - 1] += rho[1];
+  }
+  // K S = M S diag(ev): eigenpairs of M^-1/2 K M^-1/2, S = M^-1/2 Q
+  std::vector<double> A(P * P), Q, vals;
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) A[i * P + j] = K[i * P + j] / std::sqrt(M[i] * M[j]);
+  jacobi_eigen(P, A, vals, Q);
+  S.assign(P * P, 0.0);
+  ev = vals;
+  for (int r = 0; r < P; ++r)
+    for (int c = 0; c < P; ++c) S[r * P + c] = Q[r * P + c] / std::sqrt(M[r]);
+}
+
+std::vector<uint8_t> free_sides(const Numbering& nb, const std::vector<uint8_t>& mask) {
+  const int n = nb.n, p = nb.p, p3 = p * p * p;
+  std::vector<uint8_t> out(nb.ne, 0);
+  for (int64_t e = 0; e < nb.ne; ++e)
+    for (int f = 0; f < 6; ++f) {
+      if (nb.face_elem[6 * e + f] >= 0) continue;
+      const int a = f / 2, side = f % 2;
+      bool all_masked = true;
+      for (int u = 0; u < p && all_masked; ++u)
+        for (int v = 0; v < p && all_masked; ++v) {
+          int c[3];
+          c[a] = side ? n : 0;
+          c[(a + 1) % 3] = u;
+          c[(a + 2) % 3] = v;
+          if (!mask[nb.l2g[e * p3 + c[0] + p * (c[1] + p * c[2])]]) all_masked = false;
+        }
+      if (!all_masked) out[e] |= (uint8_t)(1u << (2 * a + side));
+    }
+  return out;
+}
 void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evals, std::vector<double>& evecs) {
   evecs.assign(n * n, 0.0);
   for (int i = 0; i < n; ++i) evecs[i * n + i] = 1.0;

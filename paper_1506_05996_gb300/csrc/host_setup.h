@@ -57,6 +57,15 @@ std::vector<int> patch_table(const Numbering& nb, bool full = false);
 void pencil_tables(int n, const std::vector<double>& t, const std::vector<double>& rho,
                    const std::vector<double>& D, std::vector<double>& S, std::vector<double>& ev);
 
+// The pencil of an element side with no neighbour and not Dirichlet (a natural boundary,
+// Sec. 4.2's "suitable boundary conditions"): only the present elements are assembled,
+// and the row beyond a free side is decoupled (K = M = 1). S[row*P + mode], S^T M S = I.
+void pencil_variant_tables(int n, const std::vector<double>& rho, const std::vector<double>& D, bool low_free,
+                           bool high_free, std::vector<double>& S, std::vector<double>& ev);
+// Per element: bit 2a (low side) and bit 2a+1 (high side) set when that side along axis a
+// has no neighbour and its face is not wholly masked.
+std::vector<uint8_t> free_sides(const Numbering& nb, const std::vector<uint8_t>& mask);
+
 // Mean length of the 4 element edges along xi, eta, zeta: hbox[e*3 + axis].
 std::vector<double> box_sizes(const Numbering& nb, const double* xyz);
 

@@ -62,27 +62,70 @@ __device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)
   }
 }
 
+// Plain 1D contractions with a pencil that has no reflection symmetry (an element side on
+// a natural boundary): fwd t = S^T v, bwd v = S t.
+template <int P, typename T>
+__device__ __forceinline__ void plain_fwd(const T* __restrict__ S, const T (&v)[P], T (&t)[P]) {
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    T a = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) a += S[k * P + c] * v[k];
+    t[c] = a;
+  }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void plain_bwd(const T* __restrict__ S, const T (&t)[P], T (&v)[P]) {
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    T a = 0;
+#pragma unroll
+    for (int c = 0; c < P; ++c) a += S[k * P + c] * t[c];
+    v[k] = a;
+  }
+}
+
+// The pencil of one axis: variant 0 (neighbours on both sides) folded, variants 1..3
+// (free low, free high, free both) plain.
+template <int P, typename T, bool VAR>
+__device__ __forceinline__ void axis_fwd(int v, const T* sS, const T* sSv, const T (&x)[P], T (&t)[P]) {
+  if (!VAR || v == 0) pencil_fwd<P, T>(sS, x, t);
+  else plain_fwd<P, T>(sSv + (v - 1) * P * P, x, t);
+}
+template <int P, typename T, bool VAR>
+__device__ __forceinline__ void axis_bwd(int v, const T* sS, const T* sSv, const T (&t)[P], T (&x)[P]) {
+  if (!VAR || v == 0) pencil_bwd<P, T>(sS, t, x);
+  else plain_bwd<P, T>(sSv + (v - 1) * P * P, t, x);
+}
+
 // One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
 // extended box in each of the six tensor contractions of Eq. z:
 //   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
 //   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
 template <int P, typename T, int EPB>
 constexpr int sw_smem_bytes() {
-  return (int)((P * P + P + EPB * 2 * P * P * P) * sizeof(T));
+  return (int)((4 * P * P + 4 * P + EPB * 2 * P * P * P) * sizeof(T));
 }
 
-template <int P, typename T, typename TR, int EPB>
+// VAR: some element sides lie on a natural boundary (d.pvar != null), so each axis picks its
+// pencil; without, every axis takes the folded one (the same code as before variants).
+template <int P, typename T, typename TR, int EPB, bool VAR>
 __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
                                                                     T* __restrict__ wp, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
-  __shared__ T sS[P2], sev[P], s1_all[EPB * P3], s2_all[EPB * P3];
+  __shared__ T sS[P2], sev[P], sSv[3 * P2], sevv[3 * P], s1_all[EPB * P3], s2_all[EPB * P3];
   const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
   T* s1 = s1_all + grp * P3;
   T* s2 = s2_all + grp * P3;
   const int x = tx % P, y = tx / P;
   if (threadIdx.x < P2) sS[threadIdx.x] = (T)d.S[threadIdx.x];
   if (threadIdx.x < P) sev[threadIdx.x] = (T)d.ev[threadIdx.x];
+  if (VAR) {
+    for (int q = threadIdx.x; q < 3 * P2; q += blockDim.x) sSv[q] = (T)d.Sv[q];
+    for (int q = threadIdx.x; q < 3 * P; q += blockDim.x) sevv[q] = (T)d.evv[q];
+  }
   // element groups strided over the grid (the grid may be capped below the group count to
   // leave SMs to the concurrent coarse branch); every thread of a CTA runs the same rounds
   const int ngroups = (d.ne + EPB - 1) / EPB;
@@ -93,6 +136,9 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
   const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
   const T scale = (T)(8.0 / (hxd * hyd * hzd));
+  // pencil variant per axis (bit 2a: free low side, bit 2a+1: free high side)
+  const int vb = VAR ? d.pvar[e] : 0;
+  const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
   T col[P], out[P];
   const int* ipe = d.ip + (size_t)e * P3;
 #pragma unroll
@@ -102,42 +148,45 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   }
   __syncthreads();
   // along K: line (I=x, J=y)
-  pencil_fwd<P, T>(sS, col, out);
+  axis_fwd<P, T, VAR>(vz, sS, sSv, col, out);
 #pragma unroll
   for (int c = 0; c < P; ++c) s1[x + P * (y + P * c)] = out[c];
   __syncthreads();
   // along J: line (I=x, c=y)
 #pragma unroll
   for (int J = 0; J < P; ++J) col[J] = s1[x + P * (J + P * y)];
-  pencil_fwd<P, T>(sS, col, out);
+  axis_fwd<P, T, VAR>(vy, sS, sSv, col, out);
 #pragma unroll
   for (int b = 0; b < P; ++b) s2[x + P * (b + P * y)] = out[b];
   __syncthreads();
   // along I: line (b=x, c=y), eigenvalue scaling, and back along I
 #pragma unroll
   for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
-  pencil_fwd<P, T>(sS, col, out);
+  axis_fwd<P, T, VAR>(vx, sS, sSv, col, out);
   {
     const T four = 4, lam = (T)d.lambda;
-    const T lbc = sev[x] * ihy2 + sev[y] * ihz2;
+    const T* evx = vx ? sevv + (vx - 1) * P : sev;
+    const T* evy = vy ? sevv + (vy - 1) * P : sev;
+    const T* evz = vz ? sevv + (vz - 1) * P : sev;
+    const T lbc = evy[x] * ihy2 + evz[y] * ihz2;
 #pragma unroll
-    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (sev[a] * ihx2 + lbc) + lam);
+    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (evx[a] * ihx2 + lbc) + lam);
   }
-  pencil_bwd<P, T>(sS, out, col);
+  axis_bwd<P, T, VAR>(vx, sS, sSv, out, col);
 #pragma unroll
   for (int I = 0; I < P; ++I) s2[I + P * (x + P * y)] = col[I];
   __syncthreads();
   // back along J: line (I=x, c=y)
 #pragma unroll
   for (int b = 0; b < P; ++b) out[b] = s2[x + P * (b + P * y)];
-  pencil_bwd<P, T>(sS, out, col);
+  axis_bwd<P, T, VAR>(vy, sS, sSv, out, col);
 #pragma unroll
   for (int J = 0; J < P; ++J) s1[x + P * (J + P * y)] = col[J];
   __syncthreads();
   // back along K: line (I=x, J=y)
 #pragma unroll
   for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
-  pencil_bwd<P, T>(sS, out, col);
+  axis_bwd<P, T, VAR>(vz, sS, sSv, out, col);
   if (active) {
     T* outp = wp + (size_t)e * P3;
 #pragma unroll
@@ -181,16 +230,17 @@ template <int P, typename T, typename TR, int EPB>
 cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
   if constexpr (sw_tile_supported<P, T, EPB>()) {
     int grid = (d.ne + EPB - 1) / EPB;
+    auto kernel = d.pvar != nullptr ? schwarz_local_kernel<P, T, TR, EPB, true> : schwarz_local_kernel<P, T, TR, EPB, false>;
     if (d.sw_reserve_sms > 0) {
       // as many CTAs as fit on all but sw_reserve_sms SMs, so that slots stay free
       int dev = 0, nsm = 0, per_sm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_local_kernel<P, T, TR, EPB>, EPB * P * P, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, EPB * P * P, 0);
       const int cap = (nsm - d.sw_reserve_sms) * per_sm;
       if (cap > 0 && cap < grid) grid = cap;
     }
-    schwarz_local_kernel<P, T, TR, EPB><<<grid, EPB * P * P, 0, s>>>(d, r, wp, st);
+    kernel<<<grid, EPB * P * P, 0, s>>>(d, r, wp, st);
     count_launch();
     return cudaGetLastError();
   } else {

@@ -181,3 +181,44 @@ def test_full_patch_parity(E, n, lam, seed):
     bg[torch.as_tensor(perm, device="cuda")] = torch.as_tensor(b, device="cuda")
     assert gpu.solve(bg)[2] == ref.solve(b)[1]
     gpu.close()
+
+
+@pytest.mark.parametrize("E,n,lam,seed", [(3, 4, 0.6, 23), (2, 6, 2.0, 24), (2, 3, 0.0, 25)])
+def test_neumann_patch_parity(E, n, lam, seed):
+    """P^f with natural-boundary pencils on insulated faces (Neumann) against the oracle;
+    lam = 0 too: P^f alone stays defined (the box problems are not singular)."""
+    from gpu_util import rel_err
+    P = _pair(lattice_hex_mesh(E, 0.2, seed), n, lam, neumann=True, coarse=False)
+    r = np.random.default_rng(seed).standard_normal(P.ref.G)
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), P.ref.apply_Pf(r)) <= TOL
+
+
+def test_partial_dirichlet_mask_patch_parity():
+    """Dirichlet on the x = 0 face only (sem_set_mask): the other boundary faces take the
+    natural-boundary pencil, in the library and the oracle alike."""
+    from gpu_util import rel_err
+    from oracle.problem import Problem
+    mesh = lattice_hex_mesh(3, 0.2, 26)
+    P = _pair(mesh, 4, 0.8, neumann=True, coarse=False)
+    mask = (np.abs(P.ref.coords[:, 0]) < 1e-12).astype(np.uint8)
+    mg = torch.zeros(P.gpu.n_dof, dtype=torch.uint8, device="cuda")
+    mg[torch.as_tensor(P.perm, device="cuda")] = torch.as_tensor(mask, device="cuda")
+    from paper_1506_05996_gb300 import sem
+    sem.sem_set_mask(P.gpu.h, mg)
+    ref = Problem(mesh, 4, 0.8, dirichlet=False, coarse_solver=None)
+    ref.mask = mask
+    ref._setup_schwarz()
+    r = np.random.default_rng(27).standard_normal(ref.G)
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), ref.apply_Pf(r)) <= TOL
+
+
+@pytest.mark.parametrize("n,lam", [(3, 0.7), (7, 0.1)])
+def test_insulated_single_box_patch_is_exact_inverse(n, lam):
+    """One undistorted hex, every face insulated: P^f A x = x (the box model is exact)."""
+    from paper_1506_05996_gb300.sem import SemProblem
+    mesh = lattice_hex_mesh(1, 0.0, 3, box=(0.7, 0.7, 0.7))
+    pr = SemProblem(mesh.xyz, mesh.hex2vert, n, lam, neumann=True)
+    x = torch.randn(pr.n_dof, dtype=torch.float64, device="cuda")
+    y = pr.apply_P(pr.apply_A(x), "fine")
+    assert float((y - x).abs().max()) <= 1e-10 * float(x.abs().max())
+    pr.close()

@@ -122,3 +122,29 @@ def test_full_box_nodes_extend_the_element_map_on_a_lattice():
     np.testing.assert_array_equal(present, inside)
     face = Problem(lattice_hex_mesh(E, 0.0, 7), n, 1.0, coarse_solver=None)
     assert (face.ip >= 0).sum() < present.sum()
+
+
+def test_pencil_variant_without_free_sides_is_the_extended_pencil():
+    from oracle import gll
+    for n in (2, 5, 8):
+        t, rho = gll.gll_nodes_weights(n)
+        Dh = gll.derivative_matrix(n)
+        K0, M0 = schwarz.pencil_matrices(Dh, rho)
+        K1, M1 = schwarz.pencil_variant(Dh, rho, False, False)
+        np.testing.assert_array_equal(K1, K0)
+        np.testing.assert_array_equal(M1, M0)
+
+
+@pytest.mark.parametrize("n,lam,seed", [(3, 0.7, 0), (5, 2.0, 3), (7, 0.1, 5)])
+def test_insulated_single_box_patch_is_the_exact_element_inverse(n, lam, seed):
+    """One undistorted hex with every face insulated: its patch is the element itself with
+    free sides on all axes, and the box model is exact, so P^f = A^-1 (any orientation)."""
+    from oracle.problem import Problem
+    from synth import lattice_hex_mesh
+    pr = Problem(lattice_hex_mesh(1, 0.0, seed, box=(0.7, 0.7, 0.7)), n, lam, dirichlet=False,
+                 coarse_solver=None, pencils="boundary")
+    x = np.random.default_rng(seed).standard_normal(pr.G)
+    np.testing.assert_allclose(pr.apply_Pf(pr.apply_A(x)), x, rtol=0, atol=1e-10 * np.abs(x).max())
+    ext = Problem(lattice_hex_mesh(1, 0.0, seed, box=(0.7, 0.7, 0.7)), n, lam, dirichlet=False,
+                  coarse_solver=None, pencils="extended")
+    assert np.abs(ext.apply_Pf(ext.apply_A(x)) - x).max() > 1e-3 * np.abs(x).max()
