@@ -58,6 +58,9 @@ typedef struct sem_s sem_t;
 #define SEM_PREC_FP32  1   /* Ax and P in FP32; vectors, dots, alpha/beta, residual updates in
                               FP64; the residual is recomputed with the FP64 operator whenever it
                               fell by 1e3 and before convergence is accepted */
+#define SEM_PREC_P32   2   /* P alone in FP32 (patch solves from the FP64 residual, FP32
+                              prolongation sums; the coarse AMG stays FP64); Ax, vectors, dots and
+                              recurrences in FP64, so no residual replacement is needed */
 
 /* coarse solver P_0 of the two-scale preconditioner (sem_set_coarse_solver) */
 #define SEM_COARSE_VCYCLE  0  /* smoothed aggregation, three V(1,1) damped-Jacobi cycles: a fixed SPD

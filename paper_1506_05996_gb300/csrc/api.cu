@@ -187,9 +187,9 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
     // restriction, slowed by sharing the SMs with them, would lengthen the critical path,
     // so it runs first, alone on the GPU, and only the latency-bound AMG kernels overlap.
     cudaStream_t cs = h->coarse_stream;
-    const bool restrict_first = d.fp32;
+    const bool restrict_first = d.pfp32;
     if (restrict_first) {
-      if (pcg)
+      if (pcg && d.fp32)
         PROF(h, "coarse_restrict", sem::launch_coarse_restrict_f32(d, d.r32, st, h->stream));
       else
         PROF(h, "coarse_restrict", sem::launch_coarse_restrict(d, r, st, h->stream));
@@ -204,11 +204,11 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   if (which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE) {
     // FP32 patch solves leave h->overlap_sms SMs' worth of slots to the coarse branch
     sem::DevProblem dd = d;
-    dd.sw_reserve_sms = (coarse && d.fp32) ? h->overlap_sms : 0;
+    dd.sw_reserve_sms = (coarse && d.pfp32) ? h->overlap_sms : 0;
     if (d.fp32 && pcg)
       PROF(h, "schwarz_local", sem::launch_schwarz_local_f32_in32(dd, d.r32, reinterpret_cast<float*>(d.wp), st,
                                                                   h->stream));
-    else if (d.fp32)
+    else if (d.pfp32)
       PROF(h, "schwarz_local", sem::launch_schwarz_local_f32(dd, r, reinterpret_cast<float*>(d.wp), st, h->stream));
     else
       PROF(h, "schwarz_local", sem::launch_schwarz_local(d, r, d.wp, st, h->stream));
@@ -594,11 +594,13 @@ int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const 
 
 int sem_set_precision(sem_t* h, int precision) {
   if (int rc = check_handle(h)) return rc;
-  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32) return fail(SEM_ERR_ARG, "unknown precision");
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_P32)
+    return fail(SEM_ERR_ARG, "unknown precision");
   if (precision == SEM_PREC_FP32 && !h->d.recompute && h->geo32 == nullptr)
     return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
   h->precision = precision;
   h->d.fp32 = (precision == SEM_PREC_FP32);
+  h->d.pfp32 = (precision == SEM_PREC_FP32 || precision == SEM_PREC_P32);
   return SEM_OK;
 }
 
@@ -710,7 +712,8 @@ int enqueue_replacement(sem_t* h, const double* b) {
 // Configuration bits the captured graphs depend on.
 long graph_key(const sem_t* h) {
   const sem::DevProblem& d = h->d;
-  return (long)(d.fp32 ? 1 : 0) | ((long)h->precond << 1) | ((long)h->prof.on << 3) | ((long)d.epb_ax << 4) |
+  return (long)(d.fp32 ? 1 : 0) | ((long)(d.pfp32 ? 1 : 0) << 15) | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
+         ((long)d.epb_ax << 4) |
          ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13);
 }
 

@@ -70,6 +70,7 @@ struct DevProblem {
   double lambda = 0.0;
   bool recompute = false;
   bool fp32 = false;                // operator and patch solves in FP32 (mixed path)
+  bool pfp32 = false;               // preconditioner in FP32 (with fp32, or alone: FP64 operator)
   int sw_reserve_sms = 0;           // > 0: the patch-solve grid leaves this many SMs' worth of
                                     // slots free (for the coarse branch running beside it)
   int epb_ax = 1, epb_sw = 1;       // elements per CTA of the operator / patch-solve kernels

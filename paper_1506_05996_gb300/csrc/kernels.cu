@@ -769,7 +769,7 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s) : vcycle(d, 0, d.Rc, d.Zc, st, s);
   if (err != cudaSuccess) return err;
   if (d.nlevels == 0 || d.amg_kind == 1) {
-    if (d.fp32) {
+    if (d.pfp32) {
       to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
       ++g_kernel_launches;
     }
@@ -785,7 +785,7 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
     add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
     ++g_kernel_launches;
   }
-  if (d.fp32) {
+  if (d.pfp32) {
     to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
     ++g_kernel_launches;
   }
@@ -793,7 +793,7 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
 }
 
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
-  if (d.fp32) {
+  if (d.pfp32) {
     const float* wp = reinterpret_cast<const float*>(d.wp);
     if (pcg) psum_kernel<true, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
     else psum_kernel<false, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);

@@ -103,3 +103,25 @@ def test_mixed_solve_reaches_fp64_tolerance(geom):
     # 2e-8 ||b|| / lambda_min(A); compare against the manufactured-solution error scale
     assert np.max(np.abs(u - u_ref)) <= 1e-5 * np.max(np.abs(u_ref))
     assert np.max(np.abs(u - manufactured_u(P.ref.coords))) < 1e-3
+
+
+def test_fp32_preconditioner_with_fp64_operator():
+    """SEM_PREC_P32: the preconditioner alone in FP32, through the same kernels as the mixed
+    path's FP32 P (so its results are bit-identical to them), with the FP64 operator: the
+    recursive residual stays the FP64 one and the solve needs no replacement."""
+    P = _pair(lattice_hex_mesh(6, 0.2, 4), 5, 1.0, "stored")
+    rng = np.random.default_rng(11)
+    r = P.to_gpu(rng.standard_normal(P.ref.G))
+    P.gpu.set_precision("fp32")
+    z_mixed = P.gpu.apply_P(r)
+    P.gpu.set_precision("p32")
+    z_p32 = P.gpu.apply_P(r)
+    assert torch.equal(z_mixed, z_p32)
+    b = P.ref.load(manufactured_s(P.ref.coords, 1.0))
+    u_ref, it_ref, _ = P.ref.solve(b, rtol=1e-8)
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+    assert rc == 0 and tr <= 1e-8 and abs(it - it_ref) <= 2
+    # the recursive residual is the FP64 one: its last value agrees with the true residual
+    assert abs(hist[-1] - tr) <= 1e-3 * tr
+    u = P.to_ref(x)
+    assert np.max(np.abs(u - u_ref)) <= 1e-5 * np.max(np.abs(u_ref))
