@@ -162,6 +162,13 @@ int sem_set_loop(sem_t* h, int mode);
  * it. Errors: SEM_ERR_ARG. */
 int sem_set_overlap(sem_t* h, int reserve_sms);
 
+/* sem_set_weights - overlap-weighted P^f (not in the paper, which sums the patch corrections,
+ * Sec. 4.2): weighted != 0 scales the residual entering the patch solves and their summed
+ * result by w_N = c_N^-1/2, c_N the number of patches that contain DOF N, i.e. W P^f W, still
+ * symmetric positive definite; 0 restores the paper's unweighted sum (the default). Fewer
+ * iterations on the same work per iteration. Errors: SEM_ERR_ARG. */
+int sem_set_weights(sem_t* h, int weighted);
+
 /* sem_set_coarse_solver - choose P_0 (SEM_COARSE_*); rebuilds the AMG hierarchy on the host
  * (Sec. 4.1). With SEM_COARSE_KCYCLE each coarse level above the dense one takes two
  * flexible-CG steps preconditioned by the K-cycle below it, combined as the A-orthogonal

@@ -13,7 +13,7 @@ from . import gll, numbering, geometry, operator, schwarz, coarse, amg, pcg
 
 class Problem:
     def __init__(self, mesh, n, lam, dirichlet=True, coarse_solver="amg", with_schwarz=True, patch="face",
-                 pencils="boundary"):
+                 pencils="boundary", weights="none"):
         self.mesh = mesh
         self.n = n
         self.lam = float(lam)
@@ -34,6 +34,7 @@ class Problem:
         self.coarse_solver = coarse_solver
         self.patch = patch
         self.pencils = pencils
+        self.weights = weights
         if with_schwarz:
             self._setup_schwarz()
         if coarse_solver is not None:
@@ -58,6 +59,7 @@ class Problem:
                 ev, S = schwarz.pencil_eig(Kv, Mv)
                 table.append((S, ev))
             self.variants = (var, table)
+        self.w = schwarz.cover_weights(self.ip, self.G) if self.weights == "cover" else None
 
     # --- coarse scale -------------------------------------------------------
     def _setup_coarse(self):
@@ -94,7 +96,7 @@ class Problem:
         return operator.matfree_apply(x, self.l2g, self.Dh, self.Gf, self.m_loc, self.lam, self.mask)
 
     def apply_Pf(self, r):
-        return schwarz.apply_fine(r, self.ip, self.S, self.ev, self.h, self.lam, self.mask, self.variants)
+        return schwarz.apply_fine(r, self.ip, self.S, self.ev, self.h, self.lam, self.mask, self.variants, self.w)
 
     def apply_Pc(self, r):
         rm = np.where(self.mask > 0, 0.0, r)

@@ -22,7 +22,9 @@ Readings:
     With patch = "full" (fill_edges_corners) the edge and corner layers are filled too,
     giving the (n+3)^3 nodes per subdomain that Sec. 4.2 counts.
   * h_x, h_y, h_z: mean length of the element's 4 edges along xi, eta, zeta.
-  * No overlap weights: the corrections are summed.
+  * No overlap weights: the corrections are summed (the paper's P^f, the default). Option:
+    weights w_N = c_N^(-1/2), c_N the number of patches containing node N, applied to the
+    residual before the patch solves and to the sum after them, W P^f W (symmetric).
 Pinned by: the pencil matrices equal the printed extended matrix pattern, the
 fast-diagonalisation solve equals a dense solve of the Kronecker-sum box matrix,
 S^T M S = I and K S = M S Lambda (scipy eigh), symmetry and positivity of P^f; on an
@@ -219,12 +221,22 @@ def fast_diag_solve_axes(rp, S3, ev3, h, lam):
     return np.einsum("ia,eajk->eijk", Sx, t)
 
 
-def apply_fine(r, ip, S, ev, h, lam, mask=None, variants=None):
+def cover_weights(ip, G):
+    """w_N = c_N^(-1/2), c_N the number of patches that contain node N (1 where none)."""
+    present = ip >= 0
+    cover = np.bincount(ip[present], minlength=G).astype(np.float64)
+    return 1.0 / np.sqrt(np.where(cover > 0, cover, 1.0))
+
+
+def apply_fine(r, ip, S, ev, h, lam, mask=None, variants=None, weights=None):
     """P^f r: restrict to every patch, solve each box, add the present nodes back. With
     variants = (var[E, 3] in 0..3 = low_free + 2 high_free, [(S, ev)] per variant), each
-    element uses the pencil of its sides along each axis."""
+    element uses the pencil of its sides along each axis. With weights w (per node), the
+    overlap-weighted sum W (sum_s R_s^T A_s^-1 R_s) W, W = diag(w), still symmetric."""
     Gn = r.shape[0]
     rm = r if mask is None else np.where(mask > 0, 0.0, r)
+    if weights is not None:
+        rm = rm * weights
     present = ip >= 0
     rp = np.where(present, rm[np.where(present, ip, 0)], 0.0)
     if variants is None:
@@ -237,6 +249,8 @@ def apply_fine(r, ip, S, ev, h, lam, mask=None, variants=None):
             zp[sel] = fast_diag_solve_axes(rp[sel], [table[c][0] for c in combo], [table[c][1] for c in combo],
                                            h[sel], lam)
     z = np.bincount(ip[present], weights=zp[present], minlength=Gn)
+    if weights is not None:
+        z = z * weights
     if mask is not None:
         z = np.where(mask > 0, 0.0, z)
     return z

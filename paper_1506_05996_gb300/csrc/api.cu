@@ -377,6 +377,18 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   UP(ip, ip, int);
   UP(pg_off, pg_off, int);
   UP(pg_idx, pg_idx, int);
+  {
+    // overlap weights c^-1/2 of P^f (used when sem_set_weights turns them on)
+    std::vector<double> w(nb.G);
+    std::vector<float> w32(nb.G);
+    for (int64_t g = 0; g < nb.G; ++g) {
+      const int c = pg_off[g + 1] - pg_off[g];
+      w[g] = 1.0 / std::sqrt((double)(c > 0 ? c : 1));
+      w32[g] = (float)w[g];
+    }
+    CK(h->upload(&h->pw, w, A));
+    CK(h->upload(&h->pw32, w32, A));
+  }
   UP(S, S, double);
   UP(ev, ev, double);
   {
@@ -608,6 +620,15 @@ int sem_set_overlap(sem_t* h, int reserve_sms) {
   if (int rc = check_handle(h)) return rc;
   if (reserve_sms < 0 || reserve_sms > 1024) return fail(SEM_ERR_ARG, "reserve_sms out of range");
   h->overlap_sms = reserve_sms;
+  h->invalidate();
+  return SEM_OK;
+}
+
+int sem_set_weights(sem_t* h, int weighted) {
+  if (int rc = check_handle(h)) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  h->d.pw = weighted ? h->pw : nullptr;
+  h->d.pw32 = weighted ? h->pw32 : nullptr;
   h->invalidate();
   return SEM_OK;
 }

@@ -93,6 +93,8 @@ struct DevProblem {
   const double* S = nullptr;        // P*P, S[row*P + mode]
   const double* ev = nullptr;       // P
   const uint8_t* pvar = nullptr;    // [ne] free sides (bit 2a low, 2a+1 high) or null if none
+  const double* pw = nullptr;       // overlap weights c_N^-1/2 of P^f (null: unweighted, the paper's)
+  const float* pw32 = nullptr;      // the same in FP32
   const double* Sv = nullptr;       // [3][P*P] pencils with a free low / high / both side(s)
   const double* evv = nullptr;      // [3][P]
   const double* hbox = nullptr;     // ne*3

@@ -62,6 +62,11 @@ __device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)
   }
 }
 
+// Overlap weights of P^f in the kernel's precision (null when unweighted).
+template <typename T> __device__ __forceinline__ const T* weights_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* weights_of<double>(const DevProblem& d) { return d.pw; }
+template <> __device__ __forceinline__ const float* weights_of<float>(const DevProblem& d) { return d.pw32; }
+
 // Plain 1D contractions with a pencil that has no reflection symmetry (an element side on
 // a natural boundary): fwd t = S^T v, bwd v = S t.
 template <int P, typename T>
@@ -141,10 +146,13 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
   T col[P], out[P];
   const int* ipe = d.ip + (size_t)e * P3;
+  const T* wts = weights_of<T>(d);
 #pragma unroll
   for (int K = 0; K < P; ++K) {
     const int g = ipe[x + P * (y + P * K)];
-    col[K] = (g >= 0 && !d.mask[g]) ? (T)r[g] * scale : T(0);
+    T v = (g >= 0 && !d.mask[g]) ? (T)r[g] : T(0);
+    if (wts != nullptr && g >= 0) v = v * wts[g];
+    col[K] = v * scale;
   }
   __syncthreads();
   // along K: line (I=x, J=y)

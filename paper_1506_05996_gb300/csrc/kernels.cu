@@ -294,6 +294,9 @@ template <> __device__ __forceinline__ const float* btab_of<float>(const DevProb
 template <typename T> __device__ __forceinline__ const T* zc_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* zc_of<double>(const DevProblem& d) { return d.Zc; }
 template <> __device__ __forceinline__ const float* zc_of<float>(const DevProblem& d) { return d.Zc32; }
+template <typename T> __device__ __forceinline__ const T* wts_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* wts_of<double>(const DevProblem& d) { return d.pw; }
+template <> __device__ __forceinline__ const float* wts_of<float>(const DevProblem& d) { return d.pw32; }
 
 // z = P r on the free nodes: the patch results summed over every patch containing the
 // node (fine part) plus the trilinear interpolation of the coarse correction at the node
@@ -305,13 +308,18 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   const int p = d.p, p3 = p * p * p;
   const T* __restrict__ Bt = btab_of<T>(d);
   const T* __restrict__ Zc = zc_of<T>(d);
+  const T* __restrict__ Wt = wts_of<T>(d);
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     T v = 0;
     if (!d.mask[g]) {
       if (mode & PSUM_IDENT) v += (T)r[g];
-      if (mode & PSUM_FINE)
-        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) v += wp[d.pg_idx[q]];
+      if (mode & PSUM_FINE) {
+        T vf = 0;
+        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) vf += wp[d.pg_idx[q]];
+        if (Wt != nullptr) vf = vf * Wt[g];     // overlap-weighted P^f
+        v += vf;
+      }
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
         const int l = d.owner[g], e = l / p3, lr = l % p3;
         const int* ec = d.ecv + (size_t)e * 8;

@@ -49,6 +49,7 @@ _SIGS = {
     "sem_set_precond": ([_vp, _int], _int),
     "sem_set_coarse_solver": ([_vp, _int], _int),
     "sem_set_loop": ([_vp, _int], _int),
+    "sem_set_weights": ([_vp, _int], _int),
     "sem_set_overlap": ([_vp, _int], _int),
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
@@ -187,6 +188,10 @@ def sem_set_coarse_solver(h, kind):
 
 def sem_set_overlap(h, reserve_sms):
     return _check(_lib.sem_set_overlap(h, int(reserve_sms)))
+
+
+def sem_set_weights(h, weighted):
+    return _check(_lib.sem_set_weights(h, int(bool(weighted))))
 
 
 def sem_set_loop(h, mode):

@@ -222,3 +222,25 @@ def test_insulated_single_box_patch_is_exact_inverse(n, lam):
     y = pr.apply_P(pr.apply_A(x), "fine")
     assert float((y - x).abs().max()) <= 1e-10 * float(x.abs().max())
     pr.close()
+
+
+@pytest.mark.parametrize("E,n,lam,seed", [(3, 4, 0.6, 28), (2, 7, 1.0, 29)])
+def test_overlap_weighted_patch_parity(E, n, lam, seed):
+    """W P^f W (sem_set_weights) against the oracle, P^f and the whole solve."""
+    from gpu_util import rel_err
+    from oracle.problem import Problem
+    from paper_1506_05996_gb300 import sem
+    mesh = lattice_hex_mesh(E, 0.2, seed)
+    P = _pair(mesh, n, lam)
+    ref = Problem(mesh, n, lam, weights="cover")
+    sem.sem_set_weights(P.gpu.h, 1)
+    r = np.random.default_rng(seed).standard_normal(ref.G)
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), ref.apply_Pf(r)) <= TOL
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r))), ref.apply_P(r)) <= TOL
+    b = ref.load(manufactured_s(ref.coords, lam))
+    _, it_ref, h_ref = ref.solve(b)
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b))
+    assert rc == 0 and it == it_ref and tr <= 1e-8
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-9, atol=1e-15)
+    sem.sem_set_weights(P.gpu.h, 0)
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), P.ref.apply_Pf(r)) <= TOL

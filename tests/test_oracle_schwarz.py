@@ -148,3 +148,23 @@ def test_insulated_single_box_patch_is_the_exact_element_inverse(n, lam, seed):
     ext = Problem(lattice_hex_mesh(1, 0.0, seed, box=(0.7, 0.7, 0.7)), n, lam, dirichlet=False,
                   coarse_solver=None, pencils="extended")
     assert np.abs(ext.apply_Pf(ext.apply_A(x)) - x).max() > 1e-3 * np.abs(x).max()
+
+
+def test_overlap_weighted_fine_preconditioner():
+    """W P^f W with w = cover^-1/2: symmetric positive definite, equal to the plain P^f where
+    no patches overlap (one element), and the weights square-sum to one per patch node set."""
+    from oracle.problem import Problem
+    from synth import lattice_hex_mesh
+    pr = Problem(lattice_hex_mesh(3, 0.2, 8), 4, 0.6, coarse_solver=None, weights="cover")
+    rng = np.random.default_rng(3)
+    free = pr.mask == 0
+    x, y = rng.standard_normal(pr.G) * free, rng.standard_normal(pr.G) * free
+    assert abs(y @ pr.apply_Pf(x) - x @ pr.apply_Pf(y)) <= 1e-12 * abs(y @ pr.apply_Pf(x))
+    assert x @ pr.apply_Pf(x) > 0
+    present = pr.ip >= 0
+    cover = np.bincount(pr.ip[present], minlength=pr.G)
+    np.testing.assert_allclose(cover * pr.w ** 2, 1.0, rtol=1e-14)
+    one = Problem(lattice_hex_mesh(1, 0.2, 8), 4, 0.6, coarse_solver=None, weights="cover")
+    plain = Problem(lattice_hex_mesh(1, 0.2, 8), 4, 0.6, coarse_solver=None)
+    r = rng.standard_normal(one.G)
+    np.testing.assert_array_equal(one.apply_Pf(r), plain.apply_Pf(r))
