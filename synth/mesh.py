@@ -128,6 +128,90 @@ def lattice_hex_mesh(E, a=0.0, seed=0, renumber=True, rotate=True, box=(1.0, 1.0
                    E=int(Es[0]) if np.ndim(E) == 0 else tuple(Es.tolist()), a=float(a), seed=int(seed))
 
 
+def split_triangle_hex_mesh(N, layers, a=0.0, seed=0, height=1.0, rotate=True, renumber=True):
+    """All-hex mesh with irregular edge valences on [0,1]^2 x [0,height].
+
+    The unit square is cut into N x N cells, each cell into two triangles (diagonal direction
+    drawn at random), and each triangle into three quads through its centroid and edge
+    midpoints; the quads are extruded through `layers` layers. Interior vertical edges then
+    have valence 3 (centroids), 4 (edge midpoints) or 6 to 8 (cell corners). Interior vertices
+    move by U(-a h, a h) in x and y (h = 1/N, along-boundary only on the boundary) and by
+    U(-a dz, a dz) in z off the top and bottom. Random proper rotations of the corner lists
+    and random renumbering as in lattice_hex_mesh. The split quads have small corners: up to
+    a = 0.1 every element keeps a positive Jacobian (smallest GLL-corner |J| about a fifth of
+    the median over seeds 1..11); at a = 0.2 some invert. Returns a HexMesh.
+    """
+    rng = np.random.default_rng(seed)
+    h = 1.0 / N
+    pts = {}
+    def pid(key, xy):
+        if key not in pts:
+            pts[key] = (len(pts), xy)
+        return pts[key][0]
+    quads = []
+    for i in range(N):
+        for j in range(N):
+            c = [(i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)]
+            corner = [pid(("v", a_, b_), (a_ * h, b_ * h)) for a_, b_ in c]
+            tris = [(0, 1, 2), (0, 2, 3)] if rng.random() < 0.5 else [(0, 1, 3), (1, 2, 3)]
+            for t in tris:
+                tv = [c[k] for k in t]
+                ids = [corner[k] for k in t]
+                xy = np.array([[a_ * h, b_ * h] for a_, b_ in tv])
+                cen = pid(("c", i, j, t), tuple(xy.mean(axis=0)))
+                mids = []
+                for k in range(3):
+                    e = tuple(sorted((tv[k], tv[(k + 1) % 3])))
+                    mids.append(pid(("m",) + e, tuple((xy[k] + xy[(k + 1) % 3]) / 2)))
+                for k in range(3):      # quad: vertex k, midpoint k, centroid, midpoint k-1
+                    q = [ids[k], mids[k], cen, mids[k - 1]]
+                    quads.append(q)
+    n2 = len(pts)
+    xy = np.zeros((n2, 2))
+    for key, (k, v) in pts.items():
+        xy[k] = v
+    # counter-clockwise orientation for every quad
+    for qi, q in enumerate(quads):
+        p0, p1, p2, p3 = xy[q]
+        area = 0.5 * ((p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1])
+                      + (p2[0] - p0[0]) * (p3[1] - p0[1]) - (p3[0] - p0[0]) * (p2[1] - p0[1]))
+        if area < 0:
+            quads[qi] = [q[0], q[3], q[2], q[1]]
+    on_x = (np.abs(xy[:, 0]) < 1e-12) | (np.abs(xy[:, 0] - 1) < 1e-12)
+    on_y = (np.abs(xy[:, 1]) < 1e-12) | (np.abs(xy[:, 1] - 1) < 1e-12)
+    d = rng.uniform(-a, a, size=xy.shape) * h * 0.5
+    d[on_x, 0] = 0.0
+    d[on_y, 1] = 0.0
+    xy = xy + d
+    dz = height / layers
+    zs = np.arange(layers + 1) * dz
+    zpert = rng.uniform(-a, a, size=(layers + 1, n2)) * dz
+    zpert[0] = zpert[-1] = 0.0
+    xyz = np.zeros(((layers + 1) * n2, 3))
+    for L in range(layers + 1):
+        xyz[L * n2:(L + 1) * n2, :2] = xy
+        xyz[L * n2:(L + 1) * n2, 2] = zs[L] + zpert[L]
+    hexes = []
+    for L in range(layers):
+        for q in quads:
+            lo = [L * n2 + v for v in q]
+            hi = [(L + 1) * n2 + v for v in q]
+            hexes.append(lo + hi)        # VTK order: bottom quad counter-clockwise, then top
+    hexes = np.array(hexes, dtype=np.int64)
+    if rotate:
+        rot = rng.integers(0, len(PROPER_ROTATIONS), size=hexes.shape[0])
+        hexes = np.take_along_axis(hexes, _ROT_MAPS[rot], axis=1)
+    if renumber:
+        vperm = rng.permutation(xyz.shape[0])
+        new_xyz = np.empty_like(xyz)
+        new_xyz[vperm] = xyz
+        xyz = new_xyz
+        hexes = vperm[hexes]
+        hexes = hexes[rng.permutation(hexes.shape[0])]
+    return HexMesh(xyz=np.ascontiguousarray(xyz), hex2vert=np.ascontiguousarray(hexes), E=N, a=float(a),
+                   seed=int(seed))
+
+
 def manufactured_u(xyz):
     """u*(x,y,z) = sin(pi x) sin(pi y) sin(pi z); zero on the boundary of [0,1]^3."""
     x = np.asarray(xyz, dtype=np.float64)

@@ -244,3 +244,38 @@ def test_overlap_weighted_patch_parity(E, n, lam, seed):
     np.testing.assert_allclose(hist, h_ref, rtol=1e-9, atol=1e-15)
     sem.sem_set_weights(P.gpu.h, 0)
     assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), P.ref.apply_Pf(r)) <= TOL
+
+
+@pytest.mark.parametrize("N,layers,n,lam,seed", [(3, 2, 3, 0.5, 1), (2, 2, 6, 1.0, 2)])
+def test_irregular_valence_mesh_parity(N, layers, n, lam, seed):
+    """Operator, preconditioner and solve on an all-hex mesh with edge valences 1 to 8."""
+    from gpu_util import Pair, rel_err
+    from synth import split_triangle_hex_mesh
+    mesh = split_triangle_hex_mesh(N, layers, a=0.1, seed=seed)
+    for geom in ("stored", "recompute"):
+        P = Pair(mesh, n, lam, geom=geom)
+        x = np.random.default_rng(seed).standard_normal(P.ref.G)
+        assert rel_err(P.to_ref(P.gpu.apply_A(P.to_gpu(x))), P.ref.apply_A(x)) <= TOL
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(x), "fine")), P.ref.apply_Pf(x)) <= TOL
+    assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(x), "coarse")), P.ref.apply_Pc(x)) <= TOL
+    b = P.ref.load(np.ones(P.ref.G))
+    u_ref, it_ref, h_ref = P.ref.solve(b)
+    xs, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b))
+    # these meshes are poorly conditioned (tens of iterations): rounding-order differences
+    # grow along the CG trajectory, so the early history, the count and the solution are
+    # compared (both solutions meet the 1e-8 residual)
+    assert rc == 0 and abs(it - it_ref) <= 2 and tr <= 1e-8
+    np.testing.assert_allclose(hist[:15], h_ref[:15], rtol=1e-8, atol=1e-15)
+    assert rel_err(P.to_ref(xs), u_ref) <= 1e-6
+    N2 = Pair(mesh, n, lam, neumann=True, coarse=False)
+    assert rel_err(N2.to_ref(N2.gpu.apply_P(N2.to_gpu(x), "fine")), N2.ref.apply_Pf(x)) <= TOL
+
+
+def test_inverted_element_mesh_rejected():
+    """A split-triangle mesh perturbed by 20 % has inverted corners: sem_create refuses it."""
+    from paper_1506_05996_gb300 import sem
+    from synth import split_triangle_hex_mesh
+    mesh = split_triangle_hex_mesh(2, 2, a=0.2, seed=1)
+    with pytest.raises(sem.SemError) as exc:
+        sem.SemProblem(mesh.xyz, mesh.hex2vert, 3, 0.4)
+    assert exc.value.code == sem.SEM_ERR_JACOBIAN

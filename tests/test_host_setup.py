@@ -90,3 +90,26 @@ def test_nonmanifold_mesh_rejected(lib):
     mesh.hex2vert = np.vstack([bad, extra[None, :]])
     H = HostTables(lib, mesh, 2, 0.0)
     assert H.rc == -1
+
+
+@pytest.mark.parametrize("N,layers,n,seed", [(2, 2, 3, 1), (3, 1, 4, 2), (2, 3, 2, 3)])
+def test_tables_on_irregular_valence_meshes(lib, N, layers, n, seed):
+    """Numbering, patch tables, box sizes and the AMG hierarchy on an all-hex mesh whose
+    edges have valence 1 to 8 (triangles split into quads, extruded)."""
+    from synth import split_triangle_hex_mesh
+    mesh = split_triangle_hex_mesh(N, layers, a=0.1, seed=seed)
+    H = HostTables(lib, mesh, n, 0.4)
+    assert H.rc == 0
+    ref = Problem(mesh, n, 0.4, with_schwarz=True)
+    assert H.G == ref.G
+    perm = match(ref.coords, H.coords)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    np.testing.assert_array_equal(H.boundary[perm], ref.mask)
+    p, P = n + 1, n + 3
+    l2g = H.l2g.reshape(H.ne, p, p, p)
+    np.testing.assert_array_equal(inv[l2g], ref.l2g[H.elem_perm].transpose(0, 3, 2, 1))
+    ip = H.ip.reshape(H.ne, P, P, P)
+    lib_ip_in_ref = np.where(ip >= 0, inv[np.maximum(ip, 0)], -1)
+    np.testing.assert_array_equal(lib_ip_in_ref, ref.ip[H.elem_perm].transpose(0, 3, 2, 1))
+    np.testing.assert_allclose(H.hbox.reshape(-1, 3), ref.h[H.elem_perm], rtol=1e-14)
