@@ -22,12 +22,12 @@ int corner_of_bits(int a, int b, int c) {
 
 // ---------------------------------------------------------------- GLL tables
 static void legendre(int n, double x, double& p, double& dp) {
-  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  double p0 = 1.0, p1 = x, d1 = 1.0;
   if (n == 0) { p = 1.0; dp = 0.0; return; }
   for (int k = 2; k <= n; ++k) {
     double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
     double d2 = x * d1 + k * p1;  // P_k' = x P_{k-1}' + k P_{k-1}
-    p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    p0 = p1; p1 = p2; d1 = d2;
   }
   p = p1; dp = d1;
 }
