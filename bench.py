@@ -275,6 +275,13 @@ def run_gpu(args):
     b = (m * torch.as_tensor(s_np, device="cuda")).contiguous()
     x = torch.empty_like(b)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
+    # tile shapes (elements per CTA) by the library's autotuner, per precision, before any
+    # timing: P32 tunes the FP32 patch solve on FP64 input, then the mixed path's FP32
+    # kernels, then the FP64 kernels (the handle ends in FP64)
+    tiles = {}
+    for prec in ("p32", "fp32", "fp64"):
+        prob.set_precision(prec)
+        tiles[prec] = list(S.sem_autotune(prob.h))
 
     def one_solve():
         rc, it, hist, tr = S.sem_solve(prob.h, b, x, RTOL, 1000, want_history=False)
@@ -363,6 +370,9 @@ def run_gpu(args):
     p3 = (ORDER + 1) ** 3
     L = NE * p3
     rec = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="recompute")
+    for prec in ("fp32", "fp64"):
+        rec.set_precision(prec)
+        S.sem_autotune(rec.h)
     for geom, prec, pr in (("stored", "fp64", prob), ("recompute", "fp64", rec),
                            ("stored", "fp32", prob), ("recompute", "fp32", rec)):
         ms, kms = time_apply(pr, prec=prec)
@@ -372,8 +382,12 @@ def run_gpu(args):
         fb = 8 if prec == "fp64" else 4
         geo_bytes = 7 * fb * L if geom == "stored" else 24 * 8 * NE
         alg_bytes = 16 * G + 4 * L + geo_bytes
+        # the element kernel alone: x (FP64) and the mask read, l2g, factors, local results
+        # written (FP64 or FP32)
+        k_bytes = 9 * G + 4 * L + geo_bytes + fb * L
         key = geom + ("" if prec == "fp64" else "_fp32")
         ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
+                   "ax_local_frac_hbm_roofline": k_bytes / (kms * 1e-3) / 1e9 / hbm_peak,
                    "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
                    "bytes_per_dof": alg_bytes / G,
                    "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
@@ -474,7 +488,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "n_dof": G, "n_hex": NE, "order": ORDER, "lambda": LAM,
                        "rtol": RTOL, "preconditioner": "two-scale (P^c + P^f)", "geometry": "stored",
                        "l2": "inputs larger than L2 (0.94 GB stored factors) and a 512 MB flush between steps",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "tiles_epb_ax_sw": tiles},
             "time_to_1e-8_s": per_step, "iterations": iters[-1], "true_rel_res": trs[-1],
             "wall_s": t_wall,
             "ax": ax,

@@ -209,9 +209,13 @@ int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev,
  * elements one CTA of the operator (epb_ax) and of the patch solve (epb_sw) processes,
  * 1, 2, 4 or 8 (at low order an element has only (n+1)^2 and (n+3)^2 threads). A shape not
  * compiled for the handle's order (shared-memory or thread limits) is refused with
- * SEM_ERR_ARG. sem_autotune times every compiled shape on the handle's own mesh and
- * precision and keeps the fastest; it overwrites the handle's work vectors, so call it
- * between solves. Results are bit-identical for every shape.
+ * SEM_ERR_ARG. sem_set_tiles sets the shapes of the FP64 and the FP32 kernels alike.
+ * sem_autotune times every compiled shape on the handle's own mesh and keeps the fastest,
+ * for the kernels of the precision in use only: the operator in FP32 under
+ * SEM_PREC_FP32, the patch solve in FP32 under SEM_PREC_FP32 and SEM_PREC_P32, the FP64
+ * kernels otherwise (so tuning once per precision tunes both sets). It overwrites the
+ * handle's work vectors, so call it between solves. Results are bit-identical for every
+ * shape.
  */
 int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw);
 int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host);

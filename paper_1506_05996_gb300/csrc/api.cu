@@ -112,6 +112,9 @@ int build_coarse(sem_t* h) {
   auto up_csr = [&](const sem::Csr& A, sem::DevCsr& out) -> cudaError_t {
     out.n = A.n;
     out.nnz = (int)A.val.size();
+    // about four entries per lane: 8 lanes for the 27-entry rows of the Q1 matrix
+    out.lanes = 4;
+    while (out.lanes < 32 && 4 * out.lanes * (int64_t)A.n < (int64_t)out.nnz) out.lanes *= 2;
     cudaError_t e = h->upload(&out.ptr, A.ptr, h->coarse_allocs);
     if (e == cudaSuccess) e = h->upload(&out.col, A.col, h->coarse_allocs);
     if (e == cudaSuccess) e = h->upload(&out.val, A.val, h->coarse_allocs);
@@ -735,7 +738,8 @@ long graph_key(const sem_t* h) {
   const sem::DevProblem& d = h->d;
   return (long)(d.fp32 ? 1 : 0) | ((long)(d.pfp32 ? 1 : 0) << 15) | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
          ((long)d.epb_ax << 4) |
-         ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13);
+         ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13) |
+         ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20);
 }
 
 int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
@@ -1154,8 +1158,8 @@ int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw) {
   if (int rc = check_handle(h)) return rc;
   if (!sem::ax_tile_ok(h->d.p, epb_ax) || !sem::sw_tile_ok(h->d.P, epb_sw))
     return fail(SEM_ERR_ARG, "no kernel with that many elements per CTA for this order");
-  h->d.epb_ax = epb_ax;
-  h->d.epb_sw = epb_sw;
+  h->d.epb_ax = h->d.epb_ax32 = epb_ax;
+  h->d.epb_sw = h->d.epb_sw32 = epb_sw;
   h->invalidate();
   return SEM_OK;
 }
@@ -1167,27 +1171,32 @@ int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host) {
   CK(cudaMemsetAsync(h->r, 0, sizeof(double) * h->nb.G, h->stream));
   CK(cudaMemsetAsync(d.p32, 0, sizeof(float) * h->nb.G, h->stream));
   CK(cudaMemsetAsync(d.r32, 0, sizeof(float) * h->nb.G, h->stream));
+  // the kernels of the precision in use: the FP32 operator in the mixed path, the FP32
+  // patch solve in the mixed and P32 paths, the FP64 kernels otherwise
+  int& ax = d.fp32 ? d.epb_ax32 : d.epb_ax;
+  int& sw = d.pfp32 ? d.epb_sw32 : d.epb_sw;
+  auto fa = [&]() -> cudaError_t {
+    return d.fp32 ? sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), nullptr, h->stream)
+                  : sem::launch_ax_local(d, h->p, d.wl, nullptr, h->stream);
+  };
+  auto fs = [&]() -> cudaError_t {
+    float* wp32 = reinterpret_cast<float*>(d.wp);
+    if (d.fp32) return sem::launch_schwarz_local_f32_in32(d, d.r32, wp32, nullptr, h->stream);
+    if (d.pfp32) return sem::launch_schwarz_local_f32(d, h->r, wp32, nullptr, h->stream);
+    return sem::launch_schwarz_local(d, h->r, d.wp, nullptr, h->stream);
+  };
   const int cand[4] = {1, 2, 4, 8};
   int best_ax = 1, best_sw = 1;
   float t_ax = 1e30f, t_sw = 1e30f;
   for (int c : cand) {
     float ms;
-    d.epb_ax = sem::ax_tile_ok(d.p, c) ? c : 1;
-    auto fa = [&]() -> cudaError_t {
-      return d.fp32 ? sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), nullptr, h->stream)
-                    : sem::launch_ax_local(d, h->p, d.wl, nullptr, h->stream);
-    };
-    if (d.epb_ax == c && time_launches(h, fa, 5, &ms) == SEM_OK && ms < t_ax) { t_ax = ms; best_ax = c; }
-    d.epb_sw = sem::sw_tile_ok(d.P, c) ? c : 1;
-    auto fs = [&]() -> cudaError_t {
-      return d.fp32 ? sem::launch_schwarz_local_f32_in32(d, d.r32, reinterpret_cast<float*>(d.wp), nullptr,
-                                                         h->stream)
-                    : sem::launch_schwarz_local(d, h->r, d.wp, nullptr, h->stream);
-    };
-    if (d.epb_sw == c && time_launches(h, fs, 5, &ms) == SEM_OK && ms < t_sw) { t_sw = ms; best_sw = c; }
+    ax = sem::ax_tile_ok(d.p, c) ? c : 1;
+    if (ax == c && time_launches(h, fa, 5, &ms) == SEM_OK && ms < t_ax) { t_ax = ms; best_ax = c; }
+    sw = sem::sw_tile_ok(d.P, c) ? c : 1;
+    if (sw == c && time_launches(h, fs, 5, &ms) == SEM_OK && ms < t_sw) { t_sw = ms; best_sw = c; }
   }
-  d.epb_ax = best_ax;
-  d.epb_sw = best_sw;
+  ax = best_ax;
+  sw = best_sw;
   h->invalidate();
   if (epb_ax_host) *epb_ax_host = best_ax;
   if (epb_sw_host) *epb_sw_host = best_sw;

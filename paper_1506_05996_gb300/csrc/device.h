@@ -51,6 +51,7 @@ struct PcgState {
 
 struct DevCsr {
   int n = 0, nnz = 0;
+  int lanes = 32;              // lanes per row in the AMG row kernels (4, 8, 16 or 32)
   int* ptr = nullptr;
   int* col = nullptr;
   double* val = nullptr;
@@ -73,7 +74,8 @@ struct DevProblem {
   bool pfp32 = false;               // preconditioner in FP32 (with fp32, or alone: FP64 operator)
   int sw_reserve_sms = 0;           // > 0: the patch-solve grid leaves this many SMs' worth of
                                     // slots free (for the coarse branch running beside it)
-  int epb_ax = 1, epb_sw = 1;       // elements per CTA of the operator / patch-solve kernels
+  int epb_ax = 1, epb_sw = 1;       // elements per CTA of the FP64 operator / patch-solve kernels
+  int epb_ax32 = 1, epb_sw32 = 1;   // the same for the FP32 kernels (tuned separately)
                                     // (tile shapes picked by the autotuner; 1, 2, 4 or 8)
   const float* geo32 = nullptr;     // stored factors rounded to FP32 (same layout as geo)
   // tables

@@ -215,7 +215,7 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgStat
 
 template <int p, typename T, typename TX>
 cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
-  switch (d.epb_ax) {
+  switch (sizeof(T) == 4 ? d.epb_ax32 : d.epb_ax) {
     case 2: return launch_ax_epb<p, T, TX, 2>(d, x, wl, st, s);
     case 4: return launch_ax_epb<p, T, TX, 4>(d, x, wl, st, s);
     case 8: return launch_ax_epb<p, T, TX, 8>(d, x, wl, st, s);

@@ -258,7 +258,7 @@ cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgStat
 
 template <int P, typename T, typename TR>
 cudaError_t launch_sw_P(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
-  switch (d.epb_sw) {
+  switch (sizeof(T) == 4 ? d.epb_sw32 : d.epb_sw) {
     case 2: return launch_sw_epb<P, T, TR, 2>(d, r, wp, st, s);
     case 4: return launch_sw_epb<P, T, TR, 4>(d, r, wp, st, s);
     case 8: return launch_sw_epb<P, T, TR, 8>(d, r, wp, st, s);

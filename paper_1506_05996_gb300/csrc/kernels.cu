@@ -133,62 +133,81 @@ __global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
   }
 }
 
-// AMG kernels. Sparse rows are handled by one warp each (lanes stride over the
-// row, then a fixed shuffle tree), so long coarse-level rows do not serialise.
+// AMG kernels. Sparse rows are handled by groups of LANES lanes (4..32, a power of two
+// chosen per matrix from its mean row length): the lanes stride over the row, then a fixed
+// shuffle tree. Short fine-level rows (27 entries) thus take 8 lanes instead of a warp,
+// and long coarse-level rows do not serialise. The row loop steps a warp at a time, so
+// every lane reaches the shuffles.
 __global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const double* __restrict__ b,
                                    double* __restrict__ x, double omega, const PcgState* st) {
   if (stopped(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = omega * dinv[i] * b[i];
 }
 
-__device__ __forceinline__ double warp_row_dot(const DevCsr& A, int row, const double* __restrict__ x, int lane) {
+template <int LANES>
+__device__ __forceinline__ double group_row_dot(const DevCsr& A, int row, bool ok, const double* __restrict__ x,
+                                                int lane) {
   double s = 0.0;
-  for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += 32) s += A.val[q] * x[A.col[q]];
+  if (ok)
+    for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += LANES) s += A.val[q] * x[A.col[q]];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
-#define WARP_ROWS(nrows)                                                              \
-  const int lane = threadIdx.x & 31;                                                  \
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < (nrows); i += (gridDim.x * blockDim.x) >> 5)
+#define GROUP_ROWS(nrows)                                                                               \
+  const int lane = threadIdx.x & (LANES - 1), sub = (threadIdx.x & 31) / LANES;                         \
+  for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES); w0 < (nrows);          \
+       w0 += ((gridDim.x * blockDim.x) >> 5) * (32 / LANES))
 
+template <int LANES>
 __global__ void amg_resid_kernel(DevCsr A, const double* __restrict__ b, const double* __restrict__ x,
                                  double* __restrict__ t, const PcgState* st) {
   if (stopped(st)) return;
-  WARP_ROWS(A.n) {
-    const double s = warp_row_dot(A, i, x, lane);
-    if (lane == 0) t[i] = b[i] - s;
+  GROUP_ROWS(A.n) {
+    const int i = w0 + sub;
+    const bool ok = i < A.n;
+    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
+    if (ok && lane == 0) t[i] = b[i] - s;
   }
 }
 
+template <int LANES>
 __global__ void amg_spmv_kernel(DevCsr A, const double* __restrict__ x, double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
-  WARP_ROWS(A.n) {
-    const double s = warp_row_dot(A, i, x, lane);
-    if (lane == 0) y[i] = s;
+  GROUP_ROWS(A.n) {
+    const int i = w0 + sub;
+    const bool ok = i < A.n;
+    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
+    if (ok && lane == 0) y[i] = s;
   }
 }
 
+template <int LANES>
 __global__ void amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc, double* __restrict__ x,
                                        const PcgState* st) {
   if (stopped(st)) return;
-  WARP_ROWS(P.n) {
-    const double s = warp_row_dot(P, i, xc, lane);
-    if (lane == 0) x[i] = x[i] + s;
+  GROUP_ROWS(P.n) {
+    const int i = w0 + sub;
+    const bool ok = i < P.n;
+    const double s = group_row_dot<LANES>(P, i, ok, xc, lane);
+    if (ok && lane == 0) x[i] = x[i] + s;
   }
 }
 
+template <int LANES>
 __global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv, const double* __restrict__ b,
                                        const double* __restrict__ x, double* __restrict__ xout, double omega,
                                        const PcgState* st) {
   if (stopped(st)) return;
-  WARP_ROWS(A.n) {
-    const double s = warp_row_dot(A, i, x, lane);
-    if (lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
+  GROUP_ROWS(A.n) {
+    const int i = w0 + sub;
+    const bool ok = i < A.n;
+    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
+    if (ok && lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
   }
 }
-#undef WARP_ROWS
+#undef GROUP_ROWS
 
 __global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
@@ -645,6 +664,18 @@ inline int grid_for(int n, int block, int cap) {
   return g < 1 ? 1 : (g > cap ? cap : g);
 }
 
+// Launches a row-group AMG kernel with the lane count of matrix M, one group per row.
+#define ROWS_LAUNCH(KERN, M, ...)                                                                  \
+  do {                                                                                             \
+    const int rows_ = (M).n;                                                                       \
+    switch ((M).lanes) {                                                                           \
+      case 4: KERN<4><<<grid_for(4 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;          \
+      case 8: KERN<8><<<grid_for(8 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;          \
+      case 16: KERN<16><<<grid_for(16 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;       \
+      default: KERN<32><<<grid_for(32 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;       \
+    }                                                                                              \
+  } while (0)
+
 constexpr double kOmega = 2.0 / 3.0;
 constexpr int kCycles = 3;
 
@@ -656,21 +687,21 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
     return cudaGetLastError();
   }
   const DevAmgLevel& L = d.levels[level];
-  const int n = L.A.n, gb = grid_for(n, 256, 4096), gw = grid_for(32 * n, 256, 8192);
+  const int n = L.A.n, gb = grid_for(n, 256, 4096);
   amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
   ++g_kernel_launches;
-  amg_resid_kernel<<<gw, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  ROWS_LAUNCH(amg_resid_kernel, L.A, L.A, b, L.x, L.t, st);
   ++g_kernel_launches;
   double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
   double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
   const int nc = L.R.n;
-  amg_spmv_kernel<<<grid_for(32 * nc, 256, 8192), 256, 0, s>>>(L.R, L.t, bc, st);
+  ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, bc, st);
   ++g_kernel_launches;
   cudaError_t err = vcycle(d, level + 1, bc, xc, st, s);
   if (err != cudaSuccess) return err;
-  amg_prolong_add_kernel<<<gw, 256, 0, s>>>(L.P, xc, L.x, st);
+  ROWS_LAUNCH(amg_prolong_add_kernel, L.P, L.P, xc, L.x, st);
   ++g_kernel_launches;
-  amg_jacobi_post_kernel<<<gw, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  ROWS_LAUNCH(amg_jacobi_post_kernel, L.A, L.A, L.dinv, b, L.x, out, kOmega, st);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -684,38 +715,38 @@ cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out,
     return cudaGetLastError();
   }
   const DevAmgLevel& L = d.levels[level];
-  const int n = L.A.n, gb = grid_for(n, 256, 4096), gw = grid_for(32 * n, 256, 8192);
+  const int n = L.A.n, gb = grid_for(n, 256, 4096);
   amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
-  amg_resid_kernel<<<gw, 256, 0, s>>>(L.A, b, L.x, L.t, st);
+  ROWS_LAUNCH(amg_resid_kernel, L.A, L.A, b, L.x, L.t, st);
   g_kernel_launches += 2;
   const int nc = L.R.n;
   cudaError_t err;
   double* ec;
   if (level + 1 == d.nlevels) {
-    amg_spmv_kernel<<<grid_for(32 * nc, 256, 8192), 256, 0, s>>>(L.R, L.t, d.cb, st);
+    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, d.cb, st);
     ++g_kernel_launches;
     err = kcycle(d, level + 1, d.cb, d.cx, st, s);   // the dense level: exact
     if (err != cudaSuccess) return err;
     ec = d.cx;
   } else {
     const DevAmgLevel& N = d.levels[level + 1];
-    const int gbc = grid_for(nc, 256, 4096), gwc = grid_for(32 * nc, 256, 8192);
-    amg_spmv_kernel<<<gwc, 256, 0, s>>>(L.R, L.t, N.b, st);
+    const int gbc = grid_for(nc, 256, 4096);
+    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, N.b, st);
     ++g_kernel_launches;
     if ((err = kcycle(d, level + 1, N.b, N.c1, st, s)) != cudaSuccess) return err;
-    amg_spmv_kernel<<<gwc, 256, 0, s>>>(N.A, N.c1, N.v1, st);
+    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c1, N.v1, st);
     kc_dots1_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c1, N.v1, N.b, N.scal, st);
     kc_r2_kernel<<<gbc, 256, 0, s>>>(nc, N.v1, N.scal, N.b, st);
     g_kernel_launches += 3;
     if ((err = kcycle(d, level + 1, N.b, N.c2, st, s)) != cudaSuccess) return err;
-    amg_spmv_kernel<<<gwc, 256, 0, s>>>(N.A, N.c2, N.v2, st);
+    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c2, N.v2, st);
     kc_dots2_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c2, N.v1, N.v2, N.b, N.scal, st);
     kc_combine_kernel<<<gbc, 256, 0, s>>>(nc, N.c1, N.c2, N.scal, N.y, st);
     g_kernel_launches += 3;
     ec = N.y;
   }
-  amg_prolong_add_kernel<<<gw, 256, 0, s>>>(L.P, ec, L.x, st);
-  amg_jacobi_post_kernel<<<gw, 256, 0, s>>>(L.A, L.dinv, b, L.x, out, kOmega, st);
+  ROWS_LAUNCH(amg_prolong_add_kernel, L.P, L.P, ec, L.x, st);
+  ROWS_LAUNCH(amg_jacobi_post_kernel, L.A, L.A, L.dinv, b, L.x, out, kOmega, st);
   g_kernel_launches += 2;
   return cudaGetLastError();
 }
@@ -784,9 +815,9 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
     return cudaGetLastError();
   }
   const DevCsr& A0 = d.levels[0].A;
-  const int gb = grid_for(A0.n, 256, 4096), gw = grid_for(32 * A0.n, 256, 8192);
+  const int gb = grid_for(A0.n, 256, 4096);
   for (int c = 1; c < kCycles; ++c) {
-    amg_resid_kernel<<<gw, 256, 0, s>>>(A0, d.Rc, d.Zc, d.cres, st);
+    ROWS_LAUNCH(amg_resid_kernel, A0, A0, d.Rc, d.Zc, d.cres, st);
     ++g_kernel_launches;
     err = vcycle(d, 0, d.cres, d.ctmp, st, s);
     if (err != cudaSuccess) return err;
