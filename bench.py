@@ -231,16 +231,42 @@ class Ranks:
             self.dist.destroy_process_group()
 
 
-def schwarz_flops(n, ne):
-    """Six (n+3)^4 tensor contractions (FMA = 2 flops) plus the paper's 15 (n+3)^3 term."""
+def schwarz_flops_paper(n, ne):
+    """The paper's O_P count (Sec. 4.2) with an FMA as 2 flops: six unfolded (n+3)^4
+    contractions plus 15 (n+3)^3."""
     P = n + 3
     return ne * (12.0 * P ** 4 + 15.0 * P ** 3)
 
 
-def ax_flops(n, ne):
+def ax_flops_paper(n, ne):
     """O_R = N_E [12 (n+1)^4 + 18 (n+1)^3] (Sec. 3.1)."""
     p = n + 1
     return ne * (12.0 * p ** 4 + 18.0 * p ** 3)
+
+
+def schwarz_flops(n, ne):
+    """Flops the patch kernel's algorithm executes per launch (FMA = 2, add or multiply = 1):
+    per 1D line of P = n+3 nodes, the even/odd folded forward contraction takes 2H + 2HP +
+    (P odd) NE and the backward one H (2P + 2) + (P odd) 2 NE, H = P // 2, NE = P - H;
+    3 P^2 lines each way, then P^3 scalings by the stored inverse diagonal and P^3 by
+    8/(hx hy hz)."""
+    P = n + 3
+    H, odd = P // 2, P % 2
+    NE = P - H
+    fwd = 2 * H + 2 * H * P + odd * NE
+    bwd = H * (2 * P + 2) + odd * 2 * NE
+    return ne * (3.0 * P * P * (fwd + bwd) + 2.0 * P ** 3)
+
+
+def ax_flops(n, ne):
+    """Flops the operator kernel executes per launch (FMA = 2): per 1D line of p = n+1 nodes
+    the folded D contraction takes 2H + H (4H + 2) + (p odd) 3H, H = p // 2, with 6 p^2
+    lines (3 gradients, 3 divergences); per node 15 for G grad u, 2 for lambda m u and 3 for
+    the sums of the three divergence terms."""
+    p = n + 1
+    H, odd = p // 2, p % 2
+    line = 2 * H + H * (4 * H + 2) + odd * 3 * H
+    return ne * (6.0 * p * p * line + 20.0 * p ** 3)
 
 
 def run_gpu(args):
@@ -333,9 +359,14 @@ def run_gpu(args):
     # DRAM bytes per launch from one ncu capture of the same kernel at 24^3 hexes, scaled
     # by the element count (the traffic is per element); null for other kernels
     traffic = {"schwarz_local": 169.2e6 * NE / 13824, "ax_local": 518.0e6 * NE / 13824}.get(kern)
+    paper_flops = {"schwarz_local": schwarz_flops_paper, "ax_local": ax_flops_paper}.get(kern)
     roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
             "peak_source": "FP64 FMA loop measured on this pool (nominal 1.25 TFLOP/s)",
             "achieved": (flops / (avg_ms * 1e-3) / 1e12) if flops else None,
+            "flops_per_launch": flops,
+            "flops_note": "executed by the kernel's folded algorithm, FMA = 2 (the paper's unfolded "
+                          "O_P / O_R counts are in paper_equivalent_tflops)",
+            "paper_equivalent_tflops": (paper_flops(ORDER, NE) / (avg_ms * 1e-3) / 1e12) if paper_flops else None,
             "avg_launch_ms": avg_ms, "launches": nl, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read+write of the kernel at 24^3 hexes (profiles/"
                               "hot_kernels_24cube_n7.md) scaled by the element count",
@@ -387,6 +418,7 @@ def run_gpu(args):
         k_bytes = 9 * G + 4 * L + geo_bytes + fb * L
         key = geom + ("" if prec == "fp64" else "_fp32")
         ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
+                   "paper_equivalent_tflops_ax_local": ax_flops_paper(ORDER, NE) / (kms * 1e-3) / 1e12,
                    "ax_local_frac_hbm_roofline": k_bytes / (kms * 1e-3) / 1e9 / hbm_peak,
                    "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
                    "bytes_per_dof": alg_bytes / G,

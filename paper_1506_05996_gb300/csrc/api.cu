@@ -167,6 +167,14 @@ int update_free_sides(sem_t* h) {
   CK(cudaMemcpyAsync(h->pvar, fs.data(), fs.size(), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->d.pvar = any ? h->pvar : nullptr;
+  // the patch solves' diagonals depend on the pencils of each element
+  CK(sem::launch_sw_diag(h->d, h->swd, h->sws, h->stream));
+  CK(sem::launch_sw_diag_f32(h->d, h->swd32, h->sws32, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->d.swd = h->swd;
+  h->d.sws = h->sws;
+  h->d.swd32 = h->swd32;
+  h->d.sws32 = h->sws32;
   h->invalidate();
   return SEM_OK;
 }
@@ -364,7 +372,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   }
   sem::DevProblem& d = h->d;
   d.n = n; d.p = p; d.P = P;
-  d.ne = (int)nb.ne; d.G = (int)nb.G; d.nv = (int)nb.nv;
+  d.ne = (int)nb.ne; d.G = (int)nb.G; d.nv = (int)nb.nv; d.Gi = (int)nb.Gi;
   d.lambda = lambda;
   d.recompute = (flags & SEM_GEOM_RECOMPUTE) != 0;
   auto& A = h->allocs;
@@ -417,6 +425,10 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->upload(&h->mask, h->mask_host, A));
   d.mask = h->mask;
   CK(h->alloc(&h->pvar, (size_t)nb.ne, A));
+  CK(h->alloc(&h->swd, (size_t)(nb.ne * P3), A));
+  CK(h->alloc(&h->swd32, (size_t)(nb.ne * P3), A));
+  CK(h->alloc(&h->sws, (size_t)nb.ne, A));
+  CK(h->alloc(&h->sws32, (size_t)nb.ne, A));
   if (int rc = update_free_sides(h)) return rc;
   CK(h->alloc(&d.wl, (size_t)(nb.ne * p3), A));
   CK(h->alloc(&d.wp, (size_t)(nb.ne * P3), A));

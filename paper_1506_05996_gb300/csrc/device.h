@@ -68,6 +68,8 @@ struct DevAmgLevel {
 struct DevProblem {
   int n = 0, p = 0, P = 0;
   int ne = 0, G = 0, nv = 0, nfree = 0;
+  int Gi = 0;                       // DOFs 0..Gi-1 are element interiors, numbered e m^3 + a + m(b + m c)
+                                    // for local node (a+1, b+1, c+1), m = n-1 (0: no such numbering)
   double lambda = 0.0;
   bool recompute = false;
   bool fp32 = false;                // operator and patch solves in FP32 (mixed path)
@@ -100,6 +102,12 @@ struct DevProblem {
   const double* Sv = nullptr;       // [3][P*P] pencils with a free low / high / both side(s)
   const double* evv = nullptr;      // [3][P]
   const double* hbox = nullptr;     // ne*3
+  // per element patch, from hbox, the pencil eigenvalues and lambda (sw_diag_kernel):
+  // the inverted diagonal of Eq. z at [e][(b + P c) + P^2 a] and the scale 8/(hx hy hz)
+  const double* swd = nullptr;
+  const float* swd32 = nullptr;
+  const double* sws = nullptr;
+  const float* sws32 = nullptr;
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* Btab32 = nullptr;    // the same in FP32
   const int* ecv = nullptr;
@@ -171,6 +179,8 @@ cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float
                                      cudaStream_t s);
 cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
                                           cudaStream_t s);
+cudaError_t launch_sw_diag(const DevProblem& d, double* dg, double* sc, cudaStream_t s);
+cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, float* sc, cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);

@@ -220,10 +220,14 @@ std::string number_mesh(const double* xyz, int64_t nv, const int64_t* hex, int64
   const int64_t Gprov = off_int + ne * m1 * m1 * m1;
   if (Gprov >= (int64_t)1 << 31 || ne * p3 >= (int64_t)1 << 31) return "mesh too large for 32-bit indices";
 
-  // provisional ids by entity, then first-touch renumbering in element order
-  std::vector<int> newid(Gprov, -1);
+  // element-interior nodes first, element by element in local order (DOF e m^3 + a +
+  // m (b + m c) for local node (a+1, b+1, c+1)), so that their gathers need no index
+  // table; then the shared nodes by provisional id per entity, renumbered by first touch
+  // in element order
+  const int64_t Gi = ne * m1 * m1 * m1;
+  std::vector<int> newid(off_int, -1);
   out.l2g.assign(ne * p3, -1);
-  int next = 0;
+  int next = (int)Gi;
   std::vector<int64_t> prov(p3);
   for (int64_t e = 0; e < ne; ++e) {
     const int* hv = &out.hexv[8 * e];
@@ -263,7 +267,8 @@ std::string number_mesh(const double* xyz, int64_t nv, const int64_t* hex, int64
             to_canonical(fr, n, idx[u], idx[v], cs, ct);
             id = off_face + (int64_t)elem_face[6 * e + 2 * d + s] * m1 * m1 + (cs - 1) * m1 + (ct - 1);
           } else {
-            id = off_int + e * m1 * m1 * m1 + ((i - 1) + m1 * ((j - 1) + m1 * (k - 1)));
+            out.l2g[e * p3 + i + p * (j + p * k)] = (int)(e * m1 * m1 * m1 + ((i - 1) + m1 * ((j - 1) + m1 * (k - 1))));
+            continue;
           }
           int l = i + p * (j + p * k);
           if (newid[id] < 0) newid[id] = next++;
@@ -271,6 +276,7 @@ std::string number_mesh(const double* xyz, int64_t nv, const int64_t* hex, int64
         }
   }
   out.G = next;
+  out.Gi = Gi;
 
   // vertex DOFs, face neighbours, boundary nodes
   out.vert_dof.assign(nv, -1);

@@ -29,6 +29,7 @@ struct Csr {
 struct Numbering {
   int n = 0, p = 0;
   int64_t ne = 0, nv = 0, G = 0;
+  int64_t Gi = 0;                    // DOFs 0..Gi-1: element interiors, e (n-1)^3 + local order
   std::vector<int64_t> elem_perm;    // library element e -> input element elem_perm[e]
   std::vector<int> hexv;             // [ne][8] input vertex ids, library element order
   std::vector<int> l2g;              // [ne * p^3], local node i + p(j + p k)

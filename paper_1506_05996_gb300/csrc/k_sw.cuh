@@ -104,13 +104,45 @@ __device__ __forceinline__ void axis_bwd(int v, const T* sS, const T* sSv, const
   else plain_bwd<P, T>(sSv + (v - 1) * P * P, t, x);
 }
 
+// Per-element tables of the patch solve, in the kernel's precision.
+template <typename T> __device__ __forceinline__ const T* swd_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* swd_of<double>(const DevProblem& d) { return d.swd; }
+template <> __device__ __forceinline__ const float* swd_of<float>(const DevProblem& d) { return d.swd32; }
+template <typename T> __device__ __forceinline__ const T* sws_of(const DevProblem& d);
+template <> __device__ __forceinline__ const double* sws_of<double>(const DevProblem& d) { return d.sws; }
+template <> __device__ __forceinline__ const float* sws_of<float>(const DevProblem& d) { return d.sws32; }
+
+// The diagonal of the fast diagonalisation (Eq. z) of every element patch, inverted, and
+// its scale 8/(hx hy hz): dg[e][(b + P c) + P^2 a] = 1 / (4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2)
+// + lambda) with each axis' pencil eigenvalues. One CTA of P*P threads per element; run once
+// per handle (and again when the Dirichlet set changes the pencils), so that the patch
+// kernels spend no divisions on it.
+template <int P, typename T, bool VAR>
+__global__ void __launch_bounds__(P * P) sw_diag_kernel(const DevProblem d, T* __restrict__ dg, T* __restrict__ sc) {
+  constexpr int P2 = P * P, P3 = P * P * P;
+  const int e = blockIdx.x, tx = threadIdx.x, x = tx % P, y = tx / P;
+  const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
+  const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
+  if (tx == 0) sc[e] = (T)(8.0 / (hxd * hyd * hzd));
+  const int vb = VAR ? d.pvar[e] : 0;
+  const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
+  const double* evx = vx ? d.evv + (vx - 1) * P : d.ev;
+  const double* evy = vy ? d.evv + (vy - 1) * P : d.ev;
+  const double* evz = vz ? d.evv + (vz - 1) * P : d.ev;
+  const T four = 4, lam = (T)d.lambda;
+  const T lbc = (T)evy[x] * ihy2 + (T)evz[y] * ihz2;
+  T* out = dg + (size_t)e * P3 + tx;
+#pragma unroll
+  for (int a = 0; a < P; ++a) out[a * P2] = recip(four * ((T)evx[a] * ihx2 + lbc) + lam);
+}
+
 // One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
 // extended box in each of the six tensor contractions of Eq. z:
 //   t = (S^T x S^T x S^T) r',  t /= 4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2) + lambda,
 //   z = (S x S x S) t,        r' = 8/(hx hy hz) r.
 template <int P, typename T, int EPB>
 constexpr int sw_smem_bytes() {
-  return (int)((4 * P * P + 4 * P + EPB * 2 * P * P * P) * sizeof(T));
+  return (int)((4 * P * P + EPB * 2 * P * P * P) * sizeof(T));
 }
 
 // VAR: some element sides lie on a natural boundary (d.pvar != null), so each axis picks its
@@ -120,17 +152,14 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
                                                                     T* __restrict__ wp, const PcgState* st) {
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
-  __shared__ T sS[P2], sev[P], sSv[3 * P2], sevv[3 * P], s1_all[EPB * P3], s2_all[EPB * P3];
+  __shared__ T sS[P2], sSv[3 * P2], s1_all[EPB * P3], s2_all[EPB * P3];
   const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
   T* s1 = s1_all + grp * P3;
   T* s2 = s2_all + grp * P3;
   const int x = tx % P, y = tx / P;
   if (threadIdx.x < P2) sS[threadIdx.x] = (T)d.S[threadIdx.x];
-  if (threadIdx.x < P) sev[threadIdx.x] = (T)d.ev[threadIdx.x];
-  if (VAR) {
+  if (VAR)
     for (int q = threadIdx.x; q < 3 * P2; q += blockDim.x) sSv[q] = (T)d.Sv[q];
-    for (int q = threadIdx.x; q < 3 * P; q += blockDim.x) sevv[q] = (T)d.evv[q];
-  }
   // element groups strided over the grid (the grid may be capped below the group count to
   // leave SMs to the concurrent coarse branch); every thread of a CTA runs the same rounds
   const int ngroups = (d.ne + EPB - 1) / EPB;
@@ -138,9 +167,7 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const int e_raw = blk * EPB + grp;
   const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
   const int e = active ? e_raw : d.ne - 1;
-  const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
-  const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
-  const T scale = (T)(8.0 / (hxd * hyd * hzd));
+  const T scale = sws_of<T>(d)[e];
   // pencil variant per axis (bit 2a: free low side, bit 2a+1: free high side)
   const int vb = VAR ? d.pvar[e] : 0;
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
@@ -172,13 +199,9 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
   axis_fwd<P, T, VAR>(vx, sS, sSv, col, out);
   {
-    const T four = 4, lam = (T)d.lambda;
-    const T* evx = vx ? sevv + (vx - 1) * P : sev;
-    const T* evy = vy ? sevv + (vy - 1) * P : sev;
-    const T* evz = vz ? sevv + (vz - 1) * P : sev;
-    const T lbc = evy[x] * ihy2 + evz[y] * ihz2;
+    const T* dge = swd_of<T>(d) + (size_t)e * P3 + tx;
 #pragma unroll
-    for (int a = 0; a < P; ++a) out[a] = out[a] * recip(four * (evx[a] * ihx2 + lbc) + lam);
+    for (int a = 0; a < P; ++a) out[a] = out[a] * dge[a * P2];
   }
   axis_bwd<P, T, VAR>(vx, sS, sSv, out, col);
 #pragma unroll
@@ -263,6 +286,29 @@ cudaError_t launch_sw_P(const DevProblem& d, const TR* r, T* wp, const PcgState*
     case 4: return launch_sw_epb<P, T, TR, 4>(d, r, wp, st, s);
     case 8: return launch_sw_epb<P, T, TR, 8>(d, r, wp, st, s);
     default: return launch_sw_epb<P, T, TR, 1>(d, r, wp, st, s);
+  }
+}
+
+template <int P, typename T>
+cudaError_t launch_sw_diag_P(const DevProblem& d, T* dg, T* sc, cudaStream_t s) {
+  if (d.pvar != nullptr) sw_diag_kernel<P, T, true><<<d.ne, P * P, 0, s>>>(d, dg, sc);
+  else sw_diag_kernel<P, T, false><<<d.ne, P * P, 0, s>>>(d, dg, sc);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sw_diag_t(const DevProblem& d, T* dg, T* sc, cudaStream_t s) {
+  if (d.ne == 0) return cudaSuccess;
+  switch (d.P) {
+    case 5: return launch_sw_diag_P<5, T>(d, dg, sc, s);
+    case 6: return launch_sw_diag_P<6, T>(d, dg, sc, s);
+    case 7: return launch_sw_diag_P<7, T>(d, dg, sc, s);
+    case 8: return launch_sw_diag_P<8, T>(d, dg, sc, s);
+    case 9: return launch_sw_diag_P<9, T>(d, dg, sc, s);
+    case 10: return launch_sw_diag_P<10, T>(d, dg, sc, s);
+    case 11: return launch_sw_diag_P<11, T>(d, dg, sc, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -138,6 +138,28 @@ template <typename T> __device__ __forceinline__ const T* geo_of(const DevProble
 template <> __device__ __forceinline__ const double* geo_of<double>(const DevProblem& d) { return d.geo; }
 template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
 
+// Local index of element-interior DOF g < d.Gi: the numbering puts the (n-1)^3 interior
+// nodes of each element first, element by element, in local order.
+__device__ __forceinline__ int interior_local(const DevProblem& d, int g) {
+  const int p = d.p, m = p - 2, m3 = m * m * m;
+  const int e = g / m3;
+  int r = g - e * m3;
+  const int a = r % m;
+  r /= m;
+  const int b = r % m, c = r / m;
+  return e * p * p * p + (a + 1) + p * ((b + 1) + p * (c + 1));
+}
+
+// Sum of the local copies of DOF g in wl (Eq. gather): one copy at a computed index for an
+// interior DOF, the g2l CSR in ascending local order otherwise.
+template <typename T>
+__device__ __forceinline__ T gather_dof(const DevProblem& d, const T* __restrict__ wl, int g) {
+  if (g < d.Gi) return wl[interior_local(d, g)];
+  T s = 0;
+  for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+  return s;
+}
+
 
 }  // namespace
 }  // namespace sem

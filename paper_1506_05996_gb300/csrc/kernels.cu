@@ -58,7 +58,7 @@ __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
     T s = 0;
-    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    s = gather_dof(d, wl, g);
     y[g] = (double)s;
   }
 }
@@ -66,7 +66,7 @@ __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__
 __global__ void gather_plain_kernel(const DevProblem d, const double* __restrict__ wl, double* __restrict__ y) {
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    s = gather_dof(d, wl, g);
     y[g] = s;
   }
 }
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevPr
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     T s = 0;
     if (!d.mask[g])
-      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+      s = gather_dof(d, wl, g);
     const double sd = (double)s;
     f[g] = sd;
     dot += p[g] * sd;
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem
     double res = 0.0;
     if (!d.mask[g]) {
       double s = 0.0;
-      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+      s = gather_dof(d, wl, g);
       res = b[g] - s;
     }
     r[g] = res;
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(kVecBlock) residual_of_kernel(const DevProblem
     double res = 0.0;
     if (!d.mask[g]) {
       T s = 0;
-      for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+      s = gather_dof(d, wl, g);
       res = v[g] - (double)s;
     }
     out[g] = res;
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kVecBlock) heat_rhs_kernel(const DevProblem d,
     if (!d.mask[i]) {
       const double bf = mN[i] * (d.lambda * u_prev[i] + g[i]);
       double s = 0.0;
-      for (int q = d.g2l_off[i]; q < d.g2l_off[i + 1]; ++q) s += wl[d.g2l_idx[q]];
+      s = gather_dof(d, wl, i);
       res = bf - s;
       v[0] += bf * bf;
       v[1] += res * res;
@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProbl
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) continue;
     double s = 0.0;
-    for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
+    s = gather_dof(d, wl, g);
     const double res = b[g] - s;
     dot += res * res;
   }

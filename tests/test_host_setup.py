@@ -46,6 +46,13 @@ def test_numbering_patch_and_tables(lib, E, n, a, seed, patch):
     l2g = H.l2g.reshape(H.ne, p, p, p)          # [e, k, j, i]
     ref_l2g = ref.l2g[H.elem_perm].transpose(0, 3, 2, 1)
     np.testing.assert_array_equal(inv[l2g], ref_l2g)
+    # element-interior nodes come first: DOF e m^3 + a + m (b + m c) at local (a+1, b+1, c+1)
+    m = n - 1
+    interior = l2g[:, 1:n, 1:n, 1:n]             # [e, c, b, a]
+    np.testing.assert_array_equal(interior.reshape(-1), np.arange(H.ne * m ** 3))
+    shared = np.ones((p, p, p), dtype=bool)
+    shared[1:n, 1:n, 1:n] = False
+    assert l2g[:, shared].min() == H.ne * m ** 3 and l2g[:, shared].max() == H.G - 1
     # patch tables
     ip = H.ip.reshape(H.ne, P, P, P)
     ref_ip = ref.ip[H.elem_perm].transpose(0, 3, 2, 1)
