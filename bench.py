@@ -358,7 +358,7 @@ def run_gpu(args):
         flops = None
     # DRAM bytes per launch from one ncu capture of the same kernel at 24^3 hexes, scaled
     # by the element count (the traffic is per element); null for other kernels
-    traffic = {"schwarz_local": 169.2e6 * NE / 13824, "ax_local": 518.0e6 * NE / 13824}.get(kern)
+    traffic = {"schwarz_local": 292.5e6 * NE / 13824, "ax_local": 516.0e6 * NE / 13824}.get(kern)
     paper_flops = {"schwarz_local": schwarz_flops_paper, "ax_local": ax_flops_paper}.get(kern)
     roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
             "peak_source": "FP64 FMA loop measured on this pool (nominal 1.25 TFLOP/s)",
@@ -542,20 +542,29 @@ def run_gpu(args):
 
 
 def run_kernel_case(E):
-    """A few applies of each hot kernel, FP64 then FP32, on an E^3-hex, n = 7 mesh."""
+    """A few applies of each hot kernel, FP64 then FP32, on an E^3-hex, n = 7 mesh, with the
+    tile shapes the autotuner picks; the applies sit in the NVTX range "kernels" (for
+    ncu --nvtx --nvtx-include kernels/), the tuning launches outside it."""
     import torch
     from synth import lattice_hex_mesh
     from paper_1506_05996_gb300 import sem as S
     mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
     prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
     x = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
+    tiles = {}
+    for prec in ("fp32", "fp64"):
+        prob.set_precision(prec)
+        tiles[prec] = S.sem_autotune(prob.h)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("kernels")
     for prec in ("fp64", "fp32"):
         prob.set_precision(prec)
         for _ in range(2):
             prob.apply_A(x)
             prob.apply_P(x, "two-scale")
     torch.cuda.synchronize()
-    print(json.dumps({"kernel_case": E, "n_dof": prob.n_dof}))
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"kernel_case": E, "n_dof": prob.n_dof, "tiles": tiles}))
     prob.close()
 
 
