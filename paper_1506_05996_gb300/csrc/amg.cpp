@@ -112,6 +112,29 @@ Csr aggregation_matrix(const std::vector<int>& agg, int na) {
   return T;
 }
 
+// A with every entry a_ij replaced by f(i, j, a_ij) (same pattern).
+template <class F>
+Csr map_entries(const Csr& A, F f) {
+  Csr B = A;
+  for (int i = 0; i < A.n; ++i)
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) B.val[q] = f(i, A.col[q], A.val[q]);
+  return B;
+}
+
+// M, N, Q of a smoothed level (see AmgLevel). Every row of A holds its diagonal.
+void fused_cycle_matrices(AmgLevel& lv) {
+  const double w = kAmgOmega;
+  const std::vector<double>& di = lv.dinv;
+  // I - w A D^-1 and I - w D^-1 A
+  Csr Bm = map_entries(lv.A, [&](int i, int j, double a) { return (i == j ? 1.0 : 0.0) - w * a * di[j]; });
+  Csr Cm = map_entries(lv.A, [&](int i, int j, double a) { return (i == j ? 1.0 : 0.0) - w * di[i] * a; });
+  lv.M = spgemm(lv.R, Bm);
+  lv.N = map_entries(lv.A, [&](int i, int j, double a) {
+    return (i == j ? 2.0 * w * di[i] : 0.0) - w * w * di[i] * a * di[j];
+  });
+  lv.Q = spgemm(Cm, lv.P);
+}
+
 // Runs f(i) for i in [0, n) on the host cores; each i is done by exactly one thread.
 template <class F>
 void parallel_for(int n, F f) {
@@ -196,6 +219,7 @@ std::string build_amg(const Csr& A0, Amg& out, int kind) {
     lv.R = transpose(P);
     lv.dinv.resize(A.n);
     for (int i = 0; i < A.n; ++i) lv.dinv[i] = 1.0 / d[i];
+    fused_cycle_matrices(lv);
     Csr Anext = spgemm(lv.R, spgemm(A, P));
     out.levels.push_back(std::move(lv));
     A = std::move(Anext);

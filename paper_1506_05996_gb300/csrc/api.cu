@@ -127,6 +127,14 @@ int build_coarse(sem_t* h) {
     CK(up_csr(L.A, D.A));
     CK(up_csr(L.P, D.P));
     CK(up_csr(L.R, D.R));
+    if (!L.M.val.empty()) {
+      CK(up_csr(L.M, D.M));
+      CK(up_csr(L.N, D.N));
+      CK(up_csr(L.Q, D.Q));
+      const int64_t nnz = (int64_t)L.N.val.size() + (int64_t)L.Q.val.size();
+      D.up_lanes = 4;
+      while (D.up_lanes < 32 && 4 * D.up_lanes * (int64_t)L.N.n < nnz) D.up_lanes *= 2;
+    }
     CK(h->upload(&D.dinv, L.dinv, h->coarse_allocs));
     CK(h->alloc(&D.b, L.A.n, h->coarse_allocs));
     CK(h->alloc(&D.x, L.A.n, h->coarse_allocs));

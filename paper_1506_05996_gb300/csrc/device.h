@@ -59,6 +59,8 @@ struct DevCsr {
 
 struct DevAmgLevel {
   DevCsr A, P, R;
+  DevCsr M, N, Q;              // the level's V(1,1) cycle as b_c = M b, x = N b + Q x_c (V-cycle kind)
+  int up_lanes = 32;           // lanes per row of the N b + Q x_c kernel
   double* dinv = nullptr;
   double *b = nullptr, *x = nullptr, *t = nullptr, *y = nullptr;   // rhs, iterate, residual, output (size A.n)
   // K-cycle: the two inner directions c1, c2, their images A c1, A c2, and 8 scalars

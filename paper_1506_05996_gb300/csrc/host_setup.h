@@ -84,7 +84,13 @@ void jacobi_eigen(int n, std::vector<double> A, std::vector<double>& evals, std:
 struct AmgLevel {
   Csr A, P, R;                        // R = P^T
   std::vector<double> dinv;
+  // The V(1,1) cycle of this level as two sparse products (smoothed kind only), with
+  // Jacobi weight w = kAmgOmega: the pre-smoothing from zero, the residual and the
+  // restriction give b_c = M b, M = R (I - w A D^-1); the prolongation and the
+  // post-smoothing give x = N b + Q x_c, N = 2w D^-1 - w^2 D^-1 A D^-1, Q = (I - w D^-1 A) P.
+  Csr M, N, Q;
 };
+constexpr double kAmgOmega = 2.0 / 3.0;
 struct Amg {
   std::vector<AmgLevel> levels;
   int coarsest_n = 0;

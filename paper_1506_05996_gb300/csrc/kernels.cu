@@ -207,6 +207,25 @@ __global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv
     if (ok && lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
   }
 }
+// x = z + N b + Q x_c (z may be null): the prolongation and post-smoothing of a V(1,1)
+// cycle as one pass; both rows are summed by the same lanes, then one shuffle tree.
+template <int LANES>
+__global__ void amg_up_kernel(DevCsr N, DevCsr Q, const double* __restrict__ b, const double* __restrict__ xc,
+                              const double* z, double* out, const PcgState* st) {
+  if (stopped(st)) return;
+  GROUP_ROWS(N.n) {
+    const int i = w0 + sub;
+    const bool ok = i < N.n;
+    double s = 0.0;
+    if (ok) {
+      for (int q = N.ptr[i] + lane; q < N.ptr[i + 1]; q += LANES) s += N.val[q] * b[N.col[q]];
+      for (int q = Q.ptr[i] + lane; q < Q.ptr[i + 1]; q += LANES) s += Q.val[q] * xc[Q.col[q]];
+    }
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (ok && lane == 0) out[i] = z != nullptr ? z[i] + s : s;   // z may alias out: same row
+  }
+}
 #undef GROUP_ROWS
 
 __global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
@@ -707,6 +726,33 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
 }
 
 
+// V(1,1) cycle at `level` as down and up passes (smoothed kind): b_c = M b, the next level
+// (or the dense inverse), then out = z + N b + Q x_c (z null: out = V b). Two kernels per
+// level instead of five; the same linear map as vcycle() up to rounding.
+cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double* out, const double* z,
+                         const PcgState* st, cudaStream_t s) {
+  if (level == d.nlevels) {
+    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    ++g_kernel_launches;
+    return cudaGetLastError();
+  }
+  const DevAmgLevel& L = d.levels[level];
+  double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
+  double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
+  ROWS_LAUNCH(amg_spmv_kernel, L.M, L.M, b, bc, st);
+  ++g_kernel_launches;
+  cudaError_t err = vcycle_fused(d, level + 1, bc, xc, nullptr, st, s);
+  if (err != cudaSuccess) return err;
+  switch (L.up_lanes) {
+    case 4: amg_up_kernel<4><<<grid_for(4 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
+    case 8: amg_up_kernel<8><<<grid_for(8 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
+    case 16: amg_up_kernel<16><<<grid_for(16 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
+    default: amg_up_kernel<32><<<grid_for(32 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
+  }
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
 // One K-cycle at `level` for right-hand side b, result in out (out != b).
 cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
@@ -805,7 +851,10 @@ cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, cons
 // Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero, or one K-cycle.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s) : vcycle(d, 0, d.Rc, d.Zc, st, s);
+  const bool fused = d.amg_kind == 0 && d.nlevels > 0 && d.levels[0].M.n > 0;
+  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s)
+                    : fused         ? vcycle_fused(d, 0, d.Rc, d.Zc, nullptr, st, s)
+                                    : vcycle(d, 0, d.Rc, d.Zc, st, s);
   if (err != cudaSuccess) return err;
   if (d.nlevels == 0 || d.amg_kind == 1) {
     if (d.pfp32) {
@@ -819,6 +868,11 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   for (int c = 1; c < kCycles; ++c) {
     ROWS_LAUNCH(amg_resid_kernel, A0, A0, d.Rc, d.Zc, d.cres, st);
     ++g_kernel_launches;
+    if (fused) {   // Zc += V cres, the add folded into the up pass
+      err = vcycle_fused(d, 0, d.cres, d.Zc, d.Zc, st, s);
+      if (err != cudaSuccess) return err;
+      continue;
+    }
     err = vcycle(d, 0, d.cres, d.ctmp, st, s);
     if (err != cudaSuccess) return err;
     add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);

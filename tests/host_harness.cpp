@@ -61,12 +61,21 @@ void hh_gll(double* t, double* rho, double* D) {
 }
 int hh_amg_nlevels() { return (int)g_amg.levels.size(); }
 int hh_amg_size(int l) { return l < (int)g_amg.levels.size() ? g_amg.levels[l].A.n : g_amg.coarsest_n; }
-int hh_amg_nnz(int l, int which) {   // which: 0 A, 1 P
+static const sem::Csr& amg_mat(int l, int which) {   // which: 0 A, 1 P, 2 M, 3 N, 4 Q
   const sem::AmgLevel& L = g_amg.levels[l];
-  return (int)(which == 0 ? L.A.val.size() : L.P.val.size());
+  switch (which) {
+    case 0: return L.A;
+    case 1: return L.P;
+    case 2: return L.M;
+    case 3: return L.N;
+    default: return L.Q;
+  }
 }
+int hh_amg_nnz(int l, int which) { return (int)amg_mat(l, which).val.size(); }
+int hh_amg_rows(int l, int which) { return amg_mat(l, which).n; }
+int hh_amg_cols(int l, int which) { return amg_mat(l, which).m; }
 void hh_amg_csr(int l, int which, int* ptr, int* col, double* val) {
-  const sem::Csr& A = which == 0 ? g_amg.levels[l].A : g_amg.levels[l].P;
+  const sem::Csr& A = amg_mat(l, which);
   std::memcpy(ptr, A.ptr.data(), A.ptr.size() * sizeof(int));
   std::memcpy(col, A.col.data(), A.col.size() * sizeof(int));
   std::memcpy(val, A.val.data(), A.val.size() * sizeof(double));

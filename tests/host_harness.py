@@ -56,6 +56,18 @@ class HostTables:
         self.lib = lib
         self.ne, self.p, self.P = ne, p, P
 
+    def amg_matrix(self, l, which):
+        """Level l's matrix as scipy CSR: 0 A, 1 P, 2 M, 3 N, 4 Q (the fused V-cycle)."""
+        import scipy.sparse as sp
+        n, m = self.lib.hh_amg_rows(l, which), self.lib.hh_amg_cols(l, which)
+        nnz = self.lib.hh_amg_nnz(l, which)
+        ptr = np.zeros(n + 1, dtype=np.int32)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz)
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        self.lib.hh_amg_csr(l, which, vp(ptr), vp(col), vp(val))
+        return sp.csr_matrix((val, col, ptr), shape=(n, m))
+
     def amg_level(self, l, which):
         n = self.amg_sizes[l]
         nnz = self.lib.hh_amg_nnz(l, which)

@@ -120,3 +120,26 @@ def test_tables_on_irregular_valence_meshes(lib, N, layers, n, seed):
     lib_ip_in_ref = np.where(ip >= 0, inv[np.maximum(ip, 0)], -1)
     np.testing.assert_array_equal(lib_ip_in_ref, ref.ip[H.elem_perm].transpose(0, 3, 2, 1))
     np.testing.assert_allclose(H.hbox.reshape(-1, 3), ref.h[H.elem_perm], rtol=1e-14)
+
+
+@pytest.mark.parametrize("E,n,lam", [(20, 2, 0.0), (32, 1, 0.7)])
+def test_fused_vcycle_matrices_reproduce_the_cycle(lib, E, n, lam):
+    """Per level, the two sparse products the GPU runs (b_c = M b, x = N b + Q x_c) equal the
+    V(1,1) cycle's steps done one by one with Jacobi weight 2/3: pre-smoothing from zero,
+    residual, restriction by P^T; prolongation and post-smoothing."""
+    mesh = lattice_hex_mesh(E, 0.2, 1)
+    H = HostTables(lib, mesh, n, lam, amg_kind=0)
+    assert H.rc == 0 and len(H.amg_sizes) >= 2
+    rng = np.random.default_rng(E + n)
+    w = 2.0 / 3.0
+    for l in range(len(H.amg_sizes) - 1):
+        A, P, M, N, Q = (H.amg_matrix(l, k) for k in range(5))
+        dinv = 1.0 / A.diagonal()
+        b = rng.standard_normal(A.shape[0])
+        xc = rng.standard_normal(P.shape[1])
+        x = w * dinv * b
+        bc = P.T @ (b - A @ x)
+        x1 = x + P @ xc
+        out = x1 + w * dinv * (b - A @ x1)
+        np.testing.assert_allclose(M @ b, bc, rtol=0, atol=1e-13 * np.abs(bc).max())
+        np.testing.assert_allclose(N @ b + Q @ xc, out, rtol=0, atol=1e-13 * np.abs(out).max())
