@@ -112,7 +112,8 @@ int build_coarse(sem_t* h) {
   auto up_csr = [&](const sem::Csr& A, sem::DevCsr& out) -> cudaError_t {
     out.n = A.n;
     out.nnz = (int)A.val.size();
-    // about four entries per lane: 8 lanes for the 27-entry rows of the Q1 matrix
+    // about four entries per lane: 8 lanes for the 27-entry rows of the Q1 matrix, at most
+    // a warp (wider groups measured slower on the long coarse-level rows)
     out.lanes = 4;
     while (out.lanes < 32 && 4 * out.lanes * (int64_t)A.n < (int64_t)out.nnz) out.lanes *= 2;
     cudaError_t e = h->upload(&out.ptr, A.ptr, h->coarse_allocs);
@@ -563,13 +564,14 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
 int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
   if (int rc = check_handle(h)) return rc;
   if (x_dev == nullptr || y_dev == nullptr || x_dev == y_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
+  // the element kernel writes the interior DOFs of y itself; the gather sums the rest
   if (h->d.fp32) {
     float* wl = reinterpret_cast<float*>(h->d.wl);
-    PROF(h, "ax_local", sem::launch_ax_local_f32(h->d, x_dev, wl, nullptr, h->stream));
-    PROF(h, "gather", sem::launch_gather_identity_f32(h->d, wl, x_dev, y_dev, h->stream));
+    PROF(h, "ax_local", sem::launch_ax_apply_f32(h->d, x_dev, wl, y_dev, h->stream));
+    PROF(h, "gather", sem::launch_gather_shared_f32(h->d, wl, x_dev, y_dev, h->stream));
   } else {
-    PROF(h, "ax_local", sem::launch_ax_local(h->d, x_dev, h->d.wl, nullptr, h->stream));
-    PROF(h, "gather", sem::launch_gather_identity(h->d, h->d.wl, x_dev, y_dev, h->stream));
+    PROF(h, "ax_local", sem::launch_ax_apply(h->d, x_dev, h->d.wl, y_dev, h->stream));
+    PROF(h, "gather", sem::launch_gather_shared(h->d, h->d.wl, x_dev, y_dev, h->stream));
   }
   return SEM_OK;
 }

@@ -164,6 +164,13 @@ cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, co
                             cudaStream_t s);
 cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st,
                                 cudaStream_t s);
+// y = A x with the interior-first numbering (d.Gi > 0): interior DOFs written into y by the
+// element kernel, the other local results into wl for launch_gather_shared*.
+cudaError_t launch_ax_apply(const DevProblem& d, const double* x, double* wl, double* y, cudaStream_t s);
+cudaError_t launch_ax_apply_f32(const DevProblem& d, const double* x, float* wl, double* y, cudaStream_t s);
+cudaError_t launch_gather_shared(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s);
+cudaError_t launch_gather_shared_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
+                                     cudaStream_t s);
 cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
                                      cudaStream_t s);
 // y = gather(wl); masked rows take xin (identity) - sem_apply_A.

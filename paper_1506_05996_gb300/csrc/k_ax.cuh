@@ -74,9 +74,13 @@ constexpr int ax_smem_bytes() {
   return (int)(2 * sizeof(FoldedD<p, T>) + EPB * (4 * p * p * p + 24) * sizeof(T));
 }
 
-template <int p, bool RECOMP, typename T, typename TX, int EPB>
+// DIRECT (operator application y = A x with the interior-first numbering, d.Gi > 0): an
+// element-interior node has one copy, so its result goes straight to y (x where masked) at
+// its computed DOF, without an index read; only the other nodes go to wl for the gather.
+template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT>
 __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
-                                                               T* __restrict__ wl, const PcgState* st) {
+                                                               T* __restrict__ wl, const PcgState* st,
+                                                               double* __restrict__ yd) {
   if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
   __shared__ FoldedD<p, T> Fg, Fd;
@@ -97,12 +101,20 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   if (RECOMP)
     for (int q = tid; q < 24; q += p2) sx[q] = (T)d.exyz[(size_t)e * 24 + q];
   const int* l2ge = d.l2g + (size_t)e * p3;
+  constexpr int m = p - 2;
+  // interior line (tx, ty inside): DOF of node k is gi0 + m^2 (k - 1) for 1 <= k <= p - 2
+  const bool inner_xy = DIRECT && tx >= 1 && tx <= p - 2 && ty >= 1 && ty <= p - 2;
+  const int gi0 = e * m * m * m + (tx - 1) + m * (ty - 1);
   T uk[p], rk[p], line[p], res[p];
+  unsigned masked = 0;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const int g = l2ge[l];
-    uk[k] = d.mask[g] ? T(0) : (T)x[g];
+    const bool inner = inner_xy && k >= 1 && k <= p - 2;
+    const int g = inner ? gi0 + m * m * (k - 1) : l2ge[l];
+    const bool mk = d.mask[g] != 0;
+    if (DIRECT && mk) masked |= 1u << k;
+    uk[k] = mk ? T(0) : (T)x[g];
     su[l] = uk[k];
   }
   __syncthreads();
@@ -165,7 +177,13 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    out[l] = su[l] + res[k] + rk[k];
+    const T v = su[l] + res[k] + rk[k];
+    if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
+      const int g = gi0 + m * m * (k - 1);
+      yd[g] = (masked >> k) & 1u ? (double)x[g] : (double)v;
+    } else {
+      out[l] = v;
+    }
   }
 }
 
@@ -200,12 +218,12 @@ bool ax_tile_ok_t(int p, int epb) {
   }
 }
 
-template <int p, typename T, typename TX, int EPB>
-cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+template <int p, typename T, typename TX, int EPB, bool DIRECT>
+cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd, cudaStream_t s) {
   if constexpr (ax_tile_supported<p, T, EPB>()) {
     const int grid = (d.ne + EPB - 1) / EPB;
-    if (d.recompute) ax_local_kernel<p, true, T, TX, EPB><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st);
-    else ax_local_kernel<p, false, T, TX, EPB><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st);
+    if (d.recompute) ax_local_kernel<p, true, T, TX, EPB, DIRECT><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    else ax_local_kernel<p, false, T, TX, EPB, DIRECT><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     count_launch();
     return cudaGetLastError();
   } else {
@@ -213,39 +231,32 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgStat
   }
 }
 
-template <int p, typename T, typename TX>
-cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+template <int p, typename T, typename TX, bool DIRECT>
+cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd, cudaStream_t s) {
   switch (sizeof(T) == 4 ? d.epb_ax32 : d.epb_ax) {
-    case 2: return launch_ax_epb<p, T, TX, 2>(d, x, wl, st, s);
-    case 4: return launch_ax_epb<p, T, TX, 4>(d, x, wl, st, s);
-    case 8: return launch_ax_epb<p, T, TX, 8>(d, x, wl, st, s);
-    default: return launch_ax_epb<p, T, TX, 1>(d, x, wl, st, s);
+    case 2: return launch_ax_epb<p, T, TX, 2, DIRECT>(d, x, wl, st, yd, s);
+    case 4: return launch_ax_epb<p, T, TX, 4, DIRECT>(d, x, wl, st, yd, s);
+    case 8: return launch_ax_epb<p, T, TX, 8, DIRECT>(d, x, wl, st, yd, s);
+    default: return launch_ax_epb<p, T, TX, 1, DIRECT>(d, x, wl, st, yd, s);
   }
 }
 
-template <typename T, typename TX>
-cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, cudaStream_t s) {
+// Local results of every node into wl (DIRECT = false), or, for y = A x with the
+// interior-first numbering, interior nodes into yd and the others into wl (DIRECT = true).
+template <typename T, typename TX, bool DIRECT>
+cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd,
+                              cudaStream_t s) {
+  if (DIRECT && d.Gi == 0) return cudaErrorInvalidValue;
   switch (d.p) {
-    case 3: return launch_ax_p<3, T, TX>(d, x, wl, st, s);
-    case 4: return launch_ax_p<4, T, TX>(d, x, wl, st, s);
-    case 5: return launch_ax_p<5, T, TX>(d, x, wl, st, s);
-    case 6: return launch_ax_p<6, T, TX>(d, x, wl, st, s);
-    case 7: return launch_ax_p<7, T, TX>(d, x, wl, st, s);
-    case 8: return launch_ax_p<8, T, TX>(d, x, wl, st, s);
-    case 9: return launch_ax_p<9, T, TX>(d, x, wl, st, s);
+    case 3: return launch_ax_p<3, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 4: return launch_ax_p<4, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 5: return launch_ax_p<5, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 6: return launch_ax_p<6, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 7: return launch_ax_p<7, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 8: return launch_ax_p<8, T, TX, DIRECT>(d, x, wl, st, yd, s);
+    case 9: return launch_ax_p<9, T, TX, DIRECT>(d, x, wl, st, yd, s);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<double, double>(d, x, wl, st, s);
-}
-cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl, const PcgState* st, cudaStream_t s) {
-  return launch_ax_local_t<float, double>(d, x, wl, st, s);
-}
-cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,
-                                     cudaStream_t s) {
-  return launch_ax_local_t<float, float>(d, x, wl, st, s);
 }
 
 

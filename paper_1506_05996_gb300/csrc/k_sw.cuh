@@ -325,18 +325,6 @@ cudaError_t launch_schwarz_local_t(const DevProblem& d, const TR* r, T* wp, cons
     default: return cudaErrorInvalidValue;
   }
 }
-cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
-  return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
-}
-cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float* wp, const PcgState* st,
-                                     cudaStream_t s) {
-  return launch_schwarz_local_t<float, double>(d, r, wp, st, s);
-}
-cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
-                                          cudaStream_t s) {
-  return launch_schwarz_local_t<float, float>(d, r, wp, st, s);
-}
-
 
 }  // namespace
 }  // namespace sem

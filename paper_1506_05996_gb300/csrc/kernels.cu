@@ -52,10 +52,12 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
   }
 }
 
+// y = A x on DOFs g0..G-1 (g0 = 0, or d.Gi when the operator kernel wrote the interior
+// DOFs itself): y = x on masked DOFs, else the sum of the local copies.
 template <typename T>
 __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__ wl,
-                                       const double* __restrict__ xin, double* __restrict__ y) {
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+                                       const double* __restrict__ xin, double* __restrict__ y, int g0) {
+  for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
     T s = 0;
     s = gather_dof(d, wl, g);
@@ -134,116 +136,151 @@ __global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
 }
 
 // AMG kernels. Sparse rows are handled by groups of LANES lanes (4..32, a power of two
-// chosen per matrix from its mean row length): the lanes stride over the row, then a fixed
-// shuffle tree. Short fine-level rows (27 entries) thus take 8 lanes instead of a warp,
-// and long coarse-level rows do not serialise. The row loop steps a warp at a time, so
-// every lane reaches the shuffles.
+// chosen per matrix from its mean row length, about four entries per lane): the lanes
+// stride over the row, then a fixed shuffle tree. Short fine-level rows (27 entries) take
+// 8 lanes instead of a warp. The groups step over the rows a warp at a time, so every lane
+// reaches the shuffles of every step. (Groups of several warps per row, with partial sums
+// meeting in shared memory, were measured slower for the long coarse-level rows; the
+// block-wide form, a block stepping over rows, serves the dense coarsest matrix.)
 __global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const double* __restrict__ b,
                                    double* __restrict__ x, double omega, const PcgState* st) {
   if (stopped(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = omega * dinv[i] * b[i];
 }
 
+constexpr int kRowBlock = 256;   // block size of every row-group kernel
+
+// First row of this thread's group in the first step, the step (a warp covers 32 / LANES
+// rows), and the thread's lane and group within the warp.
 template <int LANES>
-__device__ __forceinline__ double group_row_dot(const DevCsr& A, int row, bool ok, const double* __restrict__ x,
-                                                int lane) {
-  double s = 0.0;
-  if (ok)
-    for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += LANES) s += A.val[q] * x[A.col[q]];
+struct RowGroups {
+  static_assert(LANES <= 32, "row groups are at most a warp");
+  int first, step, lane, sub;
+  __device__ __forceinline__ RowGroups() {
+    lane = threadIdx.x & (LANES - 1);
+    first = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES);
+    step = ((gridDim.x * blockDim.x) >> 5) * (32 / LANES);
+    sub = (threadIdx.x & 31) / LANES;
+  }
+};
+
+// Sum over the LANES lanes of a group; every lane of the group gets it. LANES > 32 (the
+// dense kernel's whole block) adds the warps' sums in shared memory, in warp order.
+template <int LANES>
+__device__ __forceinline__ double group_sum(double s) {
+  constexpr int W = LANES < 32 ? LANES : 32;
 #pragma unroll
-  for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if constexpr (LANES > 32) {
+    constexpr int NW = LANES / 32;
+    __shared__ double red[kRowBlock / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    const int w0 = (threadIdx.x / LANES) * NW;
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) t += red[w0 + k];
+    __syncthreads();   // red is reused by the next step
+    s = t;
+  }
   return s;
 }
 
-#define GROUP_ROWS(nrows)                                                                               \
-  const int lane = threadIdx.x & (LANES - 1), sub = (threadIdx.x & 31) / LANES;                         \
-  for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LANES); w0 < (nrows);          \
-       w0 += ((gridDim.x * blockDim.x) >> 5) * (32 / LANES))
+template <int LANES>
+__device__ __forceinline__ double row_dot(const DevCsr& A, int row, bool ok, const double* __restrict__ x, int lane) {
+  double s = 0.0;
+  if (ok)
+    for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += LANES) s += A.val[q] * x[A.col[q]];
+  return s;
+}
 
 template <int LANES>
-__global__ void amg_resid_kernel(DevCsr A, const double* __restrict__ b, const double* __restrict__ x,
-                                 double* __restrict__ t, const PcgState* st) {
+__global__ void __launch_bounds__(kRowBlock) amg_resid_kernel(DevCsr A, const double* __restrict__ b,
+                                                             const double* __restrict__ x, double* __restrict__ t,
+                                                             const PcgState* st) {
   if (stopped(st)) return;
-  GROUP_ROWS(A.n) {
-    const int i = w0 + sub;
+  const RowGroups<LANES> g;
+  for (int i0 = g.first; i0 < A.n; i0 += g.step) {
+    const int i = i0 + g.sub;
     const bool ok = i < A.n;
-    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
-    if (ok && lane == 0) t[i] = b[i] - s;
+    const double s = group_sum<LANES>(row_dot<LANES>(A, i, ok, x, g.lane));
+    if (ok && g.lane == 0) t[i] = b[i] - s;
   }
 }
 
 template <int LANES>
-__global__ void amg_spmv_kernel(DevCsr A, const double* __restrict__ x, double* __restrict__ y, const PcgState* st) {
+__global__ void __launch_bounds__(kRowBlock) amg_spmv_kernel(DevCsr A, const double* __restrict__ x,
+                                                            double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
-  GROUP_ROWS(A.n) {
-    const int i = w0 + sub;
+  const RowGroups<LANES> g;
+  for (int i0 = g.first; i0 < A.n; i0 += g.step) {
+    const int i = i0 + g.sub;
     const bool ok = i < A.n;
-    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
-    if (ok && lane == 0) y[i] = s;
+    const double s = group_sum<LANES>(row_dot<LANES>(A, i, ok, x, g.lane));
+    if (ok && g.lane == 0) y[i] = s;
   }
 }
 
 template <int LANES>
-__global__ void amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc, double* __restrict__ x,
-                                       const PcgState* st) {
+__global__ void __launch_bounds__(kRowBlock) amg_prolong_add_kernel(DevCsr P, const double* __restrict__ xc,
+                                                                   double* __restrict__ x, const PcgState* st) {
   if (stopped(st)) return;
-  GROUP_ROWS(P.n) {
-    const int i = w0 + sub;
+  const RowGroups<LANES> g;
+  for (int i0 = g.first; i0 < P.n; i0 += g.step) {
+    const int i = i0 + g.sub;
     const bool ok = i < P.n;
-    const double s = group_row_dot<LANES>(P, i, ok, xc, lane);
-    if (ok && lane == 0) x[i] = x[i] + s;
+    const double s = group_sum<LANES>(row_dot<LANES>(P, i, ok, xc, g.lane));
+    if (ok && g.lane == 0) x[i] = x[i] + s;
   }
 }
 
 template <int LANES>
-__global__ void amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv, const double* __restrict__ b,
-                                       const double* __restrict__ x, double* __restrict__ xout, double omega,
-                                       const PcgState* st) {
+__global__ void __launch_bounds__(kRowBlock) amg_jacobi_post_kernel(DevCsr A, const double* __restrict__ dinv,
+                                                                   const double* __restrict__ b,
+                                                                   const double* __restrict__ x,
+                                                                   double* __restrict__ xout, double omega,
+                                                                   const PcgState* st) {
   if (stopped(st)) return;
-  GROUP_ROWS(A.n) {
-    const int i = w0 + sub;
+  const RowGroups<LANES> g;
+  for (int i0 = g.first; i0 < A.n; i0 += g.step) {
+    const int i = i0 + g.sub;
     const bool ok = i < A.n;
-    const double s = group_row_dot<LANES>(A, i, ok, x, lane);
-    if (ok && lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
+    const double s = group_sum<LANES>(row_dot<LANES>(A, i, ok, x, g.lane));
+    if (ok && g.lane == 0) xout[i] = x[i] + omega * dinv[i] * (b[i] - s);
   }
 }
+
 // x = z + N b + Q x_c (z may be null): the prolongation and post-smoothing of a V(1,1)
-// cycle as one pass; both rows are summed by the same lanes, then one shuffle tree.
+// cycle as one pass; both rows are summed by the same lanes, then one reduction.
 template <int LANES>
-__global__ void amg_up_kernel(DevCsr N, DevCsr Q, const double* __restrict__ b, const double* __restrict__ xc,
-                              const double* z, double* out, const PcgState* st) {
+__global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, const double* __restrict__ b,
+                                                          const double* __restrict__ xc, const double* z, double* out,
+                                                          const PcgState* st) {
   if (stopped(st)) return;
-  GROUP_ROWS(N.n) {
-    const int i = w0 + sub;
+  const RowGroups<LANES> g;
+  for (int i0 = g.first; i0 < N.n; i0 += g.step) {
+    const int i = i0 + g.sub;
     const bool ok = i < N.n;
-    double s = 0.0;
-    if (ok) {
-      for (int q = N.ptr[i] + lane; q < N.ptr[i + 1]; q += LANES) s += N.val[q] * b[N.col[q]];
-      for (int q = Q.ptr[i] + lane; q < Q.ptr[i + 1]; q += LANES) s += Q.val[q] * xc[Q.col[q]];
-    }
-#pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (ok && lane == 0) out[i] = z != nullptr ? z[i] + s : s;   // z may alias out: same row
+    const double s = group_sum<LANES>(row_dot<LANES>(N, i, ok, b, g.lane) + row_dot<LANES>(Q, i, ok, xc, g.lane));
+    if (ok && g.lane == 0) out[i] = z != nullptr ? z[i] + s : s;   // z may alias out: same row
   }
 }
-#undef GROUP_ROWS
 
 __global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
   if (stopped(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + y[i];
 }
 
-// x = Ainv b, one warp per row (dense coarsest level).
-__global__ void dense_mv_kernel(int n, const double* __restrict__ Ainv, const double* __restrict__ b,
-                                double* __restrict__ x, const PcgState* st) {
+// x = Ainv b at the dense coarsest level: one block of kRowBlock threads per row.
+__global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double* __restrict__ Ainv,
+                                                            const double* __restrict__ b, double* __restrict__ x,
+                                                            const PcgState* st) {
   if (stopped(st)) return;
-  const int lane = threadIdx.x & 31;
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+  for (int row = blockIdx.x; row < n; row += gridDim.x) {
     double s = 0.0;
-    for (int c = lane; c < n; c += 32) s += Ainv[(size_t)row * n + c] * b[c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[row] = s;
+    for (int c = threadIdx.x; c < n; c += kRowBlock) s += Ainv[(size_t)row * n + c] * b[c];
+    s = group_sum<kRowBlock>(s);
+    if (threadIdx.x == 0) x[row] = s;
   }
 }
 
@@ -683,16 +720,17 @@ inline int grid_for(int n, int block, int cap) {
   return g < 1 ? 1 : (g > cap ? cap : g);
 }
 
-// Launches a row-group AMG kernel with the lane count of matrix M, one group per row.
-#define ROWS_LAUNCH(KERN, M, ...)                                                                  \
-  do {                                                                                             \
-    const int rows_ = (M).n;                                                                       \
-    switch ((M).lanes) {                                                                           \
-      case 4: KERN<4><<<grid_for(4 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;          \
-      case 8: KERN<8><<<grid_for(8 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;          \
-      case 16: KERN<16><<<grid_for(16 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;       \
-      default: KERN<32><<<grid_for(32 * rows_, 256, 8192), 256, 0, s>>>(__VA_ARGS__); break;       \
-    }                                                                                              \
+// Launches a row-group AMG kernel with the lane count of matrix M, one group per row
+// (kRowBlock / lanes rows per block).
+#define ROWS_LAUNCH(KERN, M, ...)                                                                   \
+  do {                                                                                              \
+    const int rows_ = (M).n;                                                                        \
+    switch ((M).lanes) {                                                                            \
+      case 4: KERN<4><<<grid_for(rows_, kRowBlock / 4, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;     \
+      case 8: KERN<8><<<grid_for(rows_, kRowBlock / 8, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;     \
+      case 16: KERN<16><<<grid_for(rows_, kRowBlock / 16, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;  \
+      default: KERN<32><<<grid_for(rows_, kRowBlock / 32, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;  \
+    }                                                                                               \
   } while (0)
 
 constexpr double kOmega = 2.0 / 3.0;
@@ -701,7 +739,7 @@ constexpr int kCycles = 3;
 // V(1,1) cycle at `level` for right-hand side b, result in out (out != b).
 cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
   }
@@ -732,7 +770,7 @@ cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out,
 cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double* out, const double* z,
                          const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
   }
@@ -743,12 +781,8 @@ cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double
   ++g_kernel_launches;
   cudaError_t err = vcycle_fused(d, level + 1, bc, xc, nullptr, st, s);
   if (err != cudaSuccess) return err;
-  switch (L.up_lanes) {
-    case 4: amg_up_kernel<4><<<grid_for(4 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
-    case 8: amg_up_kernel<8><<<grid_for(8 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
-    case 16: amg_up_kernel<16><<<grid_for(16 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
-    default: amg_up_kernel<32><<<grid_for(32 * L.N.n, 256, 8192), 256, 0, s>>>(L.N, L.Q, b, xc, z, out, st); break;
-  }
+  const struct { int n, lanes; } up{L.N.n, L.up_lanes};   // N's rows, the level's lane count
+  ROWS_LAUNCH(amg_up_kernel, up, L.N, L.Q, b, xc, z, out, st);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -756,7 +790,7 @@ cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double
 // One K-cycle at `level` for right-hand side b, result in out (out != b).
 cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n * 32, 256, 4096), 256, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
   }
@@ -810,14 +844,25 @@ cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_o
   return cudaGetLastError();
 }
 
+cudaError_t launch_gather_shared(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
+  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_shared_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
+                                     cudaStream_t s) {
+  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
-  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 cudaError_t launch_gather_identity_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
                                        cudaStream_t s) {
-  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y);
+  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
