@@ -405,18 +405,19 @@ def run_gpu(args):
         rec.set_precision(prec)
         S.sem_autotune(rec.h)
     for geom, prec, pr in (("stored", "fp64", prob), ("recompute", "fp64", rec),
-                           ("stored", "fp32", prob), ("recompute", "fp32", rec)):
+                           ("stored", "fp32", prob), ("recompute", "fp32", rec), ("stored", "bf16", prob)):
         ms, kms = time_apply(pr, prec=prec)
         # algorithmic bytes of one apply: x read and y written (FP64, G each), l2g (int32 per
-        # local node), stored factors (7 per local node, FP64 or FP32) or the 24 vertex
+        # local node), stored factors (7 per local node, FP64, FP32 or BF16) or the 24 vertex
         # coordinates of each element
-        fb = 8 if prec == "fp64" else 4
+        fb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+        wb = 8 if prec == "fp64" else 4
         geo_bytes = 7 * fb * L if geom == "stored" else 24 * 8 * NE
         alg_bytes = 16 * G + 4 * L + geo_bytes
         # the element kernel alone: x (FP64) and the mask read, l2g, factors, local results
         # written (FP64 or FP32)
-        k_bytes = 9 * G + 4 * L + geo_bytes + fb * L
-        key = geom + ("" if prec == "fp64" else "_fp32")
+        k_bytes = 9 * G + 4 * L + geo_bytes + wb * L
+        key = geom + ("" if prec == "fp64" else "_" + prec)
         ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
                    "paper_equivalent_tflops_ax_local": ax_flops_paper(ORDER, NE) / (kms * 1e-3) / 1e12,
                    "ax_local_frac_hbm_roofline": k_bytes / (kms * 1e-3) / 1e9 / hbm_peak,

@@ -49,7 +49,8 @@ typedef struct sem_s sem_t;
 #define SEM_GEOM_STORED     0x0  /* store G1..G6 and m per GLL node (Sec. 3.1, 7 factors) */
 #define SEM_GEOM_RECOMPUTE  0x1  /* recompute them from the 8 vertices in the operator (Sec. 3.1) */
 #define SEM_NEUMANN         0x10 /* no Dirichlet nodes (default: Dirichlet on every boundary face) */
-#define SEM_MIXED           0x100 /* also keep the stored factors in FP32, for SEM_PREC_FP32 */
+#define SEM_MIXED           0x100 /* also keep the stored factors in FP32 and BF16, for
+                                       SEM_PREC_FP32 and SEM_PREC_BF16 */
 #define SEM_PATCH_FULL      0x1000 /* P^f patches with the edge and corner layers too: all (n+3)^3
                                       box nodes of Sec. 4.2 (default: face layers only) */
 
@@ -61,6 +62,12 @@ typedef struct sem_s sem_t;
 #define SEM_PREC_P32   2   /* P alone in FP32 (patch solves from the FP64 residual, FP32
                               prolongation sums; the coarse AMG stays FP64); Ax, vectors, dots and
                               recurrences in FP64, so no residual replacement is needed */
+#define SEM_PREC_BF16  3   /* sem_apply_A with the stored factors rounded to BF16 (half the bytes
+                              of the FP32 copy) and FP32 arithmetic:
+                              |y - A x| <= (2^-8 + gamma_K u32) |A|(|x|) per result, K = 4(n+1) + 16;
+                              sem_apply_P* as in SEM_PREC_FP32. Needs stored geometry and SEM_MIXED.
+                              The solves refuse it (SEM_ERR_ARG): on the smooth components that PCG
+                              leaves last, A x is far below |A|(|x|), and the mixed solve stalls */
 
 /* coarse solver P_0 of the two-scale preconditioner (sem_set_coarse_solver) */
 #define SEM_COARSE_VCYCLE  0  /* smoothed aggregation, three V(1,1) damped-Jacobi cycles: a fixed SPD
@@ -137,8 +144,9 @@ int sem_apply_P(sem_t* h, const double* r_dev, double* z_dev);
 int sem_apply_Pf(sem_t* h, const double* r_dev, double* z_dev);
 int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev);
 
-/* sem_set_precision - SEM_PREC_FP64 or SEM_PREC_FP32 for sem_apply_A, sem_apply_P* and
- * sem_solve. FP32 with stored geometry needs SEM_MIXED at create (SEM_ERR_ARG otherwise).
+/* sem_set_precision - SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_P32 or SEM_PREC_BF16 for
+ * sem_apply_A, sem_apply_P* and sem_solve. FP32 with stored geometry, and BF16, need
+ * SEM_MIXED at create (SEM_ERR_ARG otherwise; BF16 also refuses recomputed geometry).
  * In FP32, sem_apply_A / sem_apply_P* return FP64 vectors computed with FP32 element
  * arithmetic and FP64 sums over the local copies; sem_solve still reaches rtol on the true
  * FP64 residual (the returned history holds the recomputed residual at replacements). */

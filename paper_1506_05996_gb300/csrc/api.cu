@@ -193,6 +193,15 @@ int check_handle(const sem_t* h) {
   return SEM_OK;
 }
 
+// The BF16-factor operator's error, 2^-8 relative to |A|(|x|), is far larger relative to
+// A x on the smooth error components that PCG leaves last, so the iteration stalls: BF16 is
+// for operator and preconditioner applications only.
+int check_solvable(const sem_t* h) {
+  if (int rc = check_handle(h)) return rc;
+  if (h->d.bf16) return fail(SEM_ERR_ARG, "SEM_PREC_BF16 is for sem_apply_A / sem_apply_P*; solve in FP32 or FP64");
+  return SEM_OK;
+}
+
 // z = P r for the chosen parts; `pcg` adds the rz reduction / beta on the device.
 int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   sem::DevProblem& d = h->d;
@@ -462,13 +471,17 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
 
   // geometric factors (stored variant) and the assembled lumped mass
   if (!d.recompute) CK(h->alloc(&h->geo, (size_t)(7 * nb.ne * p3), A));
-  if (!d.recompute && (flags & SEM_MIXED)) CK(h->alloc(&h->geo32, (size_t)(7 * nb.ne * p3), A));
+  if (!d.recompute && (flags & SEM_MIXED)) {
+    CK(h->alloc(&h->geo32, (size_t)(7 * nb.ne * p3), A));
+    CK(h->alloc(&h->geo16, (size_t)(7 * nb.ne * p3), A));
+  }
   d.geo = h->geo;
   d.geo32 = h->geo32;
+  d.geo16 = h->geo16;
   int* bad;
   CK(h->alloc(&bad, 1, A));
   CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
-  CK(sem::launch_geometry(d, h->geo, h->geo32, d.wl, bad, h->stream));
+  CK(sem::launch_geometry(d, h->geo, h->geo32, h->geo16, d.wl, bad, h->stream));
   CK(sem::launch_gather_plain(d, d.wl, h->mN, h->stream));
   int bad_host = 0;
   CK(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -631,13 +644,17 @@ int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const 
 
 int sem_set_precision(sem_t* h, int precision) {
   if (int rc = check_handle(h)) return rc;
-  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_P32)
+  if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_P32 &&
+      precision != SEM_PREC_BF16)
     return fail(SEM_ERR_ARG, "unknown precision");
   if (precision == SEM_PREC_FP32 && !h->d.recompute && h->geo32 == nullptr)
     return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
+  if (precision == SEM_PREC_BF16 && (h->d.recompute || h->geo16 == nullptr))
+    return fail(SEM_ERR_ARG, "BF16 needs stored geometry and SEM_MIXED at sem_create");
   h->precision = precision;
-  h->d.fp32 = (precision == SEM_PREC_FP32);
-  h->d.pfp32 = (precision == SEM_PREC_FP32 || precision == SEM_PREC_P32);
+  h->d.fp32 = (precision == SEM_PREC_FP32 || precision == SEM_PREC_BF16);
+  h->d.pfp32 = (precision != SEM_PREC_FP64);
+  h->d.bf16 = (precision == SEM_PREC_BF16);
   return SEM_OK;
 }
 
@@ -761,7 +778,7 @@ long graph_key(const sem_t* h) {
   return (long)(d.fp32 ? 1 : 0) | ((long)(d.pfp32 ? 1 : 0) << 15) | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
          ((long)d.epb_ax << 4) |
          ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13) |
-         ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20);
+         ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20) | ((long)(d.bf16 ? 1 : 0) << 24);
 }
 
 int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
@@ -1023,7 +1040,7 @@ extern "C" {
 
 int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
               double* res_hist_host, double* true_rel_res_host) {
-  if (int rc = check_handle(h)) return rc;
+  if (int rc = check_solvable(h)) return rc;
   if (b_dev == nullptr || x_dev == nullptr || b_dev == x_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
   if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
   if (h->loop_mode == SEM_LOOP_DEVICE && !h->prof.on)
@@ -1041,7 +1058,7 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
 
 int sem_heat_step(sem_t* h, const double* u_prev_dev, const double* g_dev, double* u_dev, double rtol, int maxit,
                   int* iters_host, double* true_rel_res_host) {
-  if (int rc = check_handle(h)) return rc;
+  if (int rc = check_solvable(h)) return rc;
   if (!u_prev_dev || !g_dev || !u_dev || u_dev == g_dev) return fail(SEM_ERR_ARG, "bad vector arguments");
   if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
   sem::DevProblem& d = h->d;
@@ -1092,6 +1109,7 @@ int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev,
   for (int i = 0; i < count; ++i) {
     if (handles[i] == nullptr || b_dev[i] == nullptr || x_dev[i] == nullptr || b_dev[i] == x_dev[i])
       return fail(SEM_ERR_ARG, "bad handle or vector at index " + std::to_string(i));
+    if (int rc = check_solvable(handles[i])) return rc;
     for (int j = 0; j < i; ++j)
       if (handles[j] == handles[i]) return fail(SEM_ERR_ARG, "a handle appears twice");
   }

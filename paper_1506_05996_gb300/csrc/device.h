@@ -10,6 +10,8 @@
 //   cv    CSR over free vertices -> e*8 + corner
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -82,6 +84,8 @@ struct DevProblem {
   int epb_ax32 = 1, epb_sw32 = 1;   // the same for the FP32 kernels (tuned separately)
                                     // (tile shapes picked by the autotuner; 1, 2, 4 or 8)
   const float* geo32 = nullptr;     // stored factors rounded to FP32 (same layout as geo)
+  const __nv_bfloat16* geo16 = nullptr;   // the same rounded to BF16 (SEM_PREC_BF16)
+  bool bf16 = false;                // with fp32: the FP32 operator reads geo16
   // tables
   const int* l2g = nullptr;
   const double* geo = nullptr;
@@ -152,7 +156,8 @@ uint64_t kernel_launch_count();
 // --- geometry set-up ---------------------------------------------------------
 // Computes m_loc (ne*p^3) and, if geo != nullptr, the stored factors; sets *bad = 1
 // if |J| <= 0 anywhere.
-cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, double* mloc, int* bad,
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, __nv_bfloat16* geo16_out,
+                            double* mloc, int* bad,
                             cudaStream_t s);
 
 // Tile shapes (elements per CTA) compiled for an order: p = n+1 (operator), P = n+3 (patch).

@@ -172,6 +172,7 @@ struct sem_s {
   std::string coarse_err;
   double *coords = nullptr, *mN = nullptr, *geo = nullptr;
   float* geo32 = nullptr;
+  __nv_bfloat16* geo16 = nullptr;   // BF16 copy of the stored factors (SEM_MIXED)
   int precision = SEM_PREC_FP64;
   int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
   int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch

@@ -77,7 +77,8 @@ constexpr int ax_smem_bytes() {
 // DIRECT (operator application y = A x with the interior-first numbering, d.Gi > 0): an
 // element-interior node has one copy, so its result goes straight to y (x where masked) at
 // its computed DOF, without an index read; only the other nodes go to wl for the gather.
-template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT>
+// TG: the stored factors' type (T, or BF16 under SEM_PREC_BF16 with T = float).
+template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT, typename TG>
 __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
                                                                T* __restrict__ wl, const PcgState* st,
                                                                double* __restrict__ yd) {
@@ -141,10 +142,10 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
     const T ur = sA[l], us = sB[l], ut = sC[l];
     T G[6], mm;
     if (!RECOMP) {
-      const T* gp = geo_of<T>(d) + (size_t)e * 7 * p3 + l;
+      const TG* gp = geo_of<TG>(d) + (size_t)e * 7 * p3 + l;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
-      mm = gp[6 * p3];
+      for (int c = 0; c < 6; ++c) G[c] = factor<T>(gp[c * p3]);
+      mm = factor<T>(gp[6 * p3]);
     } else {
       T det;
       geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
@@ -222,8 +223,15 @@ template <int p, typename T, typename TX, int EPB, bool DIRECT>
 cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd, cudaStream_t s) {
   if constexpr (ax_tile_supported<p, T, EPB>()) {
     const int grid = (d.ne + EPB - 1) / EPB;
-    if (d.recompute) ax_local_kernel<p, true, T, TX, EPB, DIRECT><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
-    else ax_local_kernel<p, false, T, TX, EPB, DIRECT><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    constexpr bool kF32 = sizeof(T) == 4;
+    if (d.recompute) {
+      ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    } else if (kF32 && d.bf16) {
+      if constexpr (kF32)
+        ax_local_kernel<p, false, T, TX, EPB, DIRECT, __nv_bfloat16><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    } else {
+      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    }
     count_launch();
     return cudaGetLastError();
   } else {

@@ -137,6 +137,13 @@ __device__ __forceinline__ void geom_point(const T* xv, T a, T b, T c, T w, T G[
 template <typename T> __device__ __forceinline__ const T* geo_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* geo_of<double>(const DevProblem& d) { return d.geo; }
 template <> __device__ __forceinline__ const float* geo_of<float>(const DevProblem& d) { return d.geo32; }
+template <> __device__ __forceinline__ const __nv_bfloat16* geo_of<__nv_bfloat16>(const DevProblem& d) {
+  return d.geo16;
+}
+// A stored factor as the kernel's arithmetic type.
+template <typename T> __device__ __forceinline__ T factor(double v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T factor(float v) { return (T)v; }
+template <typename T> __device__ __forceinline__ T factor(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
 
 // Local index of element-interior DOF g < d.Gi: the numbering puts the (n-1)^3 interior
 // nodes of each element first, element by element, in local order.

@@ -27,7 +27,7 @@ using namespace sem;
 // ----------------------------------------------------------------- geometry
 template <int p>
 __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d, double* geo, float* geo32,
-                                                             double* mloc, int* bad) {
+                                                             __nv_bfloat16* geo16, double* mloc, int* bad) {
   constexpr int p3 = p * p * p;
   __shared__ double sx[24];
   const int e = blockIdx.x, t = threadIdx.x;
@@ -49,6 +49,12 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
 #pragma unroll
     for (int c = 0; c < 6; ++c) gp[c * p3] = (float)G[c];
     gp[6 * p3] = (float)m;
+  }
+  if (geo16 != nullptr) {   // and to BF16 (one rounding from FP64, to nearest)
+    __nv_bfloat16* gp = geo16 + (size_t)e * 7 * p3 + t;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) gp[c * p3] = __double2bfloat16(G[c]);
+    gp[6 * p3] = __double2bfloat16(m);
   }
 }
 
@@ -833,10 +839,11 @@ cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out,
 }  // namespace
 
 // ================================================================ launchers
-cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, double* mloc, int* bad,
+cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, __nv_bfloat16* geo16_out,
+                            double* mloc, int* bad,
                             cudaStream_t s) {
   switch (d.p) {
-#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, geo32_out, mloc, bad); ++g_kernel_launches; break;
+#define GEO_CASE(P_) case P_: geometry_kernel<P_><<<d.ne, P_ * P_ * P_, 0, s>>>(d, geo_out, geo32_out, geo16_out, mloc, bad); ++g_kernel_launches; break;
     GEO_CASE(2) GEO_CASE(3) GEO_CASE(4) GEO_CASE(5) GEO_CASE(6) GEO_CASE(7) GEO_CASE(8) GEO_CASE(9)
 #undef GEO_CASE
     default: return cudaErrorInvalidValue;

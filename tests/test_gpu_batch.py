@@ -17,7 +17,7 @@ def _cuda():
 
 
 @pytest.mark.parametrize("n", [3, 5, 8])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
 def test_tile_shapes_are_bit_identical(n, prec):
     from paper_1506_05996_gb300 import sem as S
     mesh = lattice_hex_mesh(5, 0.15, 3)     # 125 elements: short last CTAs for every shape

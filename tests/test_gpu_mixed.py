@@ -73,6 +73,55 @@ def test_fp32_operator_within_bound(E, n, lam, a, seed, geom):
     assert np.max(np.abs(y32 - y64)) > 0
 
 
+U_BF16 = 2.0 ** -8
+
+
+@pytest.mark.parametrize("E,n,lam,a,seed", [(2, 3, 0.0, 0.2, 0), (3, 5, 1.0, 0.2, 1), (2, 7, 0.5, 0.2, 2),
+                                            (2, 8, 2.0, 0.15, 3)])
+def test_bf16_operator_within_bound(E, n, lam, a, seed):
+    """SEM_PREC_BF16: each stored factor is rounded once from FP64 to BF16 (relative error at
+    most u_bf16 = 2^-8) and enters each product of the local result once, so on top of the
+    FP32 bound |y16 - y| <= (u_bf16 (1 + gamma_K) + gamma_K) |A|(|x|)."""
+    from oracle.operator import matfree_abs
+    P = _pair(lattice_hex_mesh(E, a, seed), n, lam, "stored")
+    x = np.random.default_rng(seed).standard_normal(P.ref.G)
+    y64 = P.ref.apply_A(x)
+    P.gpu.set_precision("bf16")
+    y16 = P.to_ref(P.gpu.apply_A(P.to_gpu(x)))
+    yabs = matfree_abs(x, P.ref.l2g, P.ref.Dh, P.ref.Gf, P.ref.m_loc, lam, P.ref.mask)
+    K = 4 * (n + 1) + 16
+    free = P.ref.mask == 0
+    bound = (U_BF16 * (1 + gamma(K)) + gamma(K)) * yabs[free]
+    ratio = np.max(np.abs(y16 - y64)[free] / bound)
+    assert ratio <= 1.0, ratio
+    # the factors really are BF16: the error exceeds the FP32 bound somewhere
+    assert np.max(np.abs(y16 - y64)[free] / (gamma(K) * yabs[free])) > 1.0
+
+
+def test_bf16_solve_is_refused():
+    """The solves refuse SEM_PREC_BF16 (the mixed PCG with the BF16-factor operator stalls short of
+    1e-8); FP32 then works on the same handle."""
+    from paper_1506_05996_gb300.sem import SemError
+    P = _pair(lattice_hex_mesh(4, 0.2, 4), 4, 1.0, "stored")
+    b = P.ref.load(manufactured_s(P.ref.coords, 1.0))
+    P.gpu.set_precision("bf16")
+    with pytest.raises(SemError):
+        P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+    P.gpu.set_precision("fp32")
+    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+    assert rc == 0 and tr <= 1e-8
+
+
+def test_bf16_needs_stored_factors():
+    from paper_1506_05996_gb300.sem import SemProblem, SemError
+    mesh = lattice_hex_mesh(2, 0.1, 5)
+    for kw in ({"geom": "recompute"}, {"geom": "stored"}):
+        pr = SemProblem(mesh.xyz, mesh.hex2vert, 3, 1.0, **kw)
+        with pytest.raises(SemError):
+            pr.set_precision("bf16")
+        pr.close()
+
+
 @pytest.mark.parametrize("E,n,lam,a,seed", [(3, 3, 0.0, 0.2, 0), (2, 7, 1.0, 0.2, 1)])
 def test_fp32_fine_preconditioner_within_bound(E, n, lam, a, seed):
     from oracle.schwarz import apply_fine_abs
