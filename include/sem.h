@@ -229,6 +229,17 @@ int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw);
 int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host);
 
 /*
+ * sem_selfcheck_convert - checks the library's binary64 -> binary32 conversion (integer
+ * operations on the IEEE-754 bit layouts, used by the PCG vector kernels that write FP32
+ * copies of FP64 vectors) against the GPU's conversion instruction: each of the n 64-bit
+ * patterns in bits_dev (device memory, caller-owned) as a binary64, rounded to binary32
+ * (nearest, ties to even). Any bit difference counts (a NaN matches any NaN);
+ * *mismatches_host (host) receives the count, 0 when they agree. Runs on the default
+ * stream and synchronises. Errors: SEM_ERR_ARG, SEM_ERR_OOM, SEM_ERR_CUDA.
+ */
+int sem_selfcheck_convert(const uint64_t* bits_dev, int64_t n, int64_t* mismatches_host);
+
+/*
  * sem_profile / sem_profile_read - per-kernel timing of the library's own launches.
  * While enabled, a CUDA event pair is recorded on the handle's stream around each
  * kernel launch (or launch group: "coarse_amg" is the whole AMG V-cycle sequence),

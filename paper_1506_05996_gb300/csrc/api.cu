@@ -304,6 +304,22 @@ int sem_create(const double* vert_xyz_host, int64_t n_vert, const int64_t* hex2v
   return SEM_OK;
 }
 
+int sem_selfcheck_convert(const uint64_t* bits_dev, int64_t n, int64_t* mismatches_host) {
+  if (n < 0 || (n > 0 && bits_dev == nullptr) || mismatches_host == nullptr)
+    return fail(SEM_ERR_ARG, "bad arguments");
+  unsigned long long* cnt = nullptr;
+  if (cudaMalloc((void**)&cnt, sizeof(unsigned long long)) != cudaSuccess) return fail(SEM_ERR_OOM, "cudaMalloc failed");
+  unsigned long long host = 0;
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(host), 0);
+  if (e == cudaSuccess)
+    e = sem::launch_convert_check(reinterpret_cast<const unsigned long long*>(bits_dev), (long long)n, cnt, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&host, cnt, sizeof(host), cudaMemcpyDeviceToHost);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return fail(SEM_ERR_CUDA, cudaGetErrorString(e));
+  *mismatches_host = (int64_t)host;
+  return SEM_OK;
+}
+
 int sem_profile(sem_t* h, int enable) {
   if (int rc = check_handle(h)) return rc;
   CK(cudaStreamSynchronize(h->stream));

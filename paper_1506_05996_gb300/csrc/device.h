@@ -194,6 +194,8 @@ cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float
 cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
                                           cudaStream_t s);
 cudaError_t launch_sw_diag(const DevProblem& d, double* dg, double* sc, cudaStream_t s);
+cudaError_t launch_convert_check(const unsigned long long* bits, long long n, unsigned long long* mismatches,
+                                 cudaStream_t s);
 cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, float* sc, cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s);

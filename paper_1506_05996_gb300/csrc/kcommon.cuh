@@ -140,6 +140,38 @@ template <> __device__ __forceinline__ const float* geo_of<float>(const DevProbl
 template <> __device__ __forceinline__ const __nv_bfloat16* geo_of<__nv_bfloat16>(const DevProblem& d) {
   return d.geo16;
 }
+// binary64 -> binary32, round to nearest (ties to even), written from the IEEE-754 bit
+// layouts with 32-bit integer operations. On this part the conversion instruction runs on
+// the FP64 pipe, at about 1/64 of the FP32 rate. The memory-bound PCG vector kernels that
+// write FP32 copies of FP64 vectors use this instead (measured faster there); inside the
+// arithmetic-heavy element kernels the instruction stays (this branchy form was measured
+// slower there). Correctly rounded, so it gives the instruction's bits
+// (sem_selfcheck_convert).
+__device__ __forceinline__ float f64_to_f32(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned sign = hi & 0x80000000u, mh = hi & 0xfffffu;
+  const int e64 = (int)((hi >> 20) & 0x7ffu);
+  if (e64 == 0x7ff)   // infinity, or NaN (kept quiet)
+    return __uint_as_float(sign | 0x7f800000u | (((mh | lo) != 0u) ? (0x400000u | (mh << 3) | (lo >> 29)) : 0u));
+  const int e = e64 - 1023 + 127;   // biased binary32 exponent
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  if (e >= 1) {
+    // 23 kept fraction bits, 29 dropped; a carry out of the fraction steps the exponent
+    // (up to infinity), as rounding requires
+    const unsigned m = (mh << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float((sign | ((unsigned)e << 23) | m) + up);
+  }
+  if (e64 == 0) return __uint_as_float(sign);   // zero or binary64 subnormal: rounds to zero
+  // binary32 subnormal or zero: q = round((2^52 + fraction) / 2^sh) units of 2^-149
+  const int sh = 52 - (e64 - 1023 + 149);       // at least 30 here
+  if (sh > 53) return __uint_as_float(sign);    // below half the smallest subnormal
+  const unsigned long long M = ((unsigned long long)(mh | 0x100000u) << 32) | lo;
+  const unsigned long long q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  const unsigned long long up = (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  return __uint_as_float(sign | (unsigned)(q + up));
+}
+
 // A stored factor as the kernel's arithmetic type.
 template <typename T> __device__ __forceinline__ T factor(double v) { return (T)v; }
 template <typename T> __device__ __forceinline__ T factor(float v) { return (T)v; }

@@ -12,6 +12,7 @@
 // Reductions are deterministic: fixed grid, fixed per-thread ranges, a fixed
 // shuffle tree per block, and the last block to finish sums the block partials
 // in index order (no spin-waits: a completion counter decides the last block).
+#include <algorithm>
 #include <cmath>
 
 #include "kcommon.cuh"
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
 
 __global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __restrict__ b, const PcgState* st) {
   if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (float)a[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = f64_to_f32(a[i]);
 }
 
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
@@ -443,7 +444,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
     r[g] = v;
-    if (mixed) d.r32[g] = (float)v;
+    if (mixed) d.r32[g] = f64_to_f32(v);
     if (flexible) d.rprev[g] = 0.0;
     u[g] = 0.0;
     dot += v * v;
@@ -486,7 +487,7 @@ __global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double pn = c ? z[g] + c[g] : z[g];
     p[g] = pn;
-    if (p32) p32[g] = (float)pn;
+    if (p32) p32[g] = f64_to_f32(pn);
   }
 }
 
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
     const double rn = ro - alpha * f[g];
     if (rprev) rprev[g] = ro;
     r[g] = rn;
-    if (r32) r32[g] = (float)rn;
+    if (r32) r32[g] = f64_to_f32(rn);
     dot += rn * rn;
   }
   double total;
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem
       res = b[g] - s;
     }
     r[g] = res;
-    d.r32[g] = (float)res;
+    d.r32[g] = f64_to_f32(res);
     dot += res * res;
   }
   double total;
@@ -597,7 +598,7 @@ __global__ void pcg_direction_kernel(const DevProblem d, const double* __restric
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double pn = (c ? z[g] + c[g] : z[g]) + beta * p[g];
     p[g] = pn;
-    if (p32) p32[g] = (float)pn;
+    if (p32) p32[g] = f64_to_f32(pn);
   }
 }
 
@@ -838,6 +839,19 @@ cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out,
 }
 }  // namespace
 
+// Self-check of the integer-op conversion against the conversion instruction, for each
+// 64-bit pattern as a binary64; NaN matches NaN whatever the payload.
+__global__ void convert_check_kernel(const unsigned long long* __restrict__ bits, long long n,
+                                     unsigned long long* mismatches) {
+  unsigned long long bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = __longlong_as_double((long long)bits[i]);
+    const float a = f64_to_f32(x), b = __double2float_rn(x);
+    if (!(__float_as_uint(a) == __float_as_uint(b) || (a != a && b != b))) ++bad;
+  }
+  if (bad) atomicAdd(mismatches, bad);
+}
+
 // ================================================================ launchers
 cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_out, __nv_bfloat16* geo16_out,
                             double* mloc, int* bad,
@@ -981,6 +995,14 @@ cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double
 
 cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
   pcg_direction_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_check(const unsigned long long* bits, long long n, unsigned long long* mismatches,
+                                 cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  convert_check_kernel<<<grid_for((int)std::min<long long>(n, 1 << 30), 256, 4096), 256, 0, s>>>(bits, n, mismatches);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

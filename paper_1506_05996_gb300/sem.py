@@ -59,6 +59,7 @@ _SIGS = {
     "sem_set_tiles": ([_vp, _int, _int], _int),
     "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
     "sem_profile": ([_vp, _int], _int),
+    "sem_selfcheck_convert": ([_vp, _i64, _P(_i64)], _int),
     "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
     "sem_net_create": ([ctypes.c_uint64, _P(_vp)], _int),
     "sem_net_destroy": ([_vp], None),
@@ -260,6 +261,15 @@ def sem_autotune(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(_lib.sem_autotune(h, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def sem_selfcheck_convert(bits):
+    """Mismatches of the library's FP64 -> FP32 conversion against the GPU's, over the 64-bit
+    patterns in `bits` (a CUDA int64 tensor)."""
+    n = ctypes.c_int64()
+    b = bits.contiguous()
+    _check(_lib.sem_selfcheck_convert(ctypes.c_void_p(b.data_ptr()), int(b.numel()), ctypes.byref(n)))
+    return n.value
 
 
 def sem_profile(h, enable):

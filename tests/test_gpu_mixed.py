@@ -174,3 +174,29 @@ def test_fp32_preconditioner_with_fp64_operator():
     assert abs(hist[-1] - tr) <= 1e-3 * tr
     u = P.to_ref(x)
     assert np.max(np.abs(u - u_ref)) <= 1e-5 * np.max(np.abs(u_ref))
+
+
+def test_integer_conversion_matches_the_hardware():
+    """The FP64 -> FP32 conversion the PCG vector kernels use (integer operations on the bit
+    layouts) gives the bits of the conversion instruction: random patterns, every binary32
+    exponent, ties and near-ties of the rounding, overflow, binary32 subnormals, zeros,
+    infinities and NaNs."""
+    from paper_1506_05996_gb300 import sem
+    rng = np.random.default_rng(99)
+    pats = [rng.integers(0, 2 ** 63, 1 << 20, dtype=np.int64) * np.where(rng.random(1 << 20) < 0.5, 1, -1)]
+    # binary64 values near binary32 ones: f * (1 + k 2^-24) with k around +-1 (ties), at all exponents
+    f = (rng.random(1 << 18) + 1.0) * np.exp2(rng.integers(-160, 130, 1 << 18)).astype(np.float64)
+    with np.errstate(over="ignore"):
+        f = f.astype(np.float32).astype(np.float64)
+    for k in (-1.0, -1.0 + 2.0 ** -29, 1.0, 1.0 - 2.0 ** -29, 1.0 + 2.0 ** -29, 3.0, 0.5):
+        pats.append((f * (1.0 + k * 2.0 ** -24)).view(np.int64))
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, 2.0 ** -149, 2.0 ** -150,
+                        1.5 * 2.0 ** -150, 2.0 ** -126, 3.4028235677973366e38, 3.4028235677973362e38,
+                        3.4028234663852886e38, 1e308, 2.0 ** -1022], dtype=np.float64).view(np.int64)
+    pats.append(special)
+    # every binary64 exponent that lands in or near the binary32 range, with several fractions
+    ex = np.arange(800, 1300, dtype=np.int64)
+    fr = np.array([0, 1, 1 << 28, (1 << 28) + 1, (1 << 29) - 1, 3 << 28, (1 << 52) - 1], dtype=np.int64)
+    pats.append(((ex[:, None] << 52) | fr[None, :]).reshape(-1))
+    bits = torch.as_tensor(np.concatenate(pats), device="cuda")
+    assert sem.sem_selfcheck_convert(bits) == 0
