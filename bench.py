@@ -248,25 +248,25 @@ def schwarz_flops(n, ne):
     """Flops the patch kernel's algorithm executes per launch (FMA = 2, add or multiply = 1):
     per 1D line of P = n+3 nodes, the even/odd folded forward contraction takes 2H + 2HP +
     (P odd) NE and the backward one H (2P + 2) + (P odd) 2 NE, H = P // 2, NE = P - H;
-    3 P^2 lines each way, then P^3 scalings by the stored inverse diagonal and P^3 by
-    8/(hx hy hz)."""
+    3 P^2 lines each way, then P^3 scalings by the stored inverse diagonal (which carries the
+    patch scale 8/(hx hy hz))."""
     P = n + 3
     H, odd = P // 2, P % 2
     NE = P - H
     fwd = 2 * H + 2 * H * P + odd * NE
     bwd = H * (2 * P + 2) + odd * 2 * NE
-    return ne * (3.0 * P * P * (fwd + bwd) + 2.0 * P ** 3)
+    return ne * (3.0 * P * P * (fwd + bwd) + 1.0 * P ** 3)
 
 
 def ax_flops(n, ne):
     """Flops the operator kernel executes per launch (FMA = 2): per 1D line of p = n+1 nodes
     the folded D contraction takes 2H + H (4H + 2) + (p odd) 3H, H = p // 2, with 6 p^2
-    lines (3 gradients, 3 divergences); per node 15 for G grad u, 2 for lambda m u and 3 for
-    the sums of the three divergence terms."""
+    lines (3 gradients, 3 divergences); per node 15 for G grad u, and 4 for the three
+    divergence terms and lambda m u (stored lambda m, one FMA)."""
     p = n + 1
     H, odd = p // 2, p % 2
     line = 2 * H + H * (4 * H + 2) + odd * 3 * H
-    return ne * (6.0 * p * p * line + 20.0 * p ** 3)
+    return ne * (6.0 * p * p * line + 19.0 * p ** 3)
 
 
 def run_gpu(args):
@@ -358,7 +358,7 @@ def run_gpu(args):
         flops = None
     # DRAM bytes per launch from one ncu capture of the same kernel at 24^3 hexes, scaled
     # by the element count (the traffic is per element); null for other kernels
-    traffic = {"schwarz_local": 292.5e6 * NE / 13824, "ax_local": 516.0e6 * NE / 13824}.get(kern)
+    traffic = {"schwarz_local": 293.1e6 * NE / 13824}.get(kern)
     paper_flops = {"schwarz_local": schwarz_flops_paper, "ax_local": ax_flops_paper}.get(kern)
     roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
             "peak_source": "FP64 FMA loop measured on this pool (nominal 1.25 TFLOP/s)",

@@ -177,13 +177,11 @@ int update_free_sides(sem_t* h) {
   CK(cudaStreamSynchronize(h->stream));
   h->d.pvar = any ? h->pvar : nullptr;
   // the patch solves' diagonals depend on the pencils of each element
-  CK(sem::launch_sw_diag(h->d, h->swd, h->sws, h->stream));
-  CK(sem::launch_sw_diag_f32(h->d, h->swd32, h->sws32, h->stream));
+  CK(sem::launch_sw_diag(h->d, h->swd, h->stream));
+  CK(sem::launch_sw_diag_f32(h->d, h->swd32, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->d.swd = h->swd;
-  h->d.sws = h->sws;
   h->d.swd32 = h->swd32;
-  h->d.sws32 = h->sws32;
   h->invalidate();
   return SEM_OK;
 }
@@ -461,8 +459,6 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->pvar, (size_t)nb.ne, A));
   CK(h->alloc(&h->swd, (size_t)(nb.ne * P3), A));
   CK(h->alloc(&h->swd32, (size_t)(nb.ne * P3), A));
-  CK(h->alloc(&h->sws, (size_t)nb.ne, A));
-  CK(h->alloc(&h->sws32, (size_t)nb.ne, A));
   if (int rc = update_free_sides(h)) return rc;
   CK(h->alloc(&d.wl, (size_t)(nb.ne * p3), A));
   CK(h->alloc(&d.wp, (size_t)(nb.ne * P3), A));

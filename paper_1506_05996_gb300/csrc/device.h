@@ -1,7 +1,7 @@
 // Device-side data of one problem and the kernel launchers (kernels.cu).
 // Layouts (all device memory, element order = the library's order):
 //   l2g   int32 [ne * p^3]       local node l = i + p (j + p k) of element e at e*p^3 + l
-//   geo   f64 [ne][7][p^3]       G1..G6 (= w|J| J^-1 J^-T entries xx xy xz yy yz zz) and m = w|J|
+//   geo   f64 [ne][7][p^3]       G1..G6 (= w|J| J^-1 J^-T entries xx xy xz yy yz zz) and lambda m, m = w|J|
 //   exyz  f64 [ne][8][3]         element vertex coordinates (VTK corner order)
 //   g2l   CSR over DOFs -> local nodes (ascending), owner[g] = first local copy
 //   ip    int32 [ne * P^3]       extended-box patch table, P = n + 3, -1 = absent
@@ -108,12 +108,10 @@ struct DevProblem {
   const double* Sv = nullptr;       // [3][P*P] pencils with a free low / high / both side(s)
   const double* evv = nullptr;      // [3][P]
   const double* hbox = nullptr;     // ne*3
-  // per element patch, from hbox, the pencil eigenvalues and lambda (sw_diag_kernel):
-  // the inverted diagonal of Eq. z at [e][(b + P c) + P^2 a] and the scale 8/(hx hy hz)
+  // per element patch, from hbox, the pencil eigenvalues and lambda (sw_diag_kernel): the
+  // inverted diagonal of Eq. z times the scale 8/(hx hy hz), at [e][(b + P c) + P^2 a]
   const double* swd = nullptr;
   const float* swd32 = nullptr;
-  const double* sws = nullptr;
-  const float* sws32 = nullptr;
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* Btab32 = nullptr;    // the same in FP32
   const int* ecv = nullptr;
@@ -193,10 +191,10 @@ cudaError_t launch_schwarz_local_f32(const DevProblem& d, const double* r, float
                                      cudaStream_t s);
 cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
                                           cudaStream_t s);
-cudaError_t launch_sw_diag(const DevProblem& d, double* dg, double* sc, cudaStream_t s);
+cudaError_t launch_sw_diag(const DevProblem& d, double* dg, cudaStream_t s);
 cudaError_t launch_convert_check(const unsigned long long* bits, long long n, unsigned long long* mismatches,
                                  cudaStream_t s);
-cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, float* sc, cudaStream_t s);
+cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);

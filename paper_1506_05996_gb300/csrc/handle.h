@@ -178,8 +178,8 @@ struct sem_s {
   int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch
   uint8_t* mask = nullptr;
   uint8_t* pvar = nullptr;          // free sides of every element (see update_free_sides)
-  double *swd = nullptr, *sws = nullptr;   // patch-solve diagonals and scales (update_free_sides)
-  float *swd32 = nullptr, *sws32 = nullptr;
+  double* swd = nullptr;             // patch-solve diagonals, scaled (update_free_sides)
+  float* swd32 = nullptr;
   double* pw = nullptr;             // overlap weights of P^f (sem_set_weights)
   float* pw32 = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;

@@ -136,24 +136,26 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   __syncthreads();
   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
   const T lam = (T)d.lambda;
+  const bool lam_zero = d.lambda == 0.0;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
     const T ur = sA[l], us = sB[l], ut = sC[l];
-    T G[6], mm;
+    T G[6], lm;   // lm: the c-term factor lambda m (stored as such; 0 skips the load)
     if (!RECOMP) {
       const TG* gp = geo_of<TG>(d) + (size_t)e * 7 * p3 + l;
 #pragma unroll
       for (int c = 0; c < 6; ++c) G[c] = factor<T>(gp[c * p3]);
-      mm = factor<T>(gp[6 * p3]);
+      lm = lam_zero ? T(0) : factor<T>(gp[6 * p3]);
     } else {
-      T det;
+      T det, mm;
       geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
+      lm = lam * mm;
     }
     sA[l] = G[0] * ur + G[1] * us + G[2] * ut;
     sB[l] = G[1] * ur + G[3] * us + G[4] * ut;
     sC[l] = G[2] * ur + G[4] * us + G[5] * ut;
-    rk[k] = lam * mm * uk[k];
+    rk[k] = lm;
   }
   __syncthreads();
   // divergence by D^T: the A lines (j=tx, k=ty) into su, then the B lines (i=tx, k=ty)
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T v = su[l] + res[k] + rk[k];
+    const T v = rk[k] * uk[k] + (su[l] + res[k]);   // lambda m u + the divergence terms
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
       yd[g] = (masked >> k) & 1u ? (double)x[g] : (double)v;

@@ -108,22 +108,20 @@ __device__ __forceinline__ void axis_bwd(int v, const T* sS, const T* sSv, const
 template <typename T> __device__ __forceinline__ const T* swd_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* swd_of<double>(const DevProblem& d) { return d.swd; }
 template <> __device__ __forceinline__ const float* swd_of<float>(const DevProblem& d) { return d.swd32; }
-template <typename T> __device__ __forceinline__ const T* sws_of(const DevProblem& d);
-template <> __device__ __forceinline__ const double* sws_of<double>(const DevProblem& d) { return d.sws; }
-template <> __device__ __forceinline__ const float* sws_of<float>(const DevProblem& d) { return d.sws32; }
 
-// The diagonal of the fast diagonalisation (Eq. z) of every element patch, inverted, and
-// its scale 8/(hx hy hz): dg[e][(b + P c) + P^2 a] = 1 / (4(l_a/hx^2 + l_b/hy^2 + l_c/hz^2)
-// + lambda) with each axis' pencil eigenvalues. One CTA of P*P threads per element; run once
-// per handle (and again when the Dirichlet set changes the pencils), so that the patch
-// kernels spend no divisions on it.
+// The diagonal of the fast diagonalisation (Eq. z) of every element patch, inverted and
+// times the patch scale 8/(hx hy hz): dg[e][(b + P c) + P^2 a] = (8/(hx hy hz)) / (4(l_a/hx^2 +
+// l_b/hy^2 + l_c/hz^2) + lambda) with each axis' pencil eigenvalues. The scale commutes with
+// the contractions, so it is applied here once instead of to every input node. One CTA of
+// P*P threads per element; run once per handle (and again when the Dirichlet set changes
+// the pencils), so that the patch kernels spend no divisions on it.
 template <int P, typename T, bool VAR>
-__global__ void __launch_bounds__(P * P) sw_diag_kernel(const DevProblem d, T* __restrict__ dg, T* __restrict__ sc) {
+__global__ void __launch_bounds__(P * P) sw_diag_kernel(const DevProblem d, T* __restrict__ dg) {
   constexpr int P2 = P * P, P3 = P * P * P;
   const int e = blockIdx.x, tx = threadIdx.x, x = tx % P, y = tx / P;
   const double hxd = d.hbox[3 * e], hyd = d.hbox[3 * e + 1], hzd = d.hbox[3 * e + 2];
   const T ihx2 = (T)(1.0 / (hxd * hxd)), ihy2 = (T)(1.0 / (hyd * hyd)), ihz2 = (T)(1.0 / (hzd * hzd));
-  if (tx == 0) sc[e] = (T)(8.0 / (hxd * hyd * hzd));
+  const T scale = (T)(8.0 / (hxd * hyd * hzd));
   const int vb = VAR ? d.pvar[e] : 0;
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
   const double* evx = vx ? d.evv + (vx - 1) * P : d.ev;
@@ -133,7 +131,7 @@ __global__ void __launch_bounds__(P * P) sw_diag_kernel(const DevProblem d, T* _
   const T lbc = (T)evy[x] * ihy2 + (T)evz[y] * ihz2;
   T* out = dg + (size_t)e * P3 + tx;
 #pragma unroll
-  for (int a = 0; a < P; ++a) out[a * P2] = recip(four * ((T)evx[a] * ihx2 + lbc) + lam);
+  for (int a = 0; a < P; ++a) out[a * P2] = scale * recip(four * ((T)evx[a] * ihx2 + lbc) + lam);
 }
 
 // One CTA of P*P threads per element (P = n + 3). Thread (x, y) owns one line of the
@@ -167,7 +165,6 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const int e_raw = blk * EPB + grp;
   const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
   const int e = active ? e_raw : d.ne - 1;
-  const T scale = sws_of<T>(d)[e];
   // pencil variant per axis (bit 2a: free low side, bit 2a+1: free high side)
   const int vb = VAR ? d.pvar[e] : 0;
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
@@ -179,7 +176,7 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
     const int g = ipe[x + P * (y + P * K)];
     T v = (g >= 0 && !d.mask[g]) ? (T)r[g] : T(0);
     if (wts != nullptr && g >= 0) v = v * wts[g];
-    col[K] = v * scale;
+    col[K] = v;
   }
   __syncthreads();
   // along K: line (I=x, J=y)
@@ -290,24 +287,24 @@ cudaError_t launch_sw_P(const DevProblem& d, const TR* r, T* wp, const PcgState*
 }
 
 template <int P, typename T>
-cudaError_t launch_sw_diag_P(const DevProblem& d, T* dg, T* sc, cudaStream_t s) {
-  if (d.pvar != nullptr) sw_diag_kernel<P, T, true><<<d.ne, P * P, 0, s>>>(d, dg, sc);
-  else sw_diag_kernel<P, T, false><<<d.ne, P * P, 0, s>>>(d, dg, sc);
+cudaError_t launch_sw_diag_P(const DevProblem& d, T* dg, cudaStream_t s) {
+  if (d.pvar != nullptr) sw_diag_kernel<P, T, true><<<d.ne, P * P, 0, s>>>(d, dg);
+  else sw_diag_kernel<P, T, false><<<d.ne, P * P, 0, s>>>(d, dg);
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_sw_diag_t(const DevProblem& d, T* dg, T* sc, cudaStream_t s) {
+cudaError_t launch_sw_diag_t(const DevProblem& d, T* dg, cudaStream_t s) {
   if (d.ne == 0) return cudaSuccess;
   switch (d.P) {
-    case 5: return launch_sw_diag_P<5, T>(d, dg, sc, s);
-    case 6: return launch_sw_diag_P<6, T>(d, dg, sc, s);
-    case 7: return launch_sw_diag_P<7, T>(d, dg, sc, s);
-    case 8: return launch_sw_diag_P<8, T>(d, dg, sc, s);
-    case 9: return launch_sw_diag_P<9, T>(d, dg, sc, s);
-    case 10: return launch_sw_diag_P<10, T>(d, dg, sc, s);
-    case 11: return launch_sw_diag_P<11, T>(d, dg, sc, s);
+    case 5: return launch_sw_diag_P<5, T>(d, dg, s);
+    case 6: return launch_sw_diag_P<6, T>(d, dg, s);
+    case 7: return launch_sw_diag_P<7, T>(d, dg, s);
+    case 8: return launch_sw_diag_P<8, T>(d, dg, s);
+    case 9: return launch_sw_diag_P<9, T>(d, dg, s);
+    case 10: return launch_sw_diag_P<10, T>(d, dg, s);
+    case 11: return launch_sw_diag_P<11, T>(d, dg, s);
     default: return cudaErrorInvalidValue;
   }
 }

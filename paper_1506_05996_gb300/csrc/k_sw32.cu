@@ -10,7 +10,7 @@ cudaError_t launch_schwarz_local_f32_in32(const DevProblem& d, const float* r, f
                                           cudaStream_t s) {
   return launch_schwarz_local_t<float, float>(d, r, wp, st, s);
 }
-cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, float* sc, cudaStream_t s) {
-  return launch_sw_diag_t<float>(d, dg, sc, s);
+cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, cudaStream_t s) {
+  return launch_sw_diag_t<float>(d, dg, s);
 }
 }  // namespace sem

@@ -5,8 +5,8 @@ namespace sem {
 cudaError_t launch_schwarz_local(const DevProblem& d, const double* r, double* wp, const PcgState* st, cudaStream_t s) {
   return launch_schwarz_local_t<double, double>(d, r, wp, st, s);
 }
-cudaError_t launch_sw_diag(const DevProblem& d, double* dg, double* sc, cudaStream_t s) {
-  return launch_sw_diag_t<double>(d, dg, sc, s);
+cudaError_t launch_sw_diag(const DevProblem& d, double* dg, cudaStream_t s) {
+  return launch_sw_diag_t<double>(d, dg, s);
 }
 bool sw_tile_ok(int P, int epb) { return sw_tile_ok_t<double>(P, epb) && sw_tile_ok_t<float>(P, epb); }
 }  // namespace sem

@@ -43,19 +43,19 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
     double* gp = geo + (size_t)e * 7 * p3 + t;
 #pragma unroll
     for (int c = 0; c < 6; ++c) gp[c * p3] = G[c];
-    gp[6 * p3] = m;
+    gp[6 * p3] = d.lambda * m;   // the c-term's factor lambda m, ready for the operator
   }
   if (geo32 != nullptr) {   // the same factors rounded to FP32 for the mixed path
     float* gp = geo32 + (size_t)e * 7 * p3 + t;
 #pragma unroll
     for (int c = 0; c < 6; ++c) gp[c * p3] = (float)G[c];
-    gp[6 * p3] = (float)m;
+    gp[6 * p3] = (float)(d.lambda * m);
   }
   if (geo16 != nullptr) {   // and to BF16 (one rounding from FP64, to nearest)
     __nv_bfloat16* gp = geo16 + (size_t)e * 7 * p3 + t;
 #pragma unroll
     for (int c = 0; c < 6; ++c) gp[c * p3] = __double2bfloat16(G[c]);
-    gp[6 * p3] = __double2bfloat16(m);
+    gp[6 * p3] = __double2bfloat16(d.lambda * m);
   }
 }
 
