@@ -128,6 +128,11 @@ int build_coarse(sem_t* h) {
     CK(up_csr(L.A, D.A));
     CK(up_csr(L.P, D.P));
     CK(up_csr(L.R, D.R));
+    if (h->amg_kind == SEM_COARSE_VCYCLE && L.M.val.empty()) {   // the V-cycle runs as M, N, Q
+      h->coarse_err = "V-cycle level without its fused cycle matrices";
+      d.nfree = 0;
+      return SEM_OK;
+    }
     if (!L.M.val.empty()) {
       CK(up_csr(L.M, D.M));
       CK(up_csr(L.N, D.N));
@@ -156,7 +161,6 @@ int build_coarse(sem_t* h) {
   CK(h->alloc(&d.cb, amg.coarsest_n, h->coarse_allocs));
   CK(h->alloc(&d.cx, amg.coarsest_n, h->coarse_allocs));
   CK(h->alloc(&d.cres, nfree, h->coarse_allocs));
-  CK(h->alloc(&d.ctmp, nfree, h->coarse_allocs));
   CK(h->alloc(&d.Rc, nfree, h->coarse_allocs));
   CK(h->alloc(&d.Zc, nfree, h->coarse_allocs));
   CK(h->alloc(&d.Zc32, nfree, h->coarse_allocs));

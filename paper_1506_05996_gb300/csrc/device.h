@@ -126,7 +126,6 @@ struct DevProblem {
   double* cb = nullptr;             // coarsest rhs / solution work
   double* cx = nullptr;
   double* cres = nullptr;           // level-0 residual for repeated cycles
-  double* ctmp = nullptr;
   // work
   double* wl = nullptr;             // ne*p^3 local results (FP32 view in the mixed path)
   double* wp = nullptr;             // ne*P^3 patch results (FP32 view in the mixed path)

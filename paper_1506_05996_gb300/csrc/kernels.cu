@@ -273,11 +273,6 @@ __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, c
   }
 }
 
-__global__ void add_kernel(int n, double* __restrict__ x, const double* __restrict__ y, const PcgState* st) {
-  if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + y[i];
-}
-
 // x = Ainv b at the dense coarsest level: one block of kRowBlock threads per row.
 __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double* __restrict__ Ainv,
                                                             const double* __restrict__ b, double* __restrict__ x,
@@ -743,37 +738,10 @@ inline int grid_for(int n, int block, int cap) {
 constexpr double kOmega = 2.0 / 3.0;
 constexpr int kCycles = 3;
 
-// V(1,1) cycle at `level` for right-hand side b, result in out (out != b).
-cudaError_t vcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
-  if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
-    ++g_kernel_launches;
-    return cudaGetLastError();
-  }
-  const DevAmgLevel& L = d.levels[level];
-  const int n = L.A.n, gb = grid_for(n, 256, 4096);
-  amg_jacobi0_kernel<<<gb, 256, 0, s>>>(n, L.dinv, b, L.x, kOmega, st);
-  ++g_kernel_launches;
-  ROWS_LAUNCH(amg_resid_kernel, L.A, L.A, b, L.x, L.t, st);
-  ++g_kernel_launches;
-  double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
-  double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
-  const int nc = L.R.n;
-  ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, bc, st);
-  ++g_kernel_launches;
-  cudaError_t err = vcycle(d, level + 1, bc, xc, st, s);
-  if (err != cudaSuccess) return err;
-  ROWS_LAUNCH(amg_prolong_add_kernel, L.P, L.P, xc, L.x, st);
-  ++g_kernel_launches;
-  ROWS_LAUNCH(amg_jacobi_post_kernel, L.A, L.A, L.dinv, b, L.x, out, kOmega, st);
-  ++g_kernel_launches;
-  return cudaGetLastError();
-}
-
-
 // V(1,1) cycle at `level` as down and up passes (smoothed kind): b_c = M b, the next level
 // (or the dense inverse), then out = z + N b + Q x_c (z null: out = V b). Two kernels per
-// level instead of five; the same linear map as vcycle() up to rounding.
+// level instead of the cycle's five steps (pre-smoothing from zero, residual, restriction,
+// prolongation, post-smoothing); the same linear map up to rounding.
 cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double* out, const double* z,
                          const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
@@ -917,10 +885,7 @@ cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, cons
 // Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero, or one K-cycle.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  const bool fused = d.amg_kind == 0 && d.nlevels > 0 && d.levels[0].M.n > 0;
-  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s)
-                    : fused         ? vcycle_fused(d, 0, d.Rc, d.Zc, nullptr, st, s)
-                                    : vcycle(d, 0, d.Rc, d.Zc, st, s);
+  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s) : vcycle_fused(d, 0, d.Rc, d.Zc, nullptr, st, s);
   if (err != cudaSuccess) return err;
   if (d.nlevels == 0 || d.amg_kind == 1) {
     if (d.pfp32) {
@@ -931,18 +896,11 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   }
   const DevCsr& A0 = d.levels[0].A;
   const int gb = grid_for(A0.n, 256, 4096);
-  for (int c = 1; c < kCycles; ++c) {
+  for (int c = 1; c < kCycles; ++c) {   // Zc += V (Rc - A0 Zc), the add folded into the up pass
     ROWS_LAUNCH(amg_resid_kernel, A0, A0, d.Rc, d.Zc, d.cres, st);
     ++g_kernel_launches;
-    if (fused) {   // Zc += V cres, the add folded into the up pass
-      err = vcycle_fused(d, 0, d.cres, d.Zc, d.Zc, st, s);
-      if (err != cudaSuccess) return err;
-      continue;
-    }
-    err = vcycle(d, 0, d.cres, d.ctmp, st, s);
+    err = vcycle_fused(d, 0, d.cres, d.Zc, d.Zc, st, s);
     if (err != cudaSuccess) return err;
-    add_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.ctmp, st);
-    ++g_kernel_launches;
   }
   if (d.pfp32) {
     to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
