@@ -141,7 +141,7 @@ template <> __device__ __forceinline__ const __nv_bfloat16* geo_of<__nv_bfloat16
   return d.geo16;
 }
 // binary64 -> binary32, round to nearest (ties to even), written from the IEEE-754 bit
-// layouts with 32-bit integer operations. On this part the conversion instruction runs on
+// layouts with 32-bit integer operations. On GB300 the conversion instruction runs on
 // the FP64 pipe, at about 1/64 of the FP32 rate. The memory-bound PCG vector kernels that
 // write FP32 copies of FP64 vectors use this instead (measured faster there); inside the
 // arithmetic-heavy element kernels the instruction stays (this branchy form was measured
