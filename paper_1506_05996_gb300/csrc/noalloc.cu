@@ -6,7 +6,7 @@
 // there), code handed a fixed memory budget by a host framework that owns every
 // allocation, or real-time loops where an allocator call is not allowed. They
 // hold the mesh tables and vectors in memory they were given, and need the
-// operator without the library asking the driver for anything.
+// operator without the library allocating memory or creating CUDA objects.
 //
 // The two kernels of the ordinary apply are reused unchanged: the element kernel
 // writes one FP64 value per local GLL node into scratch memory and the gather
