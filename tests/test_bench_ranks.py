@@ -56,3 +56,46 @@ def test_single_rank_defaults():
         os.environ.pop(k, None)
     r = bench.Ranks("gloo")
     assert r.world == 1 and r.max(3.5) == 3.5 and r.total_rate(10, 2.0) == 5.0
+
+
+def _count_fold_apply(p):
+    """Operations of one folded D contraction on a line of p nodes, counted loop by loop as
+    the operator kernel runs them (FMA = 2 flops, add / subtract / multiply = 1)."""
+    H, odd = p // 2, p % 2
+    f = 2 * H                       # even / odd sums of the line
+    for _ in range(H):
+        f += 1 if odd else 0        # middle column times v[H]
+        f += 2 * H + 2 * H          # the two H-term FMA chains
+        f += 2                      # out[i] and out[n - i]
+    if odd:
+        f += 2 * H                  # the middle output
+    return f
+
+
+def _count_pencil(P):
+    H, odd = P // 2, P % 2
+    NE = P - H
+    fwd = 2 * H
+    for c in range(P):
+        fwd += 2 * H + (1 if (odd and c < NE) else 0)
+    bwd = 0
+    for _ in range(H):
+        bwd += 2 * NE + 2 * (P - NE) + 2
+    if odd:
+        bwd += 2 * NE
+    return fwd, bwd
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8])
+def test_executed_flop_counts_follow_the_kernels(n):
+    """bench.py's roofline counts equal the operations of the folded kernels, counted loop by
+    loop: 6 p^2 operator lines and 19 flops per node (G grad u, the divergence sums and the
+    lambda m u FMA); 3 P^2 forward and 3 P^2 backward pencil lines and P^3 diagonal scalings."""
+    import bench
+    p, P = n + 1, n + 3
+    assert bench.ax_flops(n, 1) == 6 * p * p * _count_fold_apply(p) + 19 * p ** 3
+    fwd, bwd = _count_pencil(P)
+    assert bench.schwarz_flops(n, 1) == 3 * P * P * (fwd + bwd) + P ** 3
+    # the folded forms cost less than the paper's unfolded counts
+    assert bench.ax_flops(n, 1) < bench.ax_flops_paper(n, 1)
+    assert bench.schwarz_flops(n, 1) < bench.schwarz_flops_paper(n, 1)
