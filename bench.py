@@ -386,18 +386,20 @@ def run_gpu(args):
 
     # ---- operator apply: stored and recomputed geometry (HBM roofline fractions)
     def time_apply(pr, reps=20, prec="fp64"):
-        pr.set_precision(prec)
-        xin = torch.randn(G, dtype=torch.float64, device="cuda")
+        f32io = prec == "fp32io"                 # FP32 vectors in and out (sem_apply_A_f32)
+        pr.set_precision("fp32" if f32io else prec)
+        xin = torch.randn(G, dtype=torch.float32 if f32io else torch.float64, device="cuda")
         y = torch.empty_like(xin)
+        apply = S.sem_apply_A_f32 if f32io else S.sem_apply_A
         for _ in range(3):
-            S.sem_apply_A(pr.h, xin, y)
+            apply(pr.h, xin, y)
         S.sem_profile(pr.h, 1)
         evs = []
         for _ in range(reps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            S.sem_apply_A(pr.h, xin, y)
+            apply(pr.h, xin, y)
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -416,18 +418,19 @@ def run_gpu(args):
         rec.set_precision(prec)
         S.sem_autotune(rec.h)
     for geom, prec, pr in (("stored", "fp64", prob), ("recompute", "fp64", rec),
-                           ("stored", "fp32", prob), ("recompute", "fp32", rec), ("stored", "bf16", prob)):
+                           ("stored", "fp32", prob), ("recompute", "fp32", rec), ("stored", "bf16", prob),
+                           ("stored", "fp32io", prob)):
         ms, kms = time_apply(pr, prec=prec)
         # algorithmic bytes of one apply: x read and y written (FP64, G each), l2g (int32 per
         # local node), stored factors (7 per local node, FP64, FP32 or BF16) or the 24 vertex
         # coordinates of each element
-        fb = {"fp64": 8, "fp32": 4, "bf16": 2}[prec]
+        fb = {"fp64": 8, "fp32": 4, "bf16": 2, "fp32io": 4}[prec]
         wb = 8 if prec == "fp64" else 4
+        vb = 4 if prec == "fp32io" else 8       # bytes of an x or y entry
         geo_bytes = 7 * fb * L if geom == "stored" else 24 * 8 * NE
-        alg_bytes = 16 * G + 4 * L + geo_bytes
-        # the element kernel alone: x (FP64) and the mask read, l2g, factors, local results
-        # written (FP64 or FP32)
-        k_bytes = 9 * G + 4 * L + geo_bytes + wb * L
+        alg_bytes = 2 * vb * G + 4 * L + geo_bytes
+        # the element kernel alone: x and the mask read, l2g, factors, local results written
+        k_bytes = (vb + 1) * G + 4 * L + geo_bytes + wb * L
         key = geom + ("" if prec == "fp64" else "_" + prec)
         ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
                    "paper_equivalent_tflops_ax_local": ax_flops_paper(ORDER, NE) / (kms * 1e-3) / 1e12,

@@ -136,6 +136,14 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev);
  * y_i = x_i on masked nodes. x_dev and y_dev: N doubles, must not alias. */
 int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev);
 
+/* sem_apply_A_f32 - y = A x with FP32 vectors in and out (device pointers, G floats each,
+ * caller-owned, x != y): the FP32 element arithmetic of SEM_PREC_FP32 (BF16 factors under
+ * SEM_PREC_BF16) with no FP64 vector at all, so no conversions. Masked DOFs return x. For
+ * x exactly representable in FP32 the result is, to a few ulps, the FP32 rounding of what
+ * sem_apply_A returns in FP32 precision. Needs FP32 factors: SEM_MIXED at create, or recomputed geometry
+ * (SEM_ERR_ARG otherwise). Asynchronous on the handle's stream. */
+int sem_apply_A_f32(sem_t* h, const float* x_dev, float* y_dev);
+
 /* sem_apply_P / sem_apply_Pf / sem_apply_Pc - z = P r with P = P^c + P^f (Sec. 4),
  * the fine overlapping-patch part P^f alone (Sec. 4.2, Eq. z) or the coarse part
  * P^c alone (Sec. 4.1, Eq. coarse). r is read as 0 on masked nodes and z is 0

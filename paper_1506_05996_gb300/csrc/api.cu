@@ -605,6 +605,18 @@ int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
   return SEM_OK;
 }
 
+int sem_apply_A_f32(sem_t* h, const float* x_dev, float* y_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (x_dev == nullptr || y_dev == nullptr || (const void*)x_dev == (const void*)y_dev)
+    return fail(SEM_ERR_ARG, "bad vector arguments");
+  if (!h->d.recompute && h->geo32 == nullptr)
+    return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
+  float* wl = reinterpret_cast<float*>(h->d.wl);
+  PROF(h, "ax_local", sem::launch_ax_apply_f32io(h->d, x_dev, wl, y_dev, h->stream));
+  PROF(h, "gather", sem::launch_gather_shared_f32io(h->d, wl, x_dev, y_dev, h->stream));
+  return SEM_OK;
+}
+
 static int apply_P_common(sem_t* h, int which, const double* r_dev, double* z_dev) {
   if (int rc = check_handle(h)) return rc;
   if (r_dev == nullptr || z_dev == nullptr || r_dev == z_dev) return fail(SEM_ERR_ARG, "bad vector arguments");

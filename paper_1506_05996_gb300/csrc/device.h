@@ -171,6 +171,10 @@ cudaError_t launch_ax_local_f32(const DevProblem& d, const double* x, float* wl,
 cudaError_t launch_ax_apply(const DevProblem& d, const double* x, double* wl, double* y, cudaStream_t s);
 cudaError_t launch_ax_apply_f32(const DevProblem& d, const double* x, float* wl, double* y, cudaStream_t s);
 cudaError_t launch_gather_shared(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s);
+// the same with FP32 vectors in and out (no conversions)
+cudaError_t launch_ax_apply_f32io(const DevProblem& d, const float* x, float* wl, float* y, cudaStream_t s);
+cudaError_t launch_gather_shared_f32io(const DevProblem& d, const float* wl, const float* xin, float* y,
+                                       cudaStream_t s);
 cudaError_t launch_gather_shared_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
                                      cudaStream_t s);
 cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float* wl, const PcgState* st,

@@ -81,7 +81,7 @@ constexpr int ax_smem_bytes() {
 template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT, typename TG>
 __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
                                                                T* __restrict__ wl, const PcgState* st,
-                                                               double* __restrict__ yd) {
+                                                               TX* __restrict__ yd) {
   if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
   __shared__ FoldedD<p, T> Fg, Fd;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
     const T v = rk[k] * uk[k] + (su[l] + res[k]);   // lambda m u + the divergence terms
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
-      yd[g] = (masked >> k) & 1u ? (double)x[g] : (double)v;
+      yd[g] = (masked >> k) & 1u ? x[g] : (TX)v;   // y in x's type
     } else {
       out[l] = v;
     }
@@ -222,7 +222,7 @@ bool ax_tile_ok_t(int p, int epb) {
 }
 
 template <int p, typename T, typename TX, int EPB, bool DIRECT>
-cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd, cudaStream_t s) {
+cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd, cudaStream_t s) {
   if constexpr (ax_tile_supported<p, T, EPB>()) {
     const int grid = (d.ne + EPB - 1) / EPB;
     constexpr bool kF32 = sizeof(T) == 4;
@@ -242,7 +242,7 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgStat
 }
 
 template <int p, typename T, typename TX, bool DIRECT>
-cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd, cudaStream_t s) {
+cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd, cudaStream_t s) {
   switch (sizeof(T) == 4 ? d.epb_ax32 : d.epb_ax) {
     case 2: return launch_ax_epb<p, T, TX, 2, DIRECT>(d, x, wl, st, yd, s);
     case 4: return launch_ax_epb<p, T, TX, 4, DIRECT>(d, x, wl, st, yd, s);
@@ -252,9 +252,10 @@ cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState*
 }
 
 // Local results of every node into wl (DIRECT = false), or, for y = A x with the
-// interior-first numbering, interior nodes into yd and the others into wl (DIRECT = true).
+// interior-first numbering, interior nodes into yd (in x's type) and the others into wl
+// (DIRECT = true).
 template <typename T, typename TX, bool DIRECT>
-cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, double* yd,
+cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd,
                               cudaStream_t s) {
   if (DIRECT && d.Gi == 0) return cudaErrorInvalidValue;
   switch (d.p) {

@@ -12,4 +12,7 @@ cudaError_t launch_ax_local_f32_in32(const DevProblem& d, const float* x, float*
                                      cudaStream_t s) {
   return launch_ax_local_t<float, float, false>(d, x, wl, st, nullptr, s);
 }
+cudaError_t launch_ax_apply_f32io(const DevProblem& d, const float* x, float* wl, float* y, cudaStream_t s) {
+  return launch_ax_local_t<float, float, true>(d, x, wl, nullptr, y, s);
+}
 }  // namespace sem

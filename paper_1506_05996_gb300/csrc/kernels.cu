@@ -61,14 +61,14 @@ __global__ void __launch_bounds__(p * p * p) geometry_kernel(const DevProblem d,
 
 // y = A x on DOFs g0..G-1 (g0 = 0, or d.Gi when the operator kernel wrote the interior
 // DOFs itself): y = x on masked DOFs, else the sum of the local copies.
-template <typename T>
+template <typename T, typename TY>
 __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__ wl,
-                                       const double* __restrict__ xin, double* __restrict__ y, int g0) {
+                                       const TY* __restrict__ xin, TY* __restrict__ y, int g0) {
   for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
     T s = 0;
     s = gather_dof(d, wl, g);
-    y[g] = (double)s;
+    y[g] = (TY)s;
   }
 }
 
@@ -834,24 +834,30 @@ cudaError_t launch_geometry(const DevProblem& d, double* geo_out, float* geo32_o
 }
 
 cudaError_t launch_gather_shared(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
-  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
+  gather_identity_kernel<double, double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 cudaError_t launch_gather_shared_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
                                      cudaStream_t s) {
-  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
+  gather_identity_kernel<float, double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_shared_f32io(const DevProblem& d, const float* wl, const float* xin, float* y,
+                                       cudaStream_t s) {
+  gather_identity_kernel<float, float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, d.Gi);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 cudaError_t launch_gather_identity(const DevProblem& d, const double* wl, const double* xin, double* y, cudaStream_t s) {
-  gather_identity_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
+  gather_identity_kernel<double, double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 cudaError_t launch_gather_identity_f32(const DevProblem& d, const float* wl, const double* xin, double* y,
                                        cudaStream_t s) {
-  gather_identity_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
+  gather_identity_kernel<float, double><<<d.nblk, kVecBlock, 0, s>>>(d, wl, xin, y, 0);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

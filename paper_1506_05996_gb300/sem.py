@@ -43,6 +43,7 @@ _SIGS = {
     "sem_get_mask": ([_vp, _vp], _int),
     "sem_set_mask": ([_vp, _vp], _int),
     "sem_apply_A": ([_vp, _vp, _vp], _int),
+    "sem_apply_A_f32": ([_vp, _vp, _vp], _int),
     "sem_apply_P": ([_vp, _vp, _vp], _int),
     "sem_apply_Pf": ([_vp, _vp, _vp], _int),
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
@@ -157,6 +158,12 @@ def sem_get_mask(h, mask):
 
 def sem_set_mask(h, mask):
     return _check(_lib.sem_set_mask(h, _dev(mask, torch.uint8, sem_num_dofs(h))))
+
+
+def sem_apply_A_f32(h, x, y):
+    """y = A x with FP32 CUDA tensors in and out (FP32 element arithmetic, no conversions)."""
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_A_f32(h, _dev(x, torch.float32, n), _dev(y, torch.float32, n)))
 
 
 def sem_apply_A(h, x, y):

@@ -20,7 +20,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "sem.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(sem_[a-zA-Z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(sem_[a-zA-Z0-9_]+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol(lib):

@@ -200,3 +200,24 @@ def test_integer_conversion_matches_the_hardware():
     pats.append(((ex[:, None] << 52) | fr[None, :]).reshape(-1))
     bits = torch.as_tensor(np.concatenate(pats), device="cuda")
     assert sem.sem_selfcheck_convert(bits) == 0
+
+
+@pytest.mark.parametrize("geom", ["stored", "recompute"])
+def test_fp32_vector_apply_is_the_rounded_fp32_apply(geom):
+    """sem_apply_A_f32 (FP32 vectors, no conversions) runs the same element and gather
+    arithmetic as sem_apply_A in FP32 precision: for x exactly representable in FP32, its result
+    is that apply's result rounded to FP32 (to a few ulps, should the compiler contract the two
+    instantiations differently); masked DOFs return x exactly."""
+    from paper_1506_05996_gb300 import sem
+    P = _pair(lattice_hex_mesh(3, 0.2, 7), 5, 0.7, geom)
+    x32 = torch.randn(P.gpu.n_dof, dtype=torch.float32, device="cuda")
+    P.gpu.set_precision("fp32")
+    y64 = P.gpu.apply_A(x32.double())
+    y32 = torch.empty_like(x32)
+    sem.sem_apply_A_f32(P.gpu.h, x32, y32)
+    scale = float(y64.abs().max())
+    assert float((y32.double() - y64).abs().max()) <= 4 * 2.0 ** -24 * scale
+    gm = torch.zeros(P.gpu.n_dof, dtype=torch.uint8, device="cuda")
+    sem.sem_get_mask(P.gpu.h, gm)
+    masked = gm.bool()
+    assert bool(masked.any()) and torch.equal(y32[masked], x32[masked])
