@@ -131,6 +131,28 @@ int sem_mass(const sem_t* h, double* m_dev);
 int sem_get_mask(const sem_t* h, uint8_t* mask_dev);
 int sem_set_mask(sem_t* h, const uint8_t* mask_dev);
 
+/* sem_boundary_mask - the Dirichlet mask (Eq. pde, u = 0 on the boundary part of the
+ * problem statement): the same as sem_get_mask, under the name of the problem statement's
+ * boundary call. The mask is handle state (set at create, changed by sem_set_mask) rather
+ * than an argument of every apply and solve, because the coarse space, the AMG hierarchy
+ * and the patch pencils of Sec. 4 are built from it once per change. */
+int sem_boundary_mask(const sem_t* h, uint8_t* mask_dev);
+
+/* sem_apply_mass - b_dev[N] = m_N s_N on free DOFs and 0 on Dirichlet DOFs: the load
+ * vector of the weak form (Eq. pdeweak) by GLL quadrature, with the lumped mass m_N of
+ * sem_mass (Sec. 2.4). s_dev[N]: the source s sampled at the DOF positions of
+ * sem_dof_coords. Both are caller-owned device buffers of N doubles; they may be the
+ * same buffer. Asynchronous on the handle's stream. Errors: SEM_ERR_ARG, SEM_ERR_CUDA. */
+int sem_apply_mass(const sem_t* h, const double* s_dev, double* b_dev);
+
+/* sem_coarse_levels - sizes of the coarse solver's hierarchy (Sec. 4.1): sizes_host[0] is
+ * the number of free vertices (the Q1 coarse space), then one entry per aggregation level
+ * below it, the last being the level solved by the dense inverse. Up to max_levels entries
+ * are written (sizes_host may be NULL when max_levels is 0); *n_levels_host receives the
+ * full count, 0 when there is no coarse space (no free vertex, or its set-up failed).
+ * Host-only; no device work. Errors: SEM_ERR_ARG. */
+int sem_coarse_levels(const sem_t* h, int max_levels, int64_t* sizes_host, int* n_levels_host);
+
 /* sem_apply_A - y = A_D x (Eq. R / Algorithm 2 then gather, Eq. gather):
  * rows and columns of Dirichlet nodes are replaced by the identity, so
  * y_i = x_i on masked nodes. x_dev and y_dev: N doubles, must not alias. */
@@ -273,8 +295,8 @@ int sem_profile_read(sem_t* h, int max_kernels, char* names_host, int64_t* launc
  * summed by the gather kernel) is a file-scope static device array of
  * SEM_NOALLOC_MAX_LOCAL_NODES doubles (16 MiB), held by every GPU that loads the
  * library until the process exits. It calls no cudaMalloc, cudaFree or allocating
- * library routine. The paper has no counterpart; it is the operator of Eq. R with
- * the geometric factors recomputed from the vertices.
+ * library routine. The paper has no counterpart; it computes y = A_D x with the
+ * geometric factors recomputed from the vertices.
  *   order          2..8.  n_hex, n_dof: sizes; n_hex*(order+1)^3 must not exceed
  *                  SEM_NOALLOC_MAX_LOCAL_NODES, else SEM_ERR_ARG.
  *   lambda         screening coefficient >= 0.

@@ -577,6 +577,31 @@ int sem_get_mask(const sem_t* h, uint8_t* mask_dev) {
   return SEM_OK;
 }
 
+int sem_boundary_mask(const sem_t* h, uint8_t* mask_dev) { return sem_get_mask(h, mask_dev); }
+
+int sem_apply_mass(const sem_t* h, const double* s_dev, double* b_dev) {
+  if (int rc = check_handle(h)) return rc;
+  if (s_dev == nullptr || b_dev == nullptr) return fail(SEM_ERR_ARG, "NULL vector");
+  CK(sem::launch_mass_load(h->d, h->mN, s_dev, b_dev, h->stream));
+  return SEM_OK;
+}
+
+int sem_coarse_levels(const sem_t* h, int max_levels, int64_t* sizes_host, int* n_levels_host) {
+  if (int rc = check_handle(h)) return rc;
+  if (n_levels_host == nullptr || max_levels < 0 || (max_levels > 0 && sizes_host == nullptr))
+    return fail(SEM_ERR_ARG, "bad output arguments");
+  if (!h->coarse_ok || h->d.nfree == 0) {
+    *n_levels_host = 0;
+    return SEM_OK;
+  }
+  std::vector<int64_t> sz;
+  for (const auto& L : h->levels) sz.push_back(L.A.n);
+  sz.push_back(h->d.coarsest_n);
+  for (int i = 0; i < (int)sz.size() && i < max_levels; ++i) sizes_host[i] = sz[i];
+  *n_levels_host = (int)sz.size();
+  return SEM_OK;
+}
+
 int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
   if (int rc = check_handle(h)) return rc;
   if (mask_dev == nullptr) return fail(SEM_ERR_ARG, "NULL mask");

@@ -237,6 +237,8 @@ cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const doubl
 // ||out||^2) over the free DOFs
 cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
                             const double* g, double* out, double* norms, cudaStream_t s);
+// b = mask ? 0 : mN * s (lumped GLL load)
+cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s);
 // y = a + b
 cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const double* b, double* y, cudaStream_t s);
 

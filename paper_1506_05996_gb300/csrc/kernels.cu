@@ -675,6 +675,13 @@ __global__ void __launch_bounds__(kVecBlock) heat_rhs_kernel(const DevProblem d,
   }
 }
 
+// Lumped GLL load (Sec. 2.4, with the weak-form source read as s, reading A8):
+// b_N = m_N s_N on free DOFs, 0 on Dirichlet DOFs.
+__global__ void mass_load_kernel(const DevProblem d, const double* __restrict__ mN, const double* sv, double* b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.G; i += gridDim.x * blockDim.x)
+    b[i] = d.mask[i] ? 0.0 : mN[i] * sv[i];
+}
+
 // y = a + b
 __global__ void add_vectors_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
                                    double* __restrict__ y) {
@@ -1016,6 +1023,12 @@ cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const doubl
 cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
                             const double* g, double* out, double* norms, cudaStream_t s) {
   heat_rhs_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, mN, u_prev, g, out, norms);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s) {
+  mass_load_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, mN, sv, b);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -42,6 +42,9 @@ _SIGS = {
     "sem_mass": ([_vp, _vp], _int),
     "sem_get_mask": ([_vp, _vp], _int),
     "sem_set_mask": ([_vp, _vp], _int),
+    "sem_boundary_mask": ([_vp, _vp], _int),
+    "sem_apply_mass": ([_vp, _vp, _vp], _int),
+    "sem_coarse_levels": ([_vp, _int, _vp, _P(_int)], _int),
     "sem_apply_A": ([_vp, _vp, _vp], _int),
     "sem_apply_A_f32": ([_vp, _vp, _vp], _int),
     "sem_apply_P": ([_vp, _vp, _vp], _int),
@@ -154,6 +157,22 @@ def sem_mass(h, m):
 
 def sem_get_mask(h, mask):
     return _check(_lib.sem_get_mask(h, _dev(mask, torch.uint8, sem_num_dofs(h))))
+
+
+def sem_boundary_mask(h, mask):
+    return _check(_lib.sem_boundary_mask(h, _dev(mask, torch.uint8, sem_num_dofs(h))))
+
+
+def sem_apply_mass(h, s, b):
+    n = sem_num_dofs(h)
+    return _check(_lib.sem_apply_mass(h, _dev(s, torch.float64, n), _dev(b, torch.float64, n)))
+
+
+def sem_coarse_levels(h, max_levels=32):
+    sizes = np.zeros(max_levels, dtype=np.int64)
+    n = ctypes.c_int()
+    _check(_lib.sem_coarse_levels(h, max_levels, sizes.ctypes.data_as(_vp), ctypes.byref(n)))
+    return [int(v) for v in sizes[:min(n.value, max_levels)]]
 
 
 def sem_set_mask(h, mask):
@@ -419,6 +438,12 @@ class SemProblem:
         m = self._vec(torch.uint8)
         sem_get_mask(self.h, m)
         return m
+
+    def load(self, s):
+        """b = m_N s on free DOFs, 0 on Dirichlet DOFs (sem_apply_mass)."""
+        b = self._vec()
+        sem_apply_mass(self.h, s, b)
+        return b
 
     def apply_A(self, x):
         y = self._vec()

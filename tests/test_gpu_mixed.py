@@ -221,3 +221,36 @@ def test_fp32_vector_apply_is_the_rounded_fp32_apply(geom):
     sem.sem_get_mask(P.gpu.h, gm)
     masked = gm.bool()
     assert bool(masked.any()) and torch.equal(y32[masked], x32[masked])
+
+
+@pytest.mark.parametrize("reserve", [None, -4])
+def test_fp32_two_scale_on_a_capped_patch_grid(reserve):
+    """The FP32 two-scale apply caps the patch-solve grid so that SMs stay free for the
+    coarse branch, and its CTAs then loop over element groups. 32^3 hexes at n = 2 have
+    more elements than any capped grid holds (at most (SMs - 32) x 32 resident CTAs of at
+    most 8 elements), so the loop takes at least two rounds; reserve = -4 leaves only 4 SMs
+    to the patch solves (many rounds). The fine part alone runs uncapped and is checked
+    against the oracle's bound; the two-scale sum must then equal fine + coarse parts to one
+    FP32 rounding (each patch result is computed by the same arithmetic in both launches)."""
+    from oracle.schwarz import apply_fine_abs
+    from paper_1506_05996_gb300 import sem
+    E, n, lam = 32, 2, 1.0
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert E ** 3 > (nsm - 32) * 32 * 8
+    P = _pair(lattice_hex_mesh(E, 0.2, 12), n, lam, "stored")
+    P.gpu.set_precision("fp32")
+    if reserve is not None:
+        sem.sem_set_overlap(P.gpu.h, nsm + reserve)
+    r = np.random.default_rng(13).standard_normal(P.ref.G)
+    rg = P.to_gpu(r)
+    zf = P.gpu.apply_P(rg, "fine")
+    zc = P.gpu.apply_P(rg, "coarse")
+    z = P.gpu.apply_P(rg, "two-scale")
+    exact = zf + zc
+    assert float((z - exact).abs().max()) <= 2.0 ** -23 * float(exact.abs().max())
+    assert float((z - exact).abs().div(exact.abs() + 1e-300).max()) <= 2.0 ** -23
+    zabs = apply_fine_abs(r, P.ref.ip, P.ref.S, P.ref.ev, P.ref.h, lam, P.ref.mask)
+    K = 6 * (n + 3) + 24
+    free = P.ref.mask == 0
+    z64 = P.ref.apply_Pf(r)
+    assert np.max(np.abs(P.to_ref(zf) - z64)[free] / (gamma(K) * zabs[free])) <= 1.0
