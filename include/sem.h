@@ -270,6 +270,19 @@ int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host);
 int sem_selfcheck_convert(const uint64_t* bits_dev, int64_t n, int64_t* mismatches_host);
 
 /*
+ * sem_measure_fma_peak - arithmetic peak of one pipe, measured with the library's own
+ * multiply-add loop: every thread of 8 CTAs of 256 threads per SM runs 8 independent
+ * chains of `iters` fused multiply-adds in FP64 (precision = SEM_PREC_FP64) or FP32
+ * (SEM_PREC_FP32) on the current device's default stream. *tflops_host receives
+ * 2 x (multiply-adds) / (shortest of three timed launches, after one warm-up launch) in
+ * TFLOP/s, *ms_host that launch's time. It is the denominator of the element kernels'
+ * arithmetic roofline (Sec. 5 reports the kernels' GFLOP/s against the device peak). It
+ * allocates and frees a small output buffer and synchronises. Errors: SEM_ERR_ARG,
+ * SEM_ERR_OOM, SEM_ERR_CUDA.
+ */
+int sem_measure_fma_peak(int precision, int64_t iters, double* tflops_host, double* ms_host);
+
+/*
  * sem_profile / sem_profile_read - per-kernel timing of the library's own launches.
  * While enabled, a CUDA event pair is recorded on the handle's stream around each
  * kernel launch (or launch group: "coarse_amg" is the whole AMG V-cycle sequence),

@@ -64,6 +64,7 @@ _SIGS = {
     "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
     "sem_profile": ([_vp, _int], _int),
     "sem_selfcheck_convert": ([_vp, _i64, _P(_i64)], _int),
+    "sem_measure_fma_peak": ([_int, _i64, _P(_dbl), _P(_dbl)], _int),
     "sem_profile_read": ([_vp, _int, _vp, _vp, _vp, _P(_int)], _int),
     "sem_net_create": ([ctypes.c_uint64, _P(_vp)], _int),
     "sem_net_destroy": ([_vp], None),
@@ -296,6 +297,14 @@ def sem_selfcheck_convert(bits):
     b = bits.contiguous()
     _check(_lib.sem_selfcheck_convert(ctypes.c_void_p(b.data_ptr()), int(b.numel()), ctypes.byref(n)))
     return n.value
+
+
+def sem_measure_fma_peak(precision, iters):
+    """(TFLOP/s, ms) of the library's FMA loop in FP64 ("fp64") or FP32 ("fp32")."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    prec = {"fp64": SEM_PREC_FP64, "fp32": SEM_PREC_FP32}[precision]
+    _check(_lib.sem_measure_fma_peak(prec, int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def sem_profile(h, enable):
