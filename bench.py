@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 48^3-hex precision block of the default line")
     ap.add_argument("--precision-variant", action="store_true",
                     help="48^3 hexes, +-20%% (seed 2), n=7, lambda=0: FP64 vs mixed time-to-1e-8 and the "
                          "per-result error of the mixed solution")
@@ -271,11 +273,89 @@ def ax_flops(n, ne):
     return ne * (6.0 * p * p * line + 19.0 * p ** 3)
 
 
+def dw_ops_schwarz(n, ne):
+    """FP32-pipe operations (add, multiply or FMA, one each) the double-FP32 patch kernel
+    executes per launch, counted from its loops: a pair sum or difference is a TwoSum (6)
+    plus 2 adds, a pair product 1 multiply + 3 FMAs, a pair multiply-accumulate 12; per
+    1D line of P = n+3 nodes the folded forward contraction takes 2H sums, (P odd) NE
+    products and H (NE + H) multiply-accumulates, the backward one H (NE + H) + (P odd) NE
+    multiply-accumulates and 2H sums; 3 P^2 lines each way, P^3 products by the diagonal
+    and P^3 input splits (2 FP32 operations each; their integer operations are not counted)."""
+    P = n + 3
+    H, odd = P // 2, P % 2
+    NE = P - H
+    fwd = 8 * 2 * H + 4 * odd * NE + 12 * H * (NE + H)
+    bwd = 12 * H * (NE + H) + 8 * 2 * H + 12 * odd * NE
+    return ne * (3.0 * P * P * (fwd + bwd) + 4.0 * P ** 3 + 2.0 * P ** 3)
+
+
+def dw_ops_ax(n, ne):
+    """FP32-pipe operations of the double-FP32 operator kernel per launch (the counts of
+    dw_ops_schwarz): per 1D line of p = n+1 nodes, H = p // 2, 2H pair sums for the even/odd
+    folding, (p odd) H products by the middle column, 2 H^2 + (p odd) H
+    multiply-accumulates and 2H output sums, 6 p^2 lines; per node 3 metric products (a
+    product and two multiply-accumulates, 28 each), one pair sum of the divergence, the
+    lambda m u term with the last sum (20), one input split (2) and one output join (6)."""
+    p = n + 1
+    H, odd = p // 2, p % 2
+    line = 8 * 2 * H + 4 * odd * H + 12 * (2 * H * H + odd * H) + 8 * 2 * H
+    return ne * (6.0 * p * p * line + (84.0 + 8.0 + 20.0 + 2.0 + 6.0) * p ** 3)
+
+
+def _cpu_ax_worker(E, nthreads_list, reps, q):
+    """The oracle's matrix-free operator at full size: one thread, then element chunks on
+    a thread pool (numpy releases the GIL inside its loops), the gather as written."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from synth import lattice_hex_mesh
+    from oracle.problem import Problem
+    from oracle.operator import matfree_local
+    t0 = time.perf_counter()
+    pr = Problem(lattice_hex_mesh(E, A_FULL, SEED_FULL), ORDER, LAM, coarse_solver=None, with_schwarz=False)
+    t_setup = time.perf_counter() - t0
+    x = np.random.default_rng(0).standard_normal(pr.G)
+    out = {"G": int(pr.G), "setup_s": t_setup, "threads": {}}
+    for nt in nthreads_list:
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            if nt == 1:
+                pr.apply_A(x)
+            else:
+                xf = np.where(pr.mask > 0, 0.0, x)
+                ne = pr.l2g.shape[0]
+                chunks = np.array_split(np.arange(ne), 4 * nt)
+
+                def work(ix):
+                    a, b = ix[0], ix[-1] + 1
+                    return matfree_local(xf[pr.l2g[a:b]], pr.Dh, pr.Gf[:, a:b], pr.m_loc[a:b], pr.lam)
+
+                with ThreadPoolExecutor(nt) as ex:
+                    r = np.concatenate(list(ex.map(work, chunks)))
+                y = np.bincount(pr.l2g.ravel(), weights=r.ravel(), minlength=pr.G)
+                y = np.where(pr.mask > 0, x, y)
+            ts.append(time.perf_counter() - t0)
+        out["threads"][nt] = min(ts)
+    q.put(out)
+
+
+def oracle_ax_full(E, nthreads_list, reps=2):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_cpu_ax_worker, args=(E, nthreads_list, reps, q))
+    p.start()
+    res = q.get()
+    p.join()
+    return res
+
+
 def run_gpu(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
-    from synth import lattice_hex_mesh, manufactured_s
+    from synth import lattice_hex_mesh, manufactured_s, manufactured_u
     from paper_1506_05996_gb300 import sem as S
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -283,6 +363,8 @@ def run_gpu(args):
     ranks = Ranks("nccl", torch.device("cuda", local))
     world, rank = ranks.world, ranks.rank
     barrier, max_over_ranks = ranks.barrier, ranks.max
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
 
     peaks = {}
     try:
@@ -290,25 +372,34 @@ def run_gpu(args):
     except Exception:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fp64_peak_tflops = 1.20   # FP64 FMA loop measured at 1995 MHz (nominal 1.25 TFLOP/s)
-    fp64_peak_source = "FP64 FMA loop measured at 1995 MHz (nominal 1.25 TFLOP/s)"
+    hbm_source = "MEASURED_PEAKS.json hbm_gbs (copy)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"
 
-    mesh = lattice_hex_mesh(E_FULL, A_FULL, SEED_FULL)
-    stream = torch.cuda.current_stream()
-    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
+    # ---- arithmetic peaks: the library's FMA loop, with the clock sampled meanwhile
+    clk_peak = ClockSampler(local)
+    clk_peak.start()
+    fp64_tf, _ = S.sem_measure_fma_peak("fp64", 8000)
+    fp32_tf, _ = S.sem_measure_fma_peak("fp32", 400000)
+    ck = clk_peak.stop()
+    meas = {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "fp32_tops": fp32_tf / 2,
+            "sm_mhz_during": ck.get("sm_mhz"), "hbm_gbs": hbm_peak, "hbm_source": hbm_source,
+            "how": "sem_measure_fma_peak: 8 chains of dependent FMAs per thread, 2048 threads per SM, "
+                   "best of 3 CUDA-event-timed launches; FMA = 2 flops; fp32_tops counts one FP32-pipe "
+                   "operation per FMA"}
+
+    def solve_problem(E, a, seed, lam):
+        mesh = lattice_hex_mesh(E, a, seed)
+        pr = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, lam, geom="stored", mixed=True)
+        X = pr.dof_coords()
+        b = pr.load(torch.as_tensor(manufactured_s(X.cpu().numpy(), lam), device="cuda"))   # b = m_N s
+        return mesh, pr, X, b
+
+    mesh, prob, X, b = solve_problem(E_FULL, A_FULL, SEED_FULL, LAM)
     G, NE = prob.n_dof, mesh.n_hex
-    X = prob.dof_coords()
-    m = prob.mass()
-    # load b = m_N s(x_N) (input preparation, outside the timed region)
-    s_np = manufactured_s(X.cpu().numpy(), LAM)
-    b = (m * torch.as_tensor(s_np, device="cuda")).contiguous()
     x = torch.empty_like(b)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 512 MB > L2
     # tile shapes (elements per CTA) by the library's autotuner, per precision, before any
-    # timing: P32 tunes the FP32 patch solve on FP64 input, then the mixed path's FP32
-    # kernels, then the FP64 kernels (the handle ends in FP64)
+    # timing; the handle ends in SEM_PREC_FP64
     tiles = {}
-    for prec in ("p32", "fp32", "fp64"):
+    for prec in ("p32", "fp32", "fp64_native", "fp64"):
         prob.set_precision(prec)
         tiles[prec] = list(S.sem_autotune(prob.h))
 
@@ -316,77 +407,93 @@ def run_gpu(args):
         rc, it, hist, tr = S.sem_solve(prob.h, b, x, RTOL, 1000, want_history=False)
         return rc, it, tr
 
-    for _ in range(args.warmup):
-        one_solve()
-    torch.cuda.synchronize()
+    def timed_solves(steps, warmup, pre=None, clocks=None):
+        for _ in range(warmup):
+            one_solve()
+        evs, its, trs = [], [], []
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, it, tr = one_solve()
+            e1.record(stream)
+            evs.append((e0, e1))
+            its.append(it)
+            trs.append(tr)
+            if rc != 0:
+                raise RuntimeError("solve did not converge: rc=%d" % rc)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - w0
+        t = max_over_ranks(sum(a.elapsed_time(c) for a, c in evs) / 1e3) / steps
+        return t, its[-1], trs[-1], wall
 
-    # ---- timed region: K solves, L2 flushed between steps (outside the events)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    S.sem_profile(prob.h, 1)
+    # ---- headline: SEM_PREC_FP64 solves as users run them (one graph launch per solve)
+    prob.set_precision("fp64")
     clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    iters, trs = [], []
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        rc, it, tr = one_solve()
-        ev[k][1].record(stream)
-        iters.append(it)
-        trs.append(tr)
-        if rc != 0:
-            raise RuntimeError("solve did not converge: rc=%d" % rc)
-    torch.cuda.synchronize()
-    barrier()
-    t_wall = time.perf_counter() - t_wall0
+    per_step, it64, tr64, t_wall = timed_solves(args.steps, args.warmup, clocks=clocks)
     clk = clocks.stop()
-    # the FP64 pipe's peak at the clock seen during the timed region: 2 FP64 FMAs per clock
-    # per SM (the 1.20 TFLOP/s loop measurement at 1995 MHz agrees with this count)
-    if clk.get("sm_mhz"):
-        nsm = torch.cuda.get_device_properties(local).multi_processor_count
-        fp64_peak_tflops = nsm * 2 * 2 * clk["sm_mhz"] * 1e6 / 1e12
-        fp64_peak_source = ("derived: %d SMs x 2 FP64 FMA per clock x 2 flops x %.0f MHz (median SM clock "
-                            "in the timed region); an FMA loop measured 1.20 TFLOP/s at 1995 MHz"
-                            % (nsm, clk["sm_mhz"]))
+    value = ranks.total_rate(G, per_step) / 1e9
+
+    # ---- the same solves with per-kernel CUDA events (host-driven loop, one event pair per
+    # launch), for the kernel breakdown and the dominant kernel's roofline
+    S.sem_profile(prob.h, 1)
+    t_prof, _, _, _ = timed_solves(args.steps, 0)
     prof = S.sem_profile_read(prob.h)
     S.sem_profile(prob.h, 0)
-    t_local = sum(a.elapsed_time(bv) for a, bv in ev) / 1e3
-    t_steps = max_over_ranks(t_local)
-    per_step = t_steps / args.steps
-    value = ranks.total_rate(G, per_step) / 1e9
-    launches = sum(v[0] for v in prof.values())
-
-    # dominant kernel over the timed region and its roofline
+    launches_per_step = sum(v[0] for v in prof.values()) / args.steps
     kern, (nl, tot) = max(prof.items(), key=lambda kv: kv[1][1])
     avg_ms = tot / nl
-    if kern == "schwarz_local":
-        flops = schwarz_flops(ORDER, NE)
-    elif kern == "ax_local":
-        flops = ax_flops(ORDER, NE)
-    else:
-        flops = None
-    # DRAM bytes per launch from one ncu capture of the same kernel at 24^3 hexes, scaled
-    # by the element count (the traffic is per element); null for other kernels
-    traffic = {"schwarz_local": 293.1e6 * NE / 13824}.get(kern)
-    paper_flops = {"schwarz_local": schwarz_flops_paper, "ax_local": ax_flops_paper}.get(kern)
-    roof = {"kernel": kern, "bound": "alu", "unit": "TFLOP/s", "peak": fp64_peak_tflops,
-            "peak_source": fp64_peak_source,
-            "achieved": (flops / (avg_ms * 1e-3) / 1e12) if flops else None,
-            "flops_per_launch": flops,
-            "flops_note": "executed by the kernel's folded algorithm, FMA = 2 (the paper's unfolded "
-                          "O_P / O_R counts are in paper_equivalent_tflops)",
-            "paper_equivalent_tflops": (paper_flops(ORDER, NE) / (avg_ms * 1e-3) / 1e12) if paper_flops else None,
+    ops = {"schwarz_local": dw_ops_schwarz, "ax_local": dw_ops_ax}.get(kern)
+    fp64eq = {"schwarz_local": schwarz_flops, "ax_local": ax_flops}.get(kern)
+    # DRAM bytes per launch: one ncu capture of the kernel at 24^3 hexes, scaled by the
+    # element count (None until the current kernel has been captured)
+    traffic = {"schwarz_local": None}.get(kern)
+    roof = {"kernel": kern + " (double-FP32)", "bound": "alu", "unit": "Tops/s",
+            "peak": meas["fp32_tops"],
+            "peak_source": "measured FP32 FMA loop (sem_measure_fma_peak), one operation per FMA, at %s MHz"
+                           % ck.get("sm_mhz"),
+            "achieved": (ops(ORDER, NE) / (avg_ms * 1e-3) / 1e12) if ops else None,
+            "ops_per_launch": ops(ORDER, NE) if ops else None,
+            "ops_note": "FP32-pipe operations of the pair arithmetic, counted from the kernel's loops "
+                        "(TwoSum 6, pair sum 8, pair product 4, multiply-accumulate 12); integer "
+                        "operations of the binary64 splits are not counted",
+            "fp64_equivalent_tflops": (fp64eq(ORDER, NE) / (avg_ms * 1e-3) / 1e12) if fp64eq else None,
+            "fp64_pipe_peak_tflops": fp64_tf,
             "avg_launch_ms": avg_ms, "launches": nl, "traffic": traffic,
-            "traffic_source": "ncu dram__bytes_read+write of the kernel at 24^3 hexes (profiles/"
-                              "hot_kernels_24cube_n7.md) scaled by the element count",
-            "share_of_step": tot / (t_local * 1e3)}
+            "share_of_step": tot / (t_prof * args.steps * 1e3)}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] else None
 
-    # ---- operator apply: stored and recomputed geometry (HBM roofline fractions)
-    def time_apply(pr, reps=20, prec="fp64"):
-        f32io = prec == "fp32io"                 # FP32 vectors in and out (sem_apply_A_f32)
+    def variant(prec, weighted=False):
+        prob.set_precision(prec)
+        S.sem_set_weights(prob.h, 1 if weighted else 0)
+        t, it, tr, _ = timed_solves(args.steps, args.warmup)
+        prob.set_precision("fp64")
+        S.sem_set_weights(prob.h, 0)
+        return {"time_to_1e-8_s": t, "gdofs_solved": world * G / t / 1e9, "iterations": it,
+                "true_rel_res": tr, "speedup_vs_fp64": per_step / t}
+
+    native = variant("fp64_native")
+    native["dtype"] = "binary64 everywhere (FP64 pipe)"
+    native["fp64_speedup_over_native"] = native["time_to_1e-8_s"] / per_step
+    mixed = variant("fp32")
+    mixed["dtype"] = ("FP32 operator and patch solves; FP64 vectors, dots, recurrences, coarse solve, "
+                      "residual replacement (double-FP32 operator) and final check")
+    p32 = variant("p32")
+    p32["dtype"] = "double-FP32 operator; FP32 patch solves and prolongation sums; FP64 vectors and recurrences"
+    weighted = {"fp64": variant("fp64", True), "mixed": variant("fp32", True),
+                "note": "not the paper's P^f: W (sum of patch solves) W, w = c^-1/2 per DOF (c patches contain it)"}
+    prob.set_precision("fp64")
+
+    # ---- operator apply (Ax GDOF/s) and its HBM roofline
+    def time_apply(pr, prec, reps=20):
+        f32io = prec == "fp32io"
         pr.set_precision("fp32" if f32io else prec)
         xin = torch.randn(G, dtype=torch.float32 if f32io else torch.float64, device="cuda")
         y = torch.empty_like(xin)
@@ -405,10 +512,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         pk = S.sem_profile_read(pr.h)
         S.sem_profile(pr.h, 0)
-        ms = sorted(a.elapsed_time(bv) for a, bv in evs)[reps // 2]
-        kms = pk["ax_local"][1] / pk["ax_local"][0]
         pr.set_precision("fp64")
-        return ms, kms
+        return sorted(a.elapsed_time(c) for a, c in evs)[reps // 2], pk["ax_local"][1] / pk["ax_local"][0]
 
     ax = {}
     p3 = (ORDER + 1) ** 3
@@ -417,92 +522,37 @@ def run_gpu(args):
     for prec in ("fp32", "fp64"):
         rec.set_precision(prec)
         S.sem_autotune(rec.h)
-    for geom, prec, pr in (("stored", "fp64", prob), ("recompute", "fp64", rec),
+    for geom, prec, pr in (("stored", "fp64", prob), ("stored", "fp64_native", prob), ("recompute", "fp64", rec),
                            ("stored", "fp32", prob), ("recompute", "fp32", rec), ("stored", "bf16", prob),
                            ("stored", "fp32io", prob)):
-        ms, kms = time_apply(pr, prec=prec)
-        # algorithmic bytes of one apply: x read and y written (FP64, G each), l2g (int32 per
-        # local node), stored factors (7 per local node, FP64, FP32 or BF16) or the 24 vertex
-        # coordinates of each element
-        fb = {"fp64": 8, "fp32": 4, "bf16": 2, "fp32io": 4}[prec]
-        wb = 8 if prec == "fp64" else 4
-        vb = 4 if prec == "fp32io" else 8       # bytes of an x or y entry
+        ms, kms = time_apply(pr, prec)
+        # algorithmic bytes of one apply: x read and y written (G each), the local-to-global
+        # index (int32 per local node), stored factors (7 per local node: 8 bytes as binary64
+        # or as an FP32 pair, 4 as FP32, 2 as BF16) or the 24 vertex coordinates per element
+        fb = {"fp64": 8, "fp64_native": 8, "fp32": 4, "bf16": 2, "fp32io": 4}[prec]
+        vb = 4 if prec == "fp32io" else 8
+        wb = 8 if prec in ("fp64", "fp64_native") else 4
         geo_bytes = 7 * fb * L if geom == "stored" else 24 * 8 * NE
         alg_bytes = 2 * vb * G + 4 * L + geo_bytes
-        # the element kernel alone: x and the mask read, l2g, factors, local results written
-        k_bytes = (vb + 1) * G + 4 * L + geo_bytes + wb * L
+        # the element kernel alone: x and the mask read once per DOF; l2g and the factors per
+        # local node; interior DOFs of y written directly in y's type (Gi of them), the other
+        # local results in the local-result type
+        Gi = NE * (ORDER - 1) ** 3
+        k_bytes = (vb + 1) * G + 4 * L + geo_bytes + vb * Gi + wb * (L - Gi)
         key = geom + ("" if prec == "fp64" else "_" + prec)
         ax[key] = {"gdofs": G / (ms * 1e-3) / 1e9, "ms": ms, "ax_local_ms": kms,
-                   "paper_equivalent_tflops_ax_local": ax_flops_paper(ORDER, NE) / (kms * 1e-3) / 1e12,
+                   "bytes_per_dof": alg_bytes / G, "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
+                   "frac_hbm_roofline": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
                    "ax_local_frac_hbm_roofline": k_bytes / (kms * 1e-3) / 1e9 / hbm_peak,
-                   "tflops_ax_local": ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12,
-                   "bytes_per_dof": alg_bytes / G,
-                   "hbm_gbs": alg_bytes / (ms * 1e-3) / 1e9,
-                   "frac_hbm_roofline": alg_bytes / (ms * 1e-3) / 1e9 / hbm_peak}
-        if prec == "fp64":
-            ax[key]["frac_fp64_peak"] = ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12 / fp64_peak_tflops
+                   "paper_equivalent_tflops_ax_local": ax_flops_paper(ORDER, NE) / (kms * 1e-3) / 1e12}
+        if prec == "fp64_native" or (geom == "recompute" and prec == "fp64"):
+            ax[key]["frac_fp64_pipe_peak"] = ax_flops(ORDER, NE) / (kms * 1e-3) / 1e12 / fp64_tf
+        if prec == "fp64" and geom == "stored":
+            ax[key]["frac_fp32_ops_peak"] = dw_ops_ax(ORDER, NE) / (kms * 1e-3) / 1e12 / meas["fp32_tops"]
+    ax["note"] = ("bytes count x, mask and y once per DOF; stored: fp64 = double-FP32 kernel on pair "
+                  "factors, fp64_native = binary64; recompute fp64 runs binary64 (the pair kernel needs "
+                  "stored factors)")
     rec.close()
-
-    # ---- mixed path: FP32 operator / preconditioner, FP64 recurrences and replacements
-    prob.set_precision("fp32")
-    for _ in range(args.warmup):
-        one_solve()
-    S.sem_profile(prob.h, 1)
-    mev = []
-    m_iters, m_trs = [], []
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rc, it, tr = one_solve()
-        e1.record(stream)
-        mev.append((e0, e1))
-        m_iters.append(it)
-        m_trs.append(tr)
-    torch.cuda.synchronize()
-    mprof = S.sem_profile_read(prob.h)
-    S.sem_profile(prob.h, 0)
-    prob.set_precision("fp64")
-    t_mixed = max_over_ranks(sum(a.elapsed_time(bv) for a, bv in mev) / 1e3) / args.steps
-    mixed = {"time_to_1e-8_s": t_mixed, "gdofs_solved": world * G / t_mixed / 1e9, "iterations": m_iters[-1],
-             "true_rel_res": m_trs[-1], "speedup_vs_fp64": per_step / t_mixed,
-             "dtype": "FP32 operator and patch solves; FP64 vectors, dots, recurrences, coarse solve, "
-                      "residual replacement and final check",
-             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(mprof.items(), key=lambda kv: -kv[1][1])}}
-
-    def timed_variant(prec, weighted):
-        """K timed solves (events, L2 flushed) in another configuration of the same handle."""
-        prob.set_precision(prec)
-        S.sem_set_weights(prob.h, weighted)
-        for _ in range(args.warmup):
-            one_solve()
-        vev, v_iters, v_trs = [], [], []
-        torch.cuda.synchronize()
-        for k in range(args.steps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rc, it, tr = one_solve()
-            e1.record(stream)
-            vev.append((e0, e1))
-            v_iters.append(it)
-            v_trs.append(tr)
-        torch.cuda.synchronize()
-        prob.set_precision("fp64")
-        S.sem_set_weights(prob.h, 0)
-        t = max_over_ranks(sum(a.elapsed_time(bv) for a, bv in vev) / 1e3) / args.steps
-        return {"time_to_1e-8_s": t, "gdofs_solved": world * G / t / 1e9, "iterations": v_iters[-1],
-                "true_rel_res": v_trs[-1], "speedup_vs_fp64": per_step / t}
-
-    # ---- FP64 operator with an FP32 preconditioner (no residual replacement needed)
-    p32 = timed_variant("p32", False)
-    p32["dtype"] = ("FP64 operator, vectors, dots and recurrences; FP32 patch solves and prolongation sums "
-                    "(the coarse AMG in FP64)")
-    # ---- overlap-weighted P^f (not in the paper): same arithmetic per iteration, fewer iterations
-    weighted = {"fp64": timed_variant("fp64", True), "p32": timed_variant("p32", True),
-                "mixed": timed_variant("fp32", True),
-                "note": "P^f as W (sum of patch solves) W, w = c^-1/2 per DOF (c patches contain it)"}
 
     # ---- end to end through the public API with host buffers
     b_host = b.cpu().pin_memory()
@@ -512,52 +562,106 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         b_dev = b_host.to("cuda", non_blocking=True)
-        rc, it, hist, tr = S.sem_solve(prob.h, b_dev, x, RTOL, 1000, want_history=False)
+        S.sem_solve(prob.h, b_dev, x, RTOL, 1000, want_history=False)
         x_host.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
-    t_e2e = (time.perf_counter() - t0) / n_e2e
-    t_e2e = max_over_ranks(t_e2e)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / n_e2e)
+    prob.close()
+
+    # ---- precision variant (48^3 hexes, lambda = 0, seed 2): SEM_PREC_FP64 against the mixed
+    # path and binary64, errors per result against the binary64 solution
+    config3 = None
+    if not args.no_config3:
+        mesh3, pr3, X3, b3 = solve_problem(48, 0.2, 2, 0.0)
+        G3 = pr3.n_dof
+        ustar = torch.as_tensor(manufactured_u(X3.cpu().numpy()), device="cuda")
+        free = ~pr3.mask().bool()
+        sols, c3 = {}, {}
+        for prec in ("fp64_native", "fp64", "fp32"):
+            pr3.set_precision(prec)
+            S.sem_autotune(pr3.h)
+            x3 = torch.empty_like(b3)
+            S.sem_solve(pr3.h, b3, x3, RTOL, 1000, want_history=False)
+            ts = []
+            for _ in range(2):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc, it, hist, tr = S.sem_solve(pr3.h, b3, x3, RTOL, 1000, want_history=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            sols[prec] = x3
+            c3[prec] = {"time_to_1e-8_s": min(ts), "iterations": it, "true_rel_res": tr,
+                        "max_err_vs_manufactured": float((x3 - ustar)[free].abs().max())}
+        ref = sols["fp64_native"]
+        for prec in ("fp64", "fp32"):
+            dlt = sols[prec] - ref
+            c3[prec]["vs_binary64_solution"] = {"max_rel": float(dlt.abs().max() / ref.abs().max()),
+                                                "rel_l2": float(dlt.norm() / ref.norm())}
+        c3["mixed_speedup_vs_fp64"] = c3["fp64"]["time_to_1e-8_s"] / c3["fp32"]["time_to_1e-8_s"]
+        c3["mixed_speedup_vs_binary64"] = c3["fp64_native"]["time_to_1e-8_s"] / c3["fp32"]["time_to_1e-8_s"]
+        c3["fp64_vs_config2_fp64_time_ratio"] = c3["fp64"]["time_to_1e-8_s"] / per_step
+        config3 = {"workload": "unit cube 48^3 hexes, +-20% perturbation seed 2, random numbering/orientation, "
+                               "n=7, lambda=0, Dirichlet", "n_dof": G3,
+                   "note": "errors against the binary64 GPU solution (it matches the oracle to 1e-12 in the "
+                           "parity tests); time of the faster of 2 solves after one warm-up", **c3}
+        pr3.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         res = oracle_sample(E_SAMPLE, 3)
         tc = sum(res["times"]) / len(res["times"])
+        ncores = os.cpu_count() or 1
+        full = oracle_ax_full(E_FULL, [1, ncores])
+        t1, tn = full["threads"][1], full["threads"][ncores]
         cpu = {"value": res["G"] / tc / 1e9, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
                "sample": ("oracle two-scale PCG to 1e-8, same recipe at %d^3 hexes (%d DOFs, %d iterations), "
                           "mean of 3 solves, single thread" % (E_SAMPLE, res["G"], res["iters"][-1])),
-               "cpu": cpu_model(), "host_cores_available": os.cpu_count()}
+               "cpu": cpu_model(), "host_cores_available": ncores,
+               "ax_full_size": {"workload": "oracle matrix-free A x at the full 32^3, n=7 size (%d DOFs)" % full["G"],
+                                "gdofs_1_thread": full["G"] / t1 / 1e9, "s_1_thread": t1,
+                                "gdofs_all_cores": full["G"] / tn / 1e9, "s_all_cores": tn, "cores": ncores,
+                                "how": "element chunks of the oracle's local apply on a thread pool (numpy "
+                                       "releases the GIL), gather as written; best of 2",
+                                "gpu_speedup_fp64_stored": ax["stored"]["gdofs"] / (full["G"] / tn / 1e9)}}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "arith": ("SEM_PREC_FP64: binary64 vectors, dot products, alpha/beta, residual updates and the "
+                      "final true-residual check; operator and patch-solve element kernels and the P-sum in "
+                      "double-FP32 (pairs of FP32 with error-free transforms, 2^-46 per step); "
+                      "fp64_native: binary64 everywhere"),
             "config": {"workload": WORKLOAD, "n_dof": G, "n_hex": NE, "order": ORDER, "lambda": LAM,
                        "rtol": RTOL, "preconditioner": "two-scale (P^c + P^f)", "geometry": "stored",
+                       "loop": "one graph launch per solve (device-evaluated while loop)",
                        "l2": "inputs larger than L2 (0.94 GB stored factors) and a 512 MB flush between steps",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tiles_epb_ax_sw": tiles},
-            "time_to_1e-8_s": per_step, "iterations": iters[-1], "true_rel_res": trs[-1],
-            "wall_s": t_wall,
-            "ax": ax,
-            "mixed": mixed,
-            "p32": p32,
-            "weighted": weighted,
-            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-            "roofline": roof,
+            "time_to_1e-8_s": per_step, "iterations": it64, "true_rel_res": tr64, "wall_s": t_wall,
+            "fp64_native": native, "mixed": mixed, "p32": p32, "weighted": weighted,
+            "profiled": {"ms_per_step": t_prof * 1e3,
+                         "note": "host-driven loop with a CUDA event pair around every launch",
+                         "kernels_ms_per_step": {k: v[1] / args.steps
+                                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}},
+            "ax": ax, "peaks": meas, "roofline": roof, "config3": config3,
             "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,
                     "d2h_bytes_per_step": 8 * G, "s_per_step": t_e2e},
-            "gpu_launches": launches,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches_note": "kernels executed per solve (counted in the profiled pass) x steps",
             "clocks": clk,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    prob.close()
     ranks.close()
 
 
 def run_kernel_case(E):
-    """A few applies of each hot kernel, FP64 then FP32, on an E^3-hex, n = 7 mesh, with the
+    """A few applies of each hot kernel (SEM_PREC_FP64's double-FP32 kernels, binary64, FP32)
+    on an E^3-hex, n = 7 mesh, with the
     tile shapes the autotuner picks; the applies sit in the NVTX range "kernels" (for
     ncu --nvtx --nvtx-include kernels/), the tuning launches outside it."""
     import torch
@@ -567,12 +671,12 @@ def run_kernel_case(E):
     prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
     x = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
     tiles = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64_native", "fp64"):
         prob.set_precision(prec)
         tiles[prec] = S.sem_autotune(prob.h)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("kernels")
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp64_native", "fp32"):
         prob.set_precision(prec)
         for _ in range(2):
             prob.apply_A(x)

@@ -55,7 +55,14 @@ typedef struct sem_s sem_t;
                                       box nodes of Sec. 4.2 (default: face layers only) */
 
 /* arithmetic of the operator and the preconditioner (sem_set_precision) */
-#define SEM_PREC_FP64  0   /* everything in FP64 (default) */
+#define SEM_PREC_FP64  0   /* FP64 vectors, dot products, alpha/beta and residual updates; the element
+                              kernels (operator with stored factors, patch solves) compute in
+                              double-FP32: pairs of FP32 numbers with error-free sums and products on
+                              the FP32 pipe, every step within a few 2^-48 of its operands' magnitudes
+                              (binary64: 2^-53), which matches binary64 results to about 1e-14 of
+                              their magnitude (default). On GB300 the FP64 pipe is 1/64 of the FP32
+                              pipe, and these kernels were bound by it. Vector entries below 2^-80 in
+                              magnitude enter with FP32 precision, below 2^-126 as zero */
 #define SEM_PREC_FP32  1   /* Ax and P in FP32; vectors, dots, alpha/beta, residual updates in
                               FP64; the residual is recomputed with the FP64 operator whenever it
                               fell by 1e3 and before convergence is accepted */
@@ -68,6 +75,9 @@ typedef struct sem_s sem_t;
                               sem_apply_P* as in SEM_PREC_FP32. Needs stored geometry and SEM_MIXED.
                               The solves refuse it (SEM_ERR_ARG): on the smooth components that PCG
                               leaves last, A x is far below |A|(|x|), and the mixed solve stalls */
+
+#define SEM_PREC_FP64_NATIVE 4  /* everything in binary64 on the FP64 pipe (the reference
+                                    arithmetic for SEM_PREC_FP64) */
 
 /* coarse solver P_0 of the two-scale preconditioner (sem_set_coarse_solver) */
 #define SEM_COARSE_VCYCLE  0  /* smoothed aggregation, three V(1,1) damped-Jacobi cycles: a fixed SPD

@@ -183,9 +183,11 @@ int update_free_sides(sem_t* h) {
   // the patch solves' diagonals depend on the pencils of each element
   CK(sem::launch_sw_diag(h->d, h->swd, h->stream));
   CK(sem::launch_sw_diag_f32(h->d, h->swd32, h->stream));
+  CK(sem::launch_split_pairs((long long)h->nb.ne * h->d.P * h->d.P * h->d.P, h->swd, h->swddw, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   h->d.swd = h->swd;
   h->d.swd32 = h->swd32;
+  h->d.swddw = h->swddw;
   h->invalidate();
   return SEM_OK;
 }
@@ -455,6 +457,9 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   {
     std::vector<float> Bt32(Btab.begin(), Btab.end());
     UP(Btab32, Bt32, float);
+    std::vector<sem::dw> Btdw(Btab.size());
+    for (size_t q = 0; q < Btab.size(); ++q) Btdw[q] = sem::dw_split_host(Btab[q]);
+    UP(Btabdw, Btdw, sem::dw);
   }
 #undef UP
   CK(h->upload(&h->coords, coords, A));
@@ -463,6 +468,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&h->pvar, (size_t)nb.ne, A));
   CK(h->alloc(&h->swd, (size_t)(nb.ne * P3), A));
   CK(h->alloc(&h->swd32, (size_t)(nb.ne * P3), A));
+  CK(h->alloc(&h->swddw, (size_t)(nb.ne * P3), A));
+  d.dwk = true;   // SEM_PREC_FP64 (the default) runs its element kernels in double-FP32
   if (int rc = update_free_sides(h)) return rc;
   CK(h->alloc(&d.wl, (size_t)(nb.ne * p3), A));
   CK(h->alloc(&d.wp, (size_t)(nb.ne * P3), A));
@@ -487,6 +494,7 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
 
   // geometric factors (stored variant) and the assembled lumped mass
   if (!d.recompute) CK(h->alloc(&h->geo, (size_t)(7 * nb.ne * p3), A));
+  if (!d.recompute) CK(h->alloc(&h->geodw, (size_t)(7 * nb.ne * p3), A));
   if (!d.recompute && (flags & SEM_MIXED)) {
     CK(h->alloc(&h->geo32, (size_t)(7 * nb.ne * p3), A));
     CK(h->alloc(&h->geo16, (size_t)(7 * nb.ne * p3), A));
@@ -499,6 +507,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
   CK(sem::launch_geometry(d, h->geo, h->geo32, h->geo16, d.wl, bad, h->stream));
   CK(sem::launch_gather_plain(d, d.wl, h->mN, h->stream));
+  if (h->geodw != nullptr) CK(sem::launch_split_pairs((long long)7 * nb.ne * p3, h->geo, h->geodw, h->stream));
+  d.geodw = h->geodw;
   int bad_host = 0;
   CK(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -698,7 +708,7 @@ int sem_net_pair(sem_t* h, const double* b_dev, const double* x_star_dev, const 
 int sem_set_precision(sem_t* h, int precision) {
   if (int rc = check_handle(h)) return rc;
   if (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP32 && precision != SEM_PREC_P32 &&
-      precision != SEM_PREC_BF16)
+      precision != SEM_PREC_BF16 && precision != SEM_PREC_FP64_NATIVE)
     return fail(SEM_ERR_ARG, "unknown precision");
   if (precision == SEM_PREC_FP32 && !h->d.recompute && h->geo32 == nullptr)
     return fail(SEM_ERR_ARG, "FP32 with stored geometry needs SEM_MIXED at sem_create");
@@ -706,8 +716,11 @@ int sem_set_precision(sem_t* h, int precision) {
     return fail(SEM_ERR_ARG, "BF16 needs stored geometry and SEM_MIXED at sem_create");
   h->precision = precision;
   h->d.fp32 = (precision == SEM_PREC_FP32 || precision == SEM_PREC_BF16);
-  h->d.pfp32 = (precision != SEM_PREC_FP64);
+  h->d.pfp32 = (precision != SEM_PREC_FP64 && precision != SEM_PREC_FP64_NATIVE);
   h->d.bf16 = (precision == SEM_PREC_BF16);
+  // every FP64 element kernel (operator with stored factors, patch solve, the mixed path's
+  // residual replacement) runs in double-FP32 unless binary64 is asked for
+  h->d.dwk = (precision != SEM_PREC_FP64_NATIVE);
   return SEM_OK;
 }
 
@@ -831,7 +844,8 @@ long graph_key(const sem_t* h) {
   return (long)(d.fp32 ? 1 : 0) | ((long)(d.pfp32 ? 1 : 0) << 15) | ((long)h->precond << 1) | ((long)h->prof.on << 3) |
          ((long)d.epb_ax << 4) |
          ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13) |
-         ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20) | ((long)(d.bf16 ? 1 : 0) << 24);
+         ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20) | ((long)(d.bf16 ? 1 : 0) << 24) |
+         ((long)(d.dwk ? 1 : 0) << 25) | ((long)d.epb_axdw << 26) | ((long)d.epb_swdw << 30);
 }
 
 int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
@@ -1252,7 +1266,7 @@ int sem_set_tiles(sem_t* h, int epb_ax, int epb_sw) {
   if (!sem::ax_tile_ok(h->d.p, epb_ax) || !sem::sw_tile_ok(h->d.P, epb_sw))
     return fail(SEM_ERR_ARG, "no kernel with that many elements per CTA for this order");
   h->d.epb_ax = h->d.epb_ax32 = epb_ax;
-  h->d.epb_sw = h->d.epb_sw32 = epb_sw;
+  h->d.epb_sw = h->d.epb_sw32 = h->d.epb_swdw = epb_sw;
   h->invalidate();
   return SEM_OK;
 }
@@ -1266,8 +1280,8 @@ int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host) {
   CK(cudaMemsetAsync(d.r32, 0, sizeof(float) * h->nb.G, h->stream));
   // the kernels of the precision in use: the FP32 operator in the mixed path, the FP32
   // patch solve in the mixed and P32 paths, the FP64 kernels otherwise
-  int& ax = d.fp32 ? d.epb_ax32 : d.epb_ax;
-  int& sw = d.pfp32 ? d.epb_sw32 : d.epb_sw;
+  int& ax = d.fp32 ? d.epb_ax32 : ((d.dwk && !d.recompute) ? d.epb_axdw : d.epb_ax);
+  int& sw = d.pfp32 ? d.epb_sw32 : (d.dwk ? d.epb_swdw : d.epb_sw);
   auto fa = [&]() -> cudaError_t {
     return d.fp32 ? sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), nullptr, h->stream)
                   : sem::launch_ax_local(d, h->p, d.wl, nullptr, h->stream);

@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <string>
 
+#include "kdw.cuh"
+
 namespace sem {
 
 constexpr int kVecBlock = 256;          // threads per block of the vector kernels
@@ -82,9 +84,13 @@ struct DevProblem {
                                     // slots free (for the coarse branch running beside it)
   int epb_ax = 1, epb_sw = 1;       // elements per CTA of the FP64 operator / patch-solve kernels
   int epb_ax32 = 1, epb_sw32 = 1;   // the same for the FP32 kernels (tuned separately)
+  int epb_axdw = 1, epb_swdw = 1;   // and for the double-FP32 kernels of SEM_PREC_FP64
+  bool dwk = false;                 // SEM_PREC_FP64's element kernels in double-FP32 (kdw.cuh)
+                                    // instead of binary64 (SEM_PREC_FP64_NATIVE)
                                     // (tile shapes picked by the autotuner; 1, 2, 4 or 8)
   const float* geo32 = nullptr;     // stored factors rounded to FP32 (same layout as geo)
   const __nv_bfloat16* geo16 = nullptr;   // the same rounded to BF16 (SEM_PREC_BF16)
+  const dw* geodw = nullptr;        // the same as pairs of FP32 (h = fl32(G), l = fl32(G - h))
   bool bf16 = false;                // with fp32: the FP32 operator reads geo16
   // tables
   const int* l2g = nullptr;
@@ -112,8 +118,10 @@ struct DevProblem {
   // inverted diagonal of Eq. z times the scale 8/(hx hy hz), at [e][(b + P c) + P^2 a]
   const double* swd = nullptr;
   const float* swd32 = nullptr;
+  const dw* swddw = nullptr;        // the same as pairs of FP32
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* Btab32 = nullptr;    // the same in FP32
+  const dw* Btabdw = nullptr;       // the same as pairs of FP32
   const int* ecv = nullptr;
   const int* cv_off = nullptr;
   const int* cv_idx = nullptr;
@@ -237,6 +245,8 @@ cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const doubl
 // ||out||^2) over the free DOFs
 cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
                             const double* g, double* out, double* norms, cudaStream_t s);
+// dst[i] = (fl32(src[i]), fl32(src[i] - fl32(src[i]))) for the double-FP32 kernels' tables
+cudaError_t launch_split_pairs(long long n, const double* src, dw* dst, cudaStream_t s);
 // b = mask ? 0 : mN * s (lumped GLL load)
 cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s);
 // y = a + b

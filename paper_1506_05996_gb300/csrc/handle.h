@@ -173,6 +173,7 @@ struct sem_s {
   double *coords = nullptr, *mN = nullptr, *geo = nullptr;
   float* geo32 = nullptr;
   __nv_bfloat16* geo16 = nullptr;   // BF16 copy of the stored factors (SEM_MIXED)
+  sem::dw* geodw = nullptr;         // pairs-of-FP32 copy of the stored factors (SEM_PREC_FP64)
   int precision = SEM_PREC_FP64;
   int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
   int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch
@@ -180,6 +181,7 @@ struct sem_s {
   uint8_t* pvar = nullptr;          // free sides of every element (see update_free_sides)
   double* swd = nullptr;             // patch-solve diagonals, scaled (update_free_sides)
   float* swd32 = nullptr;
+  sem::dw* swddw = nullptr;          // the same as pairs of FP32 (double-FP32 patch solves)
   double* pw = nullptr;             // overlap weights of P^f (sem_set_weights)
   float* pw32 = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *f = nullptr, *u = nullptr;

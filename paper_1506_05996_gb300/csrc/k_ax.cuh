@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kcommon.cuh"
+#include "knum.cuh"
 
 namespace sem {
 namespace {
@@ -29,13 +30,13 @@ __device__ __forceinline__ void fold_fill(FoldedD<p, T>& F, const double* __rest
   auto M = [&](int i, int m) { return transpose ? D[m * p + i] : D[i * p + m]; };
   if (t < H * H) {
     const int i = t / H, m = t % H;
-    F.Fp[t] = (T)(0.5 * (M(i, m) + M(i, n - m)));
+    F.Fp[t] = num_const<T>(0.5 * (M(i, m) + M(i, n - m)));
   }
   if (t < HM * H) {
     const int i = t / H, m = t % H;
-    F.Fm[t] = (T)(0.5 * (M(i, m) - M(i, n - m)));
+    F.Fm[t] = num_const<T>(0.5 * (M(i, m) - M(i, n - m)));
   }
-  if (ODD && t < H) F.Fmid[t] = (T)M(t, H);
+  if (ODD && t < H) F.Fmid[t] = num_const<T>(M(t, H));
 }
 
 template <int p, typename T>
@@ -44,22 +45,22 @@ __device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[
   constexpr int n = p - 1;
   T e[H], o[H];
 #pragma unroll
-  for (int m = 0; m < H; ++m) { e[m] = v[m] + v[n - m]; o[m] = v[m] - v[n - m]; }
+  for (int m = 0; m < H; ++m) { e[m] = num_add(v[m], v[n - m]); o[m] = num_sub(v[m], v[n - m]); }
 #pragma unroll
   for (int i = 0; i < H; ++i) {
-    T a = ODD ? F.Fmid[i] * v[H] : T(0), sv = 0;
+    T a = ODD ? num_mul(F.Fmid[i], v[H]) : num_zero<T>(), sv = num_zero<T>();
 #pragma unroll
     for (int m = 0; m < H; ++m) {
-      a += F.Fp[i * H + m] * e[m];
-      sv += F.Fm[i * H + m] * o[m];
+      num_mac(a, F.Fp[i * H + m], e[m]);
+      num_mac(sv, F.Fm[i * H + m], o[m]);
     }
-    out[i] = sv + a;
-    out[n - i] = sv - a;
+    out[i] = num_add(sv, a);
+    out[n - i] = num_sub(sv, a);
   }
   if (ODD) {
-    T sv = 0;
+    T sv = num_zero<T>();
 #pragma unroll
-    for (int m = 0; m < H; ++m) sv += F.Fm[H * H + m] * o[m];
+    for (int m = 0; m < H; ++m) num_mac(sv, F.Fm[H * H + m], o[m]);
     out[H] = sv;
   }
 }
@@ -78,10 +79,13 @@ constexpr int ax_smem_bytes() {
 // element-interior node has one copy, so its result goes straight to y (x where masked) at
 // its computed DOF, without an index read; only the other nodes go to wl for the gather.
 // TG: the stored factors' type (T, or BF16 under SEM_PREC_BF16 with T = float).
+// T = dw (the FP64 interface on the FP32 pipe) reads the factors as pairs and stores its
+// local results joined to binary64 (TW = LocalOf<T>).
 template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT, typename TG>
 __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
-                                                               T* __restrict__ wl, const PcgState* st,
-                                                               TX* __restrict__ yd) {
+                                                               typename LocalOf<T>::type* __restrict__ wl,
+                                                               const PcgState* st, TX* __restrict__ yd) {
+  using TW = typename LocalOf<T>::type;
   if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
   __shared__ FoldedD<p, T> Fg, Fd;
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   const int tx = tid % p, ty = tid / p;
   fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
   fold_fill<p, T>(Fd, d.D, true, threadIdx.x);
-  if (RECOMP)
+  if constexpr (RECOMP)
     for (int q = tid; q < 24; q += p2) sx[q] = (T)d.exyz[(size_t)e * 24 + q];
   const int* l2ge = d.l2g + (size_t)e * p3;
   constexpr int m = p - 2;
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
     const int g = inner ? gi0 + m * m * (k - 1) : l2ge[l];
     const bool mk = d.mask[g] != 0;
     if (DIRECT && mk) masked |= 1u << k;
-    uk[k] = mk ? T(0) : (T)x[g];
+    uk[k] = mk ? num_zero<T>() : num_load<T>(x[g]);
     su[l] = uk[k];
   }
   __syncthreads();
@@ -135,26 +139,25 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   for (int k = 0; k < p; ++k) sC[tx + p * (ty + p * k)] = res[k];
   __syncthreads();
   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
-  const T lam = (T)d.lambda;
   const bool lam_zero = d.lambda == 0.0;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
     const T ur = sA[l], us = sB[l], ut = sC[l];
     T G[6], lm;   // lm: the c-term factor lambda m (stored as such; 0 skips the load)
-    if (!RECOMP) {
+    if constexpr (!RECOMP) {
       const TG* gp = geo_of<TG>(d) + (size_t)e * 7 * p3 + l;
 #pragma unroll
       for (int c = 0; c < 6; ++c) G[c] = factor<T>(gp[c * p3]);
-      lm = lam_zero ? T(0) : factor<T>(gp[6 * p3]);
+      lm = lam_zero ? num_zero<T>() : factor<T>(gp[6 * p3]);
     } else {
       T det, mm;
       geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
-      lm = lam * mm;
+      lm = (T)d.lambda * mm;
     }
-    sA[l] = G[0] * ur + G[1] * us + G[2] * ut;
-    sB[l] = G[1] * ur + G[3] * us + G[4] * ut;
-    sC[l] = G[2] * ur + G[4] * us + G[5] * ut;
+    sA[l] = num_dot3(G[0], ur, G[1], us, G[2], ut);
+    sB[l] = num_dot3(G[1], ur, G[3], us, G[4], ut);
+    sC[l] = num_dot3(G[2], ur, G[4], us, G[5], ut);
     rk[k] = lm;
   }
   __syncthreads();
@@ -170,22 +173,22 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   for (int j = 0; j < p; ++j) line[j] = sB[tx + p * (j + p * ty)];
   fold_apply<p, T>(Fd, line, res);
 #pragma unroll
-  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] += res[j];
+  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] = num_add(su[tx + p * (j + p * ty)], res[j]);
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < p; ++k) line[k] = sC[tx + p * (ty + p * k)];
   fold_apply<p, T>(Fd, line, res);
   if (!active) return;
-  T* out = wl + (size_t)e * p3;
+  TW* out = wl + (size_t)e * p3;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T v = rk[k] * uk[k] + (su[l] + res[k]);   // lambda m u + the divergence terms
+    const T v = num_fma(rk[k], uk[k], num_add(su[l], res[k]));   // lambda m u + the divergence terms
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
-      yd[g] = (masked >> k) & 1u ? x[g] : (TX)v;   // y in x's type
+      yd[g] = (masked >> k) & 1u ? x[g] : num_store<TX>(v);   // y in x's type
     } else {
-      out[l] = v;
+      out[l] = num_store<TW>(v);
     }
   }
 }
@@ -222,11 +225,15 @@ bool ax_tile_ok_t(int p, int epb) {
 }
 
 template <int p, typename T, typename TX, int EPB, bool DIRECT>
-cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd, cudaStream_t s) {
+cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, typename LocalOf<T>::type* wl, const PcgState* st,
+                          TX* yd, cudaStream_t s) {
   if constexpr (ax_tile_supported<p, T, EPB>()) {
     const int grid = (d.ne + EPB - 1) / EPB;
-    constexpr bool kF32 = sizeof(T) == 4;
-    if (d.recompute) {
+    constexpr bool kF32 = std::is_same<T, float>::value;
+    if constexpr (kIsDw<T>) {   // stored factors as pairs only (recomputed geometry stays FP64)
+      if (d.recompute || d.geodw == nullptr) return cudaErrorInvalidValue;
+      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    } else if (d.recompute) {
       ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (kF32 && d.bf16) {
       if constexpr (kF32)
@@ -242,8 +249,9 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, T* wl, const PcgStat
 }
 
 template <int p, typename T, typename TX, bool DIRECT>
-cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd, cudaStream_t s) {
-  switch (sizeof(T) == 4 ? d.epb_ax32 : d.epb_ax) {
+cudaError_t launch_ax_p(const DevProblem& d, const TX* x, typename LocalOf<T>::type* wl, const PcgState* st,
+                        TX* yd, cudaStream_t s) {
+  switch (std::is_same<T, float>::value ? d.epb_ax32 : (kIsDw<T> ? d.epb_axdw : d.epb_ax)) {
     case 2: return launch_ax_epb<p, T, TX, 2, DIRECT>(d, x, wl, st, yd, s);
     case 4: return launch_ax_epb<p, T, TX, 4, DIRECT>(d, x, wl, st, yd, s);
     case 8: return launch_ax_epb<p, T, TX, 8, DIRECT>(d, x, wl, st, yd, s);
@@ -255,8 +263,8 @@ cudaError_t launch_ax_p(const DevProblem& d, const TX* x, T* wl, const PcgState*
 // interior-first numbering, interior nodes into yd (in x's type) and the others into wl
 // (DIRECT = true).
 template <typename T, typename TX, bool DIRECT>
-cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, T* wl, const PcgState* st, TX* yd,
-                              cudaStream_t s) {
+cudaError_t launch_ax_local_t(const DevProblem& d, const TX* x, typename LocalOf<T>::type* wl, const PcgState* st,
+                              TX* yd, cudaStream_t s) {
   if (DIRECT && d.Gi == 0) return cudaErrorInvalidValue;
   switch (d.p) {
     case 3: return launch_ax_p<3, T, TX, DIRECT>(d, x, wl, st, yd, s);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kcommon.cuh"
+#include "knum.cuh"
 
 namespace sem {
 namespace {
@@ -24,19 +25,19 @@ __device__ __forceinline__ void pencil_fwd(const T* __restrict__ S, const T (&v)
   constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
   T e[H], o[H];
 #pragma unroll
-  for (int k = 0; k < H; ++k) { e[k] = v[k] + v[P - 1 - k]; o[k] = v[k] - v[P - 1 - k]; }
+  for (int k = 0; k < H; ++k) { e[k] = num_add(v[k], v[P - 1 - k]); o[k] = num_sub(v[k], v[P - 1 - k]); }
 #pragma unroll
   for (int c = 0; c < NE; ++c) {
-    T a = ODD ? S[H * P + c] * v[H] : T(0);
+    T a = ODD ? num_mul(S[H * P + c], v[H]) : num_zero<T>();
 #pragma unroll
-    for (int k = 0; k < H; ++k) a += S[k * P + c] * e[k];
+    for (int k = 0; k < H; ++k) num_mac(a, S[k * P + c], e[k]);
     t[c] = a;
   }
 #pragma unroll
   for (int c = NE; c < P; ++c) {
-    T a = 0;
+    T a = num_zero<T>();
 #pragma unroll
-    for (int k = 0; k < H; ++k) a += S[k * P + c] * o[k];
+    for (int k = 0; k < H; ++k) num_mac(a, S[k * P + c], o[k]);
     t[c] = a;
   }
 }
@@ -46,26 +47,33 @@ __device__ __forceinline__ void pencil_bwd(const T* __restrict__ S, const T (&t)
   constexpr int H = P / 2, ODD = P & 1, NE = H + ODD;
 #pragma unroll
   for (int k = 0; k < H; ++k) {
-    T E = 0, O = 0;
+    T E = num_zero<T>(), O = num_zero<T>();
 #pragma unroll
-    for (int c = 0; c < NE; ++c) E += S[k * P + c] * t[c];
+    for (int c = 0; c < NE; ++c) num_mac(E, S[k * P + c], t[c]);
 #pragma unroll
-    for (int c = NE; c < P; ++c) O += S[k * P + c] * t[c];
-    v[k] = E + O;
-    v[P - 1 - k] = E - O;
+    for (int c = NE; c < P; ++c) num_mac(O, S[k * P + c], t[c]);
+    v[k] = num_add(E, O);
+    v[P - 1 - k] = num_sub(E, O);
   }
   if (ODD) {
-    T E = 0;
+    T E = num_zero<T>();
 #pragma unroll
-    for (int c = 0; c < NE; ++c) E += S[H * P + c] * t[c];
+    for (int c = 0; c < NE; ++c) num_mac(E, S[H * P + c], t[c]);
     v[H] = E;
   }
 }
 
-// Overlap weights of P^f in the kernel's precision (null when unweighted).
-template <typename T> __device__ __forceinline__ const T* weights_of(const DevProblem& d);
-template <> __device__ __forceinline__ const double* weights_of<double>(const DevProblem& d) { return d.pw; }
-template <> __device__ __forceinline__ const float* weights_of<float>(const DevProblem& d) { return d.pw32; }
+// v times the overlap weight of P^f at DOF g in the kernel's precision (v itself when
+// unweighted, the paper's sum).
+__device__ __forceinline__ double weighted(const DevProblem& d, double v, int g) {
+  return d.pw != nullptr ? v * d.pw[g] : v;
+}
+__device__ __forceinline__ float weighted(const DevProblem& d, float v, int g) {
+  return d.pw32 != nullptr ? v * d.pw32[g] : v;
+}
+__device__ __forceinline__ dw weighted(const DevProblem& d, dw v, int g) {
+  return d.pw != nullptr ? dw_mul(v, dw_split(d.pw[g])) : v;
+}
 
 // Plain 1D contractions with a pencil that has no reflection symmetry (an element side on
 // a natural boundary): fwd t = S^T v, bwd v = S t.
@@ -73,9 +81,9 @@ template <int P, typename T>
 __device__ __forceinline__ void plain_fwd(const T* __restrict__ S, const T (&v)[P], T (&t)[P]) {
 #pragma unroll
   for (int c = 0; c < P; ++c) {
-    T a = 0;
+    T a = num_zero<T>();
 #pragma unroll
-    for (int k = 0; k < P; ++k) a += S[k * P + c] * v[k];
+    for (int k = 0; k < P; ++k) num_mac(a, S[k * P + c], v[k]);
     t[c] = a;
   }
 }
@@ -84,9 +92,9 @@ template <int P, typename T>
 __device__ __forceinline__ void plain_bwd(const T* __restrict__ S, const T (&t)[P], T (&v)[P]) {
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    T a = 0;
+    T a = num_zero<T>();
 #pragma unroll
-    for (int c = 0; c < P; ++c) a += S[k * P + c] * t[c];
+    for (int c = 0; c < P; ++c) num_mac(a, S[k * P + c], t[c]);
     v[k] = a;
   }
 }
@@ -108,6 +116,7 @@ __device__ __forceinline__ void axis_bwd(int v, const T* sS, const T* sSv, const
 template <typename T> __device__ __forceinline__ const T* swd_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* swd_of<double>(const DevProblem& d) { return d.swd; }
 template <> __device__ __forceinline__ const float* swd_of<float>(const DevProblem& d) { return d.swd32; }
+template <> __device__ __forceinline__ const dw* swd_of<dw>(const DevProblem& d) { return d.swddw; }
 
 // The diagonal of the fast diagonalisation (Eq. z) of every element patch, inverted and
 // times the patch scale 8/(hx hy hz): dg[e][(b + P c) + P^2 a] = (8/(hx hy hz)) / (4(l_a/hx^2 +
@@ -145,9 +154,12 @@ constexpr int sw_smem_bytes() {
 
 // VAR: some element sides lie on a natural boundary (d.pvar != null), so each axis picks its
 // pencil; without, every axis takes the folded one (the same code as before variants).
+// T = dw (the FP64 interface on the FP32 pipe) stores its patch results as pairs, which the
+// P-sum adds in the same arithmetic.
 template <int P, typename T, typename TR, int EPB, bool VAR>
 __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
                                                                     T* __restrict__ wp, const PcgState* st) {
+  using TW = T;
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
   __shared__ T sS[P2], sSv[3 * P2], s1_all[EPB * P3], s2_all[EPB * P3];
@@ -155,9 +167,9 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   T* s1 = s1_all + grp * P3;
   T* s2 = s2_all + grp * P3;
   const int x = tx % P, y = tx / P;
-  if (threadIdx.x < P2) sS[threadIdx.x] = (T)d.S[threadIdx.x];
+  if (threadIdx.x < P2) sS[threadIdx.x] = num_const<T>(d.S[threadIdx.x]);
   if (VAR)
-    for (int q = threadIdx.x; q < 3 * P2; q += blockDim.x) sSv[q] = (T)d.Sv[q];
+    for (int q = threadIdx.x; q < 3 * P2; q += blockDim.x) sSv[q] = num_const<T>(d.Sv[q]);
   // element groups strided over the grid (the grid may be capped below the group count to
   // leave SMs to the concurrent coarse branch); every thread of a CTA runs the same rounds
   const int ngroups = (d.ne + EPB - 1) / EPB;
@@ -170,12 +182,11 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
   T col[P], out[P];
   const int* ipe = d.ip + (size_t)e * P3;
-  const T* wts = weights_of<T>(d);
 #pragma unroll
   for (int K = 0; K < P; ++K) {
     const int g = ipe[x + P * (y + P * K)];
-    T v = (g >= 0 && !d.mask[g]) ? (T)r[g] : T(0);
-    if (wts != nullptr && g >= 0) v = v * wts[g];
+    T v = (g >= 0 && !d.mask[g]) ? num_load<T>(r[g]) : num_zero<T>();
+    if (g >= 0) v = weighted(d, v, g);
     col[K] = v;
   }
   __syncthreads();
@@ -198,7 +209,7 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   {
     const T* dge = swd_of<T>(d) + (size_t)e * P3 + tx;
 #pragma unroll
-    for (int a = 0; a < P; ++a) out[a] = out[a] * dge[a * P2];
+    for (int a = 0; a < P; ++a) out[a] = num_mul(out[a], dge[a * P2]);
   }
   axis_bwd<P, T, VAR>(vx, sS, sSv, out, col);
 #pragma unroll
@@ -216,9 +227,9 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   for (int c = 0; c < P; ++c) out[c] = s1[x + P * (y + P * c)];
   axis_bwd<P, T, VAR>(vz, sS, sSv, out, col);
   if (active) {
-    T* outp = wp + (size_t)e * P3;
+    TW* outp = wp + (size_t)e * P3;
 #pragma unroll
-    for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = col[K];
+    for (int K = 0; K < P; ++K) outp[x + P * (y + P * K)] = num_store<TW>(col[K]);
   }
   }
 }
@@ -278,7 +289,7 @@ cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgStat
 
 template <int P, typename T, typename TR>
 cudaError_t launch_sw_P(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
-  switch (sizeof(T) == 4 ? d.epb_sw32 : d.epb_sw) {
+  switch (std::is_same<T, float>::value ? d.epb_sw32 : (kIsDw<T> ? d.epb_swdw : d.epb_sw)) {
     case 2: return launch_sw_epb<P, T, TR, 2>(d, r, wp, st, s);
     case 4: return launch_sw_epb<P, T, TR, 4>(d, r, wp, st, s);
     case 8: return launch_sw_epb<P, T, TR, 8>(d, r, wp, st, s);

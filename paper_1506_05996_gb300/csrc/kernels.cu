@@ -425,6 +425,54 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
 }
 
+// The P-sum of SEM_PREC_FP64 in double-FP32: the patch results (pairs, written by the
+// double-FP32 patch solve) summed over the patches containing each node, plus the trilinear
+// interpolation of the coarse correction (8 products per DOF), joined to binary64 once per
+// DOF; the z.r reduction stays binary64.
+template <bool PCG>
+__global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, int mode, const dw* __restrict__ wp,
+                                                            const double* __restrict__ r, double* __restrict__ z) {
+  if (PCG && stopped(d.st)) return;
+  const int p = d.p, p3 = p * p * p;
+  double dot = 0.0;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    dw v = dw_zero();
+    if (!d.mask[g]) {
+      if (mode & PSUM_IDENT) v = dw_split(r[g]);
+      if (mode & PSUM_FINE) {
+        dw vf = dw_zero();
+        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) vf = dw_add(vf, wp[d.pg_idx[q]]);
+        if (d.pw != nullptr) vf = dw_mul(vf, dw_split(d.pw[g]));   // overlap-weighted P^f
+        v = dw_add(v, vf);
+      }
+      if ((mode & PSUM_COARSE) && d.nfree > 0) {
+        const int l = d.owner[g], e = l / p3, lr = l % p3;
+        const int* ec = d.ecv + (size_t)e * 8;
+        const dw* B = d.Btabdw + 8 * lr;
+        dw zc = dw_zero();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int cv = ec[c];
+          if (cv >= 0) dw_mac(zc, B[c], dw_split(d.Zc[cv]));
+        }
+        v = dw_add(v, zc);
+      }
+    }
+    const double vd = dw_join(v);
+    z[g] = vd;
+    if (PCG) dot += vd * r[g];
+  }
+  if (PCG) {
+    double total;
+    if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
+      PcgState* st = d.st;
+      if (!isfinite(total)) { st->status = -6; st->done = 1; }
+      if (st->iter > 0) st->beta = total / st->rz;
+      st->rz = total;
+    }
+  }
+}
+
 __global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __restrict__ b, const PcgState* st) {
   if (stopped(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = f64_to_f32(a[i]);
@@ -682,6 +730,16 @@ __global__ void mass_load_kernel(const DevProblem d, const double* __restrict__ 
     b[i] = d.mask[i] ? 0.0 : mN[i] * sv[i];
 }
 
+// Pairs of FP32 from binary64 table entries, to nearest: h = fl32(v), l = fl32(v - h)
+// (set-up of the double-FP32 kernels' stored factors and patch diagonals).
+__global__ void split_pairs_kernel(long long n, const double* __restrict__ src, dw* __restrict__ dst) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    const float h = __double2float_rn(v);
+    dst[i] = {h, __double2float_rn(v - (double)h)};
+  }
+}
+
 // y = a + b
 __global__ void add_vectors_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
                                    double* __restrict__ y) {
@@ -927,6 +985,10 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
     const float* wp = reinterpret_cast<const float*>(d.wp);
     if (pcg) psum_kernel<true, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
     else psum_kernel<false, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+  } else if (d.dwk) {   // the patch results are pairs (double-FP32 patch solve)
+    const dw* wp = reinterpret_cast<const dw*>(d.wp);
+    if (pcg) psum_dw_kernel<true><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    else psum_dw_kernel<false><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
   } else {
     if (pcg) psum_kernel<true, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
     else psum_kernel<false, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
@@ -1029,6 +1091,14 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
 
 cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s) {
   mass_load_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, mN, sv, b);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(long long n, const double* src, dw* dst, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((n + kVecBlock - 1) / kVecBlock, 65536);
+  split_pairs_kernel<<<(int)blocks, kVecBlock, 0, s>>>(n, src, dst);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -23,7 +23,7 @@ SEM_ERR_ARG, SEM_ERR_JACOBIAN, SEM_ERR_MESH, SEM_ERR_CUDA = -1, -2, -3, -4
 SEM_ERR_OOM, SEM_ERR_NAN, SEM_ERR_SINGULAR = -5, -6, -7
 SEM_MAXIT = 1
 SEM_GEOM_STORED, SEM_GEOM_RECOMPUTE, SEM_NEUMANN, SEM_MIXED, SEM_PATCH_FULL = 0x0, 0x1, 0x10, 0x100, 0x1000
-SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_P32, SEM_PREC_BF16 = 0, 1, 2, 3
+SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_P32, SEM_PREC_BF16, SEM_PREC_FP64_NATIVE = 0, 1, 2, 3, 4
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
 SEM_COARSE_VCYCLE, SEM_COARSE_KCYCLE = 0, 1
@@ -431,7 +431,7 @@ class SemProblem:
 
     def set_precision(self, prec):
         sem_set_precision(self.h, {"fp64": SEM_PREC_FP64, "fp32": SEM_PREC_FP32, "p32": SEM_PREC_P32,
-                                   "bf16": SEM_PREC_BF16}[prec])
+                                   "bf16": SEM_PREC_BF16, "fp64_native": SEM_PREC_FP64_NATIVE}[prec])
 
     def dof_coords(self):
         x = self._vec(n=3 * self.n_dof)

@@ -37,3 +37,15 @@ class Pair:
 
 def rel_err(a, b):
     return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# History tolerances of the solve parity tests. The recursive residual r_k = r_k-1 - alpha A p
+# carries the operator's rounding of every iteration, measured against ||b||. The
+# double-FP32 element kernels of SEM_PREC_FP64 round at 2^-46 of their operands'
+# magnitudes where binary64 rounds at 2^-53, so in that arithmetic the absolute tolerance of
+# a history entry is 2^7 times the binary64 one (SEM_PREC_FP64_NATIVE keeps the latter).
+DW_HIST_SCALE = 2.0 ** 7
+
+
+def hist_atol(base, prec="fp64"):
+    return base * (DW_HIST_SCALE if prec == "fp64" else 1.0)

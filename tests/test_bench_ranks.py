@@ -99,3 +99,49 @@ def test_executed_flop_counts_follow_the_kernels(n):
     # the folded forms cost less than the paper's unfolded counts
     assert bench.ax_flops(n, 1) < bench.ax_flops_paper(n, 1)
     assert bench.schwarz_flops(n, 1) < bench.schwarz_flops_paper(n, 1)
+
+
+# FP32-pipe operations of the pair arithmetic (csrc/kdw.cuh): dw_add / dw_sub = TwoSum (6)
+# + 2 adds, dw_mul = 1 multiply + 3 FMAs, dw_mac = dw_mul + TwoSum + 2 adds.
+DW_ADD, DW_MUL, DW_MAC = 8, 4, 12
+
+
+def _count_dw_fold(p):
+    H, odd = p // 2, p % 2
+    f = 2 * H * DW_ADD                  # even / odd sums of the line
+    for _ in range(H):
+        f += DW_MUL if odd else 0       # middle column times v[H]
+        f += 2 * H * DW_MAC             # the two H-term accumulations
+        f += 2 * DW_ADD                 # out[i] and out[n - i]
+    if odd:
+        f += H * DW_MAC                 # the middle output
+    return f
+
+
+def _count_dw_pencil(P):
+    H, odd = P // 2, P % 2
+    NE = P - H
+    fwd = 2 * H * DW_ADD
+    for c in range(P):
+        fwd += H * DW_MAC + (DW_MUL if (odd and c < NE) else 0)
+    bwd = 0
+    for _ in range(H):
+        bwd += (NE + (P - NE)) * DW_MAC + 2 * DW_ADD
+    if odd:
+        bwd += NE * DW_MAC
+    return fwd, bwd
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6, 7, 8])
+def test_pair_operation_counts_follow_the_kernels(n):
+    """The double-FP32 rooflines count the FP32 operations of the pair kernels loop by loop:
+    the same lines as the binary64 kernels with pair sums, products and multiply-accumulates;
+    per operator node 3 metric rows (a product and two multiply-accumulates), the divergence
+    sum, the lambda m u accumulate with its sum, one split and one join; per patch node one
+    diagonal product and one split."""
+    import bench
+    p, P = n + 1, n + 3
+    per_node = 3 * (DW_MUL + 2 * DW_MAC) + DW_ADD + (DW_ADD + DW_MAC) + 2 + 6
+    assert bench.dw_ops_ax(n, 1) == 6 * p * p * _count_dw_fold(p) + per_node * p ** 3
+    fwd, bwd = _count_dw_pencil(P)
+    assert bench.dw_ops_schwarz(n, 1) == 3 * P * P * (fwd + bwd) + (DW_MUL + 2) * P ** 3

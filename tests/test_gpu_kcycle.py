@@ -51,7 +51,8 @@ def test_flexible_solve_parity(kp):
     x, rc, it, hist, tr = kp.gpu.solve(kp.to_gpu(b))
     assert rc == 0 and tr <= 1e-8
     assert it == it_ref
-    np.testing.assert_allclose(hist, h_ref, rtol=1e-7, atol=1e-15)
+    from gpu_util import hist_atol
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-7, atol=hist_atol(1e-15))
 
 
 def test_mixed_and_switch_back():

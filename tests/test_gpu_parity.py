@@ -73,18 +73,21 @@ def test_preconditioner_parity(E, n, lam, a, seed):
 @pytest.mark.parametrize("E,n,lam,a,seed,pc", [(4, 3, 0.0, 0.1, 0, "two-scale"), (3, 4, 1.0, 0.2, 1, "fine"),
                                                (10, 2, 1.0, 0.2, 3, "two-scale"), (3, 3, 0.5, 0.2, 2, "none")])
 def test_pcg_parity(E, n, lam, a, seed, pc):
+    from gpu_util import hist_atol
     P = _pair(lattice_hex_mesh(E, a, seed), n, lam)
     b = P.ref.load(manufactured_s(P.ref.coords, lam))
-    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8, maxit=500, precond=pc)
     u, it_ref, hist_ref = P.ref.solve(b, rtol=1e-8, maxit=500, precond=pc)
-    assert rc == 0
-    assert it == it_ref
-    np.testing.assert_allclose(hist, hist_ref, rtol=1e-9, atol=1e-14)
-    ug = P.to_ref(x)
-    assert np.max(np.abs(ug - u)) <= 1e-10 * np.max(np.abs(u))
-    assert tr <= 2e-8
-    # the discrete solution approximates the manufactured one
-    assert np.max(np.abs(ug - manufactured_u(P.ref.coords))) < 0.05
+    for prec in ("fp64", "fp64_native"):     # double-FP32 element kernels (default) and binary64
+        P.gpu.set_precision(prec)
+        x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8, maxit=500, precond=pc)
+        assert rc == 0
+        assert it == it_ref
+        np.testing.assert_allclose(hist, hist_ref, rtol=1e-9, atol=hist_atol(1e-14, prec))
+        ug = P.to_ref(x)
+        assert np.max(np.abs(ug - u)) <= 1e-10 * np.max(np.abs(u))
+        assert tr <= 2e-8
+        # the discrete solution approximates the manufactured one
+        assert np.max(np.abs(ug - manufactured_u(P.ref.coords))) < 0.05
 
 
 def test_pcg_config1_golden():
@@ -92,11 +95,14 @@ def test_pcg_config1_golden():
     committed oracle golden file."""
     import json, os
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config1_oracle.json")))
+    from gpu_util import hist_atol
     P = _pair(lattice_hex_mesh(4, 0.1, 0), 3, 0.0)
     b = P.ref.load(manufactured_s(P.ref.coords, 0.0))
-    x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
-    assert it == gold["iterations"]
-    np.testing.assert_allclose(hist, gold["residual_history"], rtol=1e-9, atol=1e-14)
+    for prec in ("fp64", "fp64_native"):
+        P.gpu.set_precision(prec)
+        x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b), rtol=1e-8)
+        assert it == gold["iterations"]
+        np.testing.assert_allclose(hist, gold["residual_history"], rtol=1e-9, atol=hist_atol(1e-14, prec))
 
 
 def test_solve_is_deterministic():
@@ -241,7 +247,8 @@ def test_overlap_weighted_patch_parity(E, n, lam, seed):
     _, it_ref, h_ref = ref.solve(b)
     x, rc, it, hist, tr = P.gpu.solve(P.to_gpu(b))
     assert rc == 0 and it == it_ref and tr <= 1e-8
-    np.testing.assert_allclose(hist, h_ref, rtol=1e-9, atol=1e-15)
+    from gpu_util import hist_atol
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-9, atol=hist_atol(1e-15))
     sem.sem_set_weights(P.gpu.h, 0)
     assert rel_err(P.to_ref(P.gpu.apply_P(P.to_gpu(r), "fine")), P.ref.apply_Pf(r)) <= TOL
 
@@ -265,7 +272,8 @@ def test_irregular_valence_mesh_parity(N, layers, n, lam, seed):
     # grow along the CG trajectory, so the early history, the count and the solution are
     # compared (both solutions meet the 1e-8 residual)
     assert rc == 0 and abs(it - it_ref) <= 2 and tr <= 1e-8
-    np.testing.assert_allclose(hist[:15], h_ref[:15], rtol=1e-8, atol=1e-15)
+    from gpu_util import hist_atol
+    np.testing.assert_allclose(hist[:15], h_ref[:15], rtol=1e-8, atol=hist_atol(1e-15))
     assert rel_err(P.to_ref(xs), u_ref) <= 1e-6
     N2 = Pair(mesh, n, lam, neumann=True, coarse=False)
     assert rel_err(N2.to_ref(N2.gpu.apply_P(N2.to_gpu(x), "fine")), N2.ref.apply_Pf(x)) <= TOL
