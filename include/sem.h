@@ -192,6 +192,23 @@ int sem_apply_Pc(sem_t* h, const double* r_dev, double* z_dev);
  * FP64 residual (the returned history holds the recomputed residual at replacements). */
 int sem_set_precision(sem_t* h, int precision);
 
+/* sem_set_patch_solver - arithmetic of the patch solves of P^f (Sec. 4.2, Eq. z) under
+ * SEM_PREC_FP32, SEM_PREC_P32 and SEM_PREC_BF16:
+ *   SEM_PATCH_SOLVE_FP32     FP32 on the FP32 pipe (default);
+ *   SEM_PATCH_SOLVE_BF16_TC  the six contractions with S and S^T as BF16 matrix products on the
+ *                            tensor cores (tcgen05, FP32 accumulation in tensor memory; box
+ *                            values, S and every stage's input rounded to BF16): each patch
+ *                            result within about 7 * 2^-9 of |S||S^T|(|r|). The rounding between
+ *                            stages makes P^f slightly nonlinear, so sem_solve then uses the
+ *                            flexible (Polak-Ribiere) beta. Handles with natural-boundary sides
+ *                            (free element faces) keep the FP32 kernel, which needs no per-element
+ *                            pencils in a shared tile. SEM_PREC_FP64 is unaffected.
+ * Errors: SEM_ERR_ARG, SEM_ERR_OOM. A bounded wait of the tensor-core kernel that runs out is
+ * reported by the next sem_solve as SEM_ERR_CUDA. */
+#define SEM_PATCH_SOLVE_FP32     0
+#define SEM_PATCH_SOLVE_BF16_TC  1
+int sem_set_patch_solver(sem_t* h, int kind);
+
 /* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
 int sem_set_precond(sem_t* h, int which);
 

@@ -197,6 +197,10 @@ int check_handle(const sem_t* h) {
   return SEM_OK;
 }
 
+// The FP32 paths' patch solves run in BF16 on the tensor cores (sem_set_patch_solver), unless
+// some element side takes a natural-boundary pencil (the FP32 kernel serves those handles).
+bool tc_active(const sem::DevProblem& d) { return d.tc && d.pfp32 && d.pvar == nullptr; }
+
 // The BF16-factor operator's error, 2^-8 relative to |A|(|x|), is far larger relative to
 // A x on the smooth error components that PCG leaves last, so the iteration stalls: BF16 is
 // for operator and preconditioner applications only.
@@ -238,7 +242,11 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
     // FP32 patch solves leave h->overlap_sms SMs' worth of slots to the coarse branch
     sem::DevProblem dd = d;
     dd.sw_reserve_sms = (coarse && d.pfp32) ? h->overlap_sms : 0;
-    if (d.fp32 && pcg)
+    if (tc_active(d) && d.fp32 && pcg)
+      PROF(h, "schwarz_local", sem::launch_schwarz_tc_in32(dd, d.r32, reinterpret_cast<float*>(d.wp), st, h->stream));
+    else if (tc_active(d))
+      PROF(h, "schwarz_local", sem::launch_schwarz_tc(dd, r, reinterpret_cast<float*>(d.wp), st, h->stream));
+    else if (d.fp32 && pcg)
       PROF(h, "schwarz_local", sem::launch_schwarz_local_f32_in32(dd, d.r32, reinterpret_cast<float*>(d.wp), st,
                                                                   h->stream));
     else if (d.pfp32)
@@ -252,7 +260,9 @@ int apply_precond(sem_t* h, int which, const double* r, double* z, bool pcg) {
   // flexible PCG when P varies between applications: the K-cycle is nonlinear, and the
   // learned correction depends on r
   const bool learned = pcg && h->net != nullptr;
-  const bool flex = pcg && (learned || (coarse && d.amg_kind == SEM_COARSE_KCYCLE));
+  // (the BF16 patch solves round between their contractions: P is then not exactly linear)
+  const bool fine = which == SEM_PRECOND_TWO_SCALE || which == SEM_PRECOND_FINE;
+  const bool flex = pcg && (learned || (coarse && d.amg_kind == SEM_COARSE_KCYCLE) || (fine && tc_active(d)));
   PROF(h, "psum", sem::launch_psum(d, mode, r, z, pcg && !flex, h->stream));
   if (learned) {
     // z = P r + N(r - A P r), flexible PCG; the operator application and the network skip
@@ -480,6 +490,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&d.partial, (size_t)(4 * d.nblk), A));
   CK(h->alloc(&d.st, 1, A));
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), h->stream));
+  CK(h->alloc(&d.tc_err, 1, A));
+  CK(cudaMemsetAsync(d.tc_err, 0, sizeof(int), h->stream));
   CK(h->alloc(&h->r, (size_t)nb.G, A));
   CK(h->alloc(&h->z, (size_t)nb.G, A));
   CK(h->alloc(&h->p, (size_t)nb.G, A));
@@ -732,6 +744,16 @@ int sem_set_overlap(sem_t* h, int reserve_sms) {
   return SEM_OK;
 }
 
+int sem_set_patch_solver(sem_t* h, int kind) {
+  if (int rc = check_handle(h)) return rc;
+  if (kind != SEM_PATCH_SOLVE_FP32 && kind != SEM_PATCH_SOLVE_BF16_TC) return fail(SEM_ERR_ARG, "unknown patch solver");
+  CK(cudaStreamSynchronize(h->stream));
+  if (kind == SEM_PATCH_SOLVE_BF16_TC && h->d.rprev == nullptr) CK(h->alloc(&h->d.rprev, (size_t)h->nb.G, h->allocs));
+  h->d.tc = kind == SEM_PATCH_SOLVE_BF16_TC;
+  h->invalidate();
+  return SEM_OK;
+}
+
 int sem_set_weights(sem_t* h, int weighted) {
   if (int rc = check_handle(h)) return rc;
   CK(cudaStreamSynchronize(h->stream));
@@ -821,7 +843,9 @@ int enqueue_start(sem_t* h, const double* b, double rtol, int maxit) {
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
   const int mixed = d.fp32 ? 1 : 0;
   const int learned = h->net != nullptr ? 1 : 0;
-  const int flexible = (learned || (d.amg_kind == SEM_COARSE_KCYCLE && h->precond == SEM_PRECOND_TWO_SCALE)) ? 1 : 0;
+  const bool fine = h->precond == SEM_PRECOND_TWO_SCALE || h->precond == SEM_PRECOND_FINE;
+  const int flexible = (learned || (d.amg_kind == SEM_COARSE_KCYCLE && h->precond == SEM_PRECOND_TWO_SCALE) ||
+                        (fine && tc_active(d))) ? 1 : 0;
   if (learned) CK(cudaMemsetAsync(d.st_nn, 0, sizeof(sem::PcgState), s));
   PROF(h, "pcg_init", sem::launch_pcg_init(d, b, h->r, h->u, rtol, maxit, mixed, learned, flexible, h->nn_window,
                                            h->nn_ratio, h->nn_theta, h->hist, s));
@@ -845,7 +869,8 @@ long graph_key(const sem_t* h) {
          ((long)d.epb_ax << 4) |
          ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13) |
          ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20) | ((long)(d.bf16 ? 1 : 0) << 24) |
-         ((long)(d.dwk ? 1 : 0) << 25) | ((long)d.epb_axdw << 26) | ((long)d.epb_swdw << 30);
+         ((long)(d.dwk ? 1 : 0) << 25) | ((long)d.epb_axdw << 26) | ((long)d.epb_swdw << 30) |
+         ((long)(tc_active(d) ? 1 : 0) << 34);
 }
 
 int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
@@ -929,6 +954,15 @@ int solve_finish(sem_t* h, SolveCtx& c, int* iters_host, double* res_hist_host, 
     CK(cudaStreamSynchronize(s));
   }
   if (true_rel_res_host) *true_rel_res_host = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
+  if (d.tc) {
+    int tc_err = 0;
+    CK(cudaMemcpy(&tc_err, d.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tc_err) {
+      CK(cudaMemset(d.tc_err, 0, sizeof(int)));
+      return fail(SEM_ERR_CUDA, "tensor-core patch solve: a bounded wait for the MMAs ran out");
+    }
+  }
+  if (st.status == -4) return fail(SEM_ERR_CUDA, "a kernel of the solve gave up a bounded wait");
   if (st.status == -6) return fail(SEM_ERR_NAN, "NaN/Inf or non-positive curvature in PCG");
   if (!st.done) return fail(SEM_MAXIT, "maxit reached");
   return st.status == 1 ? SEM_MAXIT : SEM_OK;

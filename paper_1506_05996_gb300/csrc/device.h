@@ -85,6 +85,8 @@ struct DevProblem {
   int epb_ax = 1, epb_sw = 1;       // elements per CTA of the FP64 operator / patch-solve kernels
   int epb_ax32 = 1, epb_sw32 = 1;   // the same for the FP32 kernels (tuned separately)
   int epb_axdw = 1, epb_swdw = 1;   // and for the double-FP32 kernels of SEM_PREC_FP64
+  bool tc = false;                  // the FP32 paths' patch solves in BF16 on the tensor cores
+  int* tc_err = nullptr;            // set by the tensor-core kernel when a bounded wait ran out
   bool dwk = false;                 // SEM_PREC_FP64's element kernels in double-FP32 (kdw.cuh)
                                     // instead of binary64 (SEM_PREC_FP64_NATIVE)
                                     // (tile shapes picked by the autotuner; 1, 2, 4 or 8)
@@ -206,6 +208,11 @@ cudaError_t launch_sw_diag(const DevProblem& d, double* dg, cudaStream_t s);
 cudaError_t launch_convert_check(const unsigned long long* bits, long long n, unsigned long long* mismatches,
                                  cudaStream_t s);
 cudaError_t launch_sw_diag_f32(const DevProblem& d, float* dg, cudaStream_t s);
+// the same FP32 patch results from BF16 patch solves on the tensor cores (k_swtc.cu); needs
+// d.pvar == null (no natural-boundary pencils)
+cudaError_t launch_schwarz_tc(const DevProblem& d, const double* r, float* wp, const PcgState* st, cudaStream_t s);
+cudaError_t launch_schwarz_tc_in32(const DevProblem& d, const float* r, float* wp, const PcgState* st,
+                                   cudaStream_t s);
 cudaError_t launch_coarse_restrict(const DevProblem& d, const double* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, const PcgState* st, cudaStream_t s);
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s);

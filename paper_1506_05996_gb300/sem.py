@@ -27,6 +27,7 @@ SEM_PREC_FP64, SEM_PREC_FP32, SEM_PREC_P32, SEM_PREC_BF16, SEM_PREC_FP64_NATIVE 
 SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
 SEM_COARSE_VCYCLE, SEM_COARSE_KCYCLE = 0, 1
+SEM_PATCH_SOLVE_FP32, SEM_PATCH_SOLVE_BF16_TC = 0, 1
 SEM_LOOP_HOST, SEM_LOOP_DEVICE = 0, 1
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
@@ -54,6 +55,7 @@ _SIGS = {
     "sem_set_coarse_solver": ([_vp, _int], _int),
     "sem_set_loop": ([_vp, _int], _int),
     "sem_set_weights": ([_vp, _int], _int),
+    "sem_set_patch_solver": ([_vp, _int], _int),
     "sem_set_overlap": ([_vp, _int], _int),
     "sem_set_precision": ([_vp, _int], _int),
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
@@ -220,6 +222,11 @@ def sem_set_overlap(h, reserve_sms):
 
 def sem_set_weights(h, weighted):
     return _check(_lib.sem_set_weights(h, int(bool(weighted))))
+
+
+def sem_set_patch_solver(h, kind):
+    k = {"fp32": SEM_PATCH_SOLVE_FP32, "bf16_tc": SEM_PATCH_SOLVE_BF16_TC}.get(kind, kind)
+    return _check(_lib.sem_set_patch_solver(h, k))
 
 
 def sem_set_loop(h, mode):
