@@ -81,8 +81,10 @@ constexpr int ax_smem_bytes() {
 // TG: the stored factors' type (T, or BF16 under SEM_PREC_BF16 with T = float).
 // T = dw (the FP64 interface on the FP32 pipe) reads the factors as pairs and stores its
 // local results joined to binary64 (TW = LocalOf<T>).
+// (kIsDw: at most 96 registers a thread, as for the double-FP32 patch kernel)
 template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT, typename TG>
-__global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
+__global__ void __launch_bounds__(EPB * p * p, kIsDw<T> ? 65536 / ((((EPB * p * p) + 31) / 32) * 32 * 96) + 0 : 1)
+    ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
                                                                typename LocalOf<T>::type* __restrict__ wl,
                                                                const PcgState* st, TX* __restrict__ yd) {
   using TW = typename LocalOf<T>::type;

@@ -156,13 +156,25 @@ constexpr int sw_smem_bytes() {
 // pencil; without, every axis takes the folded one (the same code as before variants).
 // T = dw (the FP64 interface on the FP32 pipe) stores its patch results as pairs, which the
 // P-sum adds in the same arithmetic.
+// Resident CTAs per SM asked of the compiler for the double-FP32 kernels, whose pair
+// arithmetic is latency-bound at the occupancy its register count would allow: at most 96
+// registers a thread (the binary64 and FP32 instantiations keep the compiler's choice).
+constexpr int dw_min_blocks(int threads) {
+  return 65536 / (((threads + 31) / 32) * 32 * 96) > 0 ? 65536 / (((threads + 31) / 32) * 32 * 96) : 1;
+}
+
 template <int P, typename T, typename TR, int EPB, bool VAR>
-__global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
+__global__ void __launch_bounds__(EPB * P * P, kIsDw<T> ? dw_min_blocks(EPB * P * P) : 1) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
                                                                     T* __restrict__ wp, const PcgState* st) {
   using TW = T;
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
   __shared__ T sS[P2], sSv[3 * P2], s1_all[EPB * P3], s2_all[EPB * P3];
+  // double-FP32: the element's inverted diagonal, copied asynchronously at the start of the
+  // element so that its loads overlap the forward contractions (dynamic shared memory,
+  // EPB P^3 pairs; none in the other instantiations)
+  extern __shared__ __align__(16) unsigned char sw_dyn[];
+  T* sdg_all = reinterpret_cast<T*>(sw_dyn);
   const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
   T* s1 = s1_all + grp * P3;
   T* s2 = s2_all + grp * P3;
@@ -181,6 +193,16 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
   const int vb = VAR ? d.pvar[e] : 0;
   const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
   T col[P], out[P];
+  if constexpr (kIsDw<T>) {   // thread (x, y) copies the P entries it scales later
+    const T* dge = swd_of<T>(d) + (size_t)e * P3 + tx;
+    T* sdg = sdg_all + grp * P3 + tx;
+#pragma unroll
+    for (int a = 0; a < P; ++a)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdg + a * P2)),
+                   "l"(dge + a * P2)
+                   : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   const int* ipe = d.ip + (size_t)e * P3;
 #pragma unroll
   for (int K = 0; K < P; ++K) {
@@ -206,7 +228,12 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
 #pragma unroll
   for (int I = 0; I < P; ++I) col[I] = s2[I + P * (x + P * y)];
   axis_fwd<P, T, VAR>(vx, sS, sSv, col, out);
-  {
+  if constexpr (kIsDw<T>) {
+    asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's own copies
+    const T* sdg = sdg_all + grp * P3 + tx;
+#pragma unroll
+    for (int a = 0; a < P; ++a) out[a] = num_mul(out[a], sdg[a * P2]);
+  } else {
     const T* dge = swd_of<T>(d) + (size_t)e * P3 + tx;
 #pragma unroll
     for (int a = 0; a < P; ++a) out[a] = num_mul(out[a], dge[a * P2]);
@@ -275,11 +302,17 @@ cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgStat
       int dev = 0, nsm = 0, per_sm = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, EPB * P * P, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, EPB * P * P,
+                                                    kIsDw<T> ? EPB * P * P * P * (int)sizeof(T) : 0);
       const int cap = (nsm - d.sw_reserve_sms) * per_sm;
       if (cap > 0 && cap < grid) grid = cap;
     }
-    kernel<<<grid, EPB * P * P, 0, s>>>(d, r, wp, st);
+    constexpr int dyn = kIsDw<T> ? EPB * P * P * P * (int)sizeof(T) : 0;
+    if (dyn > 0) {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      if (e != cudaSuccess) return e;
+    }
+    kernel<<<grid, EPB * P * P, dyn, s>>>(d, r, wp, st);
     count_launch();
     return cudaGetLastError();
   } else {

@@ -37,7 +37,7 @@
 namespace sem {
 namespace {
 
-constexpr int kTcThreads = 128;          // 4 warps, one per TMEM lane quarter
+constexpr int kTcThreads = 256;          // 8 warps: two per TMEM lane quarter (even and odd tiles)
 constexpr int kTcRows = 128;             // M of one MMA: 128 box lines
 constexpr int kTcTileBytes = kTcRows * 16 * 2;   // 128 rows x 16 BF16
 constexpr uint32_t kTcSpin = 1u << 22;   // bound of every wait on the MMA barrier
@@ -127,7 +127,7 @@ struct TcShape {
   static constexpr int SMEM = SMEM_USED > 49152 ? SMEM_USED : 49152;
 };
 
-// One CTA of 128 threads per group of EPC elements (groups strided over the grid). wp
+// One CTA of 256 threads per group of EPC elements (groups strided over the grid). wp
 // receives FP32 patch results in the layout of the FP32 patch kernel.
 template <int P, typename TR, int EPC>
 __global__ void __launch_bounds__(kTcThreads) schwarz_tc_kernel(const DevProblem d, const TR* __restrict__ r,
@@ -193,29 +193,46 @@ __global__ void __launch_bounds__(kTcThreads) schwarz_tc_kernel(const DevProblem
   const int ngroups = (d.ne + EPC - 1) / EPC;
   for (int blk = blockIdx.x; blk < ngroups && ok; blk += gridDim.x) {
     const int e0 = blk * EPC;
-    // stage 1 input: row (J, K) of element el, k = I
-    for (int q = tid; q < EPC * P3; q += kTcThreads) {
-      const int el = q / P3, node = q % P3, e = e0 + el;
-      const int I = node % P, JK = node / P;
-      float v = 0.f;
-      if (e < d.ne) {
-        const int g = d.ip[(size_t)e * P3 + node];
-        if (g >= 0 && !d.mask[g]) {
-          v = to_f(r[g]);
-          if (d.pw32 != nullptr) v *= d.pw32[g];
+    // stage 1 input: row (J, K) of element el, k = I; four entries per thread in flight
+    // (patch-table loads, then the residual and mask loads, then the stores)
+    constexpr int NQ = EPC * P3, U = 4;
+    for (int q0 = tid; q0 < NQ; q0 += kTcThreads * U) {
+      int gi[U];
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * kTcThreads, e = e0 + q / P3;
+        gi[u] = (q < NQ && e < d.ne) ? d.ip[(size_t)e * P3 + q % P3] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        v[u] = 0.f;
+        if (gi[u] >= 0) {
+          const float rv = to_f(r[gi[u]]);
+          const bool mk = d.mask[gi[u]] != 0;
+          v[u] = mk ? 0.f : (d.pw32 != nullptr ? rv * d.pw32[gi[u]] : rv);
         }
       }
-      put(el * P2 + JK, I, v);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * kTcThreads;
+        if (q < NQ) {
+          const int el = q / P3, node = q % P3;
+          put(el * P2 + node / P, node % P, v[u]);
+        }
+      }
     }
 #pragma unroll 1
     for (int s = 0; s < 6; ++s) {
       run_stage(s < 3 ? bf_desc : bb_desc);
       if (!ok) break;
-      // every thread reads rows 32 warp + lane of each tile: line = 128 t + 32 warp + lane
-      for (int t = 0; t < NT; ++t) {
+      // warp w reads TMEM lanes 32 (w % 4) + lane of the tiles t = w / 4, w / 4 + 2, ...:
+      // line = 128 t + 32 (w % 4) + lane
+      const int quarter = warp & 3;
+      for (int t = warp >> 2; t < NT; t += 2) {
         float y[16];
-        tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16u * t, y);
-        const int line = t * kTcRows + 32 * warp + lane;
+        tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 16u * t, y);
+        const int line = t * kTcRows + 32 * quarter + lane;
         if (line >= LINES) continue;
         const int el = line / P2, lr = line % P2, al = lr % P, be = lr / P;   // row (alpha, beta)
         const int e = e0 + el;
