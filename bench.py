@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config3", action="store_true",
                     help="skip the 48^3-hex precision block of the default line")
+    ap.add_argument("--no-config4", action="store_true",
+                    help="skip the 24-problem x 4-load batching block of the default line")
     ap.add_argument("--precision-variant", action="store_true",
                     help="48^3 hexes, +-20%% (seed 2), n=7, lambda=0: FP64 vs mixed time-to-1e-8 and the "
                          "per-result error of the mixed solution")
@@ -352,6 +354,82 @@ def oracle_ax_full(E, nthreads_list, reps=2):
     return res
 
 
+def config4_block(steps, warmup, flush=None):
+    """Batching variant: 24 seeded problems (E ~ U{8..24} hexes per direction, n ~ U{3..8},
+    +-15 %, lambda = 0, Dirichlet, seed 3) with 4 Gaussian loads each, FP64 two-scale PCG to
+    1e-8. One handle per problem: its 4 loads solved one at a time (4 graph launches) against
+    one block solve (sem_solve_block, every kernel over the 4 loads; one graph launch)."""
+    import numpy as np
+    import torch
+    from synth import lattice_hex_mesh, gaussian_load
+    from paper_1506_05996_gb300 import sem as S
+    rng = np.random.default_rng(3)
+    specs = [(int(rng.integers(8, 25)), int(rng.integers(3, 9))) for _ in range(24)]
+    t0 = time.perf_counter()
+    probs = []
+    for k, (E, n) in enumerate(specs):
+        mesh = lattice_hex_mesh(E, 0.15, 3000 + k)
+        pr = S.SemProblem(mesh.xyz, mesh.hex2vert, n, 0.0)
+        free = (pr.mask() == 0).double()
+        B = torch.stack([torch.as_tensor(gaussian_load(pr.n_dof, 30000 + 4 * k + r), device="cuda") * free
+                         for r in range(4)]).contiguous()
+        S.sem_autotune(pr.h)
+        probs.append((pr, B, torch.empty_like(B)))
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    total = float(sum(4 * pr.n_dof for pr, _, _ in probs))
+
+    def one_at_a_time():
+        its = []
+        for pr, B, X in probs:
+            for r in range(4):
+                rc, it, hist, tr = S.sem_solve(pr.h, B[r], X[r], RTOL, 1000, want_history=False)
+                its.append(it)
+        return its
+
+    def block():
+        its = []
+        for pr, B, X in probs:
+            rc, it, sts, trs = S.sem_solve_block(pr.h, B, X, RTOL, 1000)
+            assert rc == 0, sts
+            its += it
+        return its
+
+    def timed(fn):
+        for _ in range(max(1, warmup)):
+            fn()
+        best = None
+        for _ in range(max(1, steps)):
+            if flush is not None:
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            its = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None or t < best else best
+        return best, its
+
+    t_seq, its_seq = timed(one_at_a_time)
+    t_blk, its_blk = timed(block)
+    same = its_seq == its_blk
+    for pr, _, _ in probs:
+        pr.close()
+    return {"workload": "24 problems: E ~ U{8..24} hexes per direction, n ~ U{3..8}, +-15% perturbation, lambda=0, "
+                        "Dirichlet, 4 Gaussian N(0,1) loads each (seed 3); SEM_PREC_FP64 two-scale PCG to 1e-8",
+            "problems": [{"E": E, "n": n} for E, n in specs], "solves": 96, "total_dofs_solved": int(total),
+            "setup_s": t_setup,
+            "one_at_a_time": {"s": t_seq, "solves_per_s": 96 / t_seq, "gdofs_solved": total / t_seq / 1e9},
+            "block_k4": {"s": t_blk, "solves_per_s": 96 / t_blk, "gdofs_solved": total / t_blk / 1e9,
+                         "speedup": t_seq / t_blk},
+            "iterations_equal": same,
+            "iterations": {"min": int(min(its_blk)), "max": int(max(its_blk)), "mean": float(np.mean(its_blk))},
+            "note": "block solves are bit-identical to the single solves (tests/test_gpu_block.py); the time of the "
+                    "faster of the timed passes, each pass all 96 solves"}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -608,6 +686,10 @@ def run_gpu(args):
                            "parity tests); time of the faster of 2 solves after one warm-up", **c3}
         pr3.close()
 
+    config4 = None
+    if not args.no_config4:
+        config4 = config4_block(max(1, min(args.steps, 3)), 1, flush)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         res = oracle_sample(E_SAMPLE, 3)
@@ -647,7 +729,7 @@ def run_gpu(args):
                          "note": "host-driven loop with a CUDA event pair around every launch",
                          "kernels_ms_per_step": {k: v[1] / args.steps
                                                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}},
-            "ax": ax, "peaks": meas, "roofline": roof, "config3": config3,
+            "ax": ax, "peaks": meas, "roofline": roof, "config3": config3, "config4": config4,
             "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,
                     "d2h_bytes_per_step": 8 * G, "s_per_step": t_e2e},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -681,6 +763,10 @@ def run_kernel_case(E):
         for _ in range(2):
             prob.apply_A(x)
             prob.apply_P(x, "two-scale")
+    S.sem_set_patch_solver(prob.h, "bf16_tc")       # the tensor-core patch solve (FP32 path)
+    for _ in range(2):
+        prob.apply_P(x, "two-scale")
+    S.sem_set_patch_solver(prob.h, "fp32")
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"kernel_case": E, "n_dof": prob.n_dof, "tiles": tiles}))

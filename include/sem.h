@@ -257,6 +257,27 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
               int* iters_host, double* res_hist_host, double* true_rel_res_host);
 
 /*
+ * sem_solve_block - k independent PCG solves (Algorithm 1) of A_D x_j = b_j on one handle,
+ * advanced together: every kernel of an iteration (operator, patch solves, coarse restriction
+ * and V-cycles, P-sum, vector updates) is one launch over all k right-hand sides (its grid's
+ * second dimension), so the tables and stored factors of the mesh serve the k solves within
+ * each launch and small problems fill the GPU k times better. Each right-hand side keeps its
+ * own alpha, beta and stop test; one that has converged stops changing while the others go
+ * on. The whole block is one graph launch. Results are bit-identical to k sem_solve calls.
+ *   k              1..SEM_MAX_BLOCK.
+ *   b_dev, x_dev   k * N doubles each (right-hand side j at offset j * N), must not alias.
+ *   iters_host, status_host, true_rel_res_host   NULL or k entries: iteration count,
+ *                  sem_solve status (SEM_OK, SEM_MAXIT or an error) and ||b_j - A x_j|| / ||b_j||.
+ * Needs SEM_PREC_FP64 or SEM_PREC_FP64_NATIVE, the V-cycle coarse solver and no attached
+ * network (SEM_ERR_ARG otherwise). The first call with a larger k than before grows the
+ * handle's solver work space to k slices (and rebuilds the coarse work vectors). Returns
+ * SEM_OK when all converged, else the most severe status. Synchronises the handle's stream.
+ */
+#define SEM_MAX_BLOCK 8
+int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double rtol, int maxit,
+                    int* iters_host, int* status_host, double* true_rel_res_host);
+
+/*
  * sem_solve_many - the PCG solves of `count` independent handles advanced together: every
  * round reads back the state of all active solves, then replays each one's iteration
  * graph on its own stream, so many small problems share the GPU (the batched form of

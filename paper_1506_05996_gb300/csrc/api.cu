@@ -142,10 +142,11 @@ int build_coarse(sem_t* h) {
       while (D.up_lanes < 32 && 4 * D.up_lanes * (int64_t)L.N.n < nnz) D.up_lanes *= 2;
     }
     CK(h->upload(&D.dinv, L.dinv, h->coarse_allocs));
-    CK(h->alloc(&D.b, L.A.n, h->coarse_allocs));
-    CK(h->alloc(&D.x, L.A.n, h->coarse_allocs));
-    CK(h->alloc(&D.t, L.A.n, h->coarse_allocs));
-    CK(h->alloc(&D.y, L.A.n, h->coarse_allocs));
+    // one slice per right-hand side of a block solve (h->kcap)
+    CK(h->alloc(&D.b, (size_t)L.A.n * h->kcap, h->coarse_allocs));
+    CK(h->alloc(&D.x, (size_t)L.A.n * h->kcap, h->coarse_allocs));
+    CK(h->alloc(&D.t, (size_t)L.A.n * h->kcap, h->coarse_allocs));
+    CK(h->alloc(&D.y, (size_t)L.A.n * h->kcap, h->coarse_allocs));
     if (h->amg_kind == SEM_COARSE_KCYCLE) {
       CK(h->alloc(&D.c1, L.A.n, h->coarse_allocs));
       CK(h->alloc(&D.c2, L.A.n, h->coarse_allocs));
@@ -158,12 +159,13 @@ int build_coarse(sem_t* h) {
   double* tmp_d;
   CK(h->upload(&tmp_d, amg.coarsest_inv, h->coarse_allocs)); d.coarsest_inv = tmp_d;
   d.coarsest_n = amg.coarsest_n;
-  CK(h->alloc(&d.cb, amg.coarsest_n, h->coarse_allocs));
-  CK(h->alloc(&d.cx, amg.coarsest_n, h->coarse_allocs));
-  CK(h->alloc(&d.cres, nfree, h->coarse_allocs));
-  CK(h->alloc(&d.Rc, nfree, h->coarse_allocs));
-  CK(h->alloc(&d.Zc, nfree, h->coarse_allocs));
-  CK(h->alloc(&d.Zc32, nfree, h->coarse_allocs));
+  const size_t kc = (size_t)h->kcap;
+  CK(h->alloc(&d.cb, amg.coarsest_n * kc, h->coarse_allocs));
+  CK(h->alloc(&d.cx, amg.coarsest_n * kc, h->coarse_allocs));
+  CK(h->alloc(&d.cres, nfree * kc, h->coarse_allocs));
+  CK(h->alloc(&d.Rc, nfree * kc, h->coarse_allocs));
+  CK(h->alloc(&d.Zc, nfree * kc, h->coarse_allocs));
+  CK(h->alloc(&d.Zc32, nfree * kc, h->coarse_allocs));
   d.nlevels = (int)h->levels.size();
   d.levels = h->levels.data();
   CK(cudaStreamSynchronize(h->stream));
@@ -808,7 +810,7 @@ int ensure_hist(sem_t* h, int maxit) {
     h->hist = nullptr;
     h->hist_cap = 0;
     const int cap = std::max(maxit + 1, 1024);
-    CK(cudaMalloc((void**)&h->hist, sizeof(double) * cap));
+    CK(cudaMalloc((void**)&h->hist, sizeof(double) * cap * h->kcap));
     h->hist_cap = cap;
   }
   return SEM_OK;
@@ -840,7 +842,7 @@ int enqueue_tail_head(sem_t* h) {
 int enqueue_start(sem_t* h, const double* b, double rtol, int maxit) {
   sem::DevProblem& d = h->d;
   cudaStream_t s = h->stream;
-  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), s));
+  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState) * d.nrhs, s));
   const int mixed = d.fp32 ? 1 : 0;
   const int learned = h->net != nullptr ? 1 : 0;
   const bool fine = h->precond == SEM_PRECOND_TWO_SCALE || h->precond == SEM_PRECOND_FINE;
@@ -870,7 +872,7 @@ long graph_key(const sem_t* h) {
          ((long)d.epb_sw << 8) | ((long)(h->net != nullptr) << 12) | ((long)d.amg_kind << 13) |
          ((long)d.epb_ax32 << 16) | ((long)d.epb_sw32 << 20) | ((long)(d.bf16 ? 1 : 0) << 24) |
          ((long)(d.dwk ? 1 : 0) << 25) | ((long)d.epb_axdw << 26) | ((long)d.epb_swdw << 30) |
-         ((long)(tc_active(d) ? 1 : 0) << 34);
+         ((long)(tc_active(d) ? 1 : 0) << 34) | ((long)d.nrhs << 35);
 }
 
 int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
@@ -1023,7 +1025,7 @@ int build_loop(sem_t* h, cudaGraph_t g, double rtol, int maxit) {
   cudaGraphConditionalHandle hw;
   CK(cudaGraphConditionalHandleCreate(&hw, g, 0, 0));
   auto set_loop = [&]() -> int {
-    CK(sem::launch_loop_cond(d.st, h->loop_guard, limit, hw, h->stream));
+    CK(sem::launch_loop_cond(d.st, d.nrhs, h->loop_guard, limit, hw, h->stream));
     return SEM_OK;
   };
   // IF (replacement requested) { FP64 residual replacement } inside graph gg after deps
@@ -1059,10 +1061,53 @@ int build_loop(sem_t* h, cudaGraph_t g, double rtol, int maxit) {
 }
 
 int ensure_loop_buffers(sem_t* h) {
-  if (h->bbuf == nullptr) CK(h->alloc(&h->bbuf, (size_t)h->nb.G, h->allocs));
+  if (h->bbuf == nullptr) CK(h->alloc(&h->bbuf, (size_t)h->nb.G * h->kcap, h->allocs));
   if (h->loop_guard == nullptr) CK(h->alloc(&h->loop_guard, 1, h->allocs));
   return SEM_OK;
 }
+
+// Grows the per-right-hand-side work buffers of the handle to k slices (block solves).
+template <class T>
+int regrow(sem_t* h, T** ptr, size_t count) {
+  if (*ptr != nullptr) {
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), (void*)*ptr);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(*ptr);
+    *ptr = nullptr;
+  }
+  CK(h->alloc(ptr, count, h->allocs));
+  return SEM_OK;
+}
+
+int ensure_block(sem_t* h, int k) {
+  if (k <= h->kcap) return SEM_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  sem::DevProblem& d = h->d;
+  const size_t G = (size_t)h->nb.G, ne = (size_t)h->nb.ne, kk = (size_t)k;
+  const size_t p3 = (size_t)d.p * d.p * d.p, P3 = (size_t)d.P * d.P * d.P;
+  h->kcap = k;
+  if (int rc = regrow(h, &h->r, G * kk)) return rc;
+  if (int rc = regrow(h, &h->z, G * kk)) return rc;
+  if (int rc = regrow(h, &h->p, G * kk)) return rc;
+  if (int rc = regrow(h, &h->f, G * kk)) return rc;
+  if (int rc = regrow(h, &h->u, G * kk)) return rc;
+  if (h->bbuf != nullptr)
+    if (int rc = regrow(h, &h->bbuf, G * kk)) return rc;
+  if (int rc = regrow(h, &d.wl, ne * p3 * kk)) return rc;
+  if (int rc = regrow(h, &d.wp, ne * P3 * kk)) return rc;
+  if (int rc = regrow(h, &d.Re, ne * 8 * kk)) return rc;
+  if (int rc = regrow(h, &d.partial, (size_t)4 * d.nblk * kk)) return rc;
+  if (int rc = regrow(h, &d.st, kk)) return rc;
+  CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState) * kk, h->stream));
+  if (h->st_host) cudaFreeHost(h->st_host);
+  h->st_host = nullptr;
+  CK(cudaMallocHost((void**)&h->st_host, sizeof(sem::PcgState) * kk));
+  if (h->hist) cudaFree(h->hist);   // regrown by ensure_hist for kcap slices
+  h->hist = nullptr;
+  h->hist_cap = 0;
+  return build_coarse(h);   // coarse vectors and AMG level work, kcap slices each
+}
+
 
 int instantiate(cudaGraph_t g, cudaGraphExec_t& exec) {
   cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
@@ -1155,6 +1200,68 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
     if (int rc = solve_advance(h, c)) return rc;
   }
   return solve_finish(h, c, iters_host, res_hist_host, true_rel_res_host);
+}
+
+int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
+                    int* status_host, double* true_rel_res_host) {
+  if (int rc = check_handle(h)) return rc;
+  sem::DevProblem& d = h->d;
+  if (k < 1 || k > SEM_MAX_BLOCK || b_dev == nullptr || x_dev == nullptr || (const void*)b_dev == (const void*)x_dev)
+    return fail(SEM_ERR_ARG, "bad block-solve arguments");
+  if (h->precision != SEM_PREC_FP64 && h->precision != SEM_PREC_FP64_NATIVE)
+    return fail(SEM_ERR_ARG, "block solves run in SEM_PREC_FP64 or SEM_PREC_FP64_NATIVE");
+  if (h->net != nullptr || d.amg_kind == SEM_COARSE_KCYCLE)
+    return fail(SEM_ERR_ARG, "block solves take the linear preconditioner (no network, V-cycle coarse solver)");
+  if (int rc = check_solvable(h)) return rc;
+  if (h->precond != SEM_PRECOND_FINE && h->precond != SEM_PRECOND_NONE &&
+      (!h->coarse_ok || (d.nfree == 0 && !h->coarse_err.empty())))
+    return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
+  if (int rc = ensure_block(h, k)) return rc;
+  if (int rc = ensure_hist(h, maxit)) return rc;
+  if (int rc = ensure_loop_buffers(h)) return rc;
+  cudaStream_t s = h->stream;
+  const size_t G = (size_t)h->nb.G;
+  d.nrhs = k;
+  d.hist_stride = h->hist_cap;
+  struct Restore {
+    sem::DevProblem& d;
+    ~Restore() { d.nrhs = 1; }
+  } restore{d};
+  const long key = graph_key(h);
+  if (h->loop.key != key || h->loop.rtol != rtol || h->loop.maxit != maxit) {
+    h->loop.reset();
+    CK(cudaStreamSynchronize(s));
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    int rc = build_loop(h, g, rtol, maxit);
+    if (rc == SEM_OK) rc = instantiate(g, h->loop.exec);
+    cudaGraphDestroy(g);
+    if (rc != SEM_OK) return rc;
+    h->loop.key = key;
+    h->loop.rtol = rtol;
+    h->loop.maxit = maxit;
+  }
+  CK(cudaMemcpyAsync(h->bbuf, b_dev, sizeof(double) * G * k, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGraphLaunch(h->loop.exec, s));
+  // true residuals ||b_j - A u_j|| and the solutions out, every right-hand side at once
+  PROF(h, "ax_local", sem::launch_ax_local(d, h->u, d.wl, nullptr, s));
+  PROF(h, "true_residual", sem::launch_true_residual(d, h->bbuf, d.wl, s));
+  CK(cudaMemcpyAsync(x_dev, h->u, sizeof(double) * G * k, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->prof.collect();
+  int worst = SEM_OK;
+  for (int j = 0; j < k; ++j) {
+    const sem::PcgState& st = h->st_host[j];
+    int rc = st.status == -6 ? SEM_ERR_NAN : (st.status == -4 ? SEM_ERR_CUDA : (!st.done || st.status == 1 ? SEM_MAXIT : SEM_OK));
+    if (iters_host) iters_host[j] = st.iter;
+    if (status_host) status_host[j] = rc;
+    if (true_rel_res_host) true_rel_res_host[j] = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
+    if (rc < 0 && (worst >= 0 || rc < worst)) worst = rc;
+    else if (rc > 0 && worst == SEM_OK) worst = rc;
+  }
+  if (worst < 0) return fail(worst, "a right-hand side of the block solve failed (see status_host)");
+  return worst;
 }
 
 int sem_heat_step(sem_t* h, const double* u_prev_dev, const double* g_dev, double* u_dev, double rtol, int maxit,

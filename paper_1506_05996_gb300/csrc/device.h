@@ -73,6 +73,12 @@ struct DevAmgLevel {
 
 struct DevProblem {
   int n = 0, p = 0, P = 0;
+  // Block solves (sem_solve_block): nrhs right-hand sides advance together, each kernel of the
+  // solve covering all of them (blockIdx.y = right-hand side). Right-hand side j's vectors,
+  // local and patch results, coarse vectors, state and reduction partials sit at j times the
+  // single-solve size after the first one's; its history at j * hist_stride.
+  int nrhs = 1;
+  int hist_stride = 0;
   int ne = 0, G = 0, nv = 0, nfree = 0;
   int Gi = 0;                       // DOFs 0..Gi-1 are element interiors, numbered e m^3 + a + m(b + m c)
                                     // for local node (a+1, b+1, c+1), m = n-1 (0: no such numbering)
@@ -261,7 +267,8 @@ cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const doubl
 
 // --- device-driven solve loop (graph conditional nodes) ----------------------------
 // WHILE condition: !st->done and ++*guard <= limit; IF condition: st->replace && !st->done
-cudaError_t launch_loop_cond(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_loop_cond(const PcgState* st, int nrhs, int* guard, int limit, cudaGraphConditionalHandle h,
+                             cudaStream_t s);
 cudaError_t launch_replace_cond(const PcgState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 
 // aux = ||b - f||^2 over free nodes

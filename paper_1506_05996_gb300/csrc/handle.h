@@ -198,6 +198,7 @@ struct sem_s {
   }
   double* hist = nullptr;
   int hist_cap = 0;
+  int kcap = 1;                      // right-hand sides the solver buffers hold (sem_solve_block)
   sem::PcgState* st_host = nullptr;  // pinned
   double *heat_b = nullptr, *heat_d = nullptr, *heat_norms = nullptr;   // sem_heat_step scratch
   // learned correction (not in the paper): attached network and its forward work space

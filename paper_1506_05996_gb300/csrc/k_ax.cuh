@@ -88,8 +88,12 @@ __global__ void __launch_bounds__(EPB * p * p, kIsDw<T> ? 65536 / ((((EPB * p * 
                                                                typename LocalOf<T>::type* __restrict__ wl,
                                                                const PcgState* st, TX* __restrict__ yd) {
   using TW = typename LocalOf<T>::type;
+  st = st_rhs(st);
   if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
+  x += (size_t)blockIdx.y * d.G;                 // right-hand side blockIdx.y of a block solve
+  wl += (size_t)blockIdx.y * d.ne * p3;
+  if (DIRECT) yd += (size_t)blockIdx.y * d.G;
   __shared__ FoldedD<p, T> Fg, Fd;
   __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
   __shared__ T sx_all[EPB * 24];
@@ -234,14 +238,14 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, typename LocalOf<T>:
     constexpr bool kF32 = std::is_same<T, float>::value;
     if constexpr (kIsDw<T>) {   // stored factors as pairs only (recomputed geometry stays FP64)
       if (d.recompute || d.geodw == nullptr) return cudaErrorInvalidValue;
-      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (d.recompute) {
-      ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+      ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (kF32 && d.bf16) {
       if constexpr (kF32)
-        ax_local_kernel<p, false, T, TX, EPB, DIRECT, __nv_bfloat16><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+        ax_local_kernel<p, false, T, TX, EPB, DIRECT, __nv_bfloat16><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else {
-      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<grid, EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     }
     count_launch();
     return cudaGetLastError();

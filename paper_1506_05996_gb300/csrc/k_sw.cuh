@@ -167,8 +167,11 @@ template <int P, typename T, typename TR, int EPB, bool VAR>
 __global__ void __launch_bounds__(EPB * P * P, kIsDw<T> ? dw_min_blocks(EPB * P * P) : 1) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
                                                                     T* __restrict__ wp, const PcgState* st) {
   using TW = T;
+  st = st_rhs(st);
   if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
+  r += (size_t)blockIdx.y * d.G;                 // right-hand side blockIdx.y of a block solve
+  wp += (size_t)blockIdx.y * d.ne * P3;
   __shared__ T sS[P2], sSv[3 * P2], s1_all[EPB * P3], s2_all[EPB * P3];
   // double-FP32: the element's inverted diagonal, copied asynchronously at the start of the
   // element so that its loads overlap the forward contractions (dynamic shared memory,
@@ -312,7 +315,7 @@ cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgStat
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
       if (e != cudaSuccess) return e;
     }
-    kernel<<<grid, EPB * P * P, dyn, s>>>(d, r, wp, st);
+    kernel<<<dim3(grid, d.nrhs), EPB * P * P, dyn, s>>>(d, r, wp, st);
     count_launch();
     return cudaGetLastError();
   } else {

@@ -286,12 +286,11 @@ cudaError_t launch_tc_P(const DevProblem& d, const TR* r, float* wp, const PcgSt
   if (e != cudaSuccess) return e;
   int grid = (d.ne + EPC - 1) / EPC;
   if (d.sw_reserve_sms > 0) {
-    int dev = 0, nsm = 0, per_sm = 0;
+    // 4 CTAs per SM (shared memory and tensor memory both hold 4) on all but the reserved SMs
+    int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kTcThreads, Sh::SMEM);
-    per_sm = per_sm < 4 ? per_sm : 4;   // tensor memory per SM
-    const int cap = (nsm - d.sw_reserve_sms) * per_sm;
+    const int cap = (nsm - d.sw_reserve_sms) * 4;
     if (cap > 0 && cap < grid) grid = cap;
   }
   kernel<<<grid, kTcThreads, Sh::SMEM, s>>>(d, r, wp, st);

@@ -13,6 +13,12 @@ namespace {
 
 __device__ __forceinline__ bool stopped(const PcgState* st) { return st != nullptr && st->done != 0; }
 
+// The state of the right-hand side this CTA works on in a block solve (blockIdx.y; the
+// first and only one otherwise), or null outside a solve.
+__device__ __forceinline__ const PcgState* st_rhs(const PcgState* st) {
+  return st != nullptr ? st + blockIdx.y : nullptr;
+}
+
 // Mixed path: replace the recursive residual by b - A u (FP64 operator) whenever it has
 // dropped by this factor since the last replacement, and before accepting convergence.
 constexpr double kReplaceFactor = 1e-3;

@@ -88,7 +88,10 @@ __global__ void gather_plain_kernel(const DevProblem d, const double* __restrict
 template <int p, typename T>
 __global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem d, const T* __restrict__ r,
                                                                 const PcgState* st) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  r += (size_t)blockIdx.y * d.G;                          // right-hand side blockIdx.y
+  double* Re = d.Re + (size_t)blockIdx.y * d.ne * 8;
   constexpr int p3 = p * p * p;
   __shared__ T sl[2][p * p], sm[2][2][p], phi[2][p];
   const int e = blockIdx.x, t = threadIdx.x;
@@ -129,16 +132,19 @@ __global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem
     T v = 0;
 #pragma unroll
     for (int k = 0; k < p; ++k) v += phi[b2][k] * sm[b0][b1][k];
-    d.Re[(size_t)e * 8 + t] = (double)v;
+    Re[(size_t)e * 8 + t] = (double)v;
   }
 }
 
 __global__ void vertex_gather_kernel(const DevProblem d, const PcgState* st) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  const double* Re = d.Re + (size_t)blockIdx.y * d.ne * 8;
+  double* Rc = d.Rc + (size_t)blockIdx.y * d.nfree;
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < d.nfree; v += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int q = d.cv_off[v]; q < d.cv_off[v + 1]; ++q) s += d.Re[d.cv_idx[q]];
-    d.Rc[v] = s;
+    for (int q = d.cv_off[v]; q < d.cv_off[v + 1]; ++q) s += Re[d.cv_idx[q]];
+    Rc[v] = s;
   }
 }
 
@@ -205,7 +211,12 @@ template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_resid_kernel(DevCsr A, const double* __restrict__ b,
                                                              const double* __restrict__ x, double* __restrict__ t,
                                                              const PcgState* st) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  const size_t o = (size_t)blockIdx.y * A.n;   // right-hand side blockIdx.y (square matrix)
+  b += o;
+  x += o;
+  t += o;
   const RowGroups<LANES> g;
   for (int i0 = g.first; i0 < A.n; i0 += g.step) {
     const int i = i0 + g.sub;
@@ -217,8 +228,11 @@ __global__ void __launch_bounds__(kRowBlock) amg_resid_kernel(DevCsr A, const do
 
 template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_spmv_kernel(DevCsr A, const double* __restrict__ x,
-                                                            double* __restrict__ y, const PcgState* st) {
+                                                            double* __restrict__ y, const PcgState* st, int sx) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  x += (size_t)blockIdx.y * sx;                // right-hand side blockIdx.y: x has sx entries
+  y += (size_t)blockIdx.y * A.n;
   const RowGroups<LANES> g;
   for (int i0 = g.first; i0 < A.n; i0 += g.step) {
     const int i = i0 + g.sub;
@@ -262,8 +276,14 @@ __global__ void __launch_bounds__(kRowBlock) amg_jacobi_post_kernel(DevCsr A, co
 template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, const double* __restrict__ b,
                                                           const double* __restrict__ xc, const double* z, double* out,
-                                                          const PcgState* st) {
+                                                          const PcgState* st, int sxc) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  const size_t o = (size_t)blockIdx.y * N.n;   // right-hand side blockIdx.y; xc has sxc entries
+  b += o;
+  out += o;
+  if (z != nullptr) z += o;
+  xc += (size_t)blockIdx.y * sxc;
   const RowGroups<LANES> g;
   for (int i0 = g.first; i0 < N.n; i0 += g.step) {
     const int i = i0 + g.sub;
@@ -277,7 +297,10 @@ __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, c
 __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double* __restrict__ Ainv,
                                                             const double* __restrict__ b, double* __restrict__ x,
                                                             const PcgState* st) {
+  st = st_rhs(st);
   if (stopped(st)) return;
+  b += (size_t)blockIdx.y * n;
+  x += (size_t)blockIdx.y * n;
   for (int row = blockIdx.x; row < n; row += gridDim.x) {
     double s = 0.0;
     for (int c = threadIdx.x; c < n; c += kRowBlock) s += Ainv[(size_t)row * n + c] * b[c];
@@ -381,10 +404,15 @@ template <> __device__ __forceinline__ const float* wts_of<float>(const DevProbl
 template <bool PCG, typename T>
 __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const T* __restrict__ wp,
                                                          const double* __restrict__ r, double* __restrict__ z) {
-  if (PCG && stopped(d.st)) return;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  if (PCG && stopped(pst)) return;
   const int p = d.p, p3 = p * p * p;
+  wp += (size_t)blockIdx.y * d.ne * d.P * d.P * d.P;
+  r += (size_t)blockIdx.y * d.G;
+  z += (size_t)blockIdx.y * d.G;
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
   const T* __restrict__ Bt = btab_of<T>(d);
-  const T* __restrict__ Zc = zc_of<T>(d);
+  const T* __restrict__ Zc = zc_of<T>(d) + (size_t)blockIdx.y * d.nfree;
   const T* __restrict__ Wt = wts_of<T>(d);
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
@@ -416,8 +444,8 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
   if (PCG) {
     double total;
-    if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
-      PcgState* st = d.st;
+    if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) {
+      PcgState* st = pst;
       if (!isfinite(total)) { st->status = -6; st->done = 1; }
       if (st->iter > 0) st->beta = total / st->rz;
       st->rz = total;
@@ -432,8 +460,14 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
 template <bool PCG>
 __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, int mode, const dw* __restrict__ wp,
                                                             const double* __restrict__ r, double* __restrict__ z) {
-  if (PCG && stopped(d.st)) return;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  if (PCG && stopped(pst)) return;
   const int p = d.p, p3 = p * p * p;
+  wp += (size_t)blockIdx.y * d.ne * d.P * d.P * d.P;
+  r += (size_t)blockIdx.y * d.G;
+  z += (size_t)blockIdx.y * d.G;
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
+  const double* const Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     dw v = dw_zero();
@@ -453,7 +487,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           const int cv = ec[c];
-          if (cv >= 0) dw_mac(zc, B[c], dw_split(d.Zc[cv]));
+          if (cv >= 0) dw_mac(zc, B[c], dw_split(Zc[cv]));
         }
         v = dw_add(v, zc);
       }
@@ -464,8 +498,8 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
   }
   if (PCG) {
     double total;
-    if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
-      PcgState* st = d.st;
+    if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) {
+      PcgState* st = pst;
       if (!isfinite(total)) { st->status = -6; st->done = 1; }
       if (st->iter > 0) st->beta = total / st->rz;
       st->rz = total;
@@ -483,6 +517,12 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
                                                              double rtol, int maxit, int mixed, int learned,
                                                              int flexible, int stall_window, double stall_ratio,
                                                              double nn_theta, double* hist) {
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
+  b += (size_t)blockIdx.y * d.G;
+  r += (size_t)blockIdx.y * d.G;
+  u += (size_t)blockIdx.y * d.G;
+  hist += (size_t)blockIdx.y * d.hist_stride;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double v = d.mask[g] ? 0.0 : b[g];
@@ -493,8 +533,8 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
     dot += v * v;
   }
   double total;
-  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
-    PcgState* st = d.st;
+  if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) {
+    PcgState* st = pst;
     st->bb = total;
     st->rtol = rtol;
     st->rr = total;
@@ -524,9 +564,12 @@ __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d,
 }
 
 __global__ void pcg_copy_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
-  if (stopped(d.st)) return;
-  float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
-  const double* __restrict__ c = (d.st->learned && d.st->nn_use) ? d.nncorr : nullptr;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  z += (size_t)blockIdx.y * d.G;
+  p += (size_t)blockIdx.y * d.G;
+  if (stopped(pst)) return;
+  float* __restrict__ p32 = pst->mixed ? d.p32 : nullptr;
+  const double* __restrict__ c = (pst->learned && pst->nn_use) ? d.nncorr : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double pn = c ? z[g] + c[g] : z[g];
     p[g] = pn;
@@ -538,7 +581,12 @@ template <typename T>
 __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevProblem d, const T* __restrict__ wl,
                                                                      const double* __restrict__ p,
                                                                      double* __restrict__ f) {
-  if (stopped(d.st)) return;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
+  wl += (size_t)blockIdx.y * d.ne * d.p * d.p * d.p;
+  p += (size_t)blockIdx.y * d.G;
+  f += (size_t)blockIdx.y * d.G;
+  if (stopped(pst)) return;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     T s = 0;
@@ -549,8 +597,8 @@ __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevPr
     dot += p[g] * sd;
   }
   double total;
-  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
-    PcgState* st = d.st;
+  if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) {
+    PcgState* st = pst;
     st->pf = total;
     if (!(total > 0.0) || !isfinite(total)) { st->status = -6; st->done = 1; }
     else st->alpha = st->rz / total;
@@ -560,11 +608,18 @@ __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevPr
 __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem d, const double* __restrict__ p,
                                                                const double* __restrict__ f, double* __restrict__ u,
                                                                double* __restrict__ r, double* hist) {
-  if (stopped(d.st)) return;
-  const double alpha = d.st->alpha;
-  float* __restrict__ r32 = d.st->mixed ? d.r32 : nullptr;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
+  p += (size_t)blockIdx.y * d.G;
+  f += (size_t)blockIdx.y * d.G;
+  u += (size_t)blockIdx.y * d.G;
+  r += (size_t)blockIdx.y * d.G;
+  hist += (size_t)blockIdx.y * d.hist_stride;
+  if (stopped(pst)) return;
+  const double alpha = pst->alpha;
+  float* __restrict__ r32 = pst->mixed ? d.r32 : nullptr;
   double dot = 0.0;
-  double* __restrict__ rprev = d.st->flexible ? d.rprev : nullptr;
+  double* __restrict__ rprev = pst->flexible ? d.rprev : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     u[g] = u[g] + alpha * p[g];
     const double ro = r[g];
@@ -575,8 +630,8 @@ __global__ void __launch_bounds__(kVecBlock) pcg_update_kernel(const DevProblem 
     dot += rn * rn;
   }
   double total;
-  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) {
-    PcgState* st = d.st;
+  if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) {
+    PcgState* st = pst;
     st->rr = total;
     const int it = ++st->iter;
     if (st->learned) {
@@ -634,10 +689,13 @@ __global__ void __launch_bounds__(kVecBlock) pcg_replace_kernel(const DevProblem
 }
 
 __global__ void pcg_direction_kernel(const DevProblem d, const double* __restrict__ z, double* __restrict__ p) {
-  if (stopped(d.st)) return;
-  const double beta = d.st->beta;
-  float* __restrict__ p32 = d.st->mixed ? d.p32 : nullptr;
-  const double* __restrict__ c = (d.st->learned && d.st->nn_use) ? d.nncorr : nullptr;
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  z += (size_t)blockIdx.y * d.G;
+  p += (size_t)blockIdx.y * d.G;
+  if (stopped(pst)) return;
+  const double beta = pst->beta;
+  float* __restrict__ p32 = pst->mixed ? d.p32 : nullptr;
+  const double* __restrict__ c = (pst->learned && pst->nn_use) ? d.nncorr : nullptr;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     const double pn = (c ? z[g] + c[g] : z[g]) + beta * p[g];
     p[g] = pn;
@@ -749,10 +807,12 @@ __global__ void add_vectors_kernel(int n, const double* __restrict__ a, const do
 // Device-driven solve loop (a CUDA graph WHILE node around one iteration): the loop runs
 // while the solve is not done, and never more than `limit` times (an independent guard,
 // so the graph ends whatever the solver state). One thread sets the condition.
-__global__ void loop_cond_kernel(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h) {
+__global__ void loop_cond_kernel(const PcgState* st, int nrhs, int* guard, int limit, cudaGraphConditionalHandle h) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int g = ++*guard;
-    cudaGraphSetConditional(h, (st->done == 0 && g <= limit) ? 1u : 0u);
+    bool open = false;   // a block solve runs until each of its right-hand sides is done
+    for (int j = 0; j < nrhs; ++j) open = open || st[j].done == 0;
+    cudaGraphSetConditional(h, (open && g <= limit) ? 1u : 0u);
   }
 }
 
@@ -770,6 +830,10 @@ __global__ void pair_delta_kernel(const DevProblem d, const double* __restrict__
 
 __global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProblem d, const double* __restrict__ b,
                                                                   const double* __restrict__ wl) {
+  PcgState* const pst = d.st + blockIdx.y;    // right-hand side blockIdx.y
+  double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
+  b += (size_t)blockIdx.y * d.G;
+  wl += (size_t)blockIdx.y * d.ne * d.p * d.p * d.p;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) continue;
@@ -779,7 +843,7 @@ __global__ void __launch_bounds__(kVecBlock) true_residual_kernel(const DevProbl
     dot += res * res;
   }
   double total;
-  if (grid_reduce<kVecBlock>(dot, d.partial, &d.st->counter, total) && threadIdx.x == 0) d.st->aux = total;
+  if (grid_reduce<kVecBlock>(dot, part, &pst->counter, total) && threadIdx.x == 0) pst->aux = total;
 }
 
 inline int grid_for(int n, int block, int cap) {
@@ -793,10 +857,10 @@ inline int grid_for(int n, int block, int cap) {
   do {                                                                                              \
     const int rows_ = (M).n;                                                                        \
     switch ((M).lanes) {                                                                            \
-      case 4: KERN<4><<<grid_for(rows_, kRowBlock / 4, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;     \
-      case 8: KERN<8><<<grid_for(rows_, kRowBlock / 8, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;     \
-      case 16: KERN<16><<<grid_for(rows_, kRowBlock / 16, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;  \
-      default: KERN<32><<<grid_for(rows_, kRowBlock / 32, 8192), kRowBlock, 0, s>>>(__VA_ARGS__); break;  \
+      case 4: KERN<4><<<dim3(grid_for(rows_, kRowBlock / 4, 8192), d.nrhs), kRowBlock, 0, s>>>(__VA_ARGS__); break;    \
+      case 8: KERN<8><<<dim3(grid_for(rows_, kRowBlock / 8, 8192), d.nrhs), kRowBlock, 0, s>>>(__VA_ARGS__); break;    \
+      case 16: KERN<16><<<dim3(grid_for(rows_, kRowBlock / 16, 8192), d.nrhs), kRowBlock, 0, s>>>(__VA_ARGS__); break; \
+      default: KERN<32><<<dim3(grid_for(rows_, kRowBlock / 32, 8192), d.nrhs), kRowBlock, 0, s>>>(__VA_ARGS__); break; \
     }                                                                                               \
   } while (0)
 
@@ -810,19 +874,21 @@ constexpr int kCycles = 3;
 cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double* out, const double* z,
                          const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    dense_mv_kernel<<<dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b,
+                                                                                       out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
   }
   const DevAmgLevel& L = d.levels[level];
   double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
   double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
-  ROWS_LAUNCH(amg_spmv_kernel, L.M, L.M, b, bc, st);
+  ROWS_LAUNCH(amg_spmv_kernel, L.M, L.M, b, bc, st, L.A.n);
   ++g_kernel_launches;
   cudaError_t err = vcycle_fused(d, level + 1, bc, xc, nullptr, st, s);
   if (err != cudaSuccess) return err;
   const struct { int n, lanes; } up{L.N.n, L.up_lanes};   // N's rows, the level's lane count
-  ROWS_LAUNCH(amg_up_kernel, up, L.N, L.Q, b, xc, z, out, st);
+  const int nc = (level + 1 == d.nlevels) ? d.coarsest_n : d.levels[level + 1].A.n;
+  ROWS_LAUNCH(amg_up_kernel, up, L.N, L.Q, b, xc, z, out, st, nc);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -830,7 +896,8 @@ cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double
 // One K-cycle at `level` for right-hand side b, result in out (out != b).
 cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<grid_for(d.coarsest_n, 1, 8192), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b, out, st);
+    dense_mv_kernel<<<dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b,
+                                                                                       out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
   }
@@ -843,7 +910,7 @@ cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out,
   cudaError_t err;
   double* ec;
   if (level + 1 == d.nlevels) {
-    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, d.cb, st);
+    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, d.cb, st, L.A.n);
     ++g_kernel_launches;
     err = kcycle(d, level + 1, d.cb, d.cx, st, s);   // the dense level: exact
     if (err != cudaSuccess) return err;
@@ -851,15 +918,15 @@ cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out,
   } else {
     const DevAmgLevel& N = d.levels[level + 1];
     const int gbc = grid_for(nc, 256, 4096);
-    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, N.b, st);
+    ROWS_LAUNCH(amg_spmv_kernel, L.R, L.R, L.t, N.b, st, L.A.n);
     ++g_kernel_launches;
     if ((err = kcycle(d, level + 1, N.b, N.c1, st, s)) != cudaSuccess) return err;
-    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c1, N.v1, st);
+    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c1, N.v1, st, N.A.n);
     kc_dots1_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c1, N.v1, N.b, N.scal, st);
     kc_r2_kernel<<<gbc, 256, 0, s>>>(nc, N.v1, N.scal, N.b, st);
     g_kernel_launches += 3;
     if ((err = kcycle(d, level + 1, N.b, N.c2, st, s)) != cudaSuccess) return err;
-    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c2, N.v2, st);
+    ROWS_LAUNCH(amg_spmv_kernel, N.A, N.A, N.c2, N.v2, st, N.A.n);
     kc_dots2_kernel<<<1, kKcBlock, 0, s>>>(nc, N.c2, N.v1, N.v2, N.b, N.scal, st);
     kc_combine_kernel<<<gbc, 256, 0, s>>>(nc, N.c1, N.c2, N.scal, N.y, st);
     g_kernel_launches += 3;
@@ -937,12 +1004,12 @@ template <typename T>
 cudaError_t launch_coarse_restrict_t(const DevProblem& d, const T* r, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
   switch (d.p) {
-#define RS_CASE(P_) case P_: coarse_restrict_kernel<P_, T><<<d.ne, P_ * P_, 0, s>>>(d, r, st); ++g_kernel_launches; break;
+#define RS_CASE(P_) case P_: coarse_restrict_kernel<P_, T><<<dim3(d.ne, d.nrhs), P_ * P_, 0, s>>>(d, r, st); ++g_kernel_launches; break;
     RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6) RS_CASE(7) RS_CASE(8) RS_CASE(9)
 #undef RS_CASE
     default: return cudaErrorInvalidValue;
   }
-  vertex_gather_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d, st);
+  vertex_gather_kernel<<<dim3(grid_for(d.nfree, 256, 4096), d.nrhs), 256, 0, s>>>(d, st);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -983,15 +1050,15 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
   if (d.pfp32) {
     const float* wp = reinterpret_cast<const float*>(d.wp);
-    if (pcg) psum_kernel<true, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
-    else psum_kernel<false, float><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    if (pcg) psum_kernel<true, float><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    else psum_kernel<false, float><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
   } else if (d.dwk) {   // the patch results are pairs (double-FP32 patch solve)
     const dw* wp = reinterpret_cast<const dw*>(d.wp);
-    if (pcg) psum_dw_kernel<true><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
-    else psum_dw_kernel<false><<<d.nblk, kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    if (pcg) psum_dw_kernel<true><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    else psum_dw_kernel<false><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
   } else {
-    if (pcg) psum_kernel<true, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
-    else psum_kernel<false, double><<<d.nblk, kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
+    if (pcg) psum_kernel<true, double><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
+    else psum_kernel<false, double><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
   }
   ++g_kernel_launches;
   return cudaGetLastError();
@@ -1000,34 +1067,34 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
 cudaError_t launch_pcg_init(const DevProblem& d, const double* b, double* r, double* u, double rtol, int maxit,
                             int mixed, int learned, int flexible, int stall_window, double stall_ratio,
                             double nn_theta, double* hist, cudaStream_t s) {
-  pcg_init_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, flexible, stall_window,
+  pcg_init_kernel<<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, b, r, u, rtol, maxit, mixed, learned, flexible, stall_window,
                                                 stall_ratio, nn_theta, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_first_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
-  pcg_copy_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  pcg_copy_kernel<<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, z, p);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_gather_alpha(const DevProblem& d, const double* p, double* f, cudaStream_t s) {
-  if (d.fp32) pcg_gather_alpha_kernel<float><<<d.nblk, kVecBlock, 0, s>>>(d, reinterpret_cast<const float*>(d.wl), p, f);
-  else pcg_gather_alpha_kernel<double><<<d.nblk, kVecBlock, 0, s>>>(d, d.wl, p, f);
+  if (d.fp32) pcg_gather_alpha_kernel<float><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, reinterpret_cast<const float*>(d.wl), p, f);
+  else pcg_gather_alpha_kernel<double><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, d.wl, p, f);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update(const DevProblem& d, const double* p, const double* f, double* u, double* r, double* hist,
                               cudaStream_t s) {
-  pcg_update_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, p, f, u, r, hist);
+  pcg_update_kernel<<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, p, f, u, r, hist);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_direction(const DevProblem& d, const double* z, double* p, cudaStream_t s) {
-  pcg_direction_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, z, p);
+  pcg_direction_kernel<<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, z, p);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -1048,7 +1115,7 @@ cudaError_t launch_pcg_replace(const DevProblem& d, const double* b, const doubl
 }
 
 cudaError_t launch_true_residual(const DevProblem& d, const double* b, const double* wl, cudaStream_t s) {
-  true_residual_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, b, wl);
+  true_residual_kernel<<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, b, wl);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
@@ -1110,8 +1177,9 @@ cudaError_t launch_add_vectors(const DevProblem& d, const double* a, const doubl
 }
 
 
-cudaError_t launch_loop_cond(const PcgState* st, int* guard, int limit, cudaGraphConditionalHandle h, cudaStream_t s) {
-  loop_cond_kernel<<<1, 32, 0, s>>>(st, guard, limit, h);
+cudaError_t launch_loop_cond(const PcgState* st, int nrhs, int* guard, int limit, cudaGraphConditionalHandle h,
+                             cudaStream_t s) {
+  loop_cond_kernel<<<1, 32, 0, s>>>(st, nrhs, guard, limit, h);
   ++g_kernel_launches;
   return cudaGetLastError();
 }

@@ -61,6 +61,7 @@ _SIGS = {
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
     "sem_solve_many": ([_int, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
+    "sem_solve_block": ([_vp, _int, _vp, _vp, _dbl, _int, _vp, _vp, _vp], _int),
     "sem_heat_step": ([_vp, _vp, _vp, _vp, _dbl, _int, _P(_int), _P(_dbl)], _int),
     "sem_set_tiles": ([_vp, _int, _int], _int),
     "sem_autotune": ([_vp, _P(_int), _P(_int)], _int),
@@ -285,6 +286,22 @@ def sem_solve_many(handles, bs, xs, rtol=1e-8, maxit=1000):
                                     ctypes.cast(X, ctypes.c_void_p), float(rtol), int(maxit),
                                     ctypes.cast(its, ctypes.c_void_p), ctypes.cast(sts, ctypes.c_void_p)))
     return rc, list(its), list(sts)
+
+
+def sem_solve_block(h, b, x, rtol=1e-8, maxit=1000):
+    """k solves at once: b and x are (k, N) contiguous CUDA float64 tensors. Returns
+    (rc, iterations[k], status[k], true_rel_res[k])."""
+    n = sem_num_dofs(h)
+    if b.dim() != 2 or b.shape[1] != n or x.shape != b.shape:
+        raise ValueError("b and x must be (k, %d)" % n)
+    k = int(b.shape[0])
+    its = np.zeros(k, dtype=np.int32)
+    sts = np.zeros(k, dtype=np.int32)
+    trs = np.zeros(k, dtype=np.float64)
+    rc = _check(_lib.sem_solve_block(h, k, _dev(b, torch.float64, k * n), _dev(x, torch.float64, k * n),
+                                     float(rtol), int(maxit), its.ctypes.data_as(_vp), sts.ctypes.data_as(_vp),
+                                     trs.ctypes.data_as(_vp)))
+    return rc, its.tolist(), sts.tolist(), trs.tolist()
 
 
 def sem_set_tiles(h, epb_ax, epb_sw):
