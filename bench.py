@@ -66,6 +66,9 @@ def parse():
                     help="P^f patches: face layers only against the full (n+3)^3 box, 32^3 n=7, FP64 and mixed")
     ap.add_argument("--train-meshes", type=int, default=200)
     ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--solve-case", type=int, default=0, metavar="E",
+                    help="only run one SEM_PREC_FP64 solve on an E^3, n=7 mesh inside the NVTX range \"solve\" "
+                         "(the launch list of a solve for ncu), then exit")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
                     help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
                          "(a small case for ncu captures), then exit")
@@ -741,6 +744,27 @@ def run_gpu(args):
     ranks.close()
 
 
+def run_solve_case(E):
+    """One SEM_PREC_FP64 solve of the headline recipe at E^3 hexes, n = 7, after a warm-up
+    solve, inside the NVTX range "solve" (for ncu --nvtx --nvtx-include solve/)."""
+    import torch
+    from synth import lattice_hex_mesh, manufactured_s
+    from paper_1506_05996_gb300 import sem as S
+    mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored")
+    X = prob.dof_coords()
+    b = prob.load(torch.as_tensor(manufactured_s(X.cpu().numpy(), LAM), device="cuda"))
+    S.sem_autotune(prob.h)
+    x, rc, it, hist, tr = prob.solve(b)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("solve")
+    x, rc, it, hist, tr = prob.solve(b)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"solve_case": E, "n_dof": prob.n_dof, "iterations": it, "true_rel_res": tr}))
+    prob.close()
+
+
 def run_kernel_case(E):
     """A few applies of each hot kernel (SEM_PREC_FP64's double-FP32 kernels, binary64, FP32)
     on an E^3-hex, n = 7 mesh, with the
@@ -1107,6 +1131,8 @@ def main():
         run_precision_variant(args)
     elif args.kernel_case:
         run_kernel_case(args.kernel_case)
+    elif args.solve_case:
+        run_solve_case(args.solve_case)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -81,19 +81,19 @@ constexpr int ax_smem_bytes() {
 // TG: the stored factors' type (T, or BF16 under SEM_PREC_BF16 with T = float).
 // T = dw (the FP64 interface on the FP32 pipe) reads the factors as pairs and stores its
 // local results joined to binary64 (TW = LocalOf<T>).
-// (kIsDw: at most 96 registers a thread, as for the double-FP32 patch kernel)
 template <int p, bool RECOMP, typename T, typename TX, int EPB, bool DIRECT, typename TG>
-__global__ void __launch_bounds__(EPB * p * p, kIsDw<T> ? 65536 / ((((EPB * p * p) + 31) / 32) * 32 * 96) + 0 : 1)
-    ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
+__global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem d, const TX* __restrict__ x,
                                                                typename LocalOf<T>::type* __restrict__ wl,
                                                                const PcgState* st, TX* __restrict__ yd) {
   using TW = typename LocalOf<T>::type;
-  st = st_rhs(st);
-  if (stopped(st)) return;
   constexpr int p2 = p * p, p3 = p * p * p;
-  x += (size_t)blockIdx.y * d.G;                 // right-hand side blockIdx.y of a block solve
-  wl += (size_t)blockIdx.y * d.ne * p3;
-  if (DIRECT) yd += (size_t)blockIdx.y * d.G;
+  if constexpr (!std::is_same<T, float>::value) {   // block solves run in the FP64 arithmetics only
+    st = st_rhs(st);
+    x += (size_t)blockIdx.y * d.G;                   // right-hand side blockIdx.y of a block solve
+    wl += (size_t)blockIdx.y * d.ne * p3;
+    if (DIRECT) yd += (size_t)blockIdx.y * d.G;
+  }
+  if (stopped(st)) return;
   __shared__ FoldedD<p, T> Fg, Fd;
   __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
   __shared__ T sx_all[EPB * 24];

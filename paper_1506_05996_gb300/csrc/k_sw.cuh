@@ -164,14 +164,16 @@ constexpr int dw_min_blocks(int threads) {
 }
 
 template <int P, typename T, typename TR, int EPB, bool VAR>
-__global__ void __launch_bounds__(EPB * P * P, kIsDw<T> ? dw_min_blocks(EPB * P * P) : 1) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
-                                                                    T* __restrict__ wp, const PcgState* st) {
+__device__ __forceinline__ void schwarz_local_body(const DevProblem& d, const TR* __restrict__ r, T* __restrict__ wp,
+                                                   const PcgState* st) {
   using TW = T;
-  st = st_rhs(st);
-  if (stopped(st)) return;
   constexpr int P2 = P * P, P3 = P * P * P;
-  r += (size_t)blockIdx.y * d.G;                 // right-hand side blockIdx.y of a block solve
-  wp += (size_t)blockIdx.y * d.ne * P3;
+  if constexpr (!std::is_same<T, float>::value) {   // block solves run in the FP64 arithmetics only
+    st = st_rhs(st);
+    r += (size_t)blockIdx.y * d.G;                   // right-hand side blockIdx.y of a block solve
+    wp += (size_t)blockIdx.y * d.ne * P3;
+  }
+  if (stopped(st)) return;
   __shared__ T sS[P2], sSv[3 * P2], s1_all[EPB * P3], s2_all[EPB * P3];
   // double-FP32: the element's inverted diagonal, copied asynchronously at the start of the
   // element so that its loads overlap the forward contractions (dynamic shared memory,
@@ -265,6 +267,19 @@ __global__ void __launch_bounds__(EPB * P * P, kIsDw<T> ? dw_min_blocks(EPB * P 
 }
 
 
+// The kernels: the binary64 and FP32 instantiations with the compiler's register choice,
+// the double-FP32 one with at most 96 registers a thread (dw_min_blocks).
+template <int P, typename T, typename TR, int EPB, bool VAR>
+__global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevProblem d, const TR* __restrict__ r,
+                                                                    T* __restrict__ wp, const PcgState* st) {
+  schwarz_local_body<P, T, TR, EPB, VAR>(d, r, wp, st);
+}
+template <int P, typename T, typename TR, int EPB, bool VAR>
+__global__ void __launch_bounds__(EPB * P * P, dw_min_blocks(EPB * P * P))
+    schwarz_local_kernel_dw(const DevProblem d, const TR* __restrict__ r, T* __restrict__ wp, const PcgState* st) {
+  schwarz_local_body<P, T, TR, EPB, VAR>(d, r, wp, st);
+}
+
 template <int P, typename T, int EPB>
 constexpr bool sw_tile_supported() {
   return sw_smem_bytes<P, T, EPB>() <= 48 * 1024 && (EPB == 1 || EPB * P * P <= 256);
@@ -299,7 +314,10 @@ template <int P, typename T, typename TR, int EPB>
 cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgState* st, cudaStream_t s) {
   if constexpr (sw_tile_supported<P, T, EPB>()) {
     int grid = (d.ne + EPB - 1) / EPB;
-    auto kernel = d.pvar != nullptr ? schwarz_local_kernel<P, T, TR, EPB, true> : schwarz_local_kernel<P, T, TR, EPB, false>;
+    auto kernel = kIsDw<T> ? (d.pvar != nullptr ? schwarz_local_kernel_dw<P, T, TR, EPB, true>
+                                                : schwarz_local_kernel_dw<P, T, TR, EPB, false>)
+                           : (d.pvar != nullptr ? schwarz_local_kernel<P, T, TR, EPB, true>
+                                                : schwarz_local_kernel<P, T, TR, EPB, false>);
     if (d.sw_reserve_sms > 0) {
       // as many CTAs as fit on all but sw_reserve_sms SMs, so that slots stay free
       int dev = 0, nsm = 0, per_sm = 0;
