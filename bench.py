@@ -566,6 +566,12 @@ def run_gpu(args):
     mixed = variant("fp32")
     mixed["dtype"] = ("FP32 operator and patch solves; FP64 vectors, dots, recurrences, coarse solve, "
                       "residual replacement (double-FP32 operator) and final check")
+    prob.set_precision("fp32")
+    S.sem_set_patch_solver(prob.h, "bf16_tc")
+    mixed_tc = variant("fp32")
+    S.sem_set_patch_solver(prob.h, "fp32")
+    mixed_tc["dtype"] = ("as mixed, with the patch solves in BF16 on the tensor cores (tcgen05, FP32 accumulation) "
+                         "and the flexible beta")
     p32 = variant("p32")
     p32["dtype"] = "double-FP32 operator; FP32 patch solves and prolongation sums; FP64 vectors and recurrences"
     weighted = {"fp64": variant("fp64", True), "mixed": variant("fp32", True),
@@ -727,7 +733,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tiles_epb_ax_sw": tiles},
             "time_to_1e-8_s": per_step, "iterations": it64, "true_rel_res": tr64, "wall_s": t_wall,
-            "fp64_native": native, "mixed": mixed, "p32": p32, "weighted": weighted,
+            "fp64_native": native, "mixed": mixed, "mixed_tc": mixed_tc, "p32": p32, "weighted": weighted,
             "profiled": {"ms_per_step": t_prof * 1e3,
                          "note": "host-driven loop with a CUDA event pair around every launch",
                          "kernels_ms_per_step": {k: v[1] / args.steps
