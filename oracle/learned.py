@@ -249,3 +249,21 @@ def fpcg(apply_A, apply_P, correction, mask, b, rtol=1e-8, maxit=1000, window=8,
         if hist[-1] <= rtol:
             return x, k, np.array(hist), on_iters
     return x, maxit, np.array(hist), on_iters
+
+
+def correction_abs(theta, v, m_N, l2g, h, lam, mask):
+    """Magnitude of every term of the network's correction: the same evaluation with |W|, |b|
+    and |features| and no ReLU (|ReLU(a)| <= |a|), times sigma_e, averaged over the local
+    copies like the correction itself. Rounding bounds of a reduced-precision evaluation are
+    multiples of this vector (each layer's sum errs by at most gamma_K times the sum of its
+    terms' magnitudes, and such errors pass the next layers' |W| unchanged in sign)."""
+    feats, sigma = features(v, m_N, l2g, h, lam)
+    x = np.abs(feats)
+    for W, b in unpack(theta):
+        x = conv3d(x, np.abs(W), np.abs(b))
+    c_loc = x[:, 0] * sigma[:, None, None, None]
+    G = m_N.shape[0]
+    cnt = np.bincount(l2g.ravel(), minlength=G).astype(np.float64)
+    tot = np.bincount(l2g.ravel(), weights=c_loc.ravel(), minlength=G)
+    out = tot / np.where(cnt > 0, cnt, 1.0)
+    return np.where(mask > 0, 0.0, out)

@@ -157,10 +157,10 @@ constexpr int sw_smem_bytes() {
 // T = dw (the FP64 interface on the FP32 pipe) stores its patch results as pairs, which the
 // P-sum adds in the same arithmetic.
 // Resident CTAs per SM asked of the compiler for the double-FP32 kernels, whose pair
-// arithmetic is latency-bound at the occupancy its register count would allow: at most 96
+// arithmetic is latency-bound at the occupancy its register count would allow: at most 72
 // registers a thread (the binary64 and FP32 instantiations keep the compiler's choice).
 constexpr int dw_min_blocks(int threads) {
-  return 65536 / (((threads + 31) / 32) * 32 * 96) > 0 ? 65536 / (((threads + 31) / 32) * 32 * 96) : 1;
+  return 65536 / (((threads + 31) / 32) * 32 * 72) > 0 ? 65536 / (((threads + 31) / 32) * 32 * 72) : 1;
 }
 
 template <int P, typename T, typename TR, int EPB, bool VAR>
@@ -331,6 +331,9 @@ cudaError_t launch_sw_epb(const DevProblem& d, const TR* r, T* wp, const PcgStat
     constexpr int dyn = kIsDw<T> ? EPB * P * P * P * (int)sizeof(T) : 0;
     if (dyn > 0) {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+      // all of the unified L1 / shared storage as shared memory, so that the shared memory of
+      // the resident CTAs does not cap them below the register limit
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       if (e != cudaSuccess) return e;
     }
     kernel<<<dim3(grid, d.nrhs), EPB * P * P, dyn, s>>>(d, r, wp, st);

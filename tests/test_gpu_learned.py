@@ -88,8 +88,19 @@ def test_forward_parity(E, n, lam, seed):
     out = torch.empty(P.gpu.n_dof, dtype=torch.float64, device="cuda")
     sem.sem_net_apply(net, P.gpu.h, P.to_gpu(v), out)
     got = P.to_ref(out)
-    ref = learned.correction(_effective(theta), v, P.ref.m_N, P.ref.l2g, P.ref.h, P.ref.lam, P.ref.mask)
-    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+    th = _effective(theta)
+    ref = learned.correction(th, v, P.ref.m_N, P.ref.l2g, P.ref.h, P.ref.lam, P.ref.mask)
+    # per-result bound: the GPU evaluates the same BF16 weights with FP32 activations and sums.
+    # Each layer's sum of 27 c_in + 1 terms errs by gamma_K of its terms' magnitudes, which pass
+    # the next layers through |W| (ReLU is 1-Lipschitz); the features (v / m hbar^2 over the
+    # rms sigma_e, a sum of p^3 squares) and the output scaling by sigma_e add about 2 p^3 + 8
+    # roundings, the average over at most 8 local copies 8 more:
+    # |N32 - N| <= gamma_K |N|abs with K = 136 + 217 + 217 + 2 p^3 + 16 (oracle.learned.correction_abs)
+    ref_abs = learned.correction_abs(th, v, P.ref.m_N, P.ref.l2g, P.ref.h, P.ref.lam, P.ref.mask)
+    K = 136 + 217 + 217 + 2 * (n + 1) ** 3 + 16
+    gK = K * 2.0 ** -24 / (1 - K * 2.0 ** -24)
+    free = P.ref.mask == 0
+    assert np.all(np.abs(got - ref)[free] <= gK * ref_abs[free])
     assert np.all(got[P.ref.mask > 0] == 0)
     sem.sem_net_destroy(net)
 
@@ -232,9 +243,10 @@ def test_training_reduces_loss():
 def test_trained_network_gain(record_property):
     """What the trained network gains over plain two-scale PCG on an unseen mesh.
 
-    Measured, not assumed: the gain is recorded (iterations and time, FP64); the test
-    requires the flexible solve to converge to 1e-8 with the safeguard and the stall rule
-    bounding any loss to a quarter of the plain iterations plus the stall window.
+    Measured, not assumed: the gain is recorded (iterations and time, FP64), and the test
+    states it: no gain (at least the plain iteration count), with the flexible solve reaching
+    1e-8 and the safeguard and the stall rule bounding the loss to a quarter of the plain
+    iterations plus the stall window.
     """
     from paper_1506_05996_gb300 import sem
     from paper_1506_05996_gb300.learn import make_problem, timed_solve, train, training_set
@@ -252,5 +264,7 @@ def test_trained_network_gain(record_property):
     record_property("time_ratio_learned_over_plain", t1 / t0)
     print("plain %d its %.2f ms | learned %d its (%d with the network) %.2f ms" % (it0, 1e3 * t0, it1, used, 1e3 * t1))
     assert rc0 == rc1 == 0 and tr1 <= 1e-8
-    assert it1 <= 1.25 * it0 + 8
+    # the measured outcome on this unseen mesh: the network gains nothing (it takes at least
+    # the plain count), and the safeguard and the stall rule bound the loss
+    assert it0 <= it1 <= 1.25 * it0 + 8, (it0, it1)
     sem.sem_net_destroy(net)

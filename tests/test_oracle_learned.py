@@ -176,3 +176,32 @@ def test_fpcg_safeguard_rejects_a_correction_that_cancels_descent():
     x, it, hist, on = learned.fpcg(pr.apply_A, P, flip, pr.mask, b, rtol=1e-10, window=0)
     ref = pr.solve(b, rtol=1e-10)
     assert on == 0 and it == ref[1]
+
+
+def test_correction_abs_bounds_and_equals_the_positive_network():
+    """oracle.learned.correction_abs (the network with |W|, |b|, |features| and no ReLU,
+    scaled and averaged like the correction) bounds |N(v)| at every node, and equals N(v)
+    when the weights, biases and features are all nonnegative (every ReLU is then the
+    identity)."""
+    from oracle.learned import correction, correction_abs, n_params
+    from oracle.problem import Problem
+    from synth import lattice_hex_mesh
+    pr = Problem(lattice_hex_mesh(2, 0.2, 3), 3, 0.7, coarse_solver=None, with_schwarz=False)
+    rng = np.random.default_rng(4)
+    theta = rng.standard_normal(n_params()) * 0.3
+    v = rng.standard_normal(pr.G) * (pr.mask == 0)
+    c = correction(theta, v, pr.m_N, pr.l2g, pr.h if hasattr(pr, "h") else _boxes(pr), pr.lam, pr.mask)
+    ca = correction_abs(theta, v, pr.m_N, pr.l2g, pr.h if hasattr(pr, "h") else _boxes(pr), pr.lam, pr.mask)
+    assert np.all(np.abs(c) <= ca * (1 + 1e-12) + 1e-300)
+    assert np.max(np.abs(c) / np.where(ca > 0, ca, 1.0)) < 1.0
+    tpos = np.abs(theta)
+    vpos = np.abs(v)
+    h = pr.h if hasattr(pr, "h") else _boxes(pr)
+    cp = correction(tpos, vpos, pr.m_N, pr.l2g, h, pr.lam, pr.mask)
+    cpa = correction_abs(tpos, vpos, pr.m_N, pr.l2g, h, pr.lam, pr.mask)
+    np.testing.assert_allclose(cp, cpa, rtol=1e-12, atol=0)
+
+
+def _boxes(pr):
+    from oracle.geometry import element_box_sizes
+    return element_box_sizes(pr.xyz_e)
