@@ -166,6 +166,7 @@ int build_coarse(sem_t* h) {
   CK(h->alloc(&d.Rc, nfree * kc, h->coarse_allocs));
   CK(h->alloc(&d.Zc, nfree * kc, h->coarse_allocs));
   CK(h->alloc(&d.Zc32, nfree * kc, h->coarse_allocs));
+  CK(h->alloc(&d.Zce, (size_t)8 * h->nb.ne * kc, h->coarse_allocs));
   d.nlevels = (int)h->levels.size();
   d.levels = h->levels.data();
   CK(cudaStreamSynchronize(h->stream));
@@ -472,6 +473,12 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
     std::vector<sem::dw> Btdw(Btab.size());
     for (size_t q = 0; q < Btab.size(); ++q) Btdw[q] = sem::dw_split_host(Btab[q]);
     UP(Btabdw, Btdw, sem::dw);
+    std::vector<sem::dw> phi(2 * p);
+    for (int i = 0; i < p; ++i) {
+      phi[2 * i] = sem::dw_split_host(0.5 * (1.0 - t[i]));
+      phi[2 * i + 1] = sem::dw_split_host(0.5 * (1.0 + t[i]));
+    }
+    UP(phidw, phi, sem::dw);
   }
 #undef UP
   CK(h->upload(&h->coords, coords, A));

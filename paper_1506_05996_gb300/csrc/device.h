@@ -130,6 +130,9 @@ struct DevProblem {
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* Btab32 = nullptr;    // the same in FP32
   const dw* Btabdw = nullptr;       // the same as pairs of FP32
+  const dw* phidw = nullptr;        // [p][2] (1 - t_i)/2 and (1 + t_i)/2 as pairs (the 1D factors of Btab)
+  dw* Zce = nullptr;                // [ne][8] coarse correction at each element's corners as pairs (0 where
+                                    // the vertex is not free), for the double-FP32 P-sum
   const int* ecv = nullptr;
   const int* cv_off = nullptr;
   const int* cv_idx = nullptr;
@@ -260,6 +263,9 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
                             const double* g, double* out, double* norms, cudaStream_t s);
 // dst[i] = (fl32(src[i]), fl32(src[i] - fl32(src[i]))) for the double-FP32 kernels' tables
 cudaError_t launch_split_pairs(long long n, const double* src, dw* dst, cudaStream_t s);
+// Zce[e][c] = split(Zc[ecv[e][c]]) (0 where the corner is not a free vertex): the coarse
+// correction at element corners for the double-FP32 P-sum
+cudaError_t launch_coarse_corners_dw(const DevProblem& d, const PcgState* st, cudaStream_t s);
 // b = mask ? 0 : mN * s (lumped GLL load)
 cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s);
 // y = a + b

@@ -453,6 +453,19 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
 }
 
+// The coarse correction at the corners of every element, as pairs: one gather per corner
+// instead of one per node of the P-sum (which then reads 8 contiguous pairs per node).
+__global__ void coarse_corners_dw_kernel(const DevProblem d, const PcgState* st) {
+  st = st_rhs(st);
+  if (stopped(st)) return;
+  const double* Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
+  dw* Zce = d.Zce + (size_t)blockIdx.y * d.ne * 8;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 8 * d.ne; q += gridDim.x * blockDim.x) {
+    const int cv = d.ecv[q];
+    Zce[q] = cv >= 0 ? dw_split(Zc[cv]) : dw_zero();
+  }
+}
+
 // The P-sum of SEM_PREC_FP64 in double-FP32: the patch results (pairs, written by the
 // double-FP32 patch solve) summed over the patches containing each node, plus the trilinear
 // interpolation of the coarse correction (8 products per DOF), joined to binary64 once per
@@ -467,7 +480,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
   r += (size_t)blockIdx.y * d.G;
   z += (size_t)blockIdx.y * d.G;
   double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
-  const double* const Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
+  const dw* const Zce = d.Zce + (size_t)blockIdx.y * d.ne * 8;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     dw v = dw_zero();
@@ -480,16 +493,19 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
         v = dw_add(v, vf);
       }
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
+        // trilinear interpolation of the element's corner values (VTK order) at the owner
+        // node (i, j, k), sum-factorised: along i, then j, then k
         const int l = d.owner[g], e = l / p3, lr = l % p3;
-        const int* ec = d.ecv + (size_t)e * 8;
-        const dw* B = d.Btabdw + 8 * lr;
-        dw zc = dw_zero();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int cv = ec[c];
-          if (cv >= 0) dw_mac(zc, B[c], dw_split(Zc[cv]));
-        }
-        v = dw_add(v, zc);
+        const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
+        const dw* Z = Zce + (size_t)e * 8;
+        const dw a0 = d.phidw[2 * i], a1 = d.phidw[2 * i + 1];
+        const dw b0 = d.phidw[2 * j], b1 = d.phidw[2 * j + 1];
+        const dw c0 = d.phidw[2 * k], c1 = d.phidw[2 * k + 1];
+        auto lerp = [](dw f0, dw x0, dw f1, dw x1) { dw s = dw_mul(f0, x0); dw_mac(s, f1, x1); return s; };
+        const dw z00 = lerp(a0, Z[0], a1, Z[1]), z10 = lerp(a0, Z[3], a1, Z[2]);
+        const dw z01 = lerp(a0, Z[4], a1, Z[5]), z11 = lerp(a0, Z[7], a1, Z[6]);
+        const dw w0 = lerp(b0, z00, b1, z10), w1 = lerp(b0, z01, b1, z11);
+        v = dw_add(v, lerp(c0, w0, c1, w1));
       }
     }
     const double vd = dw_join(v);
@@ -1029,6 +1045,8 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
     if (d.pfp32) {
       to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
       ++g_kernel_launches;
+    } else if (d.dwk) {
+      return launch_coarse_corners_dw(d, st, s);
     }
     return cudaGetLastError();
   }
@@ -1043,6 +1061,8 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   if (d.pfp32) {
     to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
     ++g_kernel_launches;
+  } else if (d.dwk) {
+    return launch_coarse_corners_dw(d, st, s);
   }
   return cudaGetLastError();
 }
@@ -1152,6 +1172,13 @@ cudaError_t launch_pair_delta(const DevProblem& d, const double* xs, const doubl
 cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double* mN, const double* u_prev,
                             const double* g, double* out, double* norms, cudaStream_t s) {
   heat_rhs_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, wl, mN, u_prev, g, out, norms);
+  ++g_kernel_launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_corners_dw(const DevProblem& d, const PcgState* st, cudaStream_t s) {
+  if (d.nfree == 0) return cudaSuccess;
+  coarse_corners_dw_kernel<<<dim3(grid_for(8 * d.ne, 256, 4096), d.nrhs), 256, 0, s>>>(d, st);
   ++g_kernel_launches;
   return cudaGetLastError();
 }
