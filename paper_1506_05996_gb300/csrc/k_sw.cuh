@@ -267,6 +267,92 @@ __device__ __forceinline__ void schwarz_local_body(const DevProblem& d, const TR
 }
 
 
+// The double-FP32 patch solve as a loop over its six line stages, in place in one shared
+// buffer per element: a stage's lines partition the box, so every thread reads and rewrites
+// only its own line, and a barrier separates the stages. Each contraction appears once in
+// the code (the unrolled form of schwarz_local_body, six copies of the pair arithmetic,
+// stalled on instruction fetch), and the shared memory is half. The arithmetic is the
+// unrolled form's, in the same order.
+//   stage s < 3 contracts axis K, J, I forward; stage s >= 3 the axis of stage 5 - s backward
+//   axis K: line (I = x, J = y), nodes at x + P y + P^2 k
+//   axis J: line (I = x, c = y), nodes at x + P^2 y + P k
+//   axis I: line (b = x, c = y), nodes at P x + P^2 y + k
+template <int P, typename TR, int EPB, bool VAR>
+__device__ __forceinline__ void schwarz_dw_body(const DevProblem& d, const TR* __restrict__ r, dw* __restrict__ wp,
+                                                const PcgState* st) {
+  using T = dw;
+  constexpr int P2 = P * P, P3 = P * P * P;
+  st = st_rhs(st);
+  r += (size_t)blockIdx.y * d.G;                   // right-hand side blockIdx.y of a block solve
+  wp += (size_t)blockIdx.y * d.ne * P3;
+  if (stopped(st)) return;
+  __shared__ T sS[P2], sSv[3 * P2], sb_all[EPB * P3];
+  extern __shared__ __align__(16) unsigned char sw_dyn[];   // the element's diagonal (EPB P^3 pairs)
+  T* sdg_all = reinterpret_cast<T*>(sw_dyn);
+  const int grp = threadIdx.x / P2, tx = threadIdx.x % P2;
+  T* sb = sb_all + grp * P3;
+  const int x = tx % P, y = tx / P;
+  if (threadIdx.x < P2) sS[threadIdx.x] = num_const<T>(d.S[threadIdx.x]);
+  if (VAR)
+    for (int q = threadIdx.x; q < 3 * P2; q += blockDim.x) sSv[q] = num_const<T>(d.Sv[q]);
+  const int ngroups = (d.ne + EPB - 1) / EPB;
+  for (int blk = blockIdx.x; blk < ngroups; blk += gridDim.x) {
+    const int e_raw = blk * EPB + grp;
+    const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
+    const int e = active ? e_raw : d.ne - 1;
+    const int vb = VAR ? d.pvar[e] : 0;
+    const int vx = vb & 3, vy = (vb >> 2) & 3, vz = (vb >> 4) & 3;
+    {   // thread (x, y) copies the P diagonal entries it scales after the third stage
+      const T* dge = d.swddw + (size_t)e * P3 + tx;
+      T* sdg = sdg_all + grp * P3 + tx;
+#pragma unroll
+      for (int a = 0; a < P; ++a)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdg + a * P2)),
+                     "l"(dge + a * P2)
+                     : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    T col[P], out[P];
+    const int* ipe = d.ip + (size_t)e * P3;
+#pragma unroll
+    for (int K = 0; K < P; ++K) {
+      const int g = ipe[x + P * (y + P * K)];
+      T v = (g >= 0 && !d.mask[g]) ? num_load<T>(r[g]) : num_zero<T>();
+      if (g >= 0) v = weighted(d, v, g);
+      col[K] = v;
+    }
+    __syncthreads();   // sS ready (first group); the previous group's last reads of sb done
+#pragma unroll 1
+    for (int stg = 0; stg < 6; ++stg) {
+      const int ax = stg < 3 ? stg : 5 - stg;   // 0: K, 1: J, 2: I
+      const int base = ax == 0 ? x + P * y : (ax == 1 ? x + P2 * y : P * x + P2 * y);
+      const int stride = ax == 0 ? P2 : (ax == 1 ? P : 1);
+      const int v = ax == 0 ? vz : (ax == 1 ? vy : vx);
+      if (stg > 0) {
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < P; ++k) col[k] = sb[base + stride * k];
+      }
+      if (stg < 3) axis_fwd<P, T, VAR>(v, sS, sSv, col, out);
+      else axis_bwd<P, T, VAR>(v, sS, sSv, col, out);
+      if (stg == 2) {   // the eigenvalue scaling (with the patch scale), line (b = x, c = y)
+        asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's own copies
+        const T* sdg = sdg_all + grp * P3 + tx;
+#pragma unroll
+        for (int a = 0; a < P; ++a) out[a] = num_mul(out[a], sdg[a * P2]);
+      }
+      if (stg < 5) {
+#pragma unroll
+        for (int k = 0; k < P; ++k) sb[base + stride * k] = out[k];
+      } else if (active) {
+        T* outp = wp + (size_t)e * P3;
+#pragma unroll
+        for (int k = 0; k < P; ++k) outp[base + stride * k] = out[k];
+      }
+    }
+  }
+}
+
 // The kernels: the binary64 and FP32 instantiations with the compiler's register choice,
 // the double-FP32 one with at most 96 registers a thread (dw_min_blocks).
 template <int P, typename T, typename TR, int EPB, bool VAR>
@@ -277,7 +363,7 @@ __global__ void __launch_bounds__(EPB * P * P) schwarz_local_kernel(const DevPro
 template <int P, typename T, typename TR, int EPB, bool VAR>
 __global__ void __launch_bounds__(EPB * P * P, dw_min_blocks(EPB * P * P))
     schwarz_local_kernel_dw(const DevProblem d, const TR* __restrict__ r, T* __restrict__ wp, const PcgState* st) {
-  schwarz_local_body<P, T, TR, EPB, VAR>(d, r, wp, st);
+  if constexpr (kIsDw<T>) schwarz_dw_body<P, TR, EPB, VAR>(d, r, wp, st);
 }
 
 template <int P, typename T, int EPB>
