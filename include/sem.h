@@ -171,8 +171,8 @@ int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev);
 /* sem_apply_A_f32 - y = A x with FP32 vectors in and out (device pointers, G floats each,
  * caller-owned, x != y): the FP32 element arithmetic of SEM_PREC_FP32 (BF16 factors under
  * SEM_PREC_BF16) with no FP64 vector at all, so no conversions. Masked DOFs return x. For
- * x exactly representable in FP32 the result is, to a few ulps, the FP32 rounding of what
- * sem_apply_A returns in FP32 precision. Needs FP32 factors: SEM_MIXED at create, or recomputed geometry
+ * x exactly representable in FP32 the result agrees with what sem_apply_A returns in FP32
+ * precision to within 4 FP32 ulps of max|y| (the two instantiations may contract differently). Needs FP32 factors: SEM_MIXED at create, or recomputed geometry
  * (SEM_ERR_ARG otherwise). Asynchronous on the handle's stream. */
 int sem_apply_A_f32(sem_t* h, const float* x_dev, float* y_dev);
 

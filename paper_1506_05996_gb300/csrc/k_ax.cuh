@@ -200,6 +200,116 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 }
 
 
+// The double-FP32 operator with its six line contractions as two loops (gradient along i, j,
+// k into A, B, C; divergence of A, B, C back into the sum), each contraction once in the code
+// (the unrolled form of ax_local_kernel stalls on instruction fetch with the pair arithmetic).
+// Same operations in the same order as the unrolled form; stored factors only.
+//   axis i: line (j = tx, k = ty), nodes at p (tx + p ty) + q
+//   axis j: line (i = tx, k = ty), nodes at tx + p^2 ty + p q
+//   axis k: line (i = tx, j = ty), nodes at tx + p ty + p^2 q
+template <int p, typename TX, int EPB, bool DIRECT>
+__global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, const TX* __restrict__ x,
+                                                            double* __restrict__ wl, const PcgState* st,
+                                                            TX* __restrict__ yd) {
+  using T = dw;
+  constexpr int p2 = p * p, p3 = p * p * p;
+  st = st_rhs(st);
+  x += (size_t)blockIdx.y * d.G;                   // right-hand side blockIdx.y of a block solve
+  wl += (size_t)blockIdx.y * d.ne * p3;
+  if (DIRECT) yd += (size_t)blockIdx.y * d.G;
+  if (stopped(st)) return;
+  __shared__ FoldedD<p, T> Fg, Fd;
+  __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
+  const int grp = threadIdx.x / p2, tid = threadIdx.x % p2;
+  const int e_raw = blockIdx.x * EPB + grp;
+  const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
+  const int e = active ? e_raw : d.ne - 1;
+  T* su = su_all + grp * p3;
+  T* const sA = sA_all + grp * p3;
+  T* const sB = sB_all + grp * p3;
+  T* const sC = sC_all + grp * p3;
+  const int tx = tid % p, ty = tid / p;
+  fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
+  fold_fill<p, T>(Fd, d.D, true, threadIdx.x);
+  const int* l2ge = d.l2g + (size_t)e * p3;
+  constexpr int m = p - 2;
+  // axis a's buffer, first node and node stride (selects, not arrays: no local memory)
+  auto buf = [&](int a) { return a == 0 ? sA : (a == 1 ? sB : sC); };
+  auto base = [&](int a) { return a == 0 ? p * (tx + p * ty) : (a == 1 ? tx + p2 * ty : tx + p * ty); };
+  auto stride = [&](int a) { return a == 0 ? 1 : (a == 1 ? p : p2); };
+  const bool inner_xy = DIRECT && tx >= 1 && tx <= p - 2 && ty >= 1 && ty <= p - 2;
+  const int gi0 = e * m * m * m + (tx - 1) + m * (ty - 1);
+  T uk[p], rk[p], line[p], res[p];
+  unsigned masked = 0;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const bool inner = inner_xy && k >= 1 && k <= p - 2;
+    const int g = inner ? gi0 + m * m * (k - 1) : l2ge[l];
+    const bool mk = d.mask[g] != 0;
+    if (DIRECT && mk) masked |= 1u << k;
+    uk[k] = mk ? num_zero<T>() : num_load<T>(x[g]);
+    su[l] = uk[k];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {   // gradient along i, j, k
+    const int b0 = base(a), st0 = stride(a);
+    T* const dst = buf(a);
+#pragma unroll
+    for (int q = 0; q < p; ++q) line[q] = su[b0 + st0 * q];
+    fold_apply<p, T>(Fg, line, res);
+#pragma unroll
+    for (int q = 0; q < p; ++q) dst[b0 + st0 * q] = res[q];
+  }
+  __syncthreads();
+  const bool lam_zero = d.lambda == 0.0;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k)
+    const int l = tx + p * (ty + p * k);
+    const T ur = sA[l], us = sB[l], ut = sC[l];
+    const T* gp = d.geodw + (size_t)e * 7 * p3 + l;
+    T G[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
+    rk[k] = lam_zero ? num_zero<T>() : gp[6 * p3];
+    sA[l] = num_dot3(G[0], ur, G[1], us, G[2], ut);
+    sB[l] = num_dot3(G[1], ur, G[3], us, G[4], ut);
+    sC[l] = num_dot3(G[2], ur, G[4], us, G[5], ut);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) {   // divergence by D^T along i (into su), j (added), k (output)
+    const int b0 = base(a), st0 = stride(a);
+    const T* const src = buf(a);
+#pragma unroll
+    for (int q = 0; q < p; ++q) line[q] = src[b0 + st0 * q];
+    fold_apply<p, T>(Fd, line, res);
+    if (a == 0) {
+#pragma unroll
+      for (int q = 0; q < p; ++q) su[b0 + q] = res[q];
+      __syncthreads();
+    } else if (a == 1) {
+#pragma unroll
+      for (int q = 0; q < p; ++q) su[b0 + p * q] = num_add(su[b0 + p * q], res[q]);
+      __syncthreads();
+    }
+  }
+  if (!active) return;
+  double* out = wl + (size_t)e * p3;
+#pragma unroll
+  for (int k = 0; k < p; ++k) {
+    const int l = tx + p * (ty + p * k);
+    const T v = num_fma(rk[k], uk[k], num_add(su[l], res[k]));   // lambda m u + the divergence terms
+    if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
+      const int g = gi0 + m * m * (k - 1);
+      yd[g] = (masked >> k) & 1u ? x[g] : num_store<TX>(v);
+    } else {
+      out[l] = num_store<double>(v);
+    }
+  }
+}
+
 template <int p, typename T, int EPB>
 constexpr bool ax_tile_supported() {
   return ax_smem_bytes<p, T, EPB>() <= 48 * 1024 && (EPB == 1 || EPB * p * p <= 256);
@@ -238,7 +348,7 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, typename LocalOf<T>:
     constexpr bool kF32 = std::is_same<T, float>::value;
     if constexpr (kIsDw<T>) {   // stored factors as pairs only (recomputed geometry stays FP64)
       if (d.recompute || d.geodw == nullptr) return cudaErrorInvalidValue;
-      ax_local_kernel<p, false, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+      ax_dw_kernel<p, TX, EPB, DIRECT><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (d.recompute) {
       ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (kF32 && d.bf16) {
