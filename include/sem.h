@@ -176,6 +176,13 @@ int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev);
  * (SEM_ERR_ARG otherwise). Asynchronous on the handle's stream. */
 int sem_apply_A_f32(sem_t* h, const float* x_dev, float* y_dev);
 
+/* sem_status - synchronise the handle's stream and report whether a kernel gave up a
+ * bounded wait on one of its barriers since the last check (the bulk copies of the FP32
+ * operator, the MMAs of the tensor-core patch solve): SEM_ERR_CUDA then, with the flag
+ * cleared and that launch's results unspecified; SEM_OK otherwise. Every solve makes the
+ * same check when it finishes; the asynchronous applies leave it to this call. */
+int sem_status(sem_t* h);
+
 /* sem_apply_P / sem_apply_Pf / sem_apply_Pc - z = P r with P = P^c + P^f (Sec. 4),
  * the fine overlapping-patch part P^f alone (Sec. 4.2, Eq. z) or the coarse part
  * P^c alone (Sec. 4.1, Eq. coarse). r is read as 0 on masked nodes and z is 0

@@ -499,8 +499,8 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   CK(h->alloc(&d.partial, (size_t)(4 * d.nblk), A));
   CK(h->alloc(&d.st, 1, A));
   CK(cudaMemsetAsync(d.st, 0, sizeof(sem::PcgState), h->stream));
-  CK(h->alloc(&d.tc_err, 1, A));
-  CK(cudaMemsetAsync(d.tc_err, 0, sizeof(int), h->stream));
+  CK(h->alloc(&d.wait_err, 1, A));
+  CK(cudaMemsetAsync(d.wait_err, 0, sizeof(int), h->stream));
   CK(h->alloc(&h->r, (size_t)nb.G, A));
   CK(h->alloc(&h->z, (size_t)nb.G, A));
   CK(h->alloc(&h->p, (size_t)nb.G, A));
@@ -644,6 +644,24 @@ int sem_set_mask(sem_t* h, const uint8_t* mask_dev) {
   CK(cudaMemcpyAsync(h->mask, h->mask_host.data(), h->nb.G, cudaMemcpyHostToDevice, h->stream));
   if (int rc = update_free_sides(h)) return rc;
   return build_coarse(h);
+}
+
+// SEM_ERR_CUDA (and the flag cleared) when a kernel's bounded wait on a barrier ran out since
+// the last check; the caller has synchronised the handle's stream.
+static int take_wait_error(sem_t* h) {
+  int err = 0;
+  CK(cudaMemcpy(&err, h->d.wait_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CK(cudaMemset(h->d.wait_err, 0, sizeof(int)));
+    return fail(SEM_ERR_CUDA, "a kernel gave up a bounded wait on a barrier (tensor-core MMAs or bulk copies)");
+  }
+  return SEM_OK;
+}
+
+int sem_status(sem_t* h) {
+  if (int rc = check_handle(h)) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  return take_wait_error(h);
 }
 
 int sem_apply_A(sem_t* h, const double* x_dev, double* y_dev) {
@@ -963,14 +981,7 @@ int solve_finish(sem_t* h, SolveCtx& c, int* iters_host, double* res_hist_host, 
     CK(cudaStreamSynchronize(s));
   }
   if (true_rel_res_host) *true_rel_res_host = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
-  if (d.tc) {
-    int tc_err = 0;
-    CK(cudaMemcpy(&tc_err, d.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tc_err) {
-      CK(cudaMemset(d.tc_err, 0, sizeof(int)));
-      return fail(SEM_ERR_CUDA, "tensor-core patch solve: a bounded wait for the MMAs ran out");
-    }
-  }
+  if (int rc = take_wait_error(h)) return rc;
   if (st.status == -4) return fail(SEM_ERR_CUDA, "a kernel of the solve gave up a bounded wait");
   if (st.status == -6) return fail(SEM_ERR_NAN, "NaN/Inf or non-positive curvature in PCG");
   if (!st.done) return fail(SEM_MAXIT, "maxit reached");

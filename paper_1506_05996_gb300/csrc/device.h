@@ -92,7 +92,7 @@ struct DevProblem {
   int epb_ax32 = 1, epb_sw32 = 1;   // the same for the FP32 kernels (tuned separately)
   int epb_axdw = 1, epb_swdw = 1;   // and for the double-FP32 kernels of SEM_PREC_FP64
   bool tc = false;                  // the FP32 paths' patch solves in BF16 on the tensor cores
-  int* tc_err = nullptr;            // set by the tensor-core kernel when a bounded wait ran out
+  int* wait_err = nullptr;          // set by a kernel whose bounded wait on a barrier ran out
   bool dwk = false;                 // SEM_PREC_FP64's element kernels in double-FP32 (kdw.cuh)
                                     // instead of binary64 (SEM_PREC_FP64_NATIVE)
                                     // (tile shapes picked by the autotuner; 1, 2, 4 or 8)

@@ -70,9 +70,22 @@ __device__ __forceinline__ void fold_apply(const FoldedD<p, T>& F, const T (&v)[
 // k = 0..p-1, for the pointwise work, and one line per direction for the contractions:
 // the gradient by D along i (line j=x, k=y), j (i=x, k=y) and k (i=x, j=y), A/B/C by the
 // geometric factors, the divergence by D^T along the same lines, plus lambda m u.
+// Shared-memory slab of one element: node (i, j, k) at i + RS j + PS k. A warp's 32 threads
+// (x = 0..7, y = 0..3 at p = 8) read the rows along i at (q, x, y), along j at (x, q, y) and
+// along k at (x, y, q). With the plain strides (8, 64) the rows along i start 32 bytes apart
+// and fall into 4 bank groups (8-way conflicts for 4-byte words, 16-way for 8-byte ones), the
+// rows along j into 8 (4-way); a row stride of 9 (PS = 72) makes i and j conflict-free for
+// 4-byte words and 2 ways for 8-byte ones (the minimum), at 2 (4-byte) or 3 (8-byte) ways
+// along k. Other orders keep the plain layout.
+template <int p>
+struct Slab {
+  static constexpr int RS = (p == 8) ? p + 1 : p, PS = RS * p, N = PS * p;
+  static __device__ __forceinline__ int at(int i, int j, int k) { return i + RS * j + PS * k; }
+};
+
 template <int p, typename T, int EPB>
 constexpr int ax_smem_bytes() {
-  return (int)(2 * sizeof(FoldedD<p, T>) + EPB * (4 * p * p * p + 24) * sizeof(T));
+  return (int)(2 * sizeof(FoldedD<p, T>) + EPB * (4 * Slab<p>::N + 24) * sizeof(T));
 }
 
 // DIRECT (operator application y = A x with the interior-first numbering, d.Gi > 0): an
@@ -95,16 +108,17 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
   }
   if (stopped(st)) return;
   __shared__ FoldedD<p, T> Fg, Fd;
-  __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
+  using SL = Slab<p>;
+  __shared__ T su_all[EPB * SL::N], sA_all[EPB * SL::N], sB_all[EPB * SL::N], sC_all[EPB * SL::N];
   __shared__ T sx_all[EPB * 24];
   const int grp = threadIdx.x / p2, tid = threadIdx.x % p2;
   const int e_raw = blockIdx.x * EPB + grp;
   const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
   const int e = active ? e_raw : d.ne - 1;
-  T* su = su_all + grp * p3;
-  T* sA = sA_all + grp * p3;
-  T* sB = sB_all + grp * p3;
-  T* sC = sC_all + grp * p3;
+  T* su = su_all + grp * SL::N;
+  T* sA = sA_all + grp * SL::N;
+  T* sB = sB_all + grp * SL::N;
+  T* sC = sC_all + grp * SL::N;
   T* sx = sx_all + grp * 24;
   const int tx = tid % p, ty = tid / p;
   fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
@@ -126,30 +140,31 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
     const bool mk = d.mask[g] != 0;
     if (DIRECT && mk) masked |= 1u << k;
     uk[k] = mk ? num_zero<T>() : num_load<T>(x[g]);
-    su[l] = uk[k];
+    su[SL::at(tx, ty, k)] = uk[k];
   }
   __syncthreads();
   // gradient: d/dxi on line (j=tx, k=ty), d/deta on line (i=tx, k=ty), d/dzeta on (i=tx, j=ty)
 #pragma unroll
-  for (int i = 0; i < p; ++i) line[i] = su[i + p * (tx + p * ty)];
+  for (int i = 0; i < p; ++i) line[i] = su[SL::at(i, tx, ty)];
   fold_apply<p, T>(Fg, line, res);
 #pragma unroll
-  for (int i = 0; i < p; ++i) sA[i + p * (tx + p * ty)] = res[i];
+  for (int i = 0; i < p; ++i) sA[SL::at(i, tx, ty)] = res[i];
 #pragma unroll
-  for (int j = 0; j < p; ++j) line[j] = su[tx + p * (j + p * ty)];
+  for (int j = 0; j < p; ++j) line[j] = su[SL::at(tx, j, ty)];
   fold_apply<p, T>(Fg, line, res);
 #pragma unroll
-  for (int j = 0; j < p; ++j) sB[tx + p * (j + p * ty)] = res[j];
+  for (int j = 0; j < p; ++j) sB[SL::at(tx, j, ty)] = res[j];
   fold_apply<p, T>(Fg, uk, res);
 #pragma unroll
-  for (int k = 0; k < p; ++k) sC[tx + p * (ty + p * k)] = res[k];
+  for (int k = 0; k < p; ++k) sC[SL::at(tx, ty, k)] = res[k];
   __syncthreads();
   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k); lambda m u kept in registers
   const bool lam_zero = d.lambda == 0.0;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T ur = sA[l], us = sB[l], ut = sC[l];
+    const int ls = SL::at(tx, ty, k);
+    const T ur = sA[ls], us = sB[ls], ut = sC[ls];
     T G[6], lm;   // lm: the c-term factor lambda m (stored as such; 0 skips the load)
     if constexpr (!RECOMP) {
       const TG* gp = geo_of<TG>(d) + (size_t)e * 7 * p3 + l;
@@ -161,35 +176,35 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
       geom_point<T>(sx, (T)d.tg[tx], (T)d.tg[ty], (T)d.tg[k], (T)(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm, det);
       lm = (T)d.lambda * mm;
     }
-    sA[l] = num_dot3(G[0], ur, G[1], us, G[2], ut);
-    sB[l] = num_dot3(G[1], ur, G[3], us, G[4], ut);
-    sC[l] = num_dot3(G[2], ur, G[4], us, G[5], ut);
+    sA[ls] = num_dot3(G[0], ur, G[1], us, G[2], ut);
+    sB[ls] = num_dot3(G[1], ur, G[3], us, G[4], ut);
+    sC[ls] = num_dot3(G[2], ur, G[4], us, G[5], ut);
     rk[k] = lm;
   }
   __syncthreads();
   // divergence by D^T: the A lines (j=tx, k=ty) into su, then the B lines (i=tx, k=ty)
   // added into su, then the C line (i=tx, j=ty) and su added in registers
 #pragma unroll
-  for (int i = 0; i < p; ++i) line[i] = sA[i + p * (tx + p * ty)];
+  for (int i = 0; i < p; ++i) line[i] = sA[SL::at(i, tx, ty)];
   fold_apply<p, T>(Fd, line, res);
 #pragma unroll
-  for (int i = 0; i < p; ++i) su[i + p * (tx + p * ty)] = res[i];
+  for (int i = 0; i < p; ++i) su[SL::at(i, tx, ty)] = res[i];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < p; ++j) line[j] = sB[tx + p * (j + p * ty)];
+  for (int j = 0; j < p; ++j) line[j] = sB[SL::at(tx, j, ty)];
   fold_apply<p, T>(Fd, line, res);
 #pragma unroll
-  for (int j = 0; j < p; ++j) su[tx + p * (j + p * ty)] = num_add(su[tx + p * (j + p * ty)], res[j]);
+  for (int j = 0; j < p; ++j) su[SL::at(tx, j, ty)] = num_add(su[SL::at(tx, j, ty)], res[j]);
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < p; ++k) line[k] = sC[tx + p * (ty + p * k)];
+  for (int k = 0; k < p; ++k) line[k] = sC[SL::at(tx, ty, k)];
   fold_apply<p, T>(Fd, line, res);
   if (!active) return;
   TW* out = wl + (size_t)e * p3;
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T v = num_fma(rk[k], uk[k], num_add(su[l], res[k]));   // lambda m u + the divergence terms
+    const T v = num_fma(rk[k], uk[k], num_add(su[SL::at(tx, ty, k)], res[k]));   // lambda m u + the divergence terms
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
       yd[g] = (masked >> k) & 1u ? x[g] : num_store<TX>(v);   // y in x's type
@@ -204,9 +219,9 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 // k into A, B, C; divergence of A, B, C back into the sum), each contraction once in the code
 // (the unrolled form of ax_local_kernel stalls on instruction fetch with the pair arithmetic).
 // Same operations in the same order as the unrolled form; stored factors only.
-//   axis i: line (j = tx, k = ty), nodes at p (tx + p ty) + q
-//   axis j: line (i = tx, k = ty), nodes at tx + p^2 ty + p q
-//   axis k: line (i = tx, j = ty), nodes at tx + p ty + p^2 q
+//   axis i: line (j = tx, k = ty), nodes (q, tx, ty) of the slab
+//   axis j: line (i = tx, k = ty), nodes (tx, q, ty)
+//   axis k: line (i = tx, j = ty), nodes (tx, ty, q)
 template <int p, typename TX, int EPB, bool DIRECT>
 __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, const TX* __restrict__ x,
                                                             double* __restrict__ wl, const PcgState* st,
@@ -219,15 +234,16 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   if (DIRECT) yd += (size_t)blockIdx.y * d.G;
   if (stopped(st)) return;
   __shared__ FoldedD<p, T> Fg, Fd;
-  __shared__ T su_all[EPB * p3], sA_all[EPB * p3], sB_all[EPB * p3], sC_all[EPB * p3];
+  using SL = Slab<p>;
+  __shared__ T su_all[EPB * SL::N], sA_all[EPB * SL::N], sB_all[EPB * SL::N], sC_all[EPB * SL::N];
   const int grp = threadIdx.x / p2, tid = threadIdx.x % p2;
   const int e_raw = blockIdx.x * EPB + grp;
   const bool active = e_raw < d.ne;            // a short last CTA recomputes its last element
   const int e = active ? e_raw : d.ne - 1;
-  T* su = su_all + grp * p3;
-  T* const sA = sA_all + grp * p3;
-  T* const sB = sB_all + grp * p3;
-  T* const sC = sC_all + grp * p3;
+  T* su = su_all + grp * SL::N;
+  T* const sA = sA_all + grp * SL::N;
+  T* const sB = sB_all + grp * SL::N;
+  T* const sC = sC_all + grp * SL::N;
   const int tx = tid % p, ty = tid / p;
   fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
   fold_fill<p, T>(Fd, d.D, true, threadIdx.x);
@@ -235,8 +251,10 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   constexpr int m = p - 2;
   // axis a's buffer, first node and node stride (selects, not arrays: no local memory)
   auto buf = [&](int a) { return a == 0 ? sA : (a == 1 ? sB : sC); };
-  auto base = [&](int a) { return a == 0 ? p * (tx + p * ty) : (a == 1 ? tx + p2 * ty : tx + p * ty); };
-  auto stride = [&](int a) { return a == 0 ? 1 : (a == 1 ? p : p2); };
+  auto base = [&](int a) {
+    return a == 0 ? SL::at(0, tx, ty) : (a == 1 ? SL::at(tx, 0, ty) : SL::at(tx, ty, 0));
+  };
+  auto stride = [&](int a) { return a == 0 ? 1 : (a == 1 ? SL::RS : SL::PS); };
   const bool inner_xy = DIRECT && tx >= 1 && tx <= p - 2 && ty >= 1 && ty <= p - 2;
   const int gi0 = e * m * m * m + (tx - 1) + m * (ty - 1);
   T uk[p], rk[p], line[p], res[p];
@@ -249,7 +267,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
     const bool mk = d.mask[g] != 0;
     if (DIRECT && mk) masked |= 1u << k;
     uk[k] = mk ? num_zero<T>() : num_load<T>(x[g]);
-    su[l] = uk[k];
+    su[SL::at(tx, ty, k)] = uk[k];
   }
   __syncthreads();
 #pragma unroll 1
@@ -267,15 +285,16 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
 #pragma unroll
   for (int k = 0; k < p; ++k) {   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k)
     const int l = tx + p * (ty + p * k);
-    const T ur = sA[l], us = sB[l], ut = sC[l];
+    const int ls = SL::at(tx, ty, k);
+    const T ur = sA[ls], us = sB[ls], ut = sC[ls];
     const T* gp = d.geodw + (size_t)e * 7 * p3 + l;
     T G[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) G[c] = gp[c * p3];
     rk[k] = lam_zero ? num_zero<T>() : gp[6 * p3];
-    sA[l] = num_dot3(G[0], ur, G[1], us, G[2], ut);
-    sB[l] = num_dot3(G[1], ur, G[3], us, G[4], ut);
-    sC[l] = num_dot3(G[2], ur, G[4], us, G[5], ut);
+    sA[ls] = num_dot3(G[0], ur, G[1], us, G[2], ut);
+    sB[ls] = num_dot3(G[1], ur, G[3], us, G[4], ut);
+    sC[ls] = num_dot3(G[2], ur, G[4], us, G[5], ut);
   }
   __syncthreads();
 #pragma unroll 1
@@ -291,7 +310,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
       __syncthreads();
     } else if (a == 1) {
 #pragma unroll
-      for (int q = 0; q < p; ++q) su[b0 + p * q] = num_add(su[b0 + p * q], res[q]);
+      for (int q = 0; q < p; ++q) su[b0 + SL::RS * q] = num_add(su[b0 + SL::RS * q], res[q]);
       __syncthreads();
     }
   }
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T v = num_fma(rk[k], uk[k], num_add(su[l], res[k]));   // lambda m u + the divergence terms
+    const T v = num_fma(rk[k], uk[k], num_add(su[SL::at(tx, ty, k)], res[k]));   // lambda m u + the divergence terms
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
       yd[g] = (masked >> k) & 1u ? x[g] : num_store<TX>(v);

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads) schwarz_tc_kernel(const DevProblem
       sw->status = -4;
       sw->done = 1;
     }
-    if (tid == 0 && d.tc_err != nullptr) atomicExch(d.tc_err, 1);
+    if (tid == 0 && d.wait_err != nullptr) atomicExch(d.wait_err, 1);
     tc_wait(mbar_a, phase);
   }
   tc_fence_before();

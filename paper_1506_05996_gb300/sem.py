@@ -48,6 +48,7 @@ _SIGS = {
     "sem_coarse_levels": ([_vp, _int, _vp, _P(_int)], _int),
     "sem_apply_A": ([_vp, _vp, _vp], _int),
     "sem_apply_A_f32": ([_vp, _vp, _vp], _int),
+    "sem_status": ([_vp], _int),
     "sem_apply_P": ([_vp, _vp, _vp], _int),
     "sem_apply_Pf": ([_vp, _vp, _vp], _int),
     "sem_apply_Pc": ([_vp, _vp, _vp], _int),
@@ -187,6 +188,11 @@ def sem_apply_A_f32(h, x, y):
     """y = A x with FP32 CUDA tensors in and out (FP32 element arithmetic, no conversions)."""
     n = sem_num_dofs(h)
     return _check(_lib.sem_apply_A_f32(h, _dev(x, torch.float32, n), _dev(y, torch.float32, n)))
+
+
+def sem_status(h):
+    """Synchronise the handle's stream; raises if a kernel gave up a bounded barrier wait."""
+    return _check(_lib.sem_status(h))
 
 
 def sem_apply_A(h, x, y):
