@@ -165,7 +165,7 @@ int build_coarse(sem_t* h) {
   CK(h->alloc(&d.cres, nfree * kc, h->coarse_allocs));
   CK(h->alloc(&d.Rc, nfree * kc, h->coarse_allocs));
   CK(h->alloc(&d.Zc, nfree * kc, h->coarse_allocs));
-  CK(h->alloc(&d.Zc32, nfree * kc, h->coarse_allocs));
+  CK(h->alloc(&d.Zce32, (size_t)8 * h->nb.ne * kc, h->coarse_allocs));
   CK(h->alloc(&d.Zce, (size_t)8 * h->nb.ne * kc, h->coarse_allocs));
   d.nlevels = (int)h->levels.size();
   d.levels = h->levels.data();
@@ -468,8 +468,12 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
   UP(hbox, hbox, double);
   UP(Btab, Btab, double);
   {
-    std::vector<float> Bt32(Btab.begin(), Btab.end());
-    UP(Btab32, Bt32, float);
+    std::vector<float> phi32(2 * p);
+    for (int i = 0; i < p; ++i) {
+      phi32[2 * i] = (float)(0.5 * (1.0 - t[i]));
+      phi32[2 * i + 1] = (float)(0.5 * (1.0 + t[i]));
+    }
+    UP(phi32, phi32, float);
     std::vector<sem::dw> Btdw(Btab.size());
     for (size_t q = 0; q < Btab.size(); ++q) Btdw[q] = sem::dw_split_host(Btab[q]);
     UP(Btabdw, Btdw, sem::dw);

@@ -128,7 +128,7 @@ struct DevProblem {
   const float* swd32 = nullptr;
   const dw* swddw = nullptr;        // the same as pairs of FP32
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
-  const float* Btab32 = nullptr;    // the same in FP32
+  const float* phi32 = nullptr;     // [p][2] (1 - t_i)/2 and (1 + t_i)/2 in FP32 (the 1D factors of Btab)
   const dw* Btabdw = nullptr;       // the same as pairs of FP32
   const dw* phidw = nullptr;        // [p][2] (1 - t_i)/2 and (1 + t_i)/2 as pairs (the 1D factors of Btab)
   dw* Zce = nullptr;                // [ne][8] coarse correction at each element's corners as pairs (0 where
@@ -151,7 +151,8 @@ struct DevProblem {
   double* Re = nullptr;             // ne*8 element coarse residuals
   double* Rc = nullptr;             // nfree coarse residual
   double* Zc = nullptr;             // nfree coarse correction
-  float* Zc32 = nullptr;            // its FP32 copy (mixed path)
+  float* Zce32 = nullptr;           // [ne][8] the coarse correction at each element's corners in FP32
+                                    // (0 where the vertex is not free), for the mixed path's P-sum
   float* p32 = nullptr;             // FP32 copies of the PCG direction and residual (mixed path)
   float* r32 = nullptr;
   double* nncorr = nullptr;         // learned correction N(s) (flexible PCG)
@@ -263,9 +264,6 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
                             const double* g, double* out, double* norms, cudaStream_t s);
 // dst[i] = (fl32(src[i]), fl32(src[i] - fl32(src[i]))) for the double-FP32 kernels' tables
 cudaError_t launch_split_pairs(long long n, const double* src, dw* dst, cudaStream_t s);
-// Zce[e][c] = split(Zc[ecv[e][c]]) (0 where the corner is not a free vertex): the coarse
-// correction at element corners for the double-FP32 P-sum
-cudaError_t launch_coarse_corners_dw(const DevProblem& d, const PcgState* st, cudaStream_t s);
 // b = mask ? 0 : mN * s (lumped GLL load)
 cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s);
 // y = a + b

@@ -195,6 +195,28 @@ __device__ __forceinline__ int interior_local(const DevProblem& d, int g) {
   return e * p * p * p + (a + 1) + p * ((b + 1) + p * (c + 1));
 }
 
+// Sum over the CSR entries q0..q1-1 of val[idx[q]], in ascending q, from 0 (the order of a
+// plain loop, so the same bits), with the first 8 index loads and then the first 8 value
+// loads issued together: the copies of a DOF cost two dependent memory latencies, not two
+// per copy. TS: the type of the sum (the values are converted to it).
+template <typename TS, typename TV>
+__device__ __forceinline__ TS csr_sum(const int* __restrict__ idx, const TV* __restrict__ val, int q0, int q1) {
+  constexpr int U = 8;
+  int ix[U];
+#pragma unroll
+  for (int c = 0; c < U; ++c) ix[c] = (q0 + c < q1) ? idx[q0 + c] : 0;
+  TV v[U];
+#pragma unroll
+  for (int c = 0; c < U; ++c)
+    if (q0 + c < q1) v[c] = val[ix[c]];
+  TS s = 0;
+#pragma unroll
+  for (int c = 0; c < U; ++c)
+    if (q0 + c < q1) s += (TS)v[c];
+  for (int q = q0 + U; q < q1; ++q) s += (TS)val[idx[q]];
+  return s;
+}
+
 // Sum of the local copies of DOF g in wl (Eq. gather): one copy at a computed index for an
 // interior DOF, the g2l CSR in ascending local order otherwise.
 template <typename T>
@@ -203,6 +225,14 @@ __device__ __forceinline__ T gather_dof(const DevProblem& d, const T* __restrict
   T s = 0;
   for (int q = d.g2l_off[g]; q < d.g2l_off[g + 1]; ++q) s += wl[d.g2l_idx[q]];
   return s;
+}
+
+// The same sum with the copies' loads issued together (csr_sum): faster in the gather pass
+// of y = A x, where almost every DOF has several copies; the same bits.
+template <typename T>
+__device__ __forceinline__ T gather_dof_ilp(const DevProblem& d, const T* __restrict__ wl, int g) {
+  if (g < d.Gi) return wl[interior_local(d, g)];
+  return csr_sum<T, T>(d.g2l_idx, wl, d.g2l_off[g], d.g2l_off[g + 1]);
 }
 
 

@@ -66,9 +66,7 @@ __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__
                                        const TY* __restrict__ xin, TY* __restrict__ y, int g0) {
   for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
     if (d.mask[g]) { y[g] = xin[g]; continue; }
-    T s = 0;
-    s = gather_dof(d, wl, g);
-    y[g] = (TY)s;
+    y[g] = (TY)gather_dof_ilp(d, wl, g);
   }
 }
 
@@ -163,6 +161,17 @@ __global__ void amg_jacobi0_kernel(int n, const double* __restrict__ dinv, const
 
 constexpr int kRowBlock = 256;   // block size of every row-group kernel
 
+// Programmatic dependent launch of the coarse solve's kernel chain: a kernel launched with
+// programmatic stream serialisation may be scheduled while its predecessor on the stream
+// drains. Each kernel of the chain waits here, before reading anything, until that
+// predecessor has completed and its writes are visible, and at once lets its own successor
+// start launching (the successor waits in turn), so the chain pays no launch gap per kernel.
+// Without the launch attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // First row of this thread's group in the first step, the step (a warp covers 32 / LANES
 // rows), and the thread's lane and group within the warp.
 template <int LANES>
@@ -211,6 +220,7 @@ template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_resid_kernel(DevCsr A, const double* __restrict__ b,
                                                              const double* __restrict__ x, double* __restrict__ t,
                                                              const PcgState* st) {
+  pdl_enter();
   st = st_rhs(st);
   if (stopped(st)) return;
   const size_t o = (size_t)blockIdx.y * A.n;   // right-hand side blockIdx.y (square matrix)
@@ -229,6 +239,7 @@ __global__ void __launch_bounds__(kRowBlock) amg_resid_kernel(DevCsr A, const do
 template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_spmv_kernel(DevCsr A, const double* __restrict__ x,
                                                             double* __restrict__ y, const PcgState* st, int sx) {
+  pdl_enter();
   st = st_rhs(st);
   if (stopped(st)) return;
   x += (size_t)blockIdx.y * sx;                // right-hand side blockIdx.y: x has sx entries
@@ -277,6 +288,7 @@ template <int LANES>
 __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, const double* __restrict__ b,
                                                           const double* __restrict__ xc, const double* z, double* out,
                                                           const PcgState* st, int sxc) {
+  pdl_enter();
   st = st_rhs(st);
   if (stopped(st)) return;
   const size_t o = (size_t)blockIdx.y * N.n;   // right-hand side blockIdx.y; xc has sxc entries
@@ -297,6 +309,7 @@ __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, c
 __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double* __restrict__ Ainv,
                                                             const double* __restrict__ b, double* __restrict__ x,
                                                             const PcgState* st) {
+  pdl_enter();
   st = st_rhs(st);
   if (stopped(st)) return;
   b += (size_t)blockIdx.y * n;
@@ -388,19 +401,16 @@ __global__ void kc_combine_kernel(int n, const double* __restrict__ c1, const do
 }
 
 // ------------------------------------------------------------ P sum and PCG
-template <typename T> __device__ __forceinline__ const T* btab_of(const DevProblem& d);
-template <> __device__ __forceinline__ const double* btab_of<double>(const DevProblem& d) { return d.Btab; }
-template <> __device__ __forceinline__ const float* btab_of<float>(const DevProblem& d) { return d.Btab32; }
-template <typename T> __device__ __forceinline__ const T* zc_of(const DevProblem& d);
-template <> __device__ __forceinline__ const double* zc_of<double>(const DevProblem& d) { return d.Zc; }
-template <> __device__ __forceinline__ const float* zc_of<float>(const DevProblem& d) { return d.Zc32; }
 template <typename T> __device__ __forceinline__ const T* wts_of(const DevProblem& d);
 template <> __device__ __forceinline__ const double* wts_of<double>(const DevProblem& d) { return d.pw; }
 template <> __device__ __forceinline__ const float* wts_of<float>(const DevProblem& d) { return d.pw32; }
 
 // z = P r on the free nodes: the patch results summed over every patch containing the
 // node (fine part) plus the trilinear interpolation of the coarse correction at the node
-// (coarse part, Eq. coarse), accumulated in T; with PCG also z.r and beta (FP64).
+// (coarse part, Eq. coarse), accumulated in T; with PCG also z.r and beta (FP64). In FP32 the
+// interpolation reads the element's 8 corner values (one contiguous 32-byte read, gathered
+// once per corner by the coarse solve's last kernel) and is sum-factorised along i, j, k; in
+// binary64 it is the 8-term sum over the corners' coarse DOFs.
 template <bool PCG, typename T>
 __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int mode, const T* __restrict__ wp,
                                                          const double* __restrict__ r, double* __restrict__ z) {
@@ -411,8 +421,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   r += (size_t)blockIdx.y * d.G;
   z += (size_t)blockIdx.y * d.G;
   double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
-  const T* __restrict__ Bt = btab_of<T>(d);
-  const T* __restrict__ Zc = zc_of<T>(d) + (size_t)blockIdx.y * d.nfree;
+  const double* __restrict__ Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
   const T* __restrict__ Wt = wts_of<T>(d);
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
@@ -427,15 +436,28 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
       }
       if ((mode & PSUM_COARSE) && d.nfree > 0) {
         const int l = d.owner[g], e = l / p3, lr = l % p3;
-        const int* ec = d.ecv + (size_t)e * 8;
-        const T* B = Bt + 8 * lr;
-        T zc = 0;
+        if constexpr (std::is_same<T, float>::value) {
+          // corner values in VTK order at the owner node (i, j, k): along i, then j, then k
+          const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
+          const float4* Z4 = reinterpret_cast<const float4*>(d.Zce32 + ((size_t)blockIdx.y * d.ne + e) * 8);
+          const float4 za = Z4[0], zb = Z4[1];
+          const float a0 = d.phi32[2 * i], a1 = d.phi32[2 * i + 1];
+          const float b0 = d.phi32[2 * j], b1 = d.phi32[2 * j + 1];
+          const float c0 = d.phi32[2 * k], c1 = d.phi32[2 * k + 1];
+          const float z00 = a0 * za.x + a1 * za.y, z10 = a0 * za.w + a1 * za.z;
+          const float z01 = a0 * zb.x + a1 * zb.y, z11 = a0 * zb.w + a1 * zb.z;
+          v += c0 * (b0 * z00 + b1 * z10) + c1 * (b0 * z01 + b1 * z11);
+        } else {
+          const int* ec = d.ecv + (size_t)e * 8;
+          const double* B = d.Btab + 8 * lr;
+          T zc = 0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int cv = ec[c];
-          if (cv >= 0) zc += B[c] * Zc[cv];
+          for (int c = 0; c < 8; ++c) {
+            const int cv = ec[c];
+            if (cv >= 0) zc += B[c] * Zc[cv];
+          }
+          v += zc;
         }
-        v += zc;
       }
     }
     const double vd = (double)v;
@@ -453,9 +475,21 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   }
 }
 
+// The coarse correction at the corners of every element in FP32 (the mixed path's P-sum),
+// rounded to nearest by the integer routine (the FP64 converter runs on the FP64 pipe).
+__global__ void coarse_corners_f32_kernel(const DevProblem d, const PcgState* st) {
+  pdl_enter();
+  if (stopped(st)) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 8 * d.ne; q += gridDim.x * blockDim.x) {
+    const int cv = d.ecv[q];
+    d.Zce32[q] = cv >= 0 ? f64_to_f32(d.Zc[cv]) : 0.0f;
+  }
+}
+
 // The coarse correction at the corners of every element, as pairs: one gather per corner
 // instead of one per node of the P-sum (which then reads 8 contiguous pairs per node).
 __global__ void coarse_corners_dw_kernel(const DevProblem d, const PcgState* st) {
+  pdl_enter();
   st = st_rhs(st);
   if (stopped(st)) return;
   const double* Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
@@ -487,8 +521,21 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
     if (!d.mask[g]) {
       if (mode & PSUM_IDENT) v = dw_split(r[g]);
       if (mode & PSUM_FINE) {
+        // the patch results in ascending patch-entry order, the first 8 loads issued together
+        const int q0 = d.pg_off[g], q1 = d.pg_off[g + 1];
+        constexpr int U = 8;
+        int ix[U];
+#pragma unroll
+        for (int c = 0; c < U; ++c) ix[c] = (q0 + c < q1) ? d.pg_idx[q0 + c] : 0;
+        dw pv[U];
+#pragma unroll
+        for (int c = 0; c < U; ++c)
+          if (q0 + c < q1) pv[c] = wp[ix[c]];
         dw vf = dw_zero();
-        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) vf = dw_add(vf, wp[d.pg_idx[q]]);
+#pragma unroll
+        for (int c = 0; c < U; ++c)
+          if (q0 + c < q1) vf = dw_add(vf, pv[c]);
+        for (int q = q0 + U; q < q1; ++q) vf = dw_add(vf, wp[d.pg_idx[q]]);
         if (d.pw != nullptr) vf = dw_mul(vf, dw_split(d.pw[g]));   // overlap-weighted P^f
         v = dw_add(v, vf);
       }
@@ -523,10 +570,6 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
   }
 }
 
-__global__ void to_f32_kernel(int n, const double* __restrict__ a, float* __restrict__ b, const PcgState* st) {
-  if (stopped(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = f64_to_f32(a[i]);
-}
 
 __global__ void __launch_bounds__(kVecBlock) pcg_init_kernel(const DevProblem d, const double* __restrict__ b,
                                                              double* __restrict__ r, double* __restrict__ u,
@@ -883,30 +926,61 @@ inline int grid_for(int n, int block, int cap) {
 constexpr double kOmega = 2.0 / 3.0;
 constexpr int kCycles = 3;
 
+// One launch of the coarse solve's kernel chain; pdl: with programmatic stream serialisation
+// (every kernel of the chain but its first, whose predecessor may be on another stream).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chain(void (*kernel)(KArgs...), dim3 grid, int block, cudaStream_t s, bool pdl, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  ++g_kernel_launches;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// ROWS_LAUNCH as a link of the chain (sets err; the next link is programmatic)
+#define ROWS_CHAIN(KERN, M, ...)                                                                                \
+  do {                                                                                                        \
+    const int rows_ = (M).n;                                                                                  \
+    switch ((M).lanes) {                                                                                      \
+      case 4: err = launch_chain(KERN<4>, dim3(grid_for(rows_, kRowBlock / 4, 8192), d.nrhs), kRowBlock, s, pdl, __VA_ARGS__); break;   \
+      case 8: err = launch_chain(KERN<8>, dim3(grid_for(rows_, kRowBlock / 8, 8192), d.nrhs), kRowBlock, s, pdl, __VA_ARGS__); break;   \
+      case 16: err = launch_chain(KERN<16>, dim3(grid_for(rows_, kRowBlock / 16, 8192), d.nrhs), kRowBlock, s, pdl, __VA_ARGS__); break; \
+      default: err = launch_chain(KERN<32>, dim3(grid_for(rows_, kRowBlock / 32, 8192), d.nrhs), kRowBlock, s, pdl, __VA_ARGS__); break; \
+    }                                                                                                         \
+    pdl = true;                                                                                               \
+  } while (0)
+
 // V(1,1) cycle at `level` as down and up passes (smoothed kind): b_c = M b, the next level
 // (or the dense inverse), then out = z + N b + Q x_c (z null: out = V b). Two kernels per
 // level instead of the cycle's five steps (pre-smoothing from zero, residual, restriction,
 // prolongation, post-smoothing); the same linear map up to rounding.
 cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double* out, const double* z,
-                         const PcgState* st, cudaStream_t s) {
+                         const PcgState* st, cudaStream_t s, bool& pdl) {
+  cudaError_t err;
   if (level == d.nlevels) {
-    dense_mv_kernel<<<dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b,
-                                                                                       out, st);
-    ++g_kernel_launches;
-    return cudaGetLastError();
+    err = launch_chain(dense_mv_kernel, dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, s, pdl,
+                       d.coarsest_n, d.coarsest_inv, b, out, st);
+    pdl = true;
+    return err;
   }
   const DevAmgLevel& L = d.levels[level];
   double* bc = (level + 1 == d.nlevels) ? d.cb : d.levels[level + 1].b;
   double* xc = (level + 1 == d.nlevels) ? d.cx : d.levels[level + 1].y;
-  ROWS_LAUNCH(amg_spmv_kernel, L.M, L.M, b, bc, st, L.A.n);
-  ++g_kernel_launches;
-  cudaError_t err = vcycle_fused(d, level + 1, bc, xc, nullptr, st, s);
+  ROWS_CHAIN(amg_spmv_kernel, L.M, L.M, b, bc, st, L.A.n);
+  if (err != cudaSuccess) return err;
+  err = vcycle_fused(d, level + 1, bc, xc, nullptr, st, s, pdl);
   if (err != cudaSuccess) return err;
   const struct { int n, lanes; } up{L.N.n, L.up_lanes};   // N's rows, the level's lane count
   const int nc = (level + 1 == d.nlevels) ? d.coarsest_n : d.levels[level + 1].A.n;
-  ROWS_LAUNCH(amg_up_kernel, up, L.N, L.Q, b, xc, z, out, st, nc);
-  ++g_kernel_launches;
-  return cudaGetLastError();
+  ROWS_CHAIN(amg_up_kernel, up, L.N, L.Q, b, xc, z, out, st, nc);
+  return err;
 }
 
 // One K-cycle at `level` for right-hand side b, result in out (out != b).
@@ -1037,34 +1111,29 @@ cudaError_t launch_coarse_restrict_f32(const DevProblem& d, const float* r, cons
 }
 
 // Zc = P_0 Rc: kCycles stationary V(1,1) cycles from zero, or one K-cycle.
+// The coarse solve (V-cycle kind: kCycles fused V-cycles, the later ones on the residual)
+// as one chain of dependent launches on stream s, then the element-corner copy of the
+// correction that the P-sum of the FP32 or double-FP32 path reads.
 cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStream_t s) {
   if (d.nfree == 0) return cudaSuccess;
-  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s) : vcycle_fused(d, 0, d.Rc, d.Zc, nullptr, st, s);
+  bool pdl = false;
+  cudaError_t err = d.amg_kind == 1 ? kcycle(d, 0, d.Rc, d.Zc, st, s)
+                                    : vcycle_fused(d, 0, d.Rc, d.Zc, nullptr, st, s, pdl);
   if (err != cudaSuccess) return err;
-  if (d.nlevels == 0 || d.amg_kind == 1) {
-    if (d.pfp32) {
-      to_f32_kernel<<<grid_for(d.nfree, 256, 4096), 256, 0, s>>>(d.nfree, d.Zc, d.Zc32, st);
-      ++g_kernel_launches;
-    } else if (d.dwk) {
-      return launch_coarse_corners_dw(d, st, s);
+  if (d.nlevels > 0 && d.amg_kind != 1) {
+    const DevCsr& A0 = d.levels[0].A;
+    for (int c = 1; c < kCycles; ++c) {   // Zc += V (Rc - A0 Zc), the add folded into the up pass
+      ROWS_CHAIN(amg_resid_kernel, A0, A0, d.Rc, d.Zc, d.cres, st);
+      if (err != cudaSuccess) return err;
+      err = vcycle_fused(d, 0, d.cres, d.Zc, d.Zc, st, s, pdl);
+      if (err != cudaSuccess) return err;
     }
-    return cudaGetLastError();
   }
-  const DevCsr& A0 = d.levels[0].A;
-  const int gb = grid_for(A0.n, 256, 4096);
-  for (int c = 1; c < kCycles; ++c) {   // Zc += V (Rc - A0 Zc), the add folded into the up pass
-    ROWS_LAUNCH(amg_resid_kernel, A0, A0, d.Rc, d.Zc, d.cres, st);
-    ++g_kernel_launches;
-    err = vcycle_fused(d, 0, d.cres, d.Zc, d.Zc, st, s);
-    if (err != cudaSuccess) return err;
-  }
-  if (d.pfp32) {
-    to_f32_kernel<<<gb, 256, 0, s>>>(A0.n, d.Zc, d.Zc32, st);
-    ++g_kernel_launches;
-  } else if (d.dwk) {
-    return launch_coarse_corners_dw(d, st, s);
-  }
-  return cudaGetLastError();
+  if (d.pfp32)
+    return launch_chain(coarse_corners_f32_kernel, dim3(grid_for(8 * d.ne, 256, 4096)), 256, s, pdl, d, st);
+  if (d.dwk)
+    return launch_chain(coarse_corners_dw_kernel, dim3(grid_for(8 * d.ne, 256, 4096), d.nrhs), 256, s, pdl, d, st);
+  return cudaSuccess;
 }
 
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
@@ -1176,12 +1245,6 @@ cudaError_t launch_heat_rhs(const DevProblem& d, const double* wl, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_corners_dw(const DevProblem& d, const PcgState* st, cudaStream_t s) {
-  if (d.nfree == 0) return cudaSuccess;
-  coarse_corners_dw_kernel<<<dim3(grid_for(8 * d.ne, 256, 4096), d.nrhs), 256, 0, s>>>(d, st);
-  ++g_kernel_launches;
-  return cudaGetLastError();
-}
 
 cudaError_t launch_mass_load(const DevProblem& d, const double* mN, const double* sv, double* b, cudaStream_t s) {
   mass_load_kernel<<<d.nblk, kVecBlock, 0, s>>>(d, mN, sv, b);
