@@ -768,9 +768,9 @@ def run_solve_case(E):
     X = prob.dof_coords()
     b = prob.load(torch.as_tensor(manufactured_s(X.cpu().numpy(), LAM), device="cuda"))
     S.sem_autotune(prob.h)
-    # the host-driven loop replays one iteration graph per iteration; ncu sees its kernel nodes
-    # (a graph with conditional nodes, the default loop, is profiled only as a whole)
-    S.sem_set_loop(prob.h, S.SEM_LOOP_HOST)
+    # the eager host loop launches each kernel of an iteration by itself, so ncu lists every
+    # launch (the graphs of the other loops are profiled only as wholes)
+    S.sem_set_loop(prob.h, S.SEM_LOOP_EAGER)
     x, rc, it, hist, tr = prob.solve(b)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("solve")

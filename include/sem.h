@@ -89,6 +89,8 @@ typedef struct sem_s sem_t;
 #define SEM_LOOP_HOST    0  /* one graph replay per iteration, the host reads the state in between */
 #define SEM_LOOP_DEVICE  1  /* the whole solve is one graph (a device-evaluated while loop); with
                                sem_solve_many all solves are one graph launch (default) */
+#define SEM_LOOP_EAGER   2  /* the host loop, each iteration's kernels launched one by one without
+                               a graph (for profilers that list single launches) */
 
 /* preconditioner choice for sem_solve (sem_set_precond) */
 #define SEM_PRECOND_TWO_SCALE 0  /* P = P^c + P^f (Sec. 4) */
@@ -219,8 +221,8 @@ int sem_set_patch_solver(sem_t* h, int kind);
 /* sem_set_precond - choose SEM_PRECOND_* for sem_solve (default two-scale). */
 int sem_set_precond(sem_t* h, int which);
 
-/* sem_set_loop - SEM_LOOP_DEVICE (default) or SEM_LOOP_HOST. Both run the same kernels in the
- * same order, so results are bit-identical. With the device loop a solve is captured once
+/* sem_set_loop - SEM_LOOP_DEVICE (default), SEM_LOOP_HOST or SEM_LOOP_EAGER. All run the same
+ * kernels in the same order, so results are bit-identical. With the device loop a solve is captured once
  * per configuration (precision, preconditioner, coarse solver, tiles, network, rtol, maxit)
  * as a graph whose while node runs one iteration per round until the device state says
  * done (never more than maxit + 2 rounds); with profiling on (sem_profile) the host loop

@@ -796,7 +796,8 @@ int sem_set_weights(sem_t* h, int weighted) {
 
 int sem_set_loop(sem_t* h, int mode) {
   if (int rc = check_handle(h)) return rc;
-  if (mode != SEM_LOOP_HOST && mode != SEM_LOOP_DEVICE) return fail(SEM_ERR_ARG, "unknown loop mode");
+  if (mode != SEM_LOOP_HOST && mode != SEM_LOOP_DEVICE && mode != SEM_LOOP_EAGER)
+    return fail(SEM_ERR_ARG, "unknown loop mode");
   h->loop_mode = mode;
   return SEM_OK;
 }
@@ -909,9 +910,9 @@ int solve_begin(sem_t* h, SolveCtx& c, double rtol, int maxit) {
   cudaStream_t s = h->stream;
   if (int rc = enqueue_start(h, c.b, rtol, maxit)) return rc;
 
-  // capture the steady-state iteration once per configuration
+  // capture the steady-state iteration once per configuration (not in the eager loop)
   const long key = graph_key(h);
-  if (h->graph.key != key) {
+  if (h->loop_mode != SEM_LOOP_EAGER && h->graph.key != key) {
     h->graph.reset();
     CK(cudaStreamSynchronize(s));
     if (h->prof.on) h->prof.collect();
@@ -963,6 +964,7 @@ int solve_advance(sem_t* h, SolveCtx& c) {
     CK(cudaStreamSynchronize(s));
     if (h->st_host->done) { c.done = true; return SEM_OK; }
   }
+  if (h->loop_mode == SEM_LOOP_EAGER) return enqueue_tail_head(h);   // the same work, launch by launch
   CK(cudaGraphLaunch(h->graph.exec, s));
   c.graph_pending = true;
   return SEM_OK;

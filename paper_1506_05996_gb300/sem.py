@@ -28,7 +28,7 @@ SEM_PRECOND_TWO_SCALE, SEM_PRECOND_FINE, SEM_PRECOND_NONE = 0, 1, 2
 SEM_NET_LOSS_L2, SEM_NET_LOSS_ENERGY, SEM_NET_LOSS_ANGLE = 0, 1, 2
 SEM_COARSE_VCYCLE, SEM_COARSE_KCYCLE = 0, 1
 SEM_PATCH_SOLVE_FP32, SEM_PATCH_SOLVE_BF16_TC = 0, 1
-SEM_LOOP_HOST, SEM_LOOP_DEVICE = 0, 1
+SEM_LOOP_HOST, SEM_LOOP_DEVICE, SEM_LOOP_EAGER = 0, 1, 2
 
 _vp, _i64, _int, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
 _P = ctypes.POINTER
@@ -237,7 +237,8 @@ def sem_set_patch_solver(h, kind):
 
 
 def sem_set_loop(h, mode):
-    return _check(_lib.sem_set_loop(h, {"host": SEM_LOOP_HOST, "device": SEM_LOOP_DEVICE}.get(mode, mode)))
+    return _check(_lib.sem_set_loop(h, {"host": SEM_LOOP_HOST, "device": SEM_LOOP_DEVICE,
+                                        "eager": SEM_LOOP_EAGER}.get(mode, mode)))
 
 
 def sem_set_precision(h, precision):

@@ -36,7 +36,8 @@ def test_device_loop_is_bit_identical_to_host_loop(prec, coarse):
     host = _run(prob, b, "host")
     dev = _run(prob, b, "device")
     again = _run(prob, b, "device")           # replay of the cached graph
-    for r in (dev, again):
+    eager = _run(prob, b, "eager")            # the host loop without graphs
+    for r in (dev, again, eager):
         assert r[0] == host[0] == 0 and r[1] == host[1]
         np.testing.assert_array_equal(r[2], host[2])
         assert torch.equal(r[4], host[4])
