@@ -65,8 +65,9 @@ template <typename T, typename TY>
 __global__ void gather_identity_kernel(const DevProblem d, const T* __restrict__ wl,
                                        const TY* __restrict__ xin, TY* __restrict__ y, int g0) {
   for (int g = g0 + blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    if (d.mask[g]) { y[g] = xin[g]; continue; }
-    y[g] = (TY)gather_dof_ilp(d, wl, g);
+    const bool mk = d.mask[g] != 0;   // applied after the gather's loads are issued
+    const T s = gather_dof_ilp(d, wl, g);
+    y[g] = mk ? xin[g] : (TY)s;
   }
 }
 
@@ -424,18 +425,24 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
   const double* __restrict__ Zc = d.Zc + (size_t)blockIdx.y * d.nfree;
   const T* __restrict__ Wt = wts_of<T>(d);
   double dot = 0.0;
+  const bool coarse = (mode & PSUM_COARSE) && d.nfree > 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    // the mask, the CSR range and the owner are read together (the mask is applied at the
+    // end, so it adds no memory latency in front of the others)
+    const bool mk = d.mask[g] != 0;
+    const int q0 = d.pg_off[g], q1 = d.pg_off[g + 1];
+    const int l = coarse ? d.owner[g] : 0;
     T v = 0;
-    if (!d.mask[g]) {
+    {
       if (mode & PSUM_IDENT) v += (T)r[g];
       if (mode & PSUM_FINE) {
         T vf = 0;
-        for (int q = d.pg_off[g]; q < d.pg_off[g + 1]; ++q) vf += wp[d.pg_idx[q]];
+        for (int q = q0; q < q1; ++q) vf += wp[d.pg_idx[q]];
         if (Wt != nullptr) vf = vf * Wt[g];     // overlap-weighted P^f
         v += vf;
       }
-      if ((mode & PSUM_COARSE) && d.nfree > 0) {
-        const int l = d.owner[g], e = l / p3, lr = l % p3;
+      if (coarse) {
+        const int e = l / p3, lr = l % p3;
         if constexpr (std::is_same<T, float>::value) {
           // corner values in VTK order at the owner node (i, j, k): along i, then j, then k
           const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_kernel(const DevProblem d, int
         }
       }
     }
-    const double vd = (double)v;
+    const double vd = mk ? 0.0 : (double)v;
     z[g] = vd;
     if (PCG) dot += vd * r[g];
   }
@@ -516,13 +523,18 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
   double* const part = d.partial + (size_t)blockIdx.y * 4 * d.nblk;
   const dw* const Zce = d.Zce + (size_t)blockIdx.y * d.ne * 8;
   double dot = 0.0;
+  const bool coarse = (mode & PSUM_COARSE) && d.nfree > 0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
+    // the mask, the CSR range and the owner are read together (the mask is applied at the
+    // end, so it adds no memory latency in front of the others)
+    const bool mk = d.mask[g] != 0;
+    const int q0 = d.pg_off[g], q1 = d.pg_off[g + 1];
+    const int l = coarse ? d.owner[g] : 0;
     dw v = dw_zero();
-    if (!d.mask[g]) {
+    {
       if (mode & PSUM_IDENT) v = dw_split(r[g]);
       if (mode & PSUM_FINE) {
         // the patch results in ascending patch-entry order, the first 8 loads issued together
-        const int q0 = d.pg_off[g], q1 = d.pg_off[g + 1];
         constexpr int U = 8;
         int ix[U];
 #pragma unroll
@@ -539,10 +551,10 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
         if (d.pw != nullptr) vf = dw_mul(vf, dw_split(d.pw[g]));   // overlap-weighted P^f
         v = dw_add(v, vf);
       }
-      if ((mode & PSUM_COARSE) && d.nfree > 0) {
+      if (coarse) {
         // trilinear interpolation of the element's corner values (VTK order) at the owner
         // node (i, j, k), sum-factorised: along i, then j, then k
-        const int l = d.owner[g], e = l / p3, lr = l % p3;
+        const int e = l / p3, lr = l % p3;
         const int i = lr % p, j = (lr / p) % p, k = lr / (p * p);
         const dw* Z = Zce + (size_t)e * 8;
         const dw a0 = d.phidw[2 * i], a1 = d.phidw[2 * i + 1];
@@ -555,7 +567,7 @@ __global__ void __launch_bounds__(kVecBlock) psum_dw_kernel(const DevProblem d, 
         v = dw_add(v, lerp(c0, w0, c1, w1));
       }
     }
-    const double vd = dw_join(v);
+    const double vd = mk ? 0.0 : dw_join(v);
     z[g] = vd;
     if (PCG) dot += vd * r[g];
   }
@@ -648,10 +660,9 @@ __global__ void __launch_bounds__(kVecBlock) pcg_gather_alpha_kernel(const DevPr
   if (stopped(pst)) return;
   double dot = 0.0;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < d.G; g += gridDim.x * blockDim.x) {
-    T s = 0;
-    if (!d.mask[g])
-      s = gather_dof(d, wl, g);
-    const double sd = (double)s;
+    const bool mk = d.mask[g] != 0;   // applied after the gather's loads are issued
+    const T s = gather_dof(d, wl, g);
+    const double sd = mk ? 0.0 : (double)s;
     f[g] = sd;
     dot += p[g] * sd;
   }
