@@ -212,7 +212,10 @@ __device__ __forceinline__ void schwarz_local_body(const DevProblem& d, const TR
 #pragma unroll
   for (int K = 0; K < P; ++K) {
     const int g = ipe[x + P * (y + P * K)];
-    T v = (g >= 0 && !d.mask[g]) ? num_load<T>(r[g]) : num_zero<T>();
+    const int gs = g >= 0 ? g : 0;   // r and the mask read together, the mask applied after
+    const TR rv = r[gs];
+    const bool use = g >= 0 && !d.mask[gs];
+    T v = use ? num_load<T>(rv) : num_zero<T>();
     if (g >= 0) v = weighted(d, v, g);
     col[K] = v;
   }
@@ -317,7 +320,10 @@ __device__ __forceinline__ void schwarz_dw_body(const DevProblem& d, const TR* _
 #pragma unroll
     for (int K = 0; K < P; ++K) {
       const int g = ipe[x + P * (y + P * K)];
-      T v = (g >= 0 && !d.mask[g]) ? num_load<T>(r[g]) : num_zero<T>();
+      const int gs = g >= 0 ? g : 0;   // r and the mask read together, the mask applied after
+      const TR rv = r[gs];
+      const bool use = g >= 0 && !d.mask[gs];
+      T v = use ? num_load<T>(rv) : num_zero<T>();
       if (g >= 0) v = weighted(d, v, g);
       col[K] = v;
     }

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(p * p) coarse_restrict_kernel(const DevProblem
     for (int i = 0; i < p; ++i) {
       const int l = i + p * (j + p * k), gl = e * p3 + l;
       const int g = d.l2g[gl];
-      const T v = (d.owner[g] == gl && !d.mask[g]) ? r[g] : T(0);
+      const T rv = r[g];   // read with the owner and the mask, which select it after
+      const T v = (d.owner[g] == gl && !d.mask[g]) ? rv : T(0);
       a0 += phi[0][i] * v;
       a1 += phi[1][i] * v;
     }
