@@ -210,11 +210,31 @@ __device__ __forceinline__ double group_sum(double s) {
   return s;
 }
 
+// This lane's part of row `row` of A times x: entries lane, lane + LANES, ... in order. Four
+// entries' column, value and x loads are issued together before their products are added
+// (in the same order as one at a time, so the same bits): a lane of the long M and Q rows
+// then waits for two memory latencies per four entries, not per entry.
 template <int LANES>
 __device__ __forceinline__ double row_dot(const DevCsr& A, int row, bool ok, const double* __restrict__ x, int lane) {
   double s = 0.0;
-  if (ok)
-    for (int q = A.ptr[row] + lane; q < A.ptr[row + 1]; q += LANES) s += A.val[q] * x[A.col[q]];
+  if (ok) {
+    const int q1 = A.ptr[row + 1];
+    int q = A.ptr[row] + lane;
+    for (; q + 3 * LANES < q1; q += 4 * LANES) {
+      int c[4];
+      double v[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = A.col[q + u * LANES];
+        v[u] = A.val[q + u * LANES];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[u] = x[c[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s += v[u] * xv[u];
+    }
+    for (; q < q1; q += LANES) s += A.val[q] * x[A.col[q]];
+  }
   return s;
 }
 
@@ -318,6 +338,7 @@ __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double
   x += (size_t)blockIdx.y * n;
   for (int row = blockIdx.x; row < n; row += gridDim.x) {
     double s = 0.0;
+#pragma unroll 4
     for (int c = threadIdx.x; c < n; c += kRowBlock) s += Ainv[(size_t)row * n + c] * b[c];
     s = group_sum<kRowBlock>(s);
     if (threadIdx.x == 0) x[row] = s;
