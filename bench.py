@@ -405,6 +405,12 @@ def config4_block(steps, warmup, flush=None):
             its += it
         return its
 
+    def many_block():
+        rc, it, sts = S.sem_solve_many_block([pr.h for pr, _, _ in probs], [B for _, B, _ in probs],
+                                             [X for _, _, X in probs], RTOL, 1000)
+        assert rc == 0, sts
+        return [i for row in it for i in row]
+
     def timed(fn):
         for _ in range(max(1, warmup)):
             fn()
@@ -424,7 +430,8 @@ def config4_block(steps, warmup, flush=None):
 
     t_seq, its_seq = timed(one_at_a_time)
     t_blk, its_blk = timed(block)
-    same = its_seq == its_blk
+    t_many, its_many = timed(many_block)
+    same = its_seq == its_blk == its_many
     for pr, _, _ in probs:
         pr.close()
     return {"workload": "24 problems: E ~ U{8..24} hexes per direction, n ~ U{3..8}, +-15% perturbation, lambda=0, "
@@ -434,10 +441,14 @@ def config4_block(steps, warmup, flush=None):
             "one_at_a_time": {"s": t_seq, "solves_per_s": 96 / t_seq, "gdofs_solved": total / t_seq / 1e9},
             "block_k4": {"s": t_blk, "solves_per_s": 96 / t_blk, "gdofs_solved": total / t_blk / 1e9,
                          "speedup": t_seq / t_blk},
+            "many_block_k4": {"s": t_many, "solves_per_s": 96 / t_many, "gdofs_solved": total / t_many / 1e9,
+                              "speedup": t_seq / t_many,
+                              "how": "sem_solve_many_block: the 24 handles' 4-column block solves as the "
+                                     "branches of one graph, one launch"},
             "iterations_equal": same,
             "iterations": {"min": int(min(its_blk)), "max": int(max(its_blk)), "mean": float(np.mean(its_blk))},
-            "note": "block solves are bit-identical to the single solves (tests/test_gpu_block.py); the time of the "
-                    "faster of the timed passes, each pass all 96 solves"}
+            "note": "block solves, batched or not, are bit-identical to the single solves (tests/test_gpu_block.py); "
+                    "the time of the faster of the timed passes, each pass all 96 solves"}
 
 
 def run_gpu(args):

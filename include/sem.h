@@ -287,17 +287,33 @@ int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double 
                     int* iters_host, int* status_host, double* true_rel_res_host);
 
 /*
- * sem_solve_many - the PCG solves of `count` independent handles advanced together: every
- * round reads back the state of all active solves, then replays each one's iteration
- * graph on its own stream, so many small problems share the GPU (the batched form of
- * Algorithm 1). Give every handle its own CUDA stream (sem_create / sem_set_stream); a
- * handle may appear once. b_dev[i] / x_dev[i]: load and solution of handles[i], as in
- * sem_solve (rtol, maxit shared). iters_host[i] and status_host[i] (either may be NULL)
- * receive each solve's iteration count and sem_solve status. Returns SEM_OK, or the
- * first error (or SEM_MAXIT) met. Synchronises all the handles' streams.
+ * sem_solve_many - the PCG solves of `count` independent handles advanced together (the
+ * batched form of Algorithm 1). With the device loop (SEM_LOOP_DEVICE, the default, on every
+ * handle) all the solves are the parallel branches of one graph, launched once, each branch a
+ * device-evaluated while loop; otherwise every round reads back the state of all active
+ * solves, then replays each one's iteration graph on its own stream. Give every handle its
+ * own CUDA stream (sem_create / sem_set_stream); a handle may appear once. b_dev[i] /
+ * x_dev[i]: load and solution of handles[i], as in sem_solve (rtol, maxit shared).
+ * iters_host[i] and status_host[i] (either may be NULL) receive each solve's iteration count
+ * and sem_solve status. Returns SEM_OK, or the first error (or SEM_MAXIT) met. Synchronises
+ * all the handles' streams.
  */
 int sem_solve_many(int count, sem_t* const* handles, const double* const* b_dev,
                    double* const* x_dev, double rtol, int maxit, int* iters_host, int* status_host);
+
+/*
+ * sem_solve_many_block - sem_solve_block on `count` handles at once: every handle's block of
+ * k right-hand sides (b_dev[i], x_dev[i]: k * N_i doubles, column j at offset j * N_i) is one
+ * branch of one graph, launched once, so problems of different sizes and orders share the GPU
+ * and each problem's kernels cover its k loads (one persistent, graph-captured launch for a
+ * batch of problems with several loads each). Requirements as for sem_solve_block on every
+ * handle; a handle may appear once. iters_host and status_host: NULL or count * k entries
+ * (handle i's column j at i * k + j). Results are bit-identical to sem_solve_block on each
+ * handle. Returns SEM_OK, or the most severe status. Synchronises the first handle's stream
+ * (the graph's) and every handle's own.
+ */
+int sem_solve_many_block(int count, sem_t* const* handles, int k, const double* const* b_dev,
+                         double* const* x_dev, double rtol, int maxit, int* iters_host, int* status_host);
 
 /*
  * sem_set_tiles / sem_autotune - tile shapes of the element kernels: the number of

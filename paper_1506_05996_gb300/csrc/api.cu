@@ -1226,8 +1226,8 @@ int sem_solve(sem_t* h, const double* b_dev, double* x_dev, double rtol, int max
   return solve_finish(h, c, iters_host, res_hist_host, true_rel_res_host);
 }
 
-int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
-                    int* status_host, double* true_rel_res_host) {
+// Checks and buffers of a k-column block solve on h (sem_solve_block, sem_solve_many_block).
+static int block_prepare(sem_t* h, int k, const double* b_dev, double* x_dev, int maxit) {
   if (int rc = check_handle(h)) return rc;
   sem::DevProblem& d = h->d;
   if (k < 1 || k > SEM_MAX_BLOCK || b_dev == nullptr || x_dev == nullptr || (const void*)b_dev == (const void*)x_dev)
@@ -1242,7 +1242,40 @@ int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double 
     return fail(SEM_ERR_SINGULAR, "coarse space unavailable: " + h->coarse_err);
   if (int rc = ensure_block(h, k)) return rc;
   if (int rc = ensure_hist(h, maxit)) return rc;
-  if (int rc = ensure_loop_buffers(h)) return rc;
+  return ensure_loop_buffers(h);
+}
+
+// After a block solve's loop ran (d.nrhs = k): the true residuals ||b_j - A u_j|| and the
+// solutions out, every right-hand side at once, then the states read back.
+static int block_finish(sem_t* h, int k, double* x_dev, int* iters_host, int* status_host,
+                        double* true_rel_res_host) {
+  sem::DevProblem& d = h->d;
+  cudaStream_t s = h->stream;
+  const size_t G = (size_t)h->nb.G;
+  PROF(h, "ax_local", sem::launch_ax_local(d, h->u, d.wl, nullptr, s));
+  PROF(h, "true_residual", sem::launch_true_residual(d, h->bbuf, d.wl, s));
+  CK(cudaMemcpyAsync(x_dev, h->u, sizeof(double) * G * k, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState) * k, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->prof.collect();
+  int worst = SEM_OK;
+  for (int j = 0; j < k; ++j) {
+    const sem::PcgState& st = h->st_host[j];
+    int rc = st.status == -6 ? SEM_ERR_NAN : (st.status == -4 ? SEM_ERR_CUDA : (!st.done || st.status == 1 ? SEM_MAXIT : SEM_OK));
+    if (iters_host) iters_host[j] = st.iter;
+    if (status_host) status_host[j] = rc;
+    if (true_rel_res_host) true_rel_res_host[j] = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
+    if (rc < 0 && (worst >= 0 || rc < worst)) worst = rc;
+    else if (rc > 0 && worst == SEM_OK) worst = rc;
+  }
+  if (int rc = take_wait_error(h)) return rc;
+  return worst;
+}
+
+int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters_host,
+                    int* status_host, double* true_rel_res_host) {
+  if (int rc = block_prepare(h, k, b_dev, x_dev, maxit)) return rc;
+  sem::DevProblem& d = h->d;
   cudaStream_t s = h->stream;
   const size_t G = (size_t)h->nb.G;
   d.nrhs = k;
@@ -1267,24 +1300,72 @@ int sem_solve_block(sem_t* h, int k, const double* b_dev, double* x_dev, double 
   }
   CK(cudaMemcpyAsync(h->bbuf, b_dev, sizeof(double) * G * k, cudaMemcpyDeviceToDevice, s));
   CK(cudaGraphLaunch(h->loop.exec, s));
-  // true residuals ||b_j - A u_j|| and the solutions out, every right-hand side at once
-  PROF(h, "ax_local", sem::launch_ax_local(d, h->u, d.wl, nullptr, s));
-  PROF(h, "true_residual", sem::launch_true_residual(d, h->bbuf, d.wl, s));
-  CK(cudaMemcpyAsync(x_dev, h->u, sizeof(double) * G * k, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->st_host, d.st, sizeof(sem::PcgState) * k, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  h->prof.collect();
+  const int worst = block_finish(h, k, x_dev, iters_host, status_host, true_rel_res_host);
+  if (worst < 0) return fail(worst, "a right-hand side of the block solve failed (see status_host)");
+  return worst;
+}
+
+int sem_solve_many_block(int count, sem_t* const* handles, int k, const double* const* b_dev,
+                         double* const* x_dev, double rtol, int maxit, int* iters_host, int* status_host) {
+  if (count < 0 || (count > 0 && (handles == nullptr || b_dev == nullptr || x_dev == nullptr)))
+    return fail(SEM_ERR_ARG, "bad arrays");
+  if (!(rtol >= 0.0) || maxit < 0) return fail(SEM_ERR_ARG, "bad rtol or maxit");
+  for (int i = 0; i < count; ++i) {
+    if (handles[i] == nullptr) return fail(SEM_ERR_ARG, "bad handle at index " + std::to_string(i));
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return fail(SEM_ERR_ARG, "a handle appears twice");
+    if (int rc = block_prepare(handles[i], k, b_dev[i], x_dev[i], maxit)) return rc;
+  }
+  if (count == 0) return SEM_OK;
+  // every handle's block loop (k right-hand sides) is one branch of one graph, launched once
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  struct Restore {
+    int count;
+    sem_t* const* hs;
+    ~Restore() {
+      for (int i = 0; i < count; ++i) hs[i]->d.nrhs = 1;
+    }
+  } restore{count, handles};
+  for (int i = 0; i < count; ++i) {
+    handles[i]->d.nrhs = k;
+    handles[i]->d.hist_stride = handles[i]->hist_cap;
+  }
+  if (!batch_matches(count, handles, rtol, maxit)) {
+    g_batch.reset();
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    int rc = SEM_OK;
+    for (int i = 0; i < count && rc == SEM_OK; ++i) {
+      cudaStreamSynchronize(handles[i]->stream);
+      rc = build_loop(handles[i], g, rtol, maxit);
+    }
+    if (rc == SEM_OK) rc = instantiate(g, g_batch.exec);
+    cudaGraphDestroy(g);
+    if (rc != SEM_OK) return rc;
+    for (int i = 0; i < count; ++i) {
+      g_batch.handles.push_back(handles[i]);
+      g_batch.epochs.push_back(handles[i]->epoch);
+      g_batch.keys.push_back(graph_key(handles[i]));
+    }
+    g_batch.rtol = rtol;
+    g_batch.maxit = maxit;
+  }
+  cudaStream_t s0 = handles[0]->stream;
+  for (int i = 0; i < count; ++i) {
+    sem_t* h = handles[i];
+    if (h->stream != s0) CK(cudaStreamSynchronize(h->stream));   // the caller's work on b
+    CK(cudaMemcpyAsync(h->bbuf, b_dev[i], sizeof(double) * h->nb.G * k, cudaMemcpyDeviceToDevice, s0));
+  }
+  CK(cudaGraphLaunch(g_batch.exec, s0));
+  CK(cudaStreamSynchronize(s0));
   int worst = SEM_OK;
-  for (int j = 0; j < k; ++j) {
-    const sem::PcgState& st = h->st_host[j];
-    int rc = st.status == -6 ? SEM_ERR_NAN : (st.status == -4 ? SEM_ERR_CUDA : (!st.done || st.status == 1 ? SEM_MAXIT : SEM_OK));
-    if (iters_host) iters_host[j] = st.iter;
-    if (status_host) status_host[j] = rc;
-    if (true_rel_res_host) true_rel_res_host[j] = st.bb > 0 ? std::sqrt(st.aux) / std::sqrt(st.bb) : 0.0;
+  for (int i = 0; i < count; ++i) {
+    const int rc = block_finish(handles[i], k, x_dev[i], iters_host ? iters_host + (size_t)i * k : nullptr,
+                                status_host ? status_host + (size_t)i * k : nullptr, nullptr);
     if (rc < 0 && (worst >= 0 || rc < worst)) worst = rc;
     else if (rc > 0 && worst == SEM_OK) worst = rc;
   }
-  if (worst < 0) return fail(worst, "a right-hand side of the block solve failed (see status_host)");
+  if (worst < 0) return fail(worst, "a right-hand side failed (see status_host)");
   return worst;
 }
 

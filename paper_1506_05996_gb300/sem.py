@@ -62,6 +62,7 @@ _SIGS = {
     "sem_solve": ([_vp, _vp, _vp, _dbl, _int, _P(_int), _vp, _P(_dbl)], _int),
     "sem_apply_A_noalloc": ([_int, _i64, _i64, _dbl] + [_vp] * 8, _int),
     "sem_solve_many": ([_int, _vp, _vp, _vp, _dbl, _int, _vp, _vp], _int),
+    "sem_solve_many_block": ([_int, _vp, _int, _vp, _vp, _dbl, _int, _vp, _vp], _int),
     "sem_solve_block": ([_vp, _int, _vp, _vp, _dbl, _int, _vp, _vp, _vp], _int),
     "sem_heat_step": ([_vp, _vp, _vp, _vp, _dbl, _int, _P(_int), _P(_dbl)], _int),
     "sem_set_tiles": ([_vp, _int, _int], _int),
@@ -309,6 +310,27 @@ def sem_solve_block(h, b, x, rtol=1e-8, maxit=1000):
                                      float(rtol), int(maxit), its.ctypes.data_as(_vp), sts.ctypes.data_as(_vp),
                                      trs.ctypes.data_as(_vp)))
     return rc, its.tolist(), sts.tolist(), trs.tolist()
+
+
+def sem_solve_many_block(handles, bs, xs, rtol=1e-8, maxit=1000):
+    """Block solves of several handles in one graph launch: bs[i], xs[i] are (k, N_i)
+    contiguous CUDA float64 tensors with the same k. Returns (rc, iterations[i][k],
+    status[i][k])."""
+    c = len(handles)
+    k = int(bs[0].shape[0]) if c else 1
+    ns = [sem_num_dofs(h) for h in handles]
+    for b, x, n in zip(bs, xs, ns):
+        if b.dim() != 2 or b.shape != (k, n) or x.shape != b.shape:
+            raise ValueError("every b and x must be (k, N) with the same k")
+    H = (ctypes.c_void_p * c)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    B = (ctypes.c_void_p * c)(*[_dev(b, torch.float64, k * n).value for b, n in zip(bs, ns)])
+    X = (ctypes.c_void_p * c)(*[_dev(x, torch.float64, k * n).value for x, n in zip(xs, ns)])
+    its = np.zeros(c * k, dtype=np.int32)
+    sts = np.zeros(c * k, dtype=np.int32)
+    rc = _check(_lib.sem_solve_many_block(c, ctypes.cast(H, ctypes.c_void_p), k, ctypes.cast(B, ctypes.c_void_p),
+                                          ctypes.cast(X, ctypes.c_void_p), float(rtol), int(maxit),
+                                          its.ctypes.data_as(_vp), sts.ctypes.data_as(_vp)))
+    return rc, its.reshape(c, k).tolist(), sts.reshape(c, k).tolist()
 
 
 def sem_set_tiles(h, epb_ax, epb_sw):

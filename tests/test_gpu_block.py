@@ -89,3 +89,38 @@ def test_block_refusals():
     with pytest.raises(SemError):
         sem.sem_solve_block(pr.h, B, X)
     pr.close()
+
+
+def test_many_block_equals_block_solves():
+    """sem_solve_many_block: several handles of different sizes and orders, k right-hand sides
+    each, as branches of one graph launch; every column bit-identical to the handle's own
+    sem_solve_block (the same kernels on the same slices), and a second launch of the cached
+    graph again."""
+    from paper_1506_05996_gb300 import sem
+    from paper_1506_05996_gb300.sem import SemProblem
+    specs = [(3, 3, 0.0, 11), (5, 2, 1.0, 12), (4, 5, 0.5, 13)]
+    k = 4
+    probs, Bs = [], []
+    for E, n, lam, seed in specs:
+        mesh = lattice_hex_mesh(E, 0.15, seed)
+        pr = SemProblem(mesh.xyz, mesh.hex2vert, n, lam)
+        free = (pr.mask() == 0).double()
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        B = (torch.randn(k, pr.n_dof, dtype=torch.float64, device="cuda", generator=g) * free).contiguous()
+        probs.append(pr)
+        Bs.append(B)
+    ref = []
+    for pr, B in zip(probs, Bs):
+        X = torch.empty_like(B)
+        rc, its, sts, _ = sem.sem_solve_block(pr.h, B, X, 1e-8, 500)
+        assert rc == 0
+        ref.append((X, its))
+    for _ in range(2):
+        Xs = [torch.empty_like(B) for B in Bs]
+        rc, its, sts = sem.sem_solve_many_block([pr.h for pr in probs], Bs, Xs, 1e-8, 500)
+        assert rc == 0 and all(s == 0 for row in sts for s in row)
+        for (Xr, itr), X, it in zip(ref, Xs, its):
+            assert it == itr
+            assert torch.equal(X, Xr)
+    for pr in probs:
+        pr.close()
