@@ -1169,6 +1169,17 @@ cudaError_t launch_coarse_solve(const DevProblem& d, const PcgState* st, cudaStr
   return cudaSuccess;
 }
 
+// Grid of a grid-stride vector kernel: at most cap CTAs (the reduction partials hold d.nblk)
+// and no more than are resident at once, so that no CTA waits for a second wave.
+template <typename K>
+int resident_grid(K kernel, int block, int cap) {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0) != cudaSuccess || nsm <= 0 || per <= 0)
+    return cap;
+  return nsm * per < cap ? nsm * per : cap;
+}
+
 cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* z, bool pcg, cudaStream_t s) {
   if (d.pfp32) {
     const float* wp = reinterpret_cast<const float*>(d.wp);
@@ -1176,8 +1187,13 @@ cudaError_t launch_psum(const DevProblem& d, int mode, const double* r, double* 
     else psum_kernel<false, float><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
   } else if (d.dwk) {   // the patch results are pairs (double-FP32 patch solve)
     const dw* wp = reinterpret_cast<const dw*>(d.wp);
-    if (pcg) psum_dw_kernel<true><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
-    else psum_dw_kernel<false><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, wp, r, z);
+    // 48-60 registers: fewer CTAs are resident than d.nblk
+    if (pcg)
+      psum_dw_kernel<true><<<dim3(resident_grid(psum_dw_kernel<true>, kVecBlock, d.nblk), d.nrhs), kVecBlock, 0, s>>>(
+          d, mode, wp, r, z);
+    else
+      psum_dw_kernel<false><<<dim3(resident_grid(psum_dw_kernel<false>, kVecBlock, d.nblk), d.nrhs), kVecBlock, 0, s>>>(
+          d, mode, wp, r, z);
   } else {
     if (pcg) psum_kernel<true, double><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
     else psum_kernel<false, double><<<dim3(d.nblk, d.nrhs), kVecBlock, 0, s>>>(d, mode, d.wp, r, z);
