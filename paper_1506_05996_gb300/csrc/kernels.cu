@@ -327,7 +327,9 @@ __global__ void __launch_bounds__(kRowBlock) amg_up_kernel(DevCsr N, DevCsr Q, c
   }
 }
 
-// x = Ainv b at the dense coarsest level: one block of kRowBlock threads per row.
+// x = Ainv b at the dense coarsest level: one warp per row (Ainv row-major), each lane's
+// entries lane, lane + 32, ... summed in order with their loads issued 4 at a time, then the
+// warp's sum.
 __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double* __restrict__ Ainv,
                                                             const double* __restrict__ b, double* __restrict__ x,
                                                             const PcgState* st) {
@@ -336,12 +338,24 @@ __global__ void __launch_bounds__(kRowBlock) dense_mv_kernel(int n, const double
   if (stopped(st)) return;
   b += (size_t)blockIdx.y * n;
   x += (size_t)blockIdx.y * n;
-  for (int row = blockIdx.x; row < n; row += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+    const double* a = Ainv + (size_t)row * n;
     double s = 0.0;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < n; c += kRowBlock) s += Ainv[(size_t)row * n + c] * b[c];
-    s = group_sum<kRowBlock>(s);
-    if (threadIdx.x == 0) x[row] = s;
+    int c = lane;
+    for (; c + 96 < n; c += 128) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        av[u] = a[c + 32 * u];
+        bv[u] = b[c + 32 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s += av[u] * bv[u];
+    }
+    for (; c < n; c += 32) s += a[c] * b[c];
+    s = group_sum<32>(s);
+    if (lane == 0) x[row] = s;
   }
 }
 
@@ -998,7 +1012,7 @@ cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double
                          const PcgState* st, cudaStream_t s, bool& pdl) {
   cudaError_t err;
   if (level == d.nlevels) {
-    err = launch_chain(dense_mv_kernel, dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, s, pdl,
+    err = launch_chain(dense_mv_kernel, dim3(grid_for(d.coarsest_n, kRowBlock / 32, 8192), d.nrhs), kRowBlock, s, pdl,
                        d.coarsest_n, d.coarsest_inv, b, out, st);
     pdl = true;
     return err;
@@ -1019,7 +1033,7 @@ cudaError_t vcycle_fused(const DevProblem& d, int level, const double* b, double
 // One K-cycle at `level` for right-hand side b, result in out (out != b).
 cudaError_t kcycle(const DevProblem& d, int level, const double* b, double* out, const PcgState* st, cudaStream_t s) {
   if (level == d.nlevels) {
-    dense_mv_kernel<<<dim3(grid_for(d.coarsest_n, 1, 8192), d.nrhs), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b,
+    dense_mv_kernel<<<dim3(grid_for(d.coarsest_n, kRowBlock / 32, 8192), d.nrhs), kRowBlock, 0, s>>>(d.coarsest_n, d.coarsest_inv, b,
                                                                                        out, st);
     ++g_kernel_launches;
     return cudaGetLastError();
