@@ -751,7 +751,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "tiles_epb_ax_sw": tiles},
             "time_to_1e-8_s": per_step, "iterations": it64, "true_rel_res": tr64, "wall_s": t_wall,
-            "fp64_native": native, "mixed": mixed, "mixed_tc": mixed_tc, "p32": p32, "weighted": weighted,
+            "fp64_native": native, "mixed": mixed, "bf16_precond": mixed_tc, "p32": p32, "weighted": weighted,
             "profiled": {"ms_per_step": t_prof * 1e3,
                          "note": "host-driven loop with a CUDA event pair around every launch",
                          "kernels_ms_per_step": {k: v[1] / args.steps
