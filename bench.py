@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--solve-case", type=int, default=0, metavar="E",
                     help="only run one SEM_PREC_FP64 solve on an E^3, n=7 mesh inside the NVTX range \"solve\" "
                          "(the launch list of a solve for ncu), then exit")
+    ap.add_argument("--solve-prec", default="fp64", choices=["fp64", "fp32"],
+                    help="with --solve-case: SEM_PREC_FP64 (default) or the mixed path (fp32)")
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
                     help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
                          "(a small case for ncu captures), then exit")
@@ -768,16 +770,17 @@ def run_gpu(args):
     ranks.close()
 
 
-def run_solve_case(E):
+def run_solve_case(E, prec="fp64"):
     """One SEM_PREC_FP64 solve of the headline recipe at E^3 hexes, n = 7, after a warm-up
     solve, inside the NVTX range "solve" (for ncu --nvtx --nvtx-include solve/)."""
     import torch
     from synth import lattice_hex_mesh, manufactured_s
     from paper_1506_05996_gb300 import sem as S
     mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
-    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored")
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=(prec == "fp32"))
     X = prob.dof_coords()
     b = prob.load(torch.as_tensor(manufactured_s(X.cpu().numpy(), LAM), device="cuda"))
+    prob.set_precision(prec)
     S.sem_autotune(prob.h)
     # the eager host loop launches each kernel of an iteration by itself, so ncu lists every
     # launch (the graphs of the other loops are profiled only as wholes)
@@ -788,7 +791,7 @@ def run_solve_case(E):
     x, rc, it, hist, tr = prob.solve(b)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"solve_case": E, "n_dof": prob.n_dof, "iterations": it, "true_rel_res": tr}))
+    print(json.dumps({"solve_case": E, "precision": prec, "n_dof": prob.n_dof, "iterations": it, "true_rel_res": tr}))
     prob.close()
 
 
@@ -1159,7 +1162,7 @@ def main():
     elif args.kernel_case:
         run_kernel_case(args.kernel_case)
     elif args.solve_case:
-        run_solve_case(args.solve_case)
+        run_solve_case(args.solve_case, args.solve_prec)
     elif args.impl == "reference":
         run_reference(args)
     else:
