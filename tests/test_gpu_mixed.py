@@ -222,6 +222,7 @@ def test_fp32_vector_apply_is_the_rounded_fp32_apply(geom):
     sem.sem_get_mask(P.gpu.h, gm)
     masked = gm.bool()
     assert bool(masked.any()) and torch.equal(y32[masked], x32[masked])
+    assert sem.sem_status(P.gpu.h) == 0   # synchronises; no kernel gave up a bounded wait
 
 
 @pytest.mark.parametrize("reserve", [None, -4])
