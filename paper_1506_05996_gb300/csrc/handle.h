@@ -176,7 +176,7 @@ struct sem_s {
   sem::dw* geodw = nullptr;         // pairs-of-FP32 copy of the stored factors (SEM_PREC_FP64)
   int precision = SEM_PREC_FP64;
   int amg_kind = 0;                 // SEM_COARSE_VCYCLE or SEM_COARSE_KCYCLE
-  int overlap_sms = 32;             // FP32 patch solves leave this many SMs to the coarse branch
+  int overlap_sms = 48;             // FP32 patch solves leave this many SMs to the coarse branch
   uint8_t* mask = nullptr;
   uint8_t* pvar = nullptr;          // free sides of every element (see update_free_sides)
   double* swd = nullptr;             // patch-solve diagonals, scaled (update_free_sides)

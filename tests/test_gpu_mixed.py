@@ -229,7 +229,7 @@ def test_fp32_vector_apply_is_the_rounded_fp32_apply(geom):
 def test_fp32_two_scale_on_a_capped_patch_grid(reserve):
     """The FP32 two-scale apply caps the patch-solve grid so that SMs stay free for the
     coarse branch, and its CTAs then loop over element groups. 32^3 hexes at n = 2 have
-    more elements than any capped grid holds (at most (SMs - 32) x 32 resident CTAs of at
+    more elements than any capped grid holds (at most (SMs - 48) x 32 resident CTAs of at
     most 8 elements), so the loop takes at least two rounds; reserve = -4 leaves only 4 SMs
     to the patch solves (many rounds). The fine part alone runs uncapped and is checked
     against the oracle's bound; the two-scale sum must then equal fine + coarse parts to one
@@ -238,7 +238,7 @@ def test_fp32_two_scale_on_a_capped_patch_grid(reserve):
     from paper_1506_05996_gb300 import sem
     E, n, lam = 32, 2, 1.0
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    assert E ** 3 > (nsm - 32) * 32 * 8
+    assert E ** 3 > (nsm - 48) * 32 * 8
     P = _pair(lattice_hex_mesh(E, 0.2, 12), n, lam, "stored")
     P.gpu.set_precision("fp32")
     if reserve is not None:
