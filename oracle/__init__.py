@@ -17,7 +17,8 @@ all-hex meshes":
   pcg.py       preconditioned conjugate gradients (Algorithm 1)
   problem.py   one object tying the pieces together
 
-Parity status of each function is stated in its module docstring; the AMG
-aggregation rule is "parity unpinned" (the paper does not define it; the
-oracle and the GPU library implement the same written rule independently).
+Parity status of each function is stated in its module docstring. The AMG
+aggregation rule is a reading (the paper does not define it; the oracle and
+the GPU library implement the same written rule independently); it is pinned
+to that written rule by cases worked out by hand (tests/test_oracle_amg_rules.py).
 """

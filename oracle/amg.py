@@ -34,7 +34,9 @@ Unsmoothed aggregation with a single V-cycle was tried first: it contracts the
 coarse error by only ~0.8 per cycle and nearly doubles the PCG iteration counts.
 Below ~2000 unknowns the smoothed Galerkin products become nearly dense and the
 pairwise passes stop coarsening, so the hierarchy ends there with a dense solve.
-Parity unpinned: no value in the paper fixes this rule; the tests pin the dense
+Pins: no value in the paper fixes this rule, so the tests pin the rule as written, on
+cases worked out by hand (a 3x3 grid, the strength threshold on both sides of 0.25, positive
+couplings, near-ties, three passes and the smoothed prolongator on a chain), and the dense
 coarsest solve, symmetry and positivity of P_0 and its A-norm contraction.
 """
 import numpy as np
