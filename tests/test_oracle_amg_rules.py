@@ -110,3 +110,27 @@ def test_three_passes_on_a_chain_give_aggregates_of_eight_and_the_smoothed_prolo
     # the coarse operator is the Galerkin product, and the dense coarsest solve inverts it
     Ac = (sp.csr_matrix(P).T @ A @ sp.csr_matrix(P)).toarray()
     np.testing.assert_allclose(H.coarsest_inv @ Ac, np.eye(375), atol=1e-9)
+
+
+def test_kcycle_hierarchy_is_unsmoothed_pairs_of_pairs():
+    """The paper's cycle (kind "kcycle") takes two pairwise passes and no smoothing: on the
+    chain the aggregates are runs of 4 and the prolongator is their 0/1 indicator."""
+    n = 4096
+    A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    H = amg.AMG(A, kind="kcycle")
+    assert H.sizes() == [4096, 1024]
+    P = H.levels[0][2].toarray()
+    expect = np.zeros((n, n // 4))
+    expect[np.arange(n), np.arange(n) // 4] = 1.0
+    np.testing.assert_array_equal(P, expect)
+
+
+def test_coarsening_that_stalls_ends_in_the_dense_solve():
+    """With no negative coupling every unknown stays a singleton, so a level would keep all
+    3,000 unknowns (more than 3/4): the hierarchy stops at once and the dense solve takes the
+    whole matrix."""
+    n = 3000
+    d = np.linspace(1.0, 2.0, n)
+    H = amg.AMG(sp.diags(d).tocsr())
+    assert H.sizes() == [3000]
+    np.testing.assert_allclose(np.diag(H.coarsest_inv), 1.0 / d, rtol=1e-14)
