@@ -44,6 +44,8 @@ def parse():
                     help="skip the 48^3-hex precision block of the default line")
     ap.add_argument("--no-config4", action="store_true",
                     help="skip the 24-problem x 4-load batching block of the default line")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the learned-correction block (training and evaluation) of the default line")
     ap.add_argument("--precision-variant", action="store_true",
                     help="48^3 hexes, +-20%% (seed 2), n=7, lambda=0: FP64 vs mixed time-to-1e-8 and the "
                          "per-result error of the mixed solution")
@@ -677,8 +679,9 @@ def run_gpu(args):
 
     # ---- precision variant (48^3 hexes, lambda = 0, seed 2): SEM_PREC_FP64 against the mixed
     # path and binary64, errors per result against the binary64 solution
+    # the variant blocks describe one GPU: replicas (N > 1) skip them
     config3 = None
-    if not args.no_config3:
+    if not args.no_config3 and world == 1:
         mesh3, pr3, X3, b3 = solve_problem(48, 0.2, 2, 0.0)
         G3 = pr3.n_dof
         ustar = torch.as_tensor(manufactured_u(X3.cpu().numpy()), device="cuda")
@@ -716,8 +719,11 @@ def run_gpu(args):
         pr3.close()
 
     config4 = None
-    if not args.no_config4:
+    if not args.no_config4 and world == 1:
         config4 = config4_block(max(1, min(args.steps, 3)), 1, flush)
+    config5 = None
+    if not args.no_config5 and world == 1:
+        config5 = learned_block(args, max(1, min(args.steps, 3)))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -758,7 +764,7 @@ def run_gpu(args):
                          "note": "host-driven loop with a CUDA event pair around every launch",
                          "kernels_ms_per_step": {k: v[1] / args.steps
                                                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}},
-            "ax": ax, "peaks": meas, "roofline": roof, "config3": config3, "config4": config4,
+            "ax": ax, "peaks": meas, "roofline": roof, "config3": config3, "config4": config4, "config5": config5,
             "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,
                     "d2h_bytes_per_step": 8 * G, "s_per_step": t_e2e},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -955,6 +961,11 @@ def run_batch_variant(args):
 def run_learned_variant(args):
     """Learned correction: GPU training on solver-harvested samples, then plain two-scale PCG
     against flexible PCG with the network (fallback on stall), FP64 and mixed."""
+    print(json.dumps(learned_block(args, max(1, args.steps))))
+
+
+def learned_block(args, steps):
+    """The learned-correction block (config 5): returns the result as a dict."""
     import numpy as np
     import torch
     from paper_1506_05996_gb300 import sem as S
@@ -987,7 +998,7 @@ def run_learned_variant(args):
         row = {}
         for name, nn in (("plain", None), ("learned", net)):
             its, ts, trs, used = [], [], [], []
-            for _ in range(max(1, args.steps)):
+            for _ in range(steps):
                 it, dt, tr, rc, u = timed_solve(prob, b, nn, rtol=RTOL, maxit=1000, window=8, ratio=0.5, theta=0.25)
                 its.append(it)
                 ts.append(dt)
@@ -998,7 +1009,7 @@ def run_learned_variant(args):
         row["time_ratio_learned_over_plain"] = row["learned"]["time_to_1e-8_s"] / row["plain"]["time_to_1e-8_s"]
         row["iteration_gain"] = row["plain"]["iterations"] - row["learned"]["iterations"]
         out[prec] = row
-    print(json.dumps({"variant": "learned", "config": {
+    res = {"variant": "learned", "config": {
         "training": "%d seeded 16^3-hex meshes (+-20%%, seeds 1000..), n=5, lambda ~ U[0,10], manufactured and "
                     "Gaussian loads; samples at PCG iterates k in {0,1,2,4,8,16}; %d Adam steps, angle loss, "
                     "lr 3e-3 cosine" % (args.train_meshes, args.train_steps),
@@ -1008,9 +1019,10 @@ def run_learned_variant(args):
         "n_dof": prob.n_dof, "params": S.sem_net_num_params()},
         "harvest_s": t_harvest, "train_s": t_train,
         "loss_first_50": float(np.mean(losses[:50])), "loss_last_300": float(np.mean(losses[-300:])),
-        "unseen_mesh_angle_cosines": quality, **out}))
+        "unseen_mesh_angle_cosines": quality, **out}
     S.sem_net_destroy(net)
     prob.close()
+    return res
 
 
 def run_heat_variant(args):
