@@ -555,9 +555,10 @@ def run_gpu(args):
     avg_ms = tot / nl
     ops = {"schwarz_local": dw_ops_schwarz, "ax_local": dw_ops_ax}.get(kern)
     fp64eq = {"schwarz_local": schwarz_flops, "ax_local": ax_flops}.get(kern)
-    # DRAM bytes per launch: one ncu capture of the kernel at 24^3 hexes, scaled by the
-    # element count (None until the current kernel has been captured)
-    traffic = {"schwarz_local": None}.get(kern)
+    # DRAM bytes per launch: one ncu capture of the kernel at 24^3 hexes (13,824 elements, 2
+    # per CTA as here; 211,711,488 bytes read + 79,164,416 written), scaled by the element
+    # count: the kernel's bytes are per element (pair diagonals, patch table, r, results)
+    traffic = {"schwarz_local": (211711488 + 79164416) / 13824 * NE}.get(kern)
     roof = {"kernel": kern + " (double-FP32)", "bound": "alu", "unit": "Tops/s",
             "peak": meas["fp32_tops"],
             "peak_source": "measured FP32 FMA loop (sem_measure_fma_peak), one operation per FMA, at %s MHz"
@@ -570,6 +571,8 @@ def run_gpu(args):
             "fp64_equivalent_tflops": (fp64eq(ORDER, NE) / (avg_ms * 1e-3) / 1e12) if fp64eq else None,
             "fp64_pipe_peak_tflops": fp64_tf,
             "avg_launch_ms": avg_ms, "launches": nl, "traffic": traffic,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at 24^3 hexes, "
+                              "scaled to this mesh by the element count" if traffic else None,
             "share_of_step": tot / (t_prof * args.steps * 1e3)}
     roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] else None
 
