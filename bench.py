@@ -46,6 +46,8 @@ def parse():
                     help="skip the 24-problem x 4-load batching block of the default line")
     ap.add_argument("--no-config5", action="store_true",
                     help="skip the learned-correction block (training and evaluation) of the default line")
+    ap.add_argument("--no-kcycle", action="store_true", help="skip the K-cycle block of the default line")
+    ap.add_argument("--no-heat", action="store_true", help="skip the heat-rod block (n = 7) of the default line")
     ap.add_argument("--precision-variant", action="store_true",
                     help="48^3 hexes, +-20%% (seed 2), n=7, lambda=0: FP64 vs mixed time-to-1e-8 and the "
                          "per-result error of the mixed solution")
@@ -727,6 +729,12 @@ def run_gpu(args):
     config5 = None
     if not args.no_config5 and world == 1:
         config5 = learned_block(args, max(1, min(args.steps, 3)))
+    kcycle = None
+    if not args.no_kcycle and world == 1:
+        kcycle = kcycle_block(args)
+    heat = None
+    if not args.no_heat and world == 1:
+        heat = heat_block(args, [7])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -768,6 +776,7 @@ def run_gpu(args):
                          "kernels_ms_per_step": {k: v[1] / args.steps
                                                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}},
             "ax": ax, "peaks": meas, "roofline": roof, "config3": config3, "config4": config4, "config5": config5,
+            "kcycle": kcycle, "heat": heat,
             "e2e": {"value": world * G / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": 8 * G,
                     "d2h_bytes_per_step": 8 * G, "s_per_step": t_e2e},
             "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -1030,6 +1039,11 @@ def learned_block(args, steps):
 
 def run_heat_variant(args):
     """The paper's heat-equation experiment (Sec. 5) on a synthetic rod: wall time for 70 steps."""
+    print(json.dumps(heat_block(args, [int(v) for v in args.heat_orders.split(",")])))
+
+
+def heat_block(args, orders):
+    """The heat-rod experiment at the given orders; returns the result as a dict."""
     import numpy as np
     import torch
     from synth import lattice_hex_mesh, moving_source
@@ -1038,7 +1052,7 @@ def run_heat_variant(args):
     lam = 1.0 / (kappa * dt)
     mesh = lattice_hex_mesh((16, 16, 244), 0.2, 5, box=(1.0, 1.0, 15.25))
     rows = []
-    for n in [int(v) for v in args.heat_orders.split(",")]:
+    for n in orders:
         t0 = time.perf_counter()
         prob = S.SemProblem(mesh.xyz, mesh.hex2vert, n, lam, geom=args.heat_geom, neumann=True,
                             mixed=(args.heat_geom == "stored"))
@@ -1067,7 +1081,7 @@ def run_heat_variant(args):
         rows.append(row)
         prob.close()
         del gs
-    print(json.dumps({"variant": "heat", "config": {
+    return {"variant": "heat", "config": {
         "workload": "rod [0,1]x[0,1]x[0,15.25], 16x16x244 = 62,464 hexes, +-20% perturbation seed 5, insulated "
                     "(Neumann) boundary; backward Euler, kappa 1e-2, dt 0.04, c = 1/dt (lambda = 1/(kappa dt) "
                     "= 2500); moving Gaussian source Q = 1000 exp(-|x-c(t)|^2/(2*0.25^2)), c(t) = (0.5, 0.5, "
@@ -1076,7 +1090,7 @@ def run_heat_variant(args):
                     + " geometric factors",
         "paper": "Table 4: 70 steps on a 62,540-hex rod, CUDA on a GTX 980 in FP32: 13.4 / 14.8 / 32.1 / 53.6 / "
                  "90.3 / 134.9 s for n = 2..7 (context: other hardware, other mesh, tolerance not stated)"},
-        "orders": rows}))
+        "orders": rows}
 
 
 def run_patch_variant(args):
@@ -1114,6 +1128,11 @@ def run_patch_variant(args):
 
 def run_kcycle_variant(args):
     """P_0 as the paper's K-cycle against the default V-cycles, same workload as the headline."""
+    print(json.dumps(kcycle_block(args)))
+
+
+def kcycle_block(args):
+    """The K-cycle against the V-cycles on the headline workload; returns the result as a dict."""
     import numpy as np
     import torch
     from synth import lattice_hex_mesh, manufactured_s
@@ -1152,12 +1171,13 @@ def run_kcycle_variant(args):
                          "coarse_amg_kernels_per_application": amg_launches / max(1, it + 1)}
         out[kind] = row
     prob.set_precision("fp64")
-    print(json.dumps({"variant": "kcycle", "config": {
+    res = {"variant": "kcycle", "config": {
         "workload": WORKLOAD, "n_dof": prob.n_dof,
         "vcycle": "smoothed aggregation (3 pairwise passes), P_0 = three V(1,1) damped-Jacobi cycles, PCG",
         "kcycle": "unsmoothed aggregation (2 passes), P_0 = one recursive K-cycle with damped Jacobi (Sec. 4.1), "
-                  "flexible PCG"}, **out}))
+                  "flexible PCG"}, **out}
     prob.close()
+    return res
 
 
 def main():
