@@ -56,7 +56,7 @@ typedef struct sem_s sem_t;
 
 /* arithmetic of the operator and the preconditioner (sem_set_precision) */
 #define SEM_PREC_FP64  0   /* FP64 vectors, dot products, alpha/beta and residual updates; the element
-                              kernels (operator with stored factors, patch solves) compute in
+                              kernels (operator with stored or recomputed factors, patch solves) compute in
                               double-FP32: pairs of FP32 numbers with error-free sums and products on
                               the FP32 pipe, every step within a few 2^-48 of its operands' magnitudes
                               (binary64: 2^-53), which matches binary64 results to about 1e-14 of

@@ -1526,7 +1526,7 @@ int sem_autotune(sem_t* h, int* epb_ax_host, int* epb_sw_host) {
   CK(cudaMemsetAsync(d.r32, 0, sizeof(float) * h->nb.G, h->stream));
   // the kernels of the precision in use: the FP32 operator in the mixed path, the FP32
   // patch solve in the mixed and P32 paths, the FP64 kernels otherwise
-  int& ax = d.fp32 ? d.epb_ax32 : ((d.dwk && !d.recompute) ? d.epb_axdw : d.epb_ax);
+  int& ax = d.fp32 ? d.epb_ax32 : (d.dwk ? d.epb_axdw : d.epb_ax);
   int& sw = d.pfp32 ? d.epb_sw32 : (d.dwk ? d.epb_swdw : d.epb_sw);
   auto fa = [&]() -> cudaError_t {
     return d.fp32 ? sem::launch_ax_local_f32_in32(d, d.p32, reinterpret_cast<float*>(d.wl), nullptr, h->stream)

@@ -218,11 +218,14 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 // The double-FP32 operator with its six line contractions as two loops (gradient along i, j,
 // k into A, B, C; divergence of A, B, C back into the sum), each contraction once in the code
 // (the unrolled form of ax_local_kernel stalls on instruction fetch with the pair arithmetic).
-// Same operations in the same order as the unrolled form; stored factors only.
+// Same operations in the same order as the unrolled form.
 //   axis i: line (j = tx, k = ty), nodes (q, tx, ty) of the slab
 //   axis j: line (i = tx, k = ty), nodes (tx, q, ty)
 //   axis k: line (i = tx, j = ty), nodes (tx, ty, q)
-template <int p, typename TX, int EPB, bool DIRECT>
+// RECOMP: the factors recomputed at every node from the element's vertices in pair arithmetic
+// (geom_point_dw), the pointwise stage as a loop; the c-term lambda m u then starts the sum
+// that the three divergence terms are added to: y = ((lambda m u + d_i) + d_j) + d_k.
+template <int p, typename TX, int EPB, bool DIRECT, bool RECOMP = false>
 __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, const TX* __restrict__ x,
                                                             double* __restrict__ wl, const PcgState* st,
                                                             TX* __restrict__ yd) {
@@ -247,6 +250,17 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   const int tx = tid % p, ty = tid / p;
   fold_fill<p, T>(Fg, d.D, false, threadIdx.x);
   fold_fill<p, T>(Fd, d.D, true, threadIdx.x);
+  // RECOMP: the element's vertices as pairs, relative to corner 0. The derivatives of the
+  // corner basis functions sum to zero, so J is unchanged in exact arithmetic, while the
+  // binary64 differences (each within 2^-53 of itself) keep the pair sums at the element's
+  // scale: summed from absolute coordinates, J would lose |x| / h of the pairs' 48 bits.
+  __shared__ T sx_all[RECOMP ? EPB * 24 : 1];
+  T* const sx = sx_all + (RECOMP ? grp * 24 : 0);
+  if constexpr (RECOMP)
+    for (int q = tid; q < 24; q += p2) {
+      const double* xe = d.exyz + (size_t)e * 24;
+      sx[q] = dw_split(xe[q] - xe[q % 3]);
+    }
   const int* l2ge = d.l2g + (size_t)e * p3;
   constexpr int m = p - 2;
   // axis a's buffer, first node and node stride (selects, not arrays: no local memory)
@@ -282,8 +296,23 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   }
   __syncthreads();
   const bool lam_zero = d.lambda == 0.0;
+  if constexpr (RECOMP) {
+    const dw lam = num_const<dw>(d.lambda);
+    const dw ga = num_const<dw>(d.tg[tx]), gb = num_const<dw>(d.tg[ty]);
+#pragma unroll 1
+    for (int k = 0; k < p; ++k) {   // pointwise, factors recomputed; su = lambda m u
+      const int ls = SL::at(tx, ty, k);
+      const T ur = sA[ls], us = sB[ls], ut = sC[ls];
+      T G[6], mm;
+      geom_point_dw(sx, ga, gb, num_const<dw>(d.tg[k]), num_const<dw>(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm);
+      sA[ls] = num_dot3(G[0], ur, G[1], us, G[2], ut);
+      sB[ls] = num_dot3(G[1], ur, G[3], us, G[4], ut);
+      sC[ls] = num_dot3(G[2], ur, G[4], us, G[5], ut);
+      su[ls] = lam_zero ? num_zero<T>() : dw_mul(dw_mul(lam, mm), su[ls]);
+    }
+  }
 #pragma unroll
-  for (int k = 0; k < p; ++k) {   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k)
+  for (int k = 0; k < (RECOMP ? 0 : p); ++k) {   // pointwise: (A, B, C) = G grad u at the nodes (tx, ty, k)
     const int l = tx + p * (ty + p * k);
     const int ls = SL::at(tx, ty, k);
     const T ur = sA[ls], us = sB[ls], ut = sC[ls];
@@ -306,7 +335,7 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
     fold_apply<p, T>(Fd, line, res);
     if (a == 0) {
 #pragma unroll
-      for (int q = 0; q < p; ++q) su[b0 + q] = res[q];
+      for (int q = 0; q < p; ++q) su[b0 + q] = RECOMP ? num_add(su[b0 + q], res[q]) : res[q];
       __syncthreads();
     } else if (a == 1) {
 #pragma unroll
@@ -319,7 +348,9 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
 #pragma unroll
   for (int k = 0; k < p; ++k) {
     const int l = tx + p * (ty + p * k);
-    const T v = num_fma(rk[k], uk[k], num_add(su[SL::at(tx, ty, k)], res[k]));   // lambda m u + the divergence terms
+    // lambda m u + the divergence terms (RECOMP: lambda m u already in su)
+    const T v = RECOMP ? num_add(su[SL::at(tx, ty, k)], res[k])
+                       : num_fma(rk[k], uk[k], num_add(su[SL::at(tx, ty, k)], res[k]));
     if (DIRECT && inner_xy && k >= 1 && k <= p - 2) {
       const int g = gi0 + m * m * (k - 1);
       yd[g] = (masked >> k) & 1u ? x[g] : num_store<TX>(v);
@@ -365,9 +396,13 @@ cudaError_t launch_ax_epb(const DevProblem& d, const TX* x, typename LocalOf<T>:
   if constexpr (ax_tile_supported<p, T, EPB>()) {
     const int grid = (d.ne + EPB - 1) / EPB;
     constexpr bool kF32 = std::is_same<T, float>::value;
-    if constexpr (kIsDw<T>) {   // stored factors as pairs only (recomputed geometry stays FP64)
-      if (d.recompute || d.geodw == nullptr) return cudaErrorInvalidValue;
-      ax_dw_kernel<p, TX, EPB, DIRECT><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+    if constexpr (kIsDw<T>) {   // stored factors as pairs, or the geometry recomputed in pairs
+      if (d.recompute)
+        ax_dw_kernel<p, TX, EPB, DIRECT, true><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
+      else if (d.geodw == nullptr)
+        return cudaErrorInvalidValue;
+      else
+        ax_dw_kernel<p, TX, EPB, DIRECT, false><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (d.recompute) {
       ax_local_kernel<p, true, T, TX, EPB, DIRECT, T><<<dim3(grid, d.nrhs), EPB * p * p, 0, s>>>(d, x, wl, st, yd);
     } else if (kF32 && d.bf16) {

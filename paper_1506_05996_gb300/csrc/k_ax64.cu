@@ -6,13 +6,13 @@ cudaError_t launch_ax_local_dw(const DevProblem& d, const double* x, double* wl,
 cudaError_t launch_ax_apply_dw(const DevProblem& d, const double* x, double* wl, double* y, cudaStream_t s);
 bool ax_tile_ok_dw(int p, int epb);
 
-// SEM_PREC_FP64: the double-FP32 kernel with stored factors (d.dwk), else binary64.
+// SEM_PREC_FP64: the double-FP32 kernel (d.dwk; stored or recomputed factors), else binary64.
 cudaError_t launch_ax_local(const DevProblem& d, const double* x, double* wl, const PcgState* st, cudaStream_t s) {
-  if (d.dwk && !d.recompute) return launch_ax_local_dw(d, x, wl, st, s);
+  if (d.dwk) return launch_ax_local_dw(d, x, wl, st, s);
   return launch_ax_local_t<double, double, false>(d, x, wl, st, nullptr, s);
 }
 cudaError_t launch_ax_apply(const DevProblem& d, const double* x, double* wl, double* y, cudaStream_t s) {
-  if (d.dwk && !d.recompute) return launch_ax_apply_dw(d, x, wl, y, s);
+  if (d.dwk) return launch_ax_apply_dw(d, x, wl, y, s);
   return launch_ax_local_t<double, double, true>(d, x, wl, nullptr, y, s);
 }
 // Whether the operator kernel exists for this order and elements per CTA, in every

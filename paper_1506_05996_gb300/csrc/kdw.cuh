@@ -159,6 +159,30 @@ DW_HD void dw_mac(dw& acc, dw x, dw y) {
 // Renormalised pair: |l| <= ulp(h) / 2.
 DW_HD dw dw_norm(dw x) { return dw_two_sum(x.h, x.l); }
 
+// x / y (double-word division, after Joldes, Muller and Popescu 2017, "Tight and rigorous
+// error bounds for basic building blocks of double-word arithmetic", DWDivDW): the quotient's
+// high part from the binary32 reciprocal of y.h, the exact remainder x - q_h y in pairs, and
+// the low part from the remainder; relative error a few u^2 for normalised y.
+DW_HD float dw_rcp_rn(float a) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(a);
+#else
+  volatile float r = 1.0f / a;
+  return r;
+#endif
+}
+DW_HD dw dw_div(dw x, dw y) {
+  const dw yn = dw_norm(y);
+  const float r = dw_rcp_rn(yn.h);
+  const float qh = dw_mul_rn(x.h, r);
+  // q_h y = TwoProduct(q_h, y.h) + q_h y.l
+  const float p = dw_mul_rn(qh, yn.h);
+  const float pe = dw_fma_rn(qh, yn.l, dw_fma_rn(qh, yn.h, -p));
+  const dw rem = dw_sub(x, {p, pe});
+  const float ql = dw_mul_rn(dw_add_rn(rem.h, rem.l), r);
+  return dw_two_sum(qh, ql);
+}
+
 // binary64 -> pair (see the header comment).
 DW_HD dw dw_split(double x) {
   const uint64_t b = dw_d2u(x);

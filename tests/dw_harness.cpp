@@ -19,7 +19,7 @@ void dwh_join(const float* h, const float* l, double* y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = sem::dw_join({h[i], l[i]});
 }
 
-// op 0: x + y, 1: x - y, 2: x * y, 3: acc + x * y (acc in ah, al)
+// op 0: x + y, 1: x - y, 2: x * y, 3: acc + x * y (acc in ah, al), 4: x / y
 void dwh_op(int op, const float* xh, const float* xl, const float* yh, const float* yl, float* ah, float* al,
             int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
@@ -28,6 +28,7 @@ void dwh_op(int op, const float* xh, const float* xl, const float* yh, const flo
     if (op == 0) r = sem::dw_add(x, y);
     else if (op == 1) r = sem::dw_sub(x, y);
     else if (op == 2) r = sem::dw_mul(x, y);
+    else if (op == 4) r = sem::dw_div(x, y);
     else {
       r = {ah[i], al[i]};
       sem::dw_mac(r, x, y);

@@ -7,6 +7,7 @@ host and checked against exact rational arithmetic (fractions.Fraction):
   non-normalised pairs;
 - add, sub, mul, multiply-accumulate: errors within small multiples of u^2 = 2^-48 of the
   operands' magnitudes (the error model the kernels' bounds rest on);
+- division (the recomputed geometric factors' w / det): within 8 u^2 |x / y|;
 - an 8-term dot product from binary64 inputs to within 8 2^-46 sum |a_j b_j|.
 The host build uses no contraction (-ffp-contract=off), as the device code uses
 never-fused intrinsics.
@@ -154,6 +155,30 @@ def test_add_sub_mul_mac_error(lib, k):
             a = F(ah0[i]) + F(al0[i])
             ex, mag = a + x * y, abs(a) + abs(x * y)
         assert abs(got - ex) <= Fr(4 * U2) * mag, (k, i)
+
+
+def test_div_error(lib):
+    """Quotient of two pairs: one reciprocal estimate of the divisor's head, the remainder
+    x - q_h y formed with an exact product, one correction term (after Joldes, Muller and
+    Popescu's pair division); its error stays within 8 u^2 of the quotient, for divisors with
+    a large or a small tail and with head and tail of either sign."""
+    rng = np.random.default_rng(21)
+    n = 4000
+    xh, xl = rand_pairs(rng, n, -20, 20)
+    yh, yl = rand_pairs(rng, n, -20, 20)
+    ah, al = op(lib, 4, xh, xl, yh, yl)
+    for i in range(n):
+        x, y = F(xh[i]) + F(xl[i]), F(yh[i]) + F(yl[i])
+        q = x / y
+        assert abs(F(ah[i]) + F(al[i]) - q) <= Fr(8 * U2) * abs(q), i
+    # a power of two divides exactly; x / x is one to within 2 u^2 (the head of the quotient
+    # may be 1 - u, the one-term correction then carries the rounded reciprocal's error)
+    h, l = rand_pairs(rng, 50, -10, 10)
+    two = np.full(50, 0.25, np.float32)
+    qh, ql = op(lib, 4, h, l, two, np.zeros(50, np.float32))
+    assert all(F(qh[i]) + F(ql[i]) == 4 * (F(h[i]) + F(l[i])) for i in range(50))
+    qh, ql = op(lib, 4, h, l, h, l)
+    assert all(abs(F(qh[i]) + F(ql[i]) - 1) <= Fr(2 * U2) for i in range(50))
 
 
 def test_dot_product_from_binary64(lib):
