@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--kernel-case", type=int, default=0, metavar="E",
                     help="only run a few operator / preconditioner applies on an E^3, n=7 mesh "
                          "(a small case for ncu captures), then exit")
+    ap.add_argument("--kernel-geom", default="stored", choices=["stored", "recompute"],
+                    help="with --kernel-case: stored or recomputed geometric factors")
     return ap.parse_args()
 
 
@@ -812,16 +814,16 @@ def run_solve_case(E, prec="fp64"):
     prob.close()
 
 
-def run_kernel_case(E):
+def run_kernel_case(E, geom="stored"):
     """A few applies of each hot kernel (SEM_PREC_FP64's double-FP32 kernels, binary64, FP32)
-    on an E^3-hex, n = 7 mesh, with the
+    on an E^3-hex, n = 7 mesh with stored or recomputed geometric factors, with the
     tile shapes the autotuner picks; the applies sit in the NVTX range "kernels" (for
     ncu --nvtx --nvtx-include kernels/), the tuning launches outside it."""
     import torch
     from synth import lattice_hex_mesh
     from paper_1506_05996_gb300 import sem as S
     mesh = lattice_hex_mesh(E, A_FULL, SEED_FULL)
-    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom="stored", mixed=True)
+    prob = S.SemProblem(mesh.xyz, mesh.hex2vert, ORDER, LAM, geom=geom, mixed=True)
     x = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
     tiles = {}
     for prec in ("fp32", "fp64_native", "fp64"):
@@ -840,7 +842,7 @@ def run_kernel_case(E):
     S.sem_set_patch_solver(prob.h, "fp32")
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"kernel_case": E, "n_dof": prob.n_dof, "tiles": tiles}))
+    print(json.dumps({"kernel_case": E, "geom": geom, "n_dof": prob.n_dof, "tiles": tiles}))
     prob.close()
 
 
@@ -1194,7 +1196,7 @@ def main():
     elif args.precision_variant:
         run_precision_variant(args)
     elif args.kernel_case:
-        run_kernel_case(args.kernel_case)
+        run_kernel_case(args.kernel_case, args.kernel_geom)
     elif args.solve_case:
         run_solve_case(args.solve_case, args.solve_prec)
     elif args.impl == "reference":
