@@ -483,6 +483,11 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
       phi[2 * i + 1] = sem::dw_split_host(0.5 * (1.0 + t[i]));
     }
     UP(phidw, phi, sem::dw);
+    std::vector<sem::dw> w3((size_t)p * p * p);
+    for (int k = 0; k < p; ++k)
+      for (int j = 0; j < p; ++j)
+        for (int i = 0; i < p; ++i) w3[i + p * (j + p * k)] = sem::dw_split_host(rho[i] * rho[j] * rho[k]);
+    UP(w3dw, w3, sem::dw);
   }
 #undef UP
   CK(h->upload(&h->coords, coords, A));

@@ -298,13 +298,14 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   const bool lam_zero = d.lambda == 0.0;
   if constexpr (RECOMP) {
     const dw lam = num_const<dw>(d.lambda);
-    const dw ga = num_const<dw>(d.tg[tx]), gb = num_const<dw>(d.tg[ty]);
+    const dw* const fa = d.phidw + 2 * tx;
+    const dw* const fb = d.phidw + 2 * ty;
 #pragma unroll 1
     for (int k = 0; k < p; ++k) {   // pointwise, factors recomputed; su = lambda m u
       const int ls = SL::at(tx, ty, k);
       const T ur = sA[ls], us = sB[ls], ut = sC[ls];
       T G[6], mm;
-      geom_point_dw(sx, ga, gb, num_const<dw>(d.tg[k]), num_const<dw>(d.rho[tx] * d.rho[ty] * d.rho[k]), G, mm);
+      geom_point_dw(sx, fa, fb, d.phidw + 2 * k, d.w3dw[tx + p * (ty + p * k)], G, mm);
       sA[ls] = num_dot3(G[0], ur, G[1], us, G[2], ut);
       sB[ls] = num_dot3(G[1], ur, G[3], us, G[4], ut);
       sC[ls] = num_dot3(G[2], ur, G[4], us, G[5], ut);

@@ -82,13 +82,11 @@ template <> __device__ __forceinline__ const dw* geo_of<dw>(const DevProblem& d)
 // recomputed-geometry form of the double-FP32 operator): the trilinear map's Jacobian from the
 // 8 vertices xv[corner*3 + dim] (relative to any common origin: J does not depend on it), its
 // cofactors, determinant and the scaled metric, the same steps as geom_point in kcommon.cuh.
-// The reference-coordinate factors (1 +- a)/2 are a pair sum and an exact halving.
-__device__ __forceinline__ void geom_point_dw(const dw* xv, dw a, dw b, dw c, dw w, dw G[6], dw& m) {
+// The reference-coordinate factors come as pairs: fa[0] = (1 - a)/2, fa[1] = (1 + a)/2 (corner
+// bit 0 / 1), and the same for b and c (a set-up table, split to nearest from binary64).
+__device__ __forceinline__ void geom_point_dw(const dw* xv, const dw* fa, const dw* fb, const dw* fc, dw w, dw G[6],
+                                              dw& m) {
   auto half = [](dw v) { return dw{0.5f * v.h, 0.5f * v.l}; };
-  const dw one = {1.0f, 0.0f};
-  const dw fa[2] = {half(dw_sub(one, a)), half(dw_add(one, a))};   // corner bit 0 / 1
-  const dw fb[2] = {half(dw_sub(one, b)), half(dw_add(one, b))};
-  const dw fc[2] = {half(dw_sub(one, c)), half(dw_add(one, c))};
   // d/da of the corner's basis function is +- fb fc / 2, and so on
   dw bc[2][2], ac[2][2], ab[2][2];
 #pragma unroll
