@@ -4,6 +4,7 @@
 #include <cstdint>
 
 #include "../paper_1506_05996_gb300/csrc/kdw.cuh"
+#include "../paper_1506_05996_gb300/csrc/kgeomdw.cuh"
 
 extern "C" {
 
@@ -46,6 +47,28 @@ void dwh_dot(const double* a, const double* b, double* out, int64_t n, int k) {
     for (int j = 0; j < k; ++j) sem::dw_mac(acc, sem::dw_split(a[i * k + j]), sem::dw_split(b[i * k + j]));
     out[i] = sem::dw_join(acc);
   }
+}
+
+// The recomputed metric of the pair operator at the p^3 nodes of one element, staged as the
+// element kernel stages it: the 8 binary64 vertices xyz[corner*3 + dim] taken relative to
+// corner 0 in binary64 and split to pairs (absolute = 1: the coordinates split as they are,
+// for the test that shows why the kernel does not); phi[2i] = (1 - t_i)/2, phi[2i + 1] = (1 + t_i)/2
+// and w3[i + p (j + p k)] = rho_i rho_j rho_k split to nearest (the set-up tables). Results
+// joined to binary64: G[c p^3 + node] for c < 6, m[node].
+void dwh_geom(const double* xyz, const double* phi, const double* w3, int p, int absolute, double* G, double* m) {
+  sem::dw xv[24], ph[2 * 16];
+  for (int q = 0; q < 24; ++q) xv[q] = sem::dw_split(absolute ? xyz[q] : xyz[q] - xyz[q % 3]);
+  for (int q = 0; q < 2 * p; ++q) ph[q] = sem::dw_split_host(phi[q]);
+  const int p3 = p * p * p;
+  for (int k = 0; k < p; ++k)
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i) {
+        const int l = i + p * (j + p * k);
+        sem::dw g[6], mm;
+        sem::geom_point_dw(xv, ph + 2 * i, ph + 2 * j, ph + 2 * k, sem::dw_split_host(w3[l]), g, mm);
+        for (int c = 0; c < 6; ++c) G[c * p3 + l] = sem::dw_join(g[c]);
+        m[l] = sem::dw_join(mm);
+      }
 }
 
 }

@@ -8,7 +8,9 @@ host and checked against exact rational arithmetic (fractions.Fraction):
 - add, sub, mul, multiply-accumulate: errors within small multiples of u^2 = 2^-48 of the
   operands' magnitudes (the error model the kernels' bounds rest on);
 - division (the recomputed geometric factors' w / det): within 8 u^2 |x / y|;
-- an 8-term dot product from binary64 inputs to within 8 2^-46 sum |a_j b_j|.
+- an 8-term dot product from binary64 inputs to within 8 2^-46 sum |a_j b_j|;
+- the recomputed metric (kgeomdw.cuh: G = w |J| J^-1 J^-T, m = w |J| per node) against the
+  oracle's binary64 factors, to within 64 u^2 of the node's largest G entry and of m.
 The host build uses no contraction (-ffp-contract=off), as the device code uses
 never-fused intrinsics.
 """
@@ -24,6 +26,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "dw_harness.cpp")
 HDR = os.path.join(ROOT, "paper_1506_05996_gb300", "csrc", "kdw.cuh")
+HDR2 = os.path.join(ROOT, "paper_1506_05996_gb300", "csrc", "kgeomdw.cuh")
 OUT = os.path.join(ROOT, "paper_1506_05996_gb300", "_build", "dw_harness.so")
 U2 = 2.0 ** -48
 
@@ -31,7 +34,7 @@ U2 = 2.0 ** -48
 @pytest.fixture(scope="module")
 def lib():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+    if not os.path.exists(OUT) or os.path.getmtime(OUT) < max(map(os.path.getmtime, (SRC, HDR, HDR2))):
         subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-o", OUT, SRC],
                        check=True)
     return ctypes.CDLL(OUT)
@@ -191,3 +194,63 @@ def test_dot_product_from_binary64(lib):
         ex = sum(F(a[i * k + j]) * F(b[i * k + j]) for j in range(k))
         mag = sum(abs(F(a[i * k + j]) * F(b[i * k + j])) for j in range(k))
         assert abs(F(out[i]) - ex) <= Fr(k * 2.0 ** -46) * mag
+
+
+def _geom(lib, xe, t, rho, absolute=False):
+    """The pair metric of one element at its p^3 nodes, as [6, i, j, k] and [i, j, k]."""
+    p = len(t)
+    phi = np.empty(2 * p)
+    phi[0::2], phi[1::2] = (1 - t) / 2, (1 + t) / 2
+    w3 = np.ascontiguousarray((rho[:, None, None] * rho[None, :, None] * rho[None, None, :]).transpose(2, 1, 0).ravel())
+    G, m = np.zeros(6 * p ** 3), np.zeros(p ** 3)
+    lib.dwh_geom(_p(np.ascontiguousarray(xe.ravel())), _p(phi), _p(w3), ctypes.c_int(p), ctypes.c_int(int(absolute)),
+                 _p(G), _p(m))
+    return G.reshape(6, p, p, p).transpose(0, 3, 2, 1), m.reshape(p, p, p).transpose(2, 1, 0)
+
+
+def test_recomputed_metric_against_binary64(lib):
+    """The pair metric that the recomputed-geometry FP64 operator evaluates per node, against
+    the oracle's binary64 geometric factors (Sec. 2.3) of the same vertices: 30 elements of the
+    32^3 lattice (+-20 %), n = 1..8, in place and moved 1000 units away.
+
+    The reference takes the vertices relative to corner 0 (the same binary64 differences the
+    pair code starts from), so it measures the pair arithmetic alone. Bound: J's entries are
+    8-term pair sums whose absolute terms add up to a few |J| on these elements, each step
+    within a few u^2 of its terms; the cofactors, the determinant and the division multiply
+    that by small condition numbers; J and the cofactors are renormalised before their
+    products. Measured worst: 20 u^2 (G and m); 127 and 65 u^2 without the renormalisation.
+    A wrong sign, index or dropped term errs by O(1)."""
+    from synth import lattice_hex_mesh
+    from oracle.gll import gll_nodes_weights
+    from oracle.geometry import geometric_factors
+    mesh = lattice_hex_mesh(32, 0.2, 1)
+    els = np.random.default_rng(7).choice(len(mesh.hex2vert), 30, replace=False)
+    for shift in (0.0, 1000.0):
+        for n in range(1, 9):
+            t, rho = gll_nodes_weights(n)
+            for e in els:
+                xe = mesh.xyz[mesh.hex2vert[e]] + shift
+                Gr, mr, _ = geometric_factors((xe - xe[0])[None], t, rho)
+                G, m = _geom(lib, xe, t, rho)
+                scale = np.abs(Gr[:, 0]).max(axis=0)
+                assert np.all(np.abs(G - Gr[:, 0]) <= 64 * U2 * scale), (shift, n, e)
+                assert np.all(np.abs(m - mr[0]) <= 64 * U2 * np.abs(mr[0])), (shift, n, e)
+
+
+def test_recomputed_metric_needs_corner_relative_vertices(lib):
+    """Why the element kernel stages its vertices relative to corner 0: summed from absolute
+    coordinates 1000 units from the origin (|x| / h = 32,000), J loses about log2(32,000) = 15
+    of the pairs' 48 bits, and the metric misses the bound above by orders of magnitude; the
+    corner-relative form meets it (previous test)."""
+    from synth import lattice_hex_mesh
+    from oracle.gll import gll_nodes_weights
+    from oracle.geometry import geometric_factors
+    mesh = lattice_hex_mesh(32, 0.2, 1)
+    t, rho = gll_nodes_weights(7)
+    xe = mesh.xyz[mesh.hex2vert[5]] + 1000.0
+    Gr, _, _ = geometric_factors((xe - xe[0])[None], t, rho)
+    scale = np.abs(Gr[:, 0]).max(axis=0)
+    G_abs, _ = _geom(lib, xe, t, rho, absolute=True)
+    G_rel, _ = _geom(lib, xe, t, rho)
+    assert np.max(np.abs(G_abs - Gr[:, 0]) / scale) > 4096 * U2
+    assert np.max(np.abs(G_rel - Gr[:, 0]) / scale) <= 64 * U2
