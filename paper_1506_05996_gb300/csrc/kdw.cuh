@@ -24,7 +24,11 @@
 // The pairs a kernel keeps (shared-memory lines, accumulators) are not renormalised after
 // every step: a low part that grew beyond ulp(h) still carries its exact share of the value
 // and enters the next products through the cross terms, whose own rounding is then
-// u |x.h| |l| = O(u^2) of the operands. Only dw_join renormalises.
+// u |x.h| |l| = O(u^2) of the operands. That holds while one operand of each product is
+// normalised (a table split at set-up, an input split from binary64): a product drops
+// x.l y.l, and after a sum that cancels by a factor R both tails can reach u R of their heads,
+// which makes the dropped term (u R)^2. Products of two computed pairs (the recomputed
+// metric's J and cofactors) renormalise them first with dw_norm; dw_join renormalises too.
 //
 // Products are formed with the _rn intrinsics, which the compiler never contracts into an
 // FMA (a contracted h = a b + c would break the error-free transforms).
