@@ -474,9 +474,6 @@ static int create_impl(sem_t* h, const double* vert_xyz_host, int64_t n_vert, co
       phi32[2 * i + 1] = (float)(0.5 * (1.0 + t[i]));
     }
     UP(phi32, phi32, float);
-    std::vector<sem::dw> Btdw(Btab.size());
-    for (size_t q = 0; q < Btab.size(); ++q) Btdw[q] = sem::dw_split_host(Btab[q]);
-    UP(Btabdw, Btdw, sem::dw);
     std::vector<sem::dw> phi(2 * p);
     for (int i = 0; i < p; ++i) {
       phi[2 * i] = sem::dw_split_host(0.5 * (1.0 - t[i]));

@@ -129,7 +129,6 @@ struct DevProblem {
   const dw* swddw = nullptr;        // the same as pairs of FP32
   const double* Btab = nullptr;     // [p^3][8] Phi_I(t_i) Phi_J(t_j) Phi_K(t_k), VTK corner order
   const float* phi32 = nullptr;     // [p][2] (1 - t_i)/2 and (1 + t_i)/2 in FP32 (the 1D factors of Btab)
-  const dw* Btabdw = nullptr;       // the same as pairs of FP32
   const dw* phidw = nullptr;        // [p][2] (1 - t_i)/2 and (1 + t_i)/2 as pairs (the 1D factors of Btab)
   const dw* w3dw = nullptr;         // [p^3] (rho_i rho_j) rho_k in binary64 as pairs, node i + p (j + p k)
   dw* Zce = nullptr;                // [ne][8] coarse correction at each element's corners as pairs (0 where
