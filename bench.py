@@ -316,19 +316,23 @@ def dw_ops_ax(n, ne):
 
 
 def dw_ops_ax_recompute(n, ne):
-    """FP32-pipe operations of the double-FP32 operator kernel with the metric recomputed per
-    node (counts as dw_ops_ax: pair product 4, multiply-accumulate 12, pair sum 8, TwoSum 6;
-    sign flips and the reciprocal estimate not counted). Lines as dw_ops_ax. Per node: the
-    metric products (84), three pair sums of the divergence terms and the lambda m u term
-    (two products, 8), the input split (2) and the output join (6), and the metric: 12 corner
-    products with a halving (6 each), 72 multiply-accumulates into J, 9 cofactors (a product
-    and a multiply-accumulate), 18 renormalisations (J and the cofactors), the determinant
-    (28), one pair division (26), 6 entries of C^T C scaled (32 each) and m (4): 1,438."""
+    """FP32-pipe operations of the double-FP32 operator kernel with the metric recomputed
+    (counts as dw_ops_ax: pair product 4, multiply-accumulate 12, pair sum 8, TwoSum 6; sign
+    flips and the reciprocal estimate not counted). Lines as dw_ops_ax. Per node: the metric
+    products (84), three pair sums of the divergence terms and the lambda m u term (two
+    products, 8), the input split (2) and the output join (6), and the metric's per-node part:
+    J's first two columns from the line's sums (6 products, 6 multiply-accumulates, 6
+    renormalisations), 9 renormalised cofactors (a product, a multiply-accumulate and a TwoSum),
+    the determinant (28), one pair division (26), 6 entries of C^T C scaled (32 each) and m
+    (4): 580. Per line (p^2 of them): 4 halvings (2), 4 corner products with a halving (6),
+    72 multiply-accumulates and 15 renormalisations: 986."""
     p = n + 1
     H, odd = p // 2, p % 2
     line = 8 * 2 * H + 4 * odd * H + 12 * (2 * H * H + odd * H) + 8 * 2 * H
-    metric = 12 * 6 + 72 * 12 + 9 * 16 + 18 * 6 + 28 + 26 + 6 * 32 + 4
-    return ne * (6.0 * p * p * line + (84.0 + 3 * 8.0 + 8.0 + 2.0 + 6.0 + metric) * p ** 3)
+    node_metric = 6 * (4 + 12) + 6 * 6 + 9 * (4 + 12 + 6) + 28 + 26 + 6 * 32 + 4
+    line_metric = 4 * 2 + 4 * 6 + 72 * 12 + 15 * 6
+    return ne * (6.0 * p * p * line + (84.0 + 3 * 8.0 + 8.0 + 2.0 + 6.0 + node_metric) * p ** 3
+                 + line_metric * p * p)
 
 
 def _cpu_ax_worker(E, nthreads_list, reps, q):

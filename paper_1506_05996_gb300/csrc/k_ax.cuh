@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(EPB * p * p) ax_local_kernel(const DevProblem 
 //   axis j: line (i = tx, k = ty), nodes (tx, q, ty)
 //   axis k: line (i = tx, j = ty), nodes (tx, ty, q)
 // RECOMP: the factors recomputed at every node from the element's vertices in pair arithmetic
-// (geom_point_dw), the pointwise stage as a loop; the c-term lambda m u then starts the sum
+// (geom_line_dw once per thread's line, geom_node_dw per node), the pointwise stage as a
+// loop; the c-term lambda m u then starts the sum
 // that the three divergence terms are added to: y = ((lambda m u + d_i) + d_j) + d_k.
 template <int p, typename TX, int EPB, bool DIRECT, bool RECOMP = false>
 __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, const TX* __restrict__ x,
@@ -298,14 +299,14 @@ __global__ void __launch_bounds__(EPB * p * p) ax_dw_kernel(const DevProblem d, 
   const bool lam_zero = d.lambda == 0.0;
   if constexpr (RECOMP) {
     const dw lam = num_const<dw>(d.lambda);
-    const dw* const fa = d.phidw + 2 * tx;
-    const dw* const fb = d.phidw + 2 * ty;
+    LineJ L;
+    geom_line_dw(sx, d.phidw + 2 * tx, d.phidw + 2 * ty, L);
 #pragma unroll 1
     for (int k = 0; k < p; ++k) {   // pointwise, factors recomputed; su = lambda m u
       const int ls = SL::at(tx, ty, k);
       const T ur = sA[ls], us = sB[ls], ut = sC[ls];
       T G[6], mm;
-      geom_point_dw(sx, fa, fb, d.phidw + 2 * k, d.w3dw[tx + p * (ty + p * k)], G, mm);
+      geom_node_dw(L, d.phidw + 2 * k, d.w3dw[tx + p * (ty + p * k)], G, mm);
       sA[ls] = num_dot3(G[0], ur, G[1], us, G[2], ut);
       sB[ls] = num_dot3(G[1], ur, G[3], us, G[4], ut);
       sC[ls] = num_dot3(G[2], ur, G[4], us, G[5], ut);

@@ -60,15 +60,18 @@ void dwh_geom(const double* xyz, const double* phi, const double* w3, int p, int
   for (int q = 0; q < 24; ++q) xv[q] = sem::dw_split(absolute ? xyz[q] : xyz[q] - xyz[q % 3]);
   for (int q = 0; q < 2 * p; ++q) ph[q] = sem::dw_split_host(phi[q]);
   const int p3 = p * p * p;
-  for (int k = 0; k < p; ++k)
-    for (int j = 0; j < p; ++j)
-      for (int i = 0; i < p; ++i) {
+  for (int j = 0; j < p; ++j)
+    for (int i = 0; i < p; ++i) {   // one line (i, j), k varying, as one thread of the kernel
+      sem::LineJ L;
+      sem::geom_line_dw(xv, ph + 2 * i, ph + 2 * j, L);
+      for (int k = 0; k < p; ++k) {
         const int l = i + p * (j + p * k);
         sem::dw g[6], mm;
-        sem::geom_point_dw(xv, ph + 2 * i, ph + 2 * j, ph + 2 * k, sem::dw_split_host(w3[l]), g, mm);
+        sem::geom_node_dw(L, ph + 2 * k, sem::dw_split_host(w3[l]), g, mm);
         for (int c = 0; c < 6; ++c) G[c * p3 + l] = sem::dw_join(g[c]);
         m[l] = sem::dw_join(mm);
       }
+    }
 }
 
 }

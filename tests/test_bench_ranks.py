@@ -148,29 +148,33 @@ def test_pair_operation_counts_follow_the_kernels(n):
 
 
 def _count_dw_metric():
-    """geom_point_dw (csrc/kgeomdw.cuh) step by step; dw_norm = one TwoSum (6), sign flips free,
-    the reciprocal estimate on the special-function unit (not counted)."""
+    """geom_line_dw and geom_node_dw (csrc/kgeomdw.cuh) step by step: (per node, per line);
+    dw_norm = one TwoSum (6), sign flips free, the reciprocal estimate on the special-function
+    unit (not counted)."""
     TWO_SUM = 6
-    corner = 12 * (DW_MUL + 2)                 # bc, ac, ab: a product and a halving (2 multiplies)
-    jac = 8 * 9 * DW_MAC                       # 8 corners x 9 entries
-    cof = 9 * (DW_MUL + DW_MAC)
-    norms = 18 * TWO_SUM                       # J and the cofactors
-    det = DW_MUL + 2 * DW_MAC
+    # per line: hb, ha (a halving = 2 multiplies), ab (a product and a halving), the corner
+    # sums (8 corners x 3 rows x 3 sums), renormalised U0, U1 (12) and J2 (3)
+    line = 4 * 2 + 4 * (DW_MUL + 2) + 8 * 3 * 3 * DW_MAC + 15 * TWO_SUM
+    # per node: J's first two columns (a product and a multiply-accumulate each, renormalised)
+    node = 6 * (DW_MUL + DW_MAC + TWO_SUM)
+    node += 9 * (DW_MUL + DW_MAC + TWO_SUM)      # cofactors, renormalised
+    node += DW_MUL + 2 * DW_MAC                  # determinant
     # dw_div: renormalise y, q_h = x_h r, p = q_h y_h, its error by two FMAs, the remainder
     # (a pair difference), one sum and one product for q_l, a final TwoSum
-    div = TWO_SUM + 1 + 1 + 2 + DW_ADD + 1 + 1 + TWO_SUM
-    scaled = 6 * (DW_MUL + 2 * DW_MAC + DW_MUL)
-    m = DW_MUL
-    return corner + jac + cof + norms + det + div + scaled + m
+    node += TWO_SUM + 1 + 1 + 2 + DW_ADD + 1 + 1 + TWO_SUM
+    node += 6 * (DW_MUL + 2 * DW_MAC + DW_MUL)   # C^T C scaled by w / det
+    node += DW_MUL                               # m
+    return node, line
 
 
 @pytest.mark.parametrize("n", [2, 5, 7, 8])
 def test_recomputed_pair_operation_counts_follow_the_kernel(n):
     """The recomputed form: the same lines; per node the 3 metric rows, three divergence sums
     (the first adds to lambda m u instead of overwriting), lambda m u as two products, the
-    split and the join, and the metric itself."""
+    split and the join, and the metric's per-node part; per line the metric's per-line part."""
     import bench
     p = n + 1
-    per_node = 3 * (DW_MUL + 2 * DW_MAC) + 3 * DW_ADD + 2 * DW_MUL + 2 + 6 + _count_dw_metric()
-    assert _count_dw_metric() == 1438
-    assert bench.dw_ops_ax_recompute(n, 1) == 6 * p * p * _count_dw_fold(p) + per_node * p ** 3
+    node, line = _count_dw_metric()
+    assert (node, line) == (580, 986)
+    per_node = 3 * (DW_MUL + 2 * DW_MAC) + 3 * DW_ADD + 2 * DW_MUL + 2 + 6 + node
+    assert bench.dw_ops_ax_recompute(n, 1) == 6 * p * p * _count_dw_fold(p) + per_node * p ** 3 + line * p * p

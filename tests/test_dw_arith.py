@@ -214,12 +214,13 @@ def test_recomputed_metric_against_binary64(lib):
     32^3 lattice (+-20 %), n = 1..8, in place and moved 1000 units away.
 
     The reference takes the vertices relative to corner 0 (the same binary64 differences the
-    pair code starts from), so it measures the pair arithmetic alone. Bound: J's entries are
-    8-term pair sums whose absolute terms add up to a few |J| on these elements, each step
-    within a few u^2 of its terms; the cofactors, the determinant and the division multiply
-    that by small condition numbers; J and the cofactors are renormalised before their
-    products. Measured worst: 20 u^2 (G and m); 127 and 65 u^2 without the renormalisation.
-    A wrong sign, index or dropped term errs by O(1)."""
+    pair code starts from), so it measures the pair arithmetic alone. The harness evaluates
+    it as the kernel does: the corner sums once per line of nodes (i, j fixed), J completed per
+    node. Bound: J's entries come from 4-term pair sums whose absolute terms add up to a few
+    |J| on these elements, each step within a few u^2 of its terms; the cofactors, the
+    determinant and the division multiply that by small condition numbers; the sums, J and the
+    cofactors are renormalised before their products. Measured worst: 17 u^2 (G and m); 127
+    and 65 u^2 without the renormalisation. A wrong sign, index or dropped term errs by O(1)."""
     from synth import lattice_hex_mesh
     from oracle.gll import gll_nodes_weights
     from oracle.geometry import geometric_factors
