@@ -37,3 +37,17 @@ def test_importing_the_binding_loads_no_oracle_module():
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip().splitlines()[-1] == "[]"
+
+
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """With libsem.so absent the binding refuses to import: there is no fallback path."""
+    import shutil
+    pkg = tmp_path / "paper_1506_05996_gb300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(PKG, "__init__.py"), pkg / "__init__.py")
+    shutil.copy(os.path.join(PKG, "sem.py"), pkg / "sem.py")
+    code = "import paper_1506_05996_gb300.sem"
+    out = subprocess.run([sys.executable, "-c", code], cwd=str(tmp_path), capture_output=True, text=True,
+                         timeout=300, env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert out.returncode != 0
+    assert "libsem.so is not built" in out.stderr
